@@ -1,0 +1,81 @@
+"""The P2S surrogate network in FP64: forward, backward, Adam.
+
+Test infrastructure only (see the package docstring).
+
+Sec. II-C: the paper (after Mao et al. 2021) maps each pixel's Zernike vector
+a_x to the basis coefficients beta_x with a small neural network.  The
+network's shape and training are not given (reading R18): J -> 256 -> 256 -> K
+with the erf form of GELU, trained with the mean squared error on per-k
+standardised weights and Adam (Kingma & Ba 2015).  Input features are
+x = a * in_scale (in_scale is 0 on the two tilt fields, reading R9); the output
+is w = y * out_scale + out_shift.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+from scipy.special import erf
+
+SQRT1_2 = 1.0 / math.sqrt(2.0)
+INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z * SQRT1_2))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z * SQRT1_2)) + z * INV_SQRT_2PI * np.exp(-0.5 * z * z)
+
+
+def forward(params: dict, x: np.ndarray):
+    """Returns (y, cache); params W1 (256 x J), b1, W2 (256 x 256), b2, W3 (K x 256), b3."""
+    x = np.asarray(x, dtype=np.float64)
+    z1 = x @ params["W1"].T + params["b1"]
+    h1 = gelu(z1)
+    z2 = h1 @ params["W2"].T + params["b2"]
+    h2 = gelu(z2)
+    y = h2 @ params["W3"].T + params["b3"]
+    return y, (x, z1, h1, z2, h2)
+
+
+def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray):
+    """Mean squared error over the B x K outputs and its gradient for every parameter."""
+    y, (x, z1, h1, z2, h2) = forward(params, x)
+    B, K = y.shape
+    r = y - np.asarray(t, dtype=np.float64)
+    loss = float(np.mean(r * r))
+    dy = 2.0 * r / (B * K)
+    g = {}
+    g["W3"] = dy.T @ h2
+    g["b3"] = dy.sum(axis=0)
+    dz2 = (dy @ params["W3"]) * gelu_grad(z2)
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ params["W2"]) * gelu_grad(z1)
+    g["W1"] = dz1.T @ x
+    g["b1"] = dz1.sum(axis=0)
+    return loss, g
+
+
+def adam_step(params: dict, grads: dict, state: dict, lr: float, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam update (bias-corrected moments) in place; step counts from 1."""
+    for k in params:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[...] = beta1 * m + (1 - beta1) * grads[k]
+        v[...] = beta2 * v + (1 - beta2) * grads[k] ** 2
+        mh = m / (1 - beta1 ** step)
+        vh = v / (1 - beta2 ** step)
+        params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+    return params
+
+
+def predict_weights(params: dict, a: np.ndarray, in_scale: np.ndarray, out_scale: np.ndarray,
+                    out_shift: np.ndarray) -> np.ndarray:
+    """w = MLP(a * in_scale) * out_scale + out_shift for Zernike vectors a (..., J)."""
+    a = np.asarray(a, dtype=np.float64)
+    shp = a.shape[:-1]
+    y, _ = forward(params, a.reshape(-1, a.shape[-1]) * in_scale)
+    return (y * out_scale + out_shift).reshape(*shp, -1)

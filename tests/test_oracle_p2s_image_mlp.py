@@ -1,0 +1,167 @@
+"""Pins for the oracle's PSF (Eq. 2), basis (Sec. II-C), warp, blur (Eq. 1, Eq. varying blur)
+and the surrogate network's gradients."""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import synthetic
+from oracle import image, mlp, p2s, zernike
+
+
+# ------------------------------------------------------------------- PSF
+def test_zero_phase_psf_symmetry_and_parseval():
+    J = 10
+    h = p2s.psf_full(np.zeros(J), J)
+    assert np.allclose(h, h[::-1, ::-1][np.r_[-1, 0:63]][:, np.r_[-1, 0:63]], rtol=1e-10)  # u -> -u about index 32
+    assert np.allclose(h, h.T, rtol=1e-10)
+    _, _, P = p2s.pupil_grid()
+    assert h.sum() == pytest.approx(64 * 64 * (P ** 2).sum(), rel=1e-12)  # Parseval
+    assert h[32, 32] == pytest.approx(P.sum() ** 2, rel=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 2, -3])
+def test_tilt_is_an_exact_shift(k):
+    # a_2 = (pi/4) k puts the PSF peak k pixels towards -x (reading R10): exact circular shift
+    J = 6
+    h0 = p2s.psf_full(np.zeros(J), J, with_tilt=True)
+    a = np.zeros(J)
+    a[0] = math.pi / 4 * k
+    hx = p2s.psf_full(a, J, with_tilt=True)
+    assert np.allclose(hx, np.roll(h0, -k, axis=1), atol=1e-9 * h0.max())
+    a = np.zeros(J)
+    a[1] = math.pi / 4 * k
+    hy = p2s.psf_full(a, J, with_tilt=True)
+    assert np.allclose(hy, np.roll(h0, -k, axis=0), atol=1e-9 * h0.max())
+
+
+def test_psf_unit_sum_and_tilt_free():
+    J = 36
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((5, J)) * 0.3
+    h = p2s.psf(a, J)
+    assert h.shape == (5, 33, 33)
+    assert np.allclose(h.sum(axis=(1, 2)), 1.0)
+    a2 = a.copy()
+    a2[:, :2] += 5.0
+    assert np.allclose(p2s.psf(a2, J), h)  # tilts never enter the P2S PSF (R9)
+
+
+def test_svd_basis_eckart_young_and_orthonormal():
+    J, n, K = 36, 120, 16
+    a = p2s.basis_draws(3, J, n, [2.0])
+    Hm = p2s.psf(a, J).reshape(n, -1)
+    Phi, s = p2s.svd_basis(Hm, K)
+    assert np.allclose(Phi @ Phi.T, np.eye(K), atol=1e-12)
+    resid = Hm - Hm @ Phi.T @ Phi
+    assert np.sum(resid ** 2) == pytest.approx(np.sum(s[K:] ** 2), rel=1e-9)
+    for k in range(K):
+        i = np.argmax(np.abs(Phi[k]))
+        assert Phi[k, i] > 0
+
+
+def test_basis_draws_have_noll_covariance():
+    J = 8
+    a = p2s.basis_draws(9, J, 20000, [3.0])
+    A0 = zernike.noll_matrix(J, 3.0)
+    emp = a.T @ a / a.shape[0]
+    sub = A0[2:, 2:]
+    sd = np.sqrt((np.outer(np.diag(sub), np.diag(sub)) + sub ** 2) / a.shape[0])
+    assert np.all(np.abs(emp[2:, 2:] - sub) < 5 * sd)
+    assert np.all(a[:, :2] == 0)
+
+
+def test_weights_recover_in_span_coefficients():
+    J, K = 12, 8
+    Phi = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    a = np.random.default_rng(2).standard_normal((3, J)) * 0.2
+    h = p2s.psf(a, J).reshape(3, -1)
+    w = p2s.weights(a, J, Phi)
+    assert np.allclose(w, h @ Phi.reshape(K, -1).T, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ image
+def test_warp_identity_shift_and_ramp():
+    img = synthetic.blobs(24, 20, 2, n=5, seed=1).astype(np.float64)
+    z = np.zeros((24, 20))
+    assert np.allclose(image.tilt_warp(img, z, z), img)
+    k = 3
+    out = image.tilt_warp(img, z + math.pi / 4 * k, z)  # sample at x + 3
+    assert np.allclose(out[:, :, :20 - k], img[:, :, k:])
+    assert np.allclose(out[:, :, 20 - k:], img[:, :, -1:])
+    out = image.tilt_warp(img, z, z - math.pi / 4 * 2)  # sample at y - 2
+    assert np.allclose(out[:, 2:], img[:, :-2])
+    yy, xx = np.meshgrid(np.arange(24.0), np.arange(20.0), indexing="ij")
+    ramp = (0.3 * xx + 0.7 * yy)[None]
+    rng = np.random.default_rng(0)
+    a2 = rng.uniform(-1, 1, (24, 20))
+    a3 = rng.uniform(-1, 1, (24, 20))
+    out = image.tilt_warp(ramp, a2, a3)
+    sx = xx + 4 / math.pi * a2
+    sy = yy + 4 / math.pi * a3
+    inside = (sx >= 0) & (sx <= 19) & (sy >= 0) & (sy <= 23)
+    assert np.allclose(out[0][inside], (0.3 * sx + 0.7 * sy)[inside], atol=1e-12)
+
+
+def test_blur_equals_direct_per_pixel_convolution():
+    C, H, W, K = 2, 20, 23, 5
+    img = synthetic.blobs(H, W, C, n=6, seed=3).astype(np.float64)
+    Phi = np.random.default_rng(4).standard_normal((K, 33, 33))
+    w = np.random.default_rng(5).standard_normal((H, W, K))
+    out = image.basis_blur(img, w, Phi)
+    h = np.einsum("yxk,kab->yxab", w, Phi)
+    assert np.allclose(out, image.direct_blur(img, h), atol=1e-10)
+
+
+def test_blur_is_a_true_convolution():
+    img = synthetic.blobs(16, 16, 1, n=4, seed=2).astype(np.float64)
+    delta = np.zeros((1, 33, 33))
+    delta[0, 16, 17] = 1.0  # u = (0, +1)
+    out = image.basis_blur(img, np.ones((16, 16, 1)), delta)
+    assert np.allclose(out[:, :, 1:], img[:, :, :-1])  # out(x) = I(x - (0, 1))
+    const = np.full((1, 16, 16), 0.25)
+    Phi = np.random.default_rng(1).standard_normal((3, 33, 33))
+    w = np.random.default_rng(2).standard_normal((16, 16, 3))
+    out = image.basis_blur(const, w, Phi)
+    assert np.allclose(out[0], 0.25 * w @ Phi.sum(axis=(1, 2)))
+
+
+# -------------------------------------------------------------------- MLP
+def _params(J, Hd, K, seed=0):
+    rng = np.random.default_rng(seed)
+    return {"W1": rng.standard_normal((Hd, J)) / math.sqrt(J), "b1": rng.standard_normal(Hd) * 0.1,
+            "W2": rng.standard_normal((Hd, Hd)) / math.sqrt(Hd), "b2": rng.standard_normal(Hd) * 0.1,
+            "W3": rng.standard_normal((K, Hd)) / math.sqrt(Hd), "b3": rng.standard_normal(K) * 0.1}
+
+
+def test_mlp_gradients_by_finite_differences():
+    J, Hd, K, B = 5, 7, 4, 6
+    P = _params(J, Hd, K)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((B, J))
+    t = rng.standard_normal((B, K))
+    _, g = mlp.loss_and_grads(P, x, t)
+    eps = 1e-6
+    for name, val in P.items():
+        flat = val.ravel()
+        for i in range(0, flat.size, max(1, flat.size // 9)):
+            old = flat[i]
+            flat[i] = old + eps
+            lp, _ = mlp.loss_and_grads(P, x, t)
+            flat[i] = old - eps
+            lm, _ = mlp.loss_and_grads(P, x, t)
+            flat[i] = old
+            assert g[name].ravel()[i] == pytest.approx((lp - lm) / (2 * eps), rel=1e-6, abs=1e-9)
+
+
+def test_gelu_and_adam_closed_forms():
+    from scipy.stats import norm
+    z = np.linspace(-5, 5, 101)
+    assert np.allclose(mlp.gelu(z), z * norm.cdf(z), atol=1e-15)
+    d = (mlp.gelu(z + 1e-6) - mlp.gelu(z - 1e-6)) / 2e-6
+    assert np.allclose(mlp.gelu_grad(z), d, atol=1e-8)
+    p = {"w": np.array([1.0, -2.0, 3.0])}
+    g = {"w": np.array([0.5, -4.0, 1e-3])}
+    mlp.adam_step(p, g, {}, lr=0.01, step=1)
+    # first Adam step moves each parameter by lr * g / (|g| + eps)
+    assert np.allclose(p["w"], [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01 * 1e-3 / (1e-3 + 1e-8)], rtol=1e-12)
