@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Frames/s of the dense-field phase-to-space (DF-P2S) simulator on one GB300.
+
+Default workload: a 512 x 512 x 3 frame (seeded rectangles and edges), J = 36
+Zernike fields on a 1024 x 1024 FFT grid, D/r0 cycling over {1, 2, 4}, K = 100
+basis PSFs of 33 x 33, learned P2S (network weights in the P2S handle).  A step
+is one frame: fields (noise -> FFT -> spectral multiply -> inverse FFT -> mix)
+-> tilt warp -> P2S weights -> basis blur, with the input image resident in HBM.
+The e2e figure runs the public simulate_frame call with the image copied in
+from pinned host memory and the frame copied back every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 512|4k|256|64]
+                  [--mode learned|exact] [--impl ours|reference]
+
+Under torchrun every rank simulates its own frames (weak scaling, no
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (H, W, C, image kind, K, D/r0 list, description)
+    "512": (512, 512, 3, "shapes", 100, [1.0, 2.0, 4.0], "512x512x3 shapes, J=36, N=1024, K=100, D/r0 in {1,2,4}"),
+    "4k": (2160, 3840, 3, "texture", 100, [4.0], "3840x2160x3 1/f^2 texture, J=36, N=4096, K=100, D/r0=4"),
+    "256": (256, 256, 3, "blobs", 100, [3.0], "256x256x3 blobs, J=36, N=512, K=100, D/r0=3"),
+    "64": (64, 64, 1, "smooth_noise", 16, [2.0], "64x64x1 smoothed noise, J=36, N=128, K=16, D/r0=2"),
+}
+J = 36
+PIX_PER_D = 8.0
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def setup_ours(workload: str, mode: str, device):
+    import torch
+    import paper_2210_06713_gb300 as d
+    from inputs import synthetic
+
+    H, W, C, kind, K, dlist, _ = WORKLOADS[workload]
+    N = d.grid_size(H, W, PIX_PER_D)
+    img = torch.as_tensor(synthetic.image_for(kind, H, W, C, seed=0), device=device).contiguous()
+    factor = d.SpectralFactor(J, N, PIX_PER_D)
+    basis_np = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    P = d.P2S(J, torch.as_tensor(basis_np, dtype=torch.float32, device=device))
+    rng = np.random.default_rng(0)
+    in_scale = np.ones(J, dtype=np.float32)
+    in_scale[:2] = 0
+    P.set_mlp(rng.standard_normal((256, J)) / 6, np.zeros(256), rng.standard_normal((256, 256)) / 16,
+              np.zeros(256), rng.standard_normal((K, 256)) / 16, np.zeros(K), in_scale,
+              np.full(K, 0.01), np.zeros(K))
+    sim = d.Simulator(factor, P, C, H, W)
+    return d, dict(H=H, W=W, C=C, K=K, N=N, dlist=dlist, img=img, factor=factor, P=P, sim=sim)
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    d, S = setup_ours(args.workload, args.mode, device)
+    H, W, C, K = S["H"], S["W"], S["C"], S["K"]
+    mode = d.P2S_LEARNED if args.mode == "learned" else d.P2S_EXACT
+    wdt = d.W_BF16 if mode == d.P2S_LEARNED else d.W_F32
+    stream = torch.cuda.current_stream()
+    fields = torch.empty(J, H, W, device=device)
+    warped = torch.empty(C, H, W, device=device)
+    w = torch.empty(H, W, K, device=device, dtype=torch.bfloat16 if wdt == d.W_BF16 else torch.float32)
+    out = torch.empty(C, H, W, device=device)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
+    nstage = 4
+    seed_base = 1000 * rank
+
+    def step(i, ev=None):
+        dr = S["dlist"][i % len(S["dlist"])]
+        if ev is not None:
+            ev[0].record(stream)
+        d.sample_zernike_fields(S["factor"], dr, seed_base, i, H, W, out=fields)
+        if ev is not None:
+            ev[1].record(stream)
+        d.tilt_warp(S["img"], fields[0], fields[1], out=warped)
+        if ev is not None:
+            ev[2].record(stream)
+        d.p2s_weights(S["P"], mode, fields, w_dtype=wdt, out=w)
+        if ev is not None:
+            ev[3].record(stream)
+        d.basis_blur(S["P"], warped, w, out=out)
+        if ev is not None:
+            ev[4].record(stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(nstage + 1)] for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # evict L2 between timed frames (outside the events)
+        step(args.warmup + i, events[i])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop() if clocks else None
+    stage_ms = np.array([[events[i][s].elapsed_time(events[i][s + 1]) for s in range(nstage)]
+                         for i in range(args.steps)])
+    frame_ms = stage_ms.sum(axis=1)
+    total_ms = float(frame_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through simulate_frame with host buffers
+    img_h = S["img"].cpu().pin_memory()
+    out_h = torch.empty(C, H, W, pin_memory=True)
+    img_d = torch.empty_like(S["img"])
+    out_d = torch.empty_like(S["img"])
+    e2e_steps = max(3, min(args.steps, 20))
+    for i in range(2):
+        img_d.copy_(img_h, non_blocking=True)
+        S["sim"].simulate_frame(img_d, S["dlist"][0], seed_base + 1, i, mode, out=out_d)
+        out_h.copy_(out_d, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        img_d.copy_(img_h, non_blocking=True)
+        S["sim"].simulate_frame(img_d, S["dlist"][i % len(S["dlist"])], seed_base + 1, i, mode, out=out_d)
+        out_h.copy_(out_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    names = ["fields", "warp", "p2s_" + args.mode, "blur"]
+    mean_stage = stage_ms.mean(axis=0)
+    peaks, peak_kind = _peaks()
+    # dominant kernel roofline
+    dom = int(np.argmax(mean_stage))
+    npix = H * W
+    if names[dom] == "blur":
+        flops = 2.0 * 1089 * (K + C) * npix  # per-pixel PSF form on FP32 CUDA cores
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "k_blur_psf", "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    elif names[dom].startswith("p2s"):
+        if args.mode == "exact":
+            flops = npix * (2.0 * 1089 * (J - 2) + 2 * 8.0 * 33 ** 3 + 2.0 * 1089 * K)
+        else:
+            flops = npix * 2.0 * (J * 256 + 256 * 256 + 256 * K)
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "k_p2s_" + args.mode, "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        N = S["N"]
+        half = N // 2 + 1
+        byt = 16.0 * J * N * half + 16.0 * J * H * half + 4.0 * J * npix + 4.0 * J * N * half + 8.0 * J * npix
+        roof = {"kernel": "fields (4 kernels)", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    value = world * args.steps / (total_ms * 1e-3)
+    line = {
+        "metric": "dense-field frames/s at 512^2 and 4K: learned vs exact P2S, same GB300, at tol",
+        "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if args.mode == "learned" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][6], "p2s": args.mode, "H": H, "W": W, "C": C, "J": J,
+                   "K": K, "N": S["N"], "l2": "flushed between timed frames (256 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)},
+        "roofline": roof,
+        "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
+                "d2h_bytes_per_step": int(4 * C * H * W)},
+        "gpu_launches": args.steps * 7,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    return line
+
+
+def run_reference_sample(args):
+    """The FP64 oracle on a bounded sample of the same workload, scaled to frames/s."""
+    from oracle import image as oimage, mlp as omlp, noise as onoise, sampler as osampler, spectrum as ospec
+    from oracle import zernike as ozern
+    from inputs import synthetic
+
+    H, W, C, kind, K, dlist, desc = WORKLOADS[args.workload]
+    N = osampler.grid_size(H, W, PIX_PER_D)
+    img = synthetic.image_for(kind, H, W, C, seed=0)
+    lam = ospec.lambdas(J, N, PIX_PER_D)  # setup, not timed (like the device factor)
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    rng = np.random.default_rng(0)
+    params = {"W1": rng.standard_normal((256, J)) / 6, "b1": np.zeros(256), "W2": rng.standard_normal((256, 256)) / 16,
+              "b2": np.zeros(256), "W3": rng.standard_normal((K, 256)) / 16, "b3": np.zeros(K)}
+    in_scale = np.ones(J)
+    in_scale[:2] = 0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    m_modes = max(1, min(J, int(budget / 0.25)))
+    tile = 64 if args.workload != "64" else 32
+    L = ozern.noll_cholesky(J, dlist[0])
+
+    def one():
+        t0 = time.perf_counter()
+        e = np.stack([onoise.gaussian_block(0, 0, 0, j, N, N) for j in range(m_modes)])
+        u = osampler.unit_fields(e, lam[:m_modes])[:, :H, :W]
+        t_fields = (time.perf_counter() - t0) * J / m_modes
+        t1 = time.perf_counter()
+        a = np.zeros((J, tile, tile))
+        a[:m_modes] = u[:, :tile, :tile]
+        a = osampler.mix(L, a)
+        wp = oimage.tilt_warp(img[:, :tile, :tile], a[0], a[1])
+        wgt = omlp.predict_weights(params, np.moveaxis(a, 0, -1), in_scale, np.full(K, 0.01), np.zeros(K))
+        oimage.basis_blur(wp, wgt, basis)
+        t_tile = (time.perf_counter() - t1) * (H * W) / (tile * tile)
+        return t_fields + t_tile
+
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    per_frame = float(np.mean(ts))
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    sample = (f"per step: fields for {m_modes}/{J} modes on the {N}x{N} grid (scaled by {J}/{m_modes}) + "
+              f"mix, warp, learned P2S and blur on a {tile}x{tile} tile (scaled by pixel count)")
+    return 1.0 / per_frame, cores, sample, desc
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="512", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="learned", choices=["learned", "exact"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, cores, sample, desc = run_reference_sample(args)
+        line = {"impl": "reference", "metric": "dense-field frames/s at 512^2 and 4K: learned vs exact P2S, same "
+                "GB300, at tol", "value": v, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "p2s": args.mode},
+                "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    line = run_ours(args, rank, world, device)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            a2 = argparse.Namespace(**vars(args))
+            a2.steps, a2.warmup = 1, 0
+            v, cores, sample, _ = run_reference_sample(a2)
+            line["cpu_baseline"] = {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

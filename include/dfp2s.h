@@ -1,0 +1,192 @@
+/*
+ * dfp2s.h -- C ABI of the GB300 (sm_103a) dense-field phase-to-space (DF-P2S)
+ * turbulence simulator.
+ *
+ * Method: N. Chimitt, X. Zhang, Z. Mao, S. H. Chan, "Real-Time Dense Field
+ * Phase-to-Space Simulation of Imaging through Atmospheric Turbulence",
+ * arXiv 2210.06713.  One frame is
+ *   1. J per-pixel Zernike coefficient fields (Noll modes 2..J+1) drawn from the
+ *      homogeneous approximation of the Zernike correlation tensor
+ *      (Sec. III-C, Eq. A-tilde): white noise -> 2-D FFT per mode ->
+ *      per-frequency multiply by the spectral square root -> inverse FFT ->
+ *      pixel-wise mixing with L, L L^T = A_0 (Noll's covariance);
+ *   2. a tilt warp by the two tilt fields (the linear-phase part of Eq. 2);
+ *   3. phase-to-space (Sec. II-C): each pixel's Zernike vector -> weights w on K
+ *      basis PSFs -> out(x) = sum_k w_k(x) (phi_k (*) I)(x) (Eq. varying blur).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status: DFP2S_OK (0) or a negative
+ *     DFP2S_E* code.  A failed call sets a thread-local message readable with
+ *     dfp2s_last_error().  No C++ exception crosses this boundary.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; *_host
+ *     are host pointers.  Handles (dfp2s_factor, dfp2s_p2s, dfp2s_ctx) are owned
+ *     by the library and released by their *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously; argument and launch errors are reported
+ *     synchronously, device-side results are ready after the stream is
+ *     synchronised.  Calls sharing one handle must be ordered on one stream.
+ *   - Layouts are row-major: images planar C x H x W float32; fields J x H x W
+ *     float32 with index 0 = Noll mode 2 (x tilt), 1 = Noll 3 (y tilt);
+ *     weights pixel-major H x W x K (float32 or bfloat16); basis K x 33 x 33.
+ *   - x is the image column, y the image row.
+ *   - The library never falls back to host computation: without a usable
+ *     sm_103a device every compute call fails with DFP2S_ECUDA.
+ */
+#ifndef DFP2S_H
+#define DFP2S_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define DFP2S_OK 0
+#define DFP2S_EINVAL (-1)      /* bad argument: null pointer, size out of range */
+#define DFP2S_ENOMEM (-2)      /* device allocation failed */
+#define DFP2S_ECUDA (-3)       /* CUDA runtime or launch error */
+#define DFP2S_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define DFP2S_EUNSUPPORTED (-5) /* valid request this build does not handle */
+
+#define DFP2S_W_F32 0   /* weight storage: float32 */
+#define DFP2S_W_BF16 1  /* weight storage: bfloat16 */
+
+#define DFP2S_P2S_EXACT 0    /* pupil-FFT PSF + projection (Eq. 2, Sec. II-C) */
+#define DFP2S_P2S_LEARNED 1  /* the trained surrogate network (Sec. II-C) */
+
+#define DFP2S_FACTOR_FACTORED 0 /* sqrt(lambda_j(f)) per mode, then mixing by L (Sec. III-C) */
+#define DFP2S_FACTOR_DENSE 1    /* per-frequency J x J symmetric root of L diag(lambda) L^T */
+
+#define DFP2S_KS 33       /* PSF / basis support is 33 x 33 pixels */
+#define DFP2S_MAX_J 64    /* at most 64 Zernike fields (Noll 2..65) */
+#define DFP2S_MAX_K 128   /* at most 128 basis PSFs */
+
+/* Copies the message of the calling thread's last failure (NUL-terminated,
+ * truncated to n bytes).  Returns the status of that failure (0 if none). */
+int dfp2s_last_error(char* buf, size_t n);
+
+/* Library build description (sm target, version); static string. */
+const char* dfp2s_version(void);
+
+/* N = next power of two >= max(H, W) + 4 pix_per_D: the FFT grid side for an
+ * H x W frame; a margin of 4 aperture diameters keeps the periodic wrap-around
+ * of the Fourier sampler (Sec. III-A) beyond the range s > 4 where the paper
+ * finds the cross-correlations vanished (Sec. III-D).  Returns N, or
+ * DFP2S_EINVAL for sizes outside 1..4096 or pix_per_D outside (0, 64]. */
+int dfp2s_grid_size(int H, int W, double pix_per_D);
+
+/* ---------------------------------------------------------- spectral factor
+ * Built once per (J, N, pix_per_D, kind) on the device (FP64 arithmetic) and
+ * reused for every frame and every D/r0: the spectra are normalised so that
+ * each field has unit variance (Sec. III-C step 1), and D/r0 only scales the
+ * mixing matrix L by (D/r0)^{5/6}.
+ *   lambda_j(f) follows the path-integrated point-source model of the
+ *   auto-correlation A_jj(s) (the paper defers its form to its reference
+ *   [Chimitt 2020]); L is the lower Cholesky factor of Noll's matrix A_0
+ *   (Eq. A matrix at s = 0, Fig. rand_gen). */
+typedef struct dfp2s_factor dfp2s_factor;
+
+typedef struct {
+  int J;            /* number of fields, Noll modes 2..J+1; 3 <= J <= DFP2S_MAX_J */
+  int N;            /* FFT grid side, power of two, 16 <= N <= 4096 */
+  double pix_per_D; /* image pixels per aperture diameter of displacement s */
+  int kind;         /* DFP2S_FACTOR_FACTORED or DFP2S_FACTOR_DENSE (N <= 2048) */
+} dfp2s_factor_params;
+
+/* Builds the factor (allocates device memory, synchronises `stream` before
+ * returning).  *out receives the handle.  Errors: EINVAL (params), ENOMEM,
+ * ECUDA. */
+int dfp2s_build_spectral_factor(const dfp2s_factor_params* params, dfp2s_factor** out, void* stream);
+int dfp2s_factor_destroy(dfp2s_factor* f);
+/* Copies the per-mode spectral multiplier sqrt(lambda_j(ky, kx)) / N^2
+ * (float32, layout J x (N/2+1) x N, kx-major: [j][kx][ky]) to dst_dev. */
+int dfp2s_factor_copy_multiplier(const dfp2s_factor* f, float* dst_dev, void* stream);
+/* Copies L (J x J, row-major, FP64, D/r0 = 1) to dst_host (synchronous). */
+int dfp2s_factor_copy_cholesky(const dfp2s_factor* f, double* dst_host);
+/* Bytes of device scratch the factor holds for one frame's FFTs. */
+int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_bytes);
+
+/* Sec. III-C: draws the J x H x W fields a of frame `frame` of stream `seed`
+ * at strength D/r0 into fields_dev (device, J*H*W floats, caller-owned).
+ * White noise: Philox-4x32-10, key = seed, counter = ((y N + x)/4,
+ * (0 << 40) | (frame << 8) | j); FP32 Box-Muller.  Requires H, W <= factor N
+ * (crop of the periodic N x N field) and uses the factor's scratch.
+ * Errors: EINVAL, ECUDA. */
+int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                int H, int W, float* fields_dev, void* stream);
+
+/* Debug/verification: the FP32 Gaussians of one (seed, tag, frame, mode) stream
+ * as rows x cols (cols % 4 == 0), into out_dev.  The same values the field
+ * sampler generates in registers (tag 0). */
+int dfp2s_gaussian_noise(uint64_t seed, uint32_t tag, uint32_t frame, uint32_t mode, int rows, int cols,
+                         float* out_dev, void* stream);
+/* Debug/verification: n raw Philox words, 4 per counter q = q0 .. q0+n/4-1 of
+ * subsequence `sub` (n % 4 == 0), into out_dev. */
+int dfp2s_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int n, uint32_t* out_dev, void* stream);
+
+/* -------------------------------------------------------- phase-to-space
+ * A P2S handle holds the PSF basis phi_k (K x 33 x 33, Sec. II-C Eq. p2s PSF)
+ * and, optionally, the surrogate network. */
+typedef struct dfp2s_p2s dfp2s_p2s;
+
+/* Creates a handle for J fields and K basis PSFs; copies basis_dev
+ * (K x 33 x 33 float32, device).  Errors: EINVAL, ENOMEM. */
+int dfp2s_p2s_create(int J, int K, const float* basis_dev, dfp2s_p2s** out);
+int dfp2s_p2s_destroy(dfp2s_p2s* p);
+
+/* Installs surrogate-network weights (all device float32, copied):
+ * W1 256 x J, b1 256, W2 256 x 256, b2 256, W3 K x 256, b3 K; in_scale J
+ * (multiplies the Zernike vector before the first layer; 0 on the tilt
+ * fields); out_scale, out_shift K (w = y * out_scale + out_shift). */
+int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1, const float* W2, const float* b2,
+                      const float* W3, const float* b3, const float* in_scale, const float* out_scale,
+                      const float* out_shift);
+
+/* Sec. II-C: per-pixel basis weights from the fields (J x H x W, device).
+ *   EXACT: PSF of Eq. (2) from modes Noll 4..J+1 on a 64 x 64 pupil grid
+ *          (aperture 32 samples across, P = 1 inside), |DFT|^2, 33 x 33 centre,
+ *          unit sum, then w = Phi^T h;
+ *   LEARNED: w = MLP(a * in_scale) * out_scale + out_shift.
+ * Writes w_dev (H x W x K, dtype w_dtype).  Errors: EINVAL (no MLP for
+ * LEARNED, sizes), ECUDA. */
+int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fields_dev, int H, int W, void* w_dev,
+                      int w_dtype, void* stream);
+
+/* Tilt warp (Eq. 2's linear phase as a shift, reading of Sec. II-C):
+ * out(c, y, x) = bilinear(img_c; x + (4/pi) a2(y,x), y + (4/pi) a3(y,x)),
+ * clamp to edge.  a2/a3 are H x W (fields 0 and 1).  img, out: C x H x W.
+ * out must not alias img.  Errors: EINVAL, ECUDA. */
+int dfp2s_tilt_warp(const float* img_dev, int C, int H, int W, const float* a2_dev, const float* a3_dev,
+                    float* out_dev, void* stream);
+
+/* Eq. (varying blur): out_c(x) = sum_k w_k(x) sum_u phi_k(u) img_c(x - u),
+ * u in [-16, 16]^2, clamp-to-edge borders.  w_dtype F32: FP32 arithmetic;
+ * BF16: image and basis rounded to bfloat16, tensor-core products with FP32
+ * accumulation.  Errors: EINVAL, ECUDA. */
+int dfp2s_basis_blur(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W, const void* w_dev,
+                     int w_dtype, float* out_dev, void* stream);
+
+/* ---------------------------------------------------------------- frames
+ * A context binds a factor and a P2S handle and owns the per-frame scratch
+ * (fields, warped image, weights) for frames up to max_C x max_H x max_W. */
+typedef struct dfp2s_ctx dfp2s_ctx;
+int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int max_C, int max_H, int max_W,
+                     dfp2s_ctx** out);
+int dfp2s_ctx_destroy(dfp2s_ctx* c);
+
+/* Fig. dfp2s: one frame.  fields (Sec. III-C) -> tilt warp -> P2S weights
+ * (p2s_mode EXACT -> FP32 weights and FP32 blur; LEARNED -> BF16 weights and
+ * the BF16 tensor-core blur) -> out (C x H x W, device).
+ * Errors: EINVAL, ECUDA. */
+int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img_dev, int C, int H, int W, double D_over_r0,
+                         uint64_t seed, uint32_t frame, int p2s_mode, float* out_dev, void* stream);
+/* Device pointers of the context's last fields / warped image / weights
+ * (valid until the next call on the context). */
+int dfp2s_ctx_buffers(const dfp2s_ctx* c, float** fields_dev, float** warped_dev, void** w_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFP2S_H */

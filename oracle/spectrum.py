@@ -46,15 +46,15 @@ def _v_rule():
     xs8, ws8 = np.polynomial.legendre.leggauss(8)
     xs16, ws16 = np.polynomial.legendre.leggauss(16)
     nodes, weights = [], []
-    # log-spaced panels in y = ln v from ln(1e-10) to 0, width 0.1
-    ys = np.linspace(math.log(1e-10), 0.0, 231)
+    # log-spaced panels in y = ln v from ln(1e-8) to 0, width ~0.2
+    ys = np.linspace(math.log(1e-8), 0.0, 93)
     for a, b in zip(ys[:-1], ys[1:]):
         y = 0.5 * (b - a) * xs8 + 0.5 * (a + b)
         v = np.exp(y)
         nodes.append(v)
         weights.append(0.5 * (b - a) * ws8 * v)  # dv = v dy
-    # uniform panels in v from 1 to 48, width 1/8
-    vs = np.linspace(1.0, 48.0, 377)
+    # uniform panels in v from 1 to 48, width 1/4
+    vs = np.linspace(1.0, 48.0, 189)
     for a, b in zip(vs[:-1], vs[1:]):
         nodes.append(0.5 * (b - a) * xs16 + 0.5 * (a + b))
         weights.append(0.5 * (b - a) * ws16)
@@ -67,18 +67,25 @@ def g_radial(n: int, n2: int, v: np.ndarray) -> np.ndarray:
     return v ** (-11.0 / 3.0) * jv(n + 1, 2 * math.pi * v) * jv(n2 + 1, 2 * math.pi * v) / (math.pi * v) ** 2
 
 
-def radial_spectrum(n: int, n2: int, f: np.ndarray) -> np.ndarray:
-    """G_nn'(f) for f > 0 (reading R1, v-form)."""
+def radial_spectra(pairs, f: np.ndarray) -> np.ndarray:
+    """G_nn'(f) for f > 0 and every (n, n') in pairs (reading R1, v-form); shape (len(pairs), len(f))."""
     f = np.atleast_1d(np.asarray(f, dtype=np.float64))
     v, w = _v_rule()
-    gw = w * g_radial(n, n2, v)
-    out = np.empty_like(f)
-    chunk = 2048
+    Gw = np.stack([w * g_radial(n, n2, v) for n, n2 in pairs], axis=1)  # (Q, P)
+    out = np.empty((len(pairs), f.size))
+    chunk = 1024
+    lv = np.log(2 * v)
     for s in range(0, f.size, chunk):
         fc = f[s:s + chunk, None]
-        K = (2 * v / (2 * v + fc)) ** (5.0 / 3.0) * 2 * v ** 2 / (fc * (2 * v + fc) ** 2)
-        out[s:s + chunk] = K @ gw
+        d = 2 * v + fc
+        K = np.exp((5.0 / 3.0) * (lv - np.log(d))) * (2 * v * v) / (fc * d * d)
+        out[:, s:s + chunk] = (K @ Gw).T
     return out
+
+
+def radial_spectrum(n: int, n2: int, f: np.ndarray) -> np.ndarray:
+    """G_nn'(f) for f > 0 (reading R1, v-form)."""
+    return radial_spectra([(n, n2)], f)[0]
 
 
 def radial_spectrum_tform(n: int, n2: int, f: float) -> float:
@@ -141,15 +148,33 @@ def torus_frequencies(N: int, pix_per_D: float):
     return np.hypot(fx, fy), np.arctan2(fy, fx), kx.astype(np.int64), ky.astype(np.int64)
 
 
-@functools.lru_cache(maxsize=32)
-def _radial_on_torus(N: int, pix_per_D: float, n: int, n2: int) -> np.ndarray:
-    fmag, _, kx, ky = torus_frequencies(N, pix_per_D)
+@functools.lru_cache(maxsize=8)
+def _radial_table(N: int, pix_per_D: float, pairs: tuple):
+    """G for every distinct |k|^2 of the N x N torus and every pair; returns (inverse index, table)."""
+    _, _, kx, ky = torus_frequencies(N, pix_per_D)
     r2 = kx * kx + ky * ky
     uniq, inv = np.unique(r2, return_inverse=True)
-    vals = np.zeros(uniq.size)
+    vals = np.zeros((len(pairs), uniq.size))
     nz = uniq > 0
-    vals[nz] = radial_spectrum(n, n2, np.sqrt(uniq[nz].astype(np.float64)) * pix_per_D / N)
-    return vals[inv].reshape(N, N)
+    vals[:, nz] = radial_spectra(list(pairs), np.sqrt(uniq[nz].astype(np.float64)) * pix_per_D / N)
+    return inv.reshape(N, N), vals
+
+
+def _all_pairs(nmax: int = 10):
+    return tuple((a, b) for a in range(1, nmax + 1) for b in range(a, nmax + 1))
+
+
+def _diag_pairs(nmax: int = 10):
+    return tuple((a, a) for a in range(1, nmax + 1))
+
+
+def _radial_on_torus(N: int, pix_per_D: float, n: int, n2: int) -> np.ndarray:
+    if n == n2:
+        pairs = _diag_pairs()
+    else:
+        pairs = _all_pairs()
+    inv, vals = _radial_table(N, pix_per_D, pairs)
+    return vals[pairs.index((min(n, n2), max(n, n2)))][inv]
 
 
 def mode_spectrum_shape(j: int, N: int, pix_per_D: float) -> np.ndarray:

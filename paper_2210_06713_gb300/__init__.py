@@ -1,0 +1,292 @@
+"""Python binding of libdfp2s, the GB300 (sm_103a) DF-P2S turbulence simulator.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``csrc/`` behind the C ABI declared in ``include/dfp2s.h``.
+PyTorch supplies device memory and the current stream.  There is no host
+fallback: a missing library or a missing GPU raises.
+
+The names follow the C ABI: build_spectral_factor, sample_zernike_fields,
+p2s_weights, tilt_warp, basis_blur, simulate_frame (plus handles).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+OK = 0
+W_F32, W_BF16 = 0, 1
+P2S_EXACT, P2S_LEARNED = 0, 1
+FACTOR_FACTORED, FACTOR_DENSE = 0, 1
+KS = 33
+MAX_J = 64
+MAX_K = 128
+
+# every entry point declared in include/dfp2s.h, with its ctypes signature
+_c = ctypes
+_vp, _i, _u32, _u64, _d, _sz = _c.c_void_p, _c.c_int, _c.c_uint32, _c.c_uint64, _c.c_double, _c.c_size_t
+
+
+class FactorParams(ctypes.Structure):
+    _fields_ = [("J", _i), ("N", _i), ("pix_per_D", _d), ("kind", _i)]
+
+
+SIGNATURES = {
+    "dfp2s_last_error": (_i, [_c.c_char_p, _sz]),
+    "dfp2s_version": (_c.c_char_p, []),
+    "dfp2s_grid_size": (_i, [_i, _i, _d]),
+    "dfp2s_build_spectral_factor": (_i, [_c.POINTER(FactorParams), _c.POINTER(_vp), _vp]),
+    "dfp2s_factor_destroy": (_i, [_vp]),
+    "dfp2s_factor_copy_multiplier": (_i, [_vp, _vp, _vp]),
+    "dfp2s_factor_copy_cholesky": (_i, [_vp, _vp]),
+    "dfp2s_factor_info": (_i, [_vp, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_sz)]),
+    "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
+    "dfp2s_p2s_create": (_i, [_i, _i, _vp, _c.POINTER(_vp)]),
+    "dfp2s_p2s_destroy": (_i, [_vp]),
+    "dfp2s_p2s_set_mlp": (_i, [_vp] + [_vp] * 9),
+    "dfp2s_p2s_weights": (_i, [_vp, _i, _vp, _i, _i, _vp, _i, _vp]),
+    "dfp2s_tilt_warp": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "dfp2s_basis_blur": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
+    "dfp2s_ctx_create": (_i, [_vp, _vp, _i, _i, _i, _c.POINTER(_vp)]),
+    "dfp2s_ctx_destroy": (_i, [_vp]),
+    "dfp2s_simulate_frame": (_i, [_vp, _vp, _i, _i, _i, _d, _u64, _u32, _i, _vp, _vp]),
+    "dfp2s_ctx_buffers": (_i, [_vp, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
+}
+
+_LIB = None
+
+
+class DFP2SError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dfp2s error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libdfp2s.so (building it first if needed); raises if that is impossible."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libdfp2s is not built ({_build.LIB}); run paper_2210_06713_gb300.build")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        buf = ctypes.create_string_buffer(512)
+        load().dfp2s_last_error(buf, 512)
+        raise DFP2SError(rc, buf.value.decode(errors="replace"))
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def grid_size(H: int, W: int, pix_per_D: float = 8.0) -> int:
+    n = load().dfp2s_grid_size(H, W, pix_per_D)
+    if n < 0:
+        _check(n)
+    return n
+
+
+# ------------------------------------------------------------------ factor
+class SpectralFactor:
+    """Spectral factor of the homogeneous tensor approximation for (J, N, pix_per_D)."""
+
+    def __init__(self, J: int, N: int, pix_per_D: float = 8.0, kind: int = FACTOR_FACTORED, stream=None):
+        lib = load()
+        self.J, self.N, self.pix_per_D, self.kind = J, N, pix_per_D, kind
+        h = ctypes.c_void_p()
+        p = FactorParams(J, N, pix_per_D, kind)
+        _check(lib.dfp2s_build_spectral_factor(ctypes.byref(p), ctypes.byref(h), _stream(stream)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def multiplier(self) -> torch.Tensor:
+        out = torch.empty(self.J, self.N // 2 + 1, self.N, dtype=torch.float32, device="cuda")
+        _check(load().dfp2s_factor_copy_multiplier(self._h, _ptr(out), _stream()))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def cholesky(self):
+        import numpy as np
+        L = np.empty((self.J, self.J), dtype=np.float64)
+        _check(load().dfp2s_factor_copy_cholesky(self._h, L.ctypes.data_as(ctypes.c_void_p)))
+        return L
+
+    def scratch_bytes(self) -> int:
+        s = ctypes.c_size_t()
+        _check(load().dfp2s_factor_info(self._h, None, None, ctypes.byref(s)))
+        return s.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dfp2s_factor_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_spectral_factor(J: int, N: int, pix_per_D: float = 8.0, kind: int = FACTOR_FACTORED) -> SpectralFactor:
+    return SpectralFactor(J, N, pix_per_D, kind)
+
+
+def sample_zernike_fields(factor: SpectralFactor, D_over_r0: float, seed: int, frame: int, H: int, W: int,
+                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_sample_zernike_fields(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
+                                              _stream(stream)))
+    return out
+
+
+def gaussian_noise(seed: int, tag: int, frame: int, mode: int, rows: int, cols: int) -> torch.Tensor:
+    out = torch.empty(rows, cols, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_gaussian_noise(seed, tag, frame, mode, rows, cols, _ptr(out), _stream()))
+    return out
+
+
+def philox_words(seed: int, sub: int, q0: int, n: int) -> torch.Tensor:
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(load().dfp2s_philox_words(seed, sub, q0, n, _ptr(out), _stream()))
+    return out
+
+
+# --------------------------------------------------------------------- P2S
+class P2S:
+    """PSF basis (K x 33 x 33) and optional surrogate network."""
+
+    def __init__(self, J: int, basis: torch.Tensor):
+        lib = load()
+        basis = basis.to(device="cuda", dtype=torch.float32).contiguous()
+        self.J, self.K = J, basis.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib.dfp2s_p2s_create(J, self.K, _ptr(basis), ctypes.byref(h)))
+        self._h = h
+        self.has_mlp = False
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_mlp(self, W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift):
+        ts = [torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
+              for t in (W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift)]
+        _check(load().dfp2s_p2s_set_mlp(self._h, *[_ptr(t) for t in ts]))
+        self.has_mlp = True
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dfp2s_p2s_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def p2s_weights(p: P2S, mode: int, fields: torch.Tensor, w_dtype: int = W_F32, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    J, H, W = fields.shape
+    if out is None:
+        out = torch.empty(H, W, p.K, dtype=torch.float32 if w_dtype == W_F32 else torch.bfloat16, device="cuda")
+    _check(load().dfp2s_p2s_weights(p.handle, mode, _ptr(fields), H, W, _ptr(out), w_dtype, _stream(stream)))
+    return out
+
+
+def tilt_warp(img: torch.Tensor, a2: torch.Tensor, a3: torch.Tensor, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    C, H, W = img.shape
+    if out is None:
+        out = torch.empty_like(img)
+    _check(load().dfp2s_tilt_warp(_ptr(img), C, H, W, _ptr(a2), _ptr(a3), _ptr(out), _stream(stream)))
+    return out
+
+
+def basis_blur(p: P2S, img: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    C, H, W = img.shape
+    if out is None:
+        out = torch.empty_like(img)
+    wdt = W_BF16 if w.dtype == torch.bfloat16 else W_F32
+    _check(load().dfp2s_basis_blur(p.handle, _ptr(img), C, H, W, _ptr(w), wdt, _ptr(out), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------ frames
+class Simulator:
+    """A frame context: factor + P2S handle + per-frame scratch (Fig. dfp2s)."""
+
+    def __init__(self, factor: SpectralFactor, p2s: P2S, max_C: int, max_H: int, max_W: int):
+        h = ctypes.c_void_p()
+        _check(load().dfp2s_ctx_create(factor.handle, p2s.handle, max_C, max_H, max_W, ctypes.byref(h)))
+        self._h = h
+        self.factor, self.p2s = factor, p2s
+        self.max_shape = (max_C, max_H, max_W)
+
+    def simulate_frame(self, img: torch.Tensor, D_over_r0: float, seed: int, frame: int, mode: int = P2S_EXACT,
+                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        C, H, W = img.shape
+        if out is None:
+            out = torch.empty_like(img)
+        _check(load().dfp2s_simulate_frame(self._h, _ptr(img), C, H, W, D_over_r0, seed, frame, mode, _ptr(out),
+                                           _stream(stream)))
+        return out
+
+    def buffers(self, J: int, C: int, H: int, W: int, K: int, w_dtype=torch.float32):
+        f, wp, w = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().dfp2s_ctx_buffers(self._h, ctypes.byref(f), ctypes.byref(wp), ctypes.byref(w)))
+        return f.value, wp.value, w.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dfp2s_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate_frame(sim: Simulator, img: torch.Tensor, D_over_r0: float, seed: int, frame: int,
+                   mode: int = P2S_EXACT, out: torch.Tensor | None = None) -> torch.Tensor:
+    return sim.simulate_frame(img, D_over_r0, seed, frame, mode, out)

@@ -1,0 +1,373 @@
+// C ABI of libdfp2s (declared in include/dfp2s.h): argument checks, handle
+// lifetimes, scratch ownership and the per-frame pipeline of Fig. dfp2s.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+// ---------------------------------------------------------------- errors
+namespace {
+thread_local char g_err[512] = {0};
+thread_local int g_err_code = 0;
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+}  // namespace
+
+int dfp2s_fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  g_err_code = code;
+  return code;
+}
+
+int dfp2s_fail_cuda(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return dfp2s_fail(DFP2S_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return dfp2s_fail(DFP2S_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CHECK_ARG(cond, ...)                          \
+  do {                                                \
+    if (!(cond)) return dfp2s_fail(DFP2S_EINVAL, __VA_ARGS__); \
+  } while (0)
+
+#define CHECK_LAUNCH(expr)                                                          \
+  do {                                                                              \
+    if ((expr) != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), #expr);      \
+  } while (0)
+
+extern "C" int dfp2s_last_error(char* buf, size_t n) {
+  if (buf && n) {
+    strncpy(buf, g_err, n - 1);
+    buf[n - 1] = 0;
+  }
+  return g_err_code;
+}
+
+extern "C" const char* dfp2s_version(void) { return "dfp2s 0.1 sm_103a"; }
+
+extern "C" int dfp2s_grid_size(int H, int W, double pix_per_D) {
+  CHECK_ARG(H >= 1 && W >= 1 && H <= 4096 && W <= 4096, "image size %dx%d out of range", H, W);
+  CHECK_ARG(pix_per_D > 0 && pix_per_D <= 64, "pix_per_D %g out of range", pix_per_D);
+  const int need = (H > W ? H : W) + (int)ceil(4.0 * pix_per_D);
+  int N = 1;
+  while (N < need) N *= 2;
+  CHECK_ARG(N <= 4096, "grid %d exceeds 4096", N);
+  return N;
+}
+
+// ------------------------------------------------------------ spectral factor
+struct dfp2s_factor {
+  dfp2s_factor_dev d;
+  int kind;
+  int device;
+};
+
+static void factor_free(dfp2s_factor* f) {
+  if (!f) return;
+  cudaFree(f->d.mult);
+  cudaFree(f->d.L64);
+  cudaFree(f->d.L32);
+  cudaFree(f->d.tw);
+  cudaFree(f->d.scratch);
+  delete f;
+}
+
+extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_factor** out, void* stream) {
+  CHECK_ARG(p && out, "null argument");
+  *out = nullptr;
+  CHECK_ARG(p->J >= 3 && p->J <= DFP2S_MAX_J, "J = %d out of range [3, %d]", p->J, DFP2S_MAX_J);
+  CHECK_ARG(is_pow2(p->N) && p->N >= 16 && p->N <= 4096, "N = %d must be a power of two in [16, 4096]", p->N);
+  CHECK_ARG(p->pix_per_D > 0 && p->pix_per_D <= 64, "pix_per_D out of range");
+  CHECK_ARG(p->kind == DFP2S_FACTOR_FACTORED || p->kind == DFP2S_FACTOR_DENSE, "unknown factor kind");
+  if (p->kind == DFP2S_FACTOR_DENSE) return dfp2s_fail(DFP2S_EUNSUPPORTED, "dense factor not built in this version");
+  dfp2s_factor* f = new dfp2s_factor();
+  memset(&f->d, 0, sizeof(f->d));
+  f->d.J = p->J;
+  f->d.N = p->N;
+  f->d.pix_per_D = p->pix_per_D;
+  f->kind = p->kind;
+  cudaGetDevice(&f->device);
+  const size_t half = (size_t)(p->N / 2 + 1) * p->N;
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&f->d.mult, (size_t)p->J * half * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&f->d.L64, (size_t)p->J * p->J * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&f->d.L32, (size_t)p->J * p->J * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&f->d.tw, (size_t)p->N * sizeof(float2))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&f->d.scratch, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
+    factor_free(f);
+    return dfp2s_fail_cuda(e, "factor allocation");
+  }
+  const int rc = dfp2s_factor_build_device(&f->d, as_stream(stream));
+  if (rc != DFP2S_OK) {
+    factor_free(f);
+    return rc;
+  }
+  *out = f;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_factor_destroy(dfp2s_factor* f) {
+  factor_free(f);
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_factor_copy_multiplier(const dfp2s_factor* f, float* dst, void* stream) {
+  CHECK_ARG(f && dst, "null argument");
+  const size_t n = (size_t)f->d.J * (f->d.N / 2 + 1) * f->d.N;
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(dst, f->d.mult, n * sizeof(float), cudaMemcpyDeviceToDevice, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_factor_copy_cholesky(const dfp2s_factor* f, double* dst_host) {
+  CHECK_ARG(f && dst_host, "null argument");
+  DFP2S_CUDA_TRY(cudaMemcpy(dst_host, f->d.L64, (size_t)f->d.J * f->d.J * sizeof(double), cudaMemcpyDeviceToHost));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_bytes) {
+  CHECK_ARG(f, "null factor");
+  if (J) *J = f->d.J;
+  if (N) *N = f->d.N;
+  if (scratch_bytes) *scratch_bytes = (size_t)f->d.J * (f->d.N / 2 + 1) * f->d.N * sizeof(float2);
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                           int H, int W, float* fields, void* stream) {
+  CHECK_ARG(f && fields, "null argument");
+  CHECK_ARG(H >= 1 && W >= 1 && H <= f->d.N && W <= f->d.N, "frame %dx%d does not fit the %d grid", H, W, f->d.N);
+  CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
+  const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+  CHECK_LAUNCH(dfp2s_launch_sample_fields(f->d.scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame,
+                                          f->d.L32, scale, fields, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_gaussian_noise(uint64_t seed, uint32_t tag, uint32_t frame, uint32_t mode, int rows, int cols,
+                                    float* out, void* stream) {
+  CHECK_ARG(out && rows >= 1 && cols >= 4 && cols % 4 == 0, "bad noise shape %dx%d", rows, cols);
+  CHECK_ARG(mode < 256 && tag < (1u << 24), "mode/tag out of range");
+  const uint64_t sub = ((uint64_t)tag << 40) | ((uint64_t)frame << 8) | mode;
+  CHECK_LAUNCH(dfp2s_launch_gaussian(seed, sub, (size_t)rows * cols / 4, out, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int n, uint32_t* out, void* stream) {
+  CHECK_ARG(out && n >= 4 && n % 4 == 0, "n must be a positive multiple of 4");
+  CHECK_LAUNCH(dfp2s_launch_philox_words(seed, sub, q0, n / 4, out, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+// ---------------------------------------------------------------------- P2S
+struct dfp2s_p2s {
+  dfp2s_p2s_dev d;
+};
+
+static void p2s_free(dfp2s_p2s* p) {
+  if (!p) return;
+  void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt, p->d.mask, p->d.dft, p->d.W1, p->d.b1, p->d.W2,
+                  p->d.b2, p->d.W3, p->d.b3, p->d.in_scale, p->d.out_scale, p->d.out_shift};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+extern "C" int dfp2s_p2s_create(int J, int K, const float* basis, dfp2s_p2s** out) {
+  CHECK_ARG(out && basis, "null argument");
+  *out = nullptr;
+  CHECK_ARG(J >= 3 && J <= DFP2S_MAX_J, "J = %d out of range", J);
+  CHECK_ARG(K >= 1 && K <= DFP2S_MAX_K, "K = %d out of range [1, %d]", K, DFP2S_MAX_K);
+  dfp2s_p2s* p = new dfp2s_p2s();
+  memset(&p->d, 0, sizeof(p->d));
+  p->d.J = J;
+  p->d.K = K;
+  const size_t n2 = DFP2S_KS * DFP2S_KS;
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&p->d.basis, K * n2 * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d.phiT, K * n2 * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d.zt, (J - 2) * n2 * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d.mask, n2 * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d.dft, n2 * sizeof(float2))) != cudaSuccess) {
+    p2s_free(p);
+    return dfp2s_fail_cuda(e, "p2s allocation");
+  }
+  if ((e = cudaMemcpy(p->d.basis, basis, K * n2 * sizeof(float), cudaMemcpyDefault)) != cudaSuccess) {
+    p2s_free(p);
+    return dfp2s_fail_cuda(e, "basis copy");
+  }
+  if (dfp2s_p2s_build_tables(&p->d, 0) != DFP2S_OK || (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    p2s_free(p);
+    return dfp2s_fail_cuda(cudaGetLastError(), "p2s tables");
+  }
+  *out = p;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_p2s_destroy(dfp2s_p2s* p) {
+  p2s_free(p);
+  return DFP2S_OK;
+}
+
+// copies an (rows x cols) row-major device matrix to a newly allocated transposed (cols x rows) one
+static cudaError_t copy_transposed(float** dst, const float* src, int rows, int cols) {
+  std::vector<float> h((size_t)rows * cols), t((size_t)rows * cols);
+  cudaError_t e = cudaMemcpy(h.data(), src, h.size() * sizeof(float), cudaMemcpyDefault);
+  if (e != cudaSuccess) return e;
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) t[(size_t)c * rows + r] = h[(size_t)r * cols + c];
+  if ((e = cudaMalloc((void**)dst, t.size() * sizeof(float))) != cudaSuccess) return e;
+  return cudaMemcpy(*dst, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
+}
+
+static cudaError_t copy_vec(float** dst, const float* src, int n) {
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(float));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, n * sizeof(float), cudaMemcpyDefault);
+}
+
+extern "C" int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1, const float* W2, const float* b2,
+                                 const float* W3, const float* b3, const float* in_scale, const float* out_scale,
+                                 const float* out_shift) {
+  CHECK_ARG(p && W1 && b1 && W2 && b2 && W3 && b3 && in_scale && out_scale && out_shift, "null argument");
+  const int J = p->d.J, K = p->d.K;
+  float** olds[] = {&p->d.W1, &p->d.b1, &p->d.W2, &p->d.b2, &p->d.W3, &p->d.b3,
+                    &p->d.in_scale, &p->d.out_scale, &p->d.out_shift};
+  for (float** o : olds)
+    if (*o) {
+      cudaFree(*o);
+      *o = nullptr;
+    }
+  p->d.has_mlp = 0;
+  cudaError_t e;
+  if ((e = copy_transposed(&p->d.W1, W1, 256, J)) != cudaSuccess || (e = copy_vec(&p->d.b1, b1, 256)) != cudaSuccess ||
+      (e = copy_transposed(&p->d.W2, W2, 256, 256)) != cudaSuccess ||
+      (e = copy_vec(&p->d.b2, b2, 256)) != cudaSuccess || (e = copy_transposed(&p->d.W3, W3, K, 256)) != cudaSuccess ||
+      (e = copy_vec(&p->d.b3, b3, K)) != cudaSuccess || (e = copy_vec(&p->d.in_scale, in_scale, J)) != cudaSuccess ||
+      (e = copy_vec(&p->d.out_scale, out_scale, K)) != cudaSuccess ||
+      (e = copy_vec(&p->d.out_shift, out_shift, K)) != cudaSuccess)
+    return dfp2s_fail_cuda(e, "mlp weights");
+  p->d.has_mlp = 1;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fields, int H, int W, void* w,
+                                 int w_dtype, void* stream) {
+  CHECK_ARG(p && fields && w, "null argument");
+  CHECK_ARG(H >= 1 && W >= 1 && (size_t)H * W <= (1u << 26), "frame %dx%d out of range", H, W);
+  CHECK_ARG(w_dtype == DFP2S_W_F32 || w_dtype == DFP2S_W_BF16, "unknown weight dtype");
+  if (mode == DFP2S_P2S_EXACT) {
+    CHECK_LAUNCH(dfp2s_launch_p2s_exact(&p->d, fields, H, W, w, w_dtype, as_stream(stream)));
+  } else if (mode == DFP2S_P2S_LEARNED) {
+    CHECK_ARG(p->d.has_mlp, "no surrogate network installed");
+    CHECK_LAUNCH(dfp2s_launch_p2s_mlp(&p->d, fields, H, W, w, w_dtype, as_stream(stream)));
+  } else {
+    return dfp2s_fail(DFP2S_EINVAL, "unknown P2S mode %d", mode);
+  }
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_tilt_warp(const float* img, int C, int H, int W, const float* a2, const float* a3, float* out,
+                               void* stream) {
+  CHECK_ARG(img && a2 && a3 && out, "null argument");
+  CHECK_ARG(img != out, "out must not alias img");
+  CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 && W <= (1 << 20), "bad image shape");
+  CHECK_LAUNCH(dfp2s_launch_tilt_warp(img, C, H, W, a2, a3, out, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_basis_blur(const dfp2s_p2s* p, const float* img, int C, int H, int W, const void* w,
+                                int w_dtype, float* out, void* stream) {
+  CHECK_ARG(p && img && w && out, "null argument");
+  CHECK_ARG(img != out, "out must not alias img");
+  CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 * 4 && W <= (1 << 20), "bad image shape");
+  CHECK_ARG(w_dtype == DFP2S_W_F32 || w_dtype == DFP2S_W_BF16, "unknown weight dtype");
+  CHECK_LAUNCH(dfp2s_launch_blur(&p->d, img, C, H, W, w, w_dtype, out, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+// ------------------------------------------------------------------ frames
+struct dfp2s_ctx {
+  const dfp2s_factor* f;
+  const dfp2s_p2s* p;
+  int maxC, maxH, maxW;
+  float* fields;
+  float* warped;
+  void* w;
+};
+
+extern "C" int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int maxC, int maxH, int maxW,
+                                dfp2s_ctx** out) {
+  CHECK_ARG(f && p && out, "null argument");
+  *out = nullptr;
+  CHECK_ARG(f->d.J == p->d.J, "factor J %d != p2s J %d", f->d.J, p->d.J);
+  CHECK_ARG(maxC >= 1 && maxC <= 64 && maxH >= 1 && maxW >= 1 && maxH <= f->d.N && maxW <= f->d.N,
+            "context shape does not fit the factor grid");
+  dfp2s_ctx* c = new dfp2s_ctx();
+  c->f = f;
+  c->p = p;
+  c->maxC = maxC;
+  c->maxH = maxH;
+  c->maxW = maxW;
+  c->fields = nullptr;
+  c->warped = nullptr;
+  c->w = nullptr;
+  const size_t npix = (size_t)maxH * maxW;
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&c->fields, (size_t)f->d.J * npix * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->warped, (size_t)maxC * npix * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&c->w, (size_t)p->d.K * npix * sizeof(float))) != cudaSuccess) {
+    cudaFree(c->fields);
+    cudaFree(c->warped);
+    cudaFree(c->w);
+    delete c;
+    return dfp2s_fail_cuda(e, "context allocation");
+  }
+  *out = c;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_ctx_destroy(dfp2s_ctx* c) {
+  if (!c) return DFP2S_OK;
+  cudaFree(c->fields);
+  cudaFree(c->warped);
+  cudaFree(c->w);
+  delete c;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_ctx_buffers(const dfp2s_ctx* c, float** fields, float** warped, void** w) {
+  CHECK_ARG(c, "null context");
+  if (fields) *fields = c->fields;
+  if (warped) *warped = c->warped;
+  if (w) *w = c->w;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H, int W, double D_over_r0,
+                                    uint64_t seed, uint32_t frame, int p2s_mode, float* out, void* stream) {
+  CHECK_ARG(c && img && out, "null argument");
+  CHECK_ARG(img != out, "out must not alias img");
+  CHECK_ARG(C >= 1 && C <= c->maxC && H >= 1 && H <= c->maxH && W >= 1 && W <= c->maxW,
+            "frame %dx%dx%d exceeds the context's %dx%dx%d", C, H, W, c->maxC, c->maxH, c->maxW);
+  CHECK_ARG(p2s_mode == DFP2S_P2S_EXACT || p2s_mode == DFP2S_P2S_LEARNED, "unknown P2S mode");
+  int rc = dfp2s_sample_zernike_fields(c->f, D_over_r0, seed, frame, H, W, c->fields, stream);
+  if (rc) return rc;
+  const size_t npix = (size_t)H * W;
+  rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
+  if (rc) return rc;
+  const int wdt = p2s_mode == DFP2S_P2S_EXACT ? DFP2S_W_F32 : DFP2S_W_BF16;
+  rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, wdt, stream);
+  if (rc) return rc;
+  return dfp2s_basis_blur(c->p, c->warped, C, H, W, c->w, wdt, out, stream);
+}

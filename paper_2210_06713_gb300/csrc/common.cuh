@@ -1,0 +1,257 @@
+// Shared device helpers for the DF-P2S kernels (sm_103a).
+//
+//  * Philox-4x32-10 counter-based generator (Salmon et al., SC 2011) and the
+//    FP32 Box-Muller transform with this library's own log and sin/cos, written
+//    so that every value is reproducible bit for bit on any IEEE FP32 machine:
+//    each step is one correctly rounded operation (__fmul_rn, __fadd_rn, ...),
+//    so no multiply-add is ever contracted.
+//  * complex helpers and a shared-memory Stockham FFT in which every thread
+//    keeps 8 complex values in registers (radix-8/4/2 stages).
+//  * status codes and launch-error checks used by the host code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dfp2s.h"
+
+#define DFP2S_DEV __device__ __forceinline__
+
+// ----------------------------------------------------------------- Philox
+// The published round: two 32x32->64 multiplies, a Feistel-like permutation,
+// and a Weyl-sequence key schedule.
+DFP2S_DEV uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    if (r < 9) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+  }
+  return c;
+}
+
+// Stream layout: key = seed, counter = (q, subsequence), subsequence =
+// (tag << 40) | (frame << 8) | mode; counter q covers positions 4q..4q+3.
+DFP2S_DEV uint4 philox_at(uint64_t seed, uint64_t sub, uint64_t q) {
+  return philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)sub, (uint32_t)(sub >> 32)),
+                       (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// ln(u) for a positive normal FP32 u: u = 2^e m with m in [sqrt(1/2), sqrt(2)),
+// ln m = 2 atanh(s) = 2s + s^3 (2/3 + s^2 (2/5 + s^2 (2/7 + s^2 (2/9 + s^2 2/11)))),
+// s = (m-1)/(m+1); e ln 2 with ln 2 split into a 12-bit head and an FP32 tail.
+DFP2S_DEV float dfp2s_log(float u) {
+  const uint32_t bits = __float_as_uint(u);
+  int e = (int)(bits >> 23) - 127;
+  float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+  if (m > 0x1.6a09e6p+0f) {  // sqrt(2) rounded to FP32
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
+  }
+  const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float s2 = __fmul_rn(s, s);
+  float p = 0x1.745d18p-3f;                         // 2/11
+  p = __fadd_rn(__fmul_rn(p, s2), 0x1.c71c72p-3f);  // 2/9
+  p = __fadd_rn(__fmul_rn(p, s2), 0x1.24924ap-2f);  // 2/7
+  p = __fadd_rn(__fmul_rn(p, s2), 0x1.99999ap-2f);  // 2/5
+  p = __fadd_rn(__fmul_rn(p, s2), 0x1.555556p-1f);  // 2/3
+  float t = __fmul_rn(s, s2);
+  t = __fmul_rn(t, p);
+  const float logm = __fadd_rn(__fadd_rn(s, s), t);
+  const float ef = (float)e;
+  float lo = __fmul_rn(ef, 0x1.0bfbe8p-15f);  // ln2 - head
+  lo = __fadd_rn(lo, logm);
+  const float hi = __fmul_rn(ef, 0x1.62ep-1f);  // head of ln 2 (12 significant bits)
+  return __fadd_rn(hi, lo);
+}
+
+// cos and sin of 2 pi u, u = (2k+1) 2^-24.  Quarter turns v = 4u = (2k+1) 2^-22;
+// q = round(v) and r = v - q in [-1/2, 1/2] exactly in integers; Taylor series of
+// sin((pi/2) r) to r^9 and cos((pi/2) r) to r^10, then the quadrant.
+DFP2S_DEV void dfp2s_sincos_2pi(uint32_t k, float* cs, float* sn) {
+  const int64_t num = 2 * (int64_t)k + 1;
+  const int64_t q = (num + (1 << 21)) >> 22;
+  const int64_t rnum = num - (q << 22);
+  const float r = __fmul_rn((float)rnum, 0x1.0p-22f);
+  const float r2 = __fmul_rn(r, r);
+  float sp = 0x1.507834p-13f;
+  sp = __fadd_rn(__fmul_rn(sp, r2), -0x1.32d2ccp-8f);
+  sp = __fadd_rn(__fmul_rn(sp, r2), 0x1.466bc6p-4f);
+  sp = __fadd_rn(__fmul_rn(sp, r2), -0x1.4abbcep-1f);
+  sp = __fadd_rn(__fmul_rn(sp, r2), 0x1.921fb6p+0f);
+  const float s = __fmul_rn(r, sp);
+  float cp = -0x1.a6d1f2p-16f;
+  cp = __fadd_rn(__fmul_rn(cp, r2), 0x1.e1f506p-11f);
+  cp = __fadd_rn(__fmul_rn(cp, r2), -0x1.55d3c8p-6f);
+  cp = __fadd_rn(__fmul_rn(cp, r2), 0x1.03c1fp-2f);
+  cp = __fadd_rn(__fmul_rn(cp, r2), -0x1.3bd3ccp+0f);
+  const float c = __fadd_rn(__fmul_rn(cp, r2), 1.0f);
+  switch ((int)(q & 3)) {
+    case 0: *cs = c; *sn = s; break;
+    case 1: *cs = -s; *sn = c; break;
+    case 2: *cs = -c; *sn = -s; break;
+    default: *cs = s; *sn = -c; break;
+  }
+}
+
+// Two N(0,1) samples from two Philox words: r = sqrt(-2 ln u_a), angle 2 pi u_b.
+DFP2S_DEV float2 dfp2s_box_muller(uint32_t wa, uint32_t wb) {
+  const uint32_t ka = wa >> 9;
+  const float ua = __fmul_rn((float)(2u * ka + 1u), 0x1.0p-24f);
+  const float t = __fmul_rn(dfp2s_log(ua), -2.0f);
+  const float r = __fsqrt_rn(t);
+  float c, s;
+  dfp2s_sincos_2pi(wb >> 9, &c, &s);
+  return make_float2(__fmul_rn(r, c), __fmul_rn(r, s));
+}
+
+// Four Gaussians for positions 4q..4q+3 of one (seed, sub) stream.
+DFP2S_DEV float4 dfp2s_gauss4(uint64_t seed, uint64_t sub, uint64_t q) {
+  const uint4 w = philox_at(seed, sub, q);
+  const float2 a = dfp2s_box_muller(w.x, w.y);
+  const float2 b = dfp2s_box_muller(w.z, w.w);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+DFP2S_DEV uint64_t dfp2s_subsequence(uint32_t tag, uint32_t frame, uint32_t mode) {
+  return ((uint64_t)tag << 40) | ((uint64_t)frame << 8) | (uint64_t)mode;
+}
+
+// ---------------------------------------------------------------- complex
+DFP2S_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+DFP2S_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+DFP2S_DEV float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+DFP2S_DEV float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+DFP2S_DEV float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+DFP2S_DEV float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+DFP2S_DEV float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---------------------------------------------------------- FFT building blocks
+// In-register DFTs, unnormalised, sign -1 (forward) or +1 (INV) in the exponent.
+template <bool INV>
+DFP2S_DEV void dft2(float2& a, float2& b) {
+  const float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+DFP2S_DEV void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s0 = cadd(a0, a2), d0 = csub(a0, a2);
+  const float2 s1 = cadd(a1, a3), d1 = mul_mi<INV>(csub(a1, a3));
+  a0 = cadd(s0, s1);
+  a2 = csub(s0, s1);
+  a1 = cadd(d0, d1);
+  a3 = csub(d0, d1);
+}
+
+template <bool INV>
+DFP2S_DEV void dft8(float2* v) {
+  // radix-2 split into even/odd halves, each a DFT-4, then W8 twiddles.
+  const float r = 0.70710678118654752f;
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  // o_k *= exp(-+ 2 pi i k / 8)
+  o1 = INV ? make_float2(r * (o1.x - o1.y), r * (o1.x + o1.y)) : make_float2(r * (o1.x + o1.y), r * (o1.y - o1.x));
+  o2 = mul_mi<INV>(o2);
+  o3 = INV ? make_float2(-r * (o3.x + o3.y), r * (o3.x - o3.y)) : make_float2(r * (o3.y - o3.x), -r * (o3.x + o3.y));
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+// Shared-memory index with one pad slot every 8 entries (breaks the stride-8
+// bank conflicts of the Stockham scatter).
+DFP2S_DEV int fpad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int fpad_size(int n) { return n + (n >> 3); }
+
+// One Stockham autosort stage (Govindaraju et al., SC 2008) of an FFT of
+// length N held in shared memory `buf` (padded with fpad): with sub-transform
+// length Ns and radix R it reads x[j + r N/R], multiplies by the twiddles
+// w^(r k), k = j mod Ns, w = exp(-+2 pi i / (Ns R)), does a DFT-R and writes
+// y[(j - k) R + k + r Ns].  The NT = N/8 threads of the group each own 8 values
+// (8/R butterflies), so a stage is load -> barrier -> compute -> store ->
+// barrier and runs in place.  `tw` holds exp(-2 pi i m / N), m in [0, N),
+// rounded from FP64.
+template <int R, bool INV, typename Sync>
+DFP2S_DEV void fft_stage(float2* buf, int N, int Ns, int t, const float2* __restrict__ tw, Sync sync) {
+  constexpr int PER = 8 / R;
+  const int nb = N >> 3;
+  const int nbutter = N / R;
+  float2 v[8];
+#pragma unroll
+  for (int bi = 0; bi < PER; ++bi)
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[bi * R + r] = buf[fpad(t + bi * nb + r * nbutter)];
+  sync();
+#pragma unroll
+  for (int bi = 0; bi < PER; ++bi) {
+    const int j = t + bi * nb;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const int step = N / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(tw + r * k * step);
+        v[bi * R + r] = INV ? cmulc(v[bi * R + r], w) : cmul(v[bi * R + r], w);
+      }
+    }
+    if (R == 8) dft8<INV>(v + bi * R);
+    else if (R == 4) dft4<INV>(v[bi * R], v[bi * R + 1], v[bi * R + 2], v[bi * R + 3]);
+    else dft2<INV>(v[bi * R], v[bi * R + 1]);
+  }
+#pragma unroll
+  for (int bi = 0; bi < PER; ++bi) {
+    const int j = t + bi * nb;
+    const int k = j & (Ns - 1);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[fpad(base + r * Ns)] = v[bi * R + r];
+  }
+  sync();
+}
+
+// Full FFT of length N (power of two, 8 <= N <= 4096), unnormalised: radix-8
+// stages, then one radix-4 or radix-2 stage for the rest.  The caller must have
+// made `buf` visible to the group (barrier) before the call.
+template <bool INV, typename Sync>
+DFP2S_DEV void fft_smem(float2* buf, int N, int t, const float2* __restrict__ tw, Sync sync) {
+  int Ns = 1;
+  int rem = N;
+  while (rem >= 8) {
+    fft_stage<8, INV>(buf, N, Ns, t, tw, sync);
+    Ns *= 8;
+    rem >>= 3;
+  }
+  if (rem == 4) fft_stage<4, INV>(buf, N, Ns, t, tw, sync);
+  else if (rem == 2) fft_stage<2, INV>(buf, N, Ns, t, tw, sync);
+}
+
+// ------------------------------------------------------------- host helpers
+#define DFP2S_CUDA_TRY(expr)                                      \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return dfp2s_fail_cuda(_e, #expr);    \
+  } while (0)
+
+int dfp2s_fail(int code, const char* fmt, ...);
+int dfp2s_fail_cuda(cudaError_t e, const char* what);

@@ -1,0 +1,317 @@
+// Spectral factor of the homogeneous approximation (Sec. III-C), built on the
+// device in FP64.
+//
+//   A_0  Noll's covariance of modes 2..J+1 (Eq. A matrix at s = 0), closed form
+//        K sqrt((n+1)(n'+1)) (-1)^((n+n'-2m)/2) Gamma((n+n'-5/3)/2) /
+//        [Gamma((n-n'+17/3)/2) Gamma((n'-n+17/3)/2) Gamma((n+n'+23/3)/2)]
+//        for equal m and equal angular function, K = c Gamma(14/3) 2^{-5/3}
+//        pi^{8/3}, c = [(24/5)Gamma(6/5)]^{5/6} Gamma(11/6)^2 / (2 pi^{11/3})
+//        (the coefficient of the Kolmogorov phase spectrum whose structure
+//        function is 6.88 (r/r0)^{5/3}, Eq. fried_struct); L = chol(A_0).
+//   lambda_j(f) the spectrum of the auto-correlation A_jj(s) under the
+//        path-integrated point-source model: with u = f (1-t)/(2t) for a layer
+//        at path fraction t,
+//          P_j(f) = (n+1) Theta_j(phi) int_0^1 (1-t)^{5/3} ((1-t)/(2t))^2 u^{-11/3}
+//                   [J_{n+1}(2 pi u)/(pi u)]^2 dt,
+//        evaluated as G_n(f) = int_0^inf (2v/(2v+f))^{5/3} 2v^2/(f (2v+f)^2) g_n(v) dv,
+//        g_n(v) = v^{-11/3} [J_{n+1}(2 pi v)/(pi v)]^2, with a composite
+//        Gauss-Legendre rule (8-point panels log-spaced on [1e-7, 1], 16-point
+//        panels of width 1/2 on [1, 48]).  Theta_j = 1 (m = 0), 2 cos^2(m phi)
+//        (even j), 2 sin^2(m phi) (odd j).  lambda_j = N^2 P_j / sum_{k != 0} P_j
+//        over the N x N torus (unit variance), lambda_j(0) = 0.
+//   The stored multiplier is sqrt(lambda_j)/N^2, which also carries the 1/N^2
+//   of the inverse FFT.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kMaxOrders = 11;  // radial orders 1..10 cover Noll 2..65
+
+DFP2S_DEV void noll_nm(int j, int* n, int* m) {
+  int nn = 0;
+  while ((nn + 1) * (nn + 2) / 2 < j) ++nn;
+  const int r = j - nn * (nn + 1) / 2 - 1;
+  *n = nn;
+  *m = (nn % 2 == 0) ? 2 * ((r + 1) / 2) : 2 * (r / 2) + 1;
+}
+
+// A_0 (D/r0 = 1) and its lower Cholesky factor; one CTA.
+__global__ void k_noll_chol(int J, double* __restrict__ L64, float* __restrict__ L32, int* __restrict__ err) {
+  __shared__ double A[64 * 64];
+  const double pi = 3.14159265358979323846;
+  const double c = pow((24.0 / 5.0) * tgamma(6.0 / 5.0), 5.0 / 6.0) * tgamma(11.0 / 6.0) * tgamma(11.0 / 6.0) /
+                   (2.0 * pow(pi, 11.0 / 3.0));
+  const double K = c * tgamma(14.0 / 3.0) * pow(2.0, -5.0 / 3.0) * pow(pi, 8.0 / 3.0);
+  for (int idx = threadIdx.x; idx < J * J; idx += blockDim.x) {
+    const int a = idx / J, b = idx - a * J;
+    const int i = a + 2, j = b + 2;
+    int ni, mi, nj, mj;
+    noll_nm(i, &ni, &mi);
+    noll_nm(j, &nj, &mj);
+    double v = 0.0;
+    if (mi == mj && (mi == 0 || (i & 1) == (j & 1))) {
+      const double sign = (((ni + nj - 2 * mi) / 2) & 1) ? -1.0 : 1.0;
+      const double lg = lgamma((ni + nj - 5.0 / 3.0) / 2.0) - lgamma((ni - nj + 17.0 / 3.0) / 2.0) -
+                        lgamma((nj - ni + 17.0 / 3.0) / 2.0) - lgamma((ni + nj + 23.0 / 3.0) / 2.0);
+      v = K * sqrt((double)((ni + 1) * (nj + 1))) * sign * exp(lg);
+    }
+    A[idx] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Cholesky-Banachiewicz, lower triangle in place
+    for (int i = 0; i < J; ++i) {
+      for (int j = 0; j <= i; ++j) {
+        double s = A[i * J + j];
+        for (int k = 0; k < j; ++k) s -= A[i * J + k] * A[j * J + k];
+        if (i == j) {
+          if (!(s > 0.0)) {
+            *err = 1;
+            s = 1e-300;
+          }
+          A[i * J + i] = sqrt(s);
+        } else {
+          A[i * J + j] = s / A[j * J + j];
+        }
+      }
+      for (int j = i + 1; j < J; ++j) A[i * J + j] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < J * J; idx += blockDim.x) {
+    L64[idx] = A[idx];
+    L32[idx] = (float)A[idx];
+  }
+}
+
+// g_n(v_q) * w_q for every needed radial order n (layout [q][o]).
+__global__ void k_gtab(const double* __restrict__ v, const double* __restrict__ w, int Q, const int* __restrict__ orders,
+                       int no, double* __restrict__ gtab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Q * no) return;
+  const int q = i / no, o = i - q * no;
+  const double pi = 3.14159265358979323846;
+  const double x = v[q];
+  const double jb = jn(orders[o] + 1, 2.0 * pi * x);
+  gtab[i] = w[q] * pow(x, -11.0 / 3.0) * jb * jb / (pi * pi * x * x);
+}
+
+// G_n(f) on the octant 0 <= b <= a <= N/2 of integer frequency pairs, index a(a+1)/2 + b.
+__global__ void k_radial(const double* __restrict__ v, const double* __restrict__ gtab, int Q, int no, int N,
+                         double fscale, double* __restrict__ G, int noct) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= noct) return;
+  int a = (int)((sqrt(8.0 * i + 1.0) - 1.0) * 0.5);
+  while (a * (a + 1) / 2 > i) --a;
+  while ((a + 1) * (a + 2) / 2 <= i) ++a;
+  const int b = i - a * (a + 1) / 2;
+  const double f = sqrt((double)a * a + (double)b * b) * fscale;
+  double acc[kMaxOrders];
+#pragma unroll
+  for (int o = 0; o < kMaxOrders; ++o) acc[o] = 0.0;
+  if (f > 0.0) {
+    for (int q = 0; q < Q; ++q) {
+      const double x = v[q];
+      const double d = 2.0 * x + f;
+      const double K = exp((5.0 / 3.0) * log(2.0 * x / d)) * 2.0 * x * x / (f * d * d);
+      const double* g = gtab + (size_t)q * no;
+#pragma unroll
+      for (int o = 0; o < kMaxOrders; ++o)
+        if (o < no) acc[o] = fma(K, g[o], acc[o]);
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < kMaxOrders; ++o)
+    if (o < no) G[(size_t)o * noct + i] = acc[o];
+}
+
+struct ModeInfo {
+  int n, m, odd, o;  // radial order, azimuthal frequency, sin (odd Noll index), order slot
+};
+
+// P_j at half-plane bin (kx, ky) (kx in [0, N/2], ky in [0, N) FFT order).
+DFP2S_DEV double mode_power(const ModeInfo& mi, int kx, int ky, int N, const double* __restrict__ G, int noct) {
+  const int sky = ky < N / 2 ? ky : ky - N;
+  if (kx == 0 && sky == 0) return 0.0;
+  const int ay = sky < 0 ? -sky : sky;
+  const int a = kx > ay ? kx : ay, b = kx > ay ? ay : kx;
+  const double g = G[(size_t)mi.o * noct + a * (a + 1) / 2 + b];
+  double ang = 1.0;
+  if (mi.m != 0) {
+    const double phi = atan2((double)sky, (double)kx);
+    double s, c;
+    sincos(mi.m * phi, &s, &c);
+    ang = mi.odd ? 2.0 * s * s : 2.0 * c * c;
+  }
+  return (mi.n + 1) * ang * g;
+}
+
+__global__ void k_lambda_sums(const ModeInfo* __restrict__ modes, int J, int N, const double* __restrict__ G, int noct,
+                              double* __restrict__ sums) {
+  __shared__ double part[64];
+  for (int j = threadIdx.x; j < J; j += blockDim.x) part[j] = 0.0;
+  __syncthreads();
+  const int half = N / 2 + 1;
+  const size_t total = (size_t)half * N;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < total;
+  const int kx = live ? (int)(i / N) : 0, ky = live ? (int)(i - (size_t)kx * N) : 0;
+  const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+  for (int j = 0; j < J; ++j) {
+    double p = live ? wgt * mode_power(modes[j], kx, ky, N, G, noct) : 0.0;
+    for (int off = 16; off > 0; off >>= 1) p += __shfl_down_sync(0xffffffffu, p, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&part[j], p);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < J; j += blockDim.x) atomicAdd(&sums[j], part[j]);
+}
+
+__global__ void k_lambda_write(const ModeInfo* __restrict__ modes, int J, int N, const double* __restrict__ G, int noct,
+                               const double* __restrict__ sums, float* __restrict__ mult) {
+  const int half = N / 2 + 1;
+  const size_t total = (size_t)half * N;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int kx = (int)(i / N), ky = (int)(i - (size_t)kx * N);
+  for (int j = 0; j < J; ++j) {
+    const double p = mode_power(modes[j], kx, ky, N, G, noct);
+    mult[(size_t)j * total + i] = (float)(sqrt(p / sums[j]) / N);
+  }
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+void v_rule(std::vector<double>& v, std::vector<double>& w) {
+  std::vector<double> x8, w8, x16, w16;
+  gauss_legendre(8, x8, w8);
+  gauss_legendre(16, x16, w16);
+  const double y0 = log(1e-7), y1 = 0.0;
+  const int nlog = 65;
+  for (int p = 0; p < nlog; ++p) {
+    const double a = y0 + (y1 - y0) * p / nlog, b = y0 + (y1 - y0) * (p + 1) / nlog;
+    for (int i = 0; i < 8; ++i) {
+      const double y = 0.5 * (b - a) * x8[i] + 0.5 * (a + b);
+      const double vv = exp(y);
+      v.push_back(vv);
+      w.push_back(0.5 * (b - a) * w8[i] * vv);
+    }
+  }
+  for (int p = 0; p < 94; ++p) {
+    const double a = 1.0 + 0.5 * p, b = a + 0.5;
+    for (int i = 0; i < 16; ++i) {
+      v.push_back(0.5 * (b - a) * x16[i] + 0.5 * (a + b));
+      w.push_back(0.5 * (b - a) * w16[i]);
+    }
+  }
+}
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, n * sizeof(T)); }
+};
+
+}  // namespace
+
+int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st) {
+  const int J = f->J, N = f->N;
+  // ---- twiddles (FP64 -> FP32)
+  {
+    std::vector<float2> tw(N);
+    const double pi = 3.14159265358979323846;
+    for (int m = 0; m < N; ++m) {
+      const double a = -2.0 * pi * m / N;
+      tw[m] = make_float2((float)cos(a), (float)sin(a));
+    }
+    DFP2S_CUDA_TRY(cudaMemcpyAsync(f->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice, st));
+    DFP2S_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  // ---- modes and radial orders
+  std::vector<ModeInfo> modes(J);
+  std::vector<int> orders;
+  for (int j = 0; j < J; ++j) {
+    const int nj = j + 2;
+    int n = 0;
+    while ((n + 1) * (n + 2) / 2 < nj) ++n;
+    const int r = nj - n * (n + 1) / 2 - 1;
+    const int m = (n % 2 == 0) ? 2 * ((r + 1) / 2) : 2 * (r / 2) + 1;
+    int o = -1;
+    for (size_t k = 0; k < orders.size(); ++k)
+      if (orders[k] == n) o = (int)k;
+    if (o < 0) {
+      o = (int)orders.size();
+      orders.push_back(n);
+    }
+    modes[j] = ModeInfo{n, m, nj & 1, o};
+  }
+  if ((int)orders.size() > kMaxOrders) return dfp2s_fail(DFP2S_EINVAL, "too many radial orders");
+  std::vector<double> hv, hw;
+  v_rule(hv, hw);
+  const int Q = (int)hv.size();
+  const int no = (int)orders.size();
+  const int noct = (N / 2 + 1) * (N / 2 + 2) / 2;
+
+  DevBuf<double> dv, dw, gtab, G, sums;
+  DevBuf<int> dord, derr;
+  DevBuf<ModeInfo> dmodes;
+  DFP2S_CUDA_TRY(dv.alloc(Q));
+  DFP2S_CUDA_TRY(dw.alloc(Q));
+  DFP2S_CUDA_TRY(gtab.alloc((size_t)Q * no));
+  DFP2S_CUDA_TRY(G.alloc((size_t)no * noct));
+  DFP2S_CUDA_TRY(sums.alloc(J));
+  DFP2S_CUDA_TRY(dord.alloc(no));
+  DFP2S_CUDA_TRY(derr.alloc(1));
+  DFP2S_CUDA_TRY(dmodes.alloc(J));
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(dv.p, hv.data(), Q * sizeof(double), cudaMemcpyHostToDevice, st));
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(dw.p, hw.data(), Q * sizeof(double), cudaMemcpyHostToDevice, st));
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(dord.p, orders.data(), no * sizeof(int), cudaMemcpyHostToDevice, st));
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(dmodes.p, modes.data(), J * sizeof(ModeInfo), cudaMemcpyHostToDevice, st));
+  DFP2S_CUDA_TRY(cudaMemsetAsync(sums.p, 0, J * sizeof(double), st));
+  DFP2S_CUDA_TRY(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
+
+  k_noll_chol<<<1, 256, 0, st>>>(J, f->L64, f->L32, derr.p);
+  k_gtab<<<(Q * no + 255) / 256, 256, 0, st>>>(dv.p, dw.p, Q, dord.p, no, gtab.p);
+  k_radial<<<(noct + 127) / 128, 128, 0, st>>>(dv.p, gtab.p, Q, no, N, f->pix_per_D / N, G.p, noct);
+  const size_t total = (size_t)(N / 2 + 1) * N;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  k_lambda_sums<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p);
+  k_lambda_write<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p, f->mult);
+  DFP2S_CUDA_TRY(cudaGetLastError());
+  int herr = 0;
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DFP2S_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr) return dfp2s_fail(DFP2S_ECUDA, "Noll matrix is not positive definite on the device");
+  return DFP2S_OK;
+}

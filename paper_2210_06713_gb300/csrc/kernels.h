@@ -1,0 +1,52 @@
+// Internal launcher declarations shared by the translation units of libdfp2s.
+// Every launcher enqueues work on `st` and returns DFP2S_OK or DFP2S_ECUDA.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+// fields.cu -- Sec. III-C sampler passes
+int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
+                               uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
+                               cudaStream_t st);
+int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st);
+int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cudaStream_t st);
+
+// factor.cu -- FP64 spectral factor build
+struct dfp2s_factor_dev {
+  int J, N;
+  double pix_per_D;
+  float* mult;     // J x (N/2+1) x N, sqrt(lambda)/N^2
+  double* L64;     // J x J, D/r0 = 1
+  float* L32;      // J x J
+  float2* tw;      // N twiddles exp(-2 pi i m / N)
+  float2* scratch; // J x (N/2+1) x N spectrum
+};
+int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st);
+
+// warp.cu
+int dfp2s_launch_tilt_warp(const float* img, int C, int H, int W, const float* a2, const float* a3, float* out,
+                           cudaStream_t st);
+
+// p2s.cu -- exact P2S constants and kernel
+struct dfp2s_p2s_dev {
+  int J, K;
+  float* basis;   // K x 1089
+  float* phiT;    // 1089 x K (transposed basis)
+  float* zt;      // (J-2) x 1089 Zernike values of Noll 4..J+1 on the 33 x 33 pupil window
+  float* mask;    // 1089 aperture mask
+  float2* dft;    // 33 x 33, exp(-2 pi i (k-16)(i-16) / 64)
+  // surrogate network (optional)
+  int has_mlp;
+  float *W1, *b1, *W2, *b2, *W3, *b3, *in_scale, *out_scale, *out_shift;
+};
+int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
+int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
+                           cudaStream_t st);
+int dfp2s_launch_p2s_mlp(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
+                         cudaStream_t st);
+
+// blur.cu
+int dfp2s_launch_blur(const dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
+                      float* out, cudaStream_t st);

@@ -1,0 +1,197 @@
+"""GPU parity: every stage of the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: integer work (Philox words) and the FP32 Gaussians bit-exact; FP32
+stages rel-L2 <= 1e-5 (rel-L2 = ||x - y||_2 / ||y||_2 over the whole tensor, in
+FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from inputs import synthetic
+from oracle import image, mlp, noise, p2s, sampler, spectrum, zernike
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel_l2(x, y):
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_06713_gb300 as d
+    d.load()
+    return d
+
+
+def cu(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+# ------------------------------------------------------------------ noise
+@pytest.mark.parametrize("seed,sub,q0", [(0, 0, 0), (0x123456789ABCDEF, (3 << 40) | (77 << 8) | 5, 12345),
+                                         (2 ** 64 - 1, 2 ** 64 - 1, 2 ** 40)])
+def test_philox_words_bit_exact(lib, seed, sub, q0):
+    n = 4 * 4096
+    g = lib.philox_words(seed, sub, q0, n).cpu().numpy().view(np.uint32)
+    q = np.arange(q0, q0 + n // 4, dtype=np.uint64)
+    w = noise.philox_words(seed, sub, q)
+    assert np.array_equal(g, np.stack(w, axis=-1).ravel())
+
+
+@pytest.mark.parametrize("seed,tag,frame,mode", [(0, 0, 0, 0), (7, 0, 123456, 35), (2 ** 63 + 5, 3, 2 ** 32 - 1, 255)])
+def test_gaussians_bit_exact(lib, seed, tag, frame, mode):
+    g = lib.gaussian_noise(seed, tag, frame, mode, 256, 512).cpu().numpy()
+    o = noise.gaussian_block(seed, tag, frame, mode, 256, 512)
+    assert np.array_equal(g.view(np.uint32), o.view(np.uint32))
+
+
+# ----------------------------------------------------------------- factor
+@pytest.mark.parametrize("J,N,ppd", [(36, 128, 8.0), (15, 64, 2.0), (6, 16, 2.0), (36, 512, 8.0)])
+def test_spectral_factor_matches_oracle(lib, J, N, ppd):
+    f = lib.SpectralFactor(J, N, ppd)
+    m = f.multiplier().cpu().numpy().astype(np.float64)  # [j][kx][ky]
+    lam = spectrum.lambdas(J, N, ppd)  # [j][ky][kx]
+    ref = np.sqrt(lam[:, :, : N // 2 + 1]).transpose(0, 2, 1) / N ** 2
+    assert rel_l2(m, ref) < 1e-6
+    assert np.max(np.abs(m - ref)) <= 2e-6 * ref.max()
+    L = f.cholesky()
+    assert np.allclose(L, zernike.noll_cholesky(J, 1.0), rtol=1e-11, atol=1e-14)
+
+
+# ----------------------------------------------------------------- fields
+@pytest.mark.parametrize("J,H,W,N,ppd,d,seed,frame", [
+    (36, 64, 64, 128, 8.0, 2.0, 0, 0),      # small plain-method workload
+    (36, 50, 37, 128, 8.0, 3.0, 5, 9),      # ragged crop, odd height
+    (15, 16, 16, 64, 2.0, 1.0, 1, 1),       # J = 15
+    (36, 256, 256, 512, 8.0, 3.0, 0, 3),    # 256 x 256 workload
+])
+def test_fields_match_oracle(lib, J, H, W, N, ppd, d, seed, frame):
+    f = lib.SpectralFactor(J, N, ppd)
+    g = lib.sample_zernike_fields(f, d, seed, frame, H, W).cpu().numpy()
+    o = sampler.sample_fields(seed, frame, J, H, W, d, ppd, N)
+    assert rel_l2(g, o) < TOL
+    for j in (0, 1, J - 1):
+        assert rel_l2(g[j], o[j]) < 3 * TOL
+
+
+def test_fields_full_size_512(lib):
+    # the 512 x 512 benchmark workload (N = 1024), every sample against the oracle
+    J, H, W, N = 36, 512, 512, 1024
+    f = lib.SpectralFactor(J, N, 8.0)
+    g = lib.sample_zernike_fields(f, 4.0, 11, 2, H, W).cpu().numpy()
+    o = sampler.sample_fields(11, 2, J, H, W, 4.0, 8.0, N)
+    assert rel_l2(g, o) < TOL
+
+
+def test_fields_are_deterministic_and_frame_dependent(lib):
+    f = lib.SpectralFactor(36, 128, 8.0)
+    a = lib.sample_zernike_fields(f, 2.0, 3, 4, 64, 64).cpu()
+    b = lib.sample_zernike_fields(f, 2.0, 3, 4, 64, 64).cpu()
+    c = lib.sample_zernike_fields(f, 2.0, 3, 5, 64, 64).cpu()
+    assert torch.equal(a, b)
+    assert not torch.equal(a, c)
+    # D/r0 only scales the fields by (D/r0)^{5/6}
+    e = lib.sample_zernike_fields(f, 4.0, 3, 4, 64, 64).cpu()
+    assert torch.allclose(e, a * 2 ** (5 / 6), rtol=1e-5, atol=1e-6)
+
+
+# -------------------------------------------------------------------- warp
+@pytest.mark.parametrize("C,H,W", [(1, 64, 64), (3, 37, 53), (2, 5, 3), (3, 256, 256)])
+def test_tilt_warp_matches_oracle(lib, C, H, W):
+    img = synthetic.blobs(H, W, C, n=8, seed=C)
+    fld = synthetic.random_fields(2, H, W, scale=2.0, seed=H)
+    g = lib.tilt_warp(cu(img), cu(fld[0]), cu(fld[1])).cpu().numpy()
+    o = image.tilt_warp(img, fld[0], fld[1])
+    assert rel_l2(g, o) < TOL
+
+
+# --------------------------------------------------------------------- P2S
+@pytest.mark.parametrize("J,K,H,W,d", [(36, 16, 24, 20, 2.0), (36, 100, 9, 13, 4.0), (15, 32, 8, 8, 1.0)])
+def test_exact_weights_match_oracle(lib, J, K, H, W, d):
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=K).reshape(K, 33, 33)
+    a = sampler.sample_fields(3, 1, J, H, W, d, 8.0, sampler.grid_size(H, W))
+    P = lib.P2S(J, cu(basis))
+    g = lib.p2s_weights(P, lib.P2S_EXACT, cu(a)).cpu().numpy()
+    o = p2s.weights_field(a, basis)
+    assert rel_l2(g, o) < TOL
+    gb = lib.p2s_weights(P, lib.P2S_EXACT, cu(a), w_dtype=lib.W_BF16).float().cpu().numpy()
+    assert rel_l2(gb, o) < 4e-3  # bfloat16 storage
+
+
+def test_exact_weights_with_svd_basis(lib):
+    J, K = 36, 16
+    basis = p2s.build_basis(0, J, K, 400, [2.0])
+    a = sampler.sample_fields(0, 0, J, 16, 16, 2.0, 8.0, 128)
+    P = lib.P2S(J, cu(basis))
+    g = lib.p2s_weights(P, lib.P2S_EXACT, cu(a)).cpu().numpy()
+    assert rel_l2(g, p2s.weights_field(a, basis)) < TOL
+
+
+# -------------------------------------------------------------------- blur
+@pytest.mark.parametrize("C,H,W,K", [(1, 64, 64, 16), (3, 37, 45, 100), (5, 20, 33, 7)])
+def test_blur_fp32_matches_oracle(lib, C, H, W, K):
+    img = synthetic.blobs(H, W, C, n=6, seed=K)
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=C).reshape(K, 33, 33)
+    w = np.random.default_rng(H).standard_normal((H, W, K)).astype(np.float32)
+    P = lib.P2S(36, cu(basis))
+    g = lib.basis_blur(P, cu(img), cu(w)).cpu().numpy()
+    o = image.basis_blur(img, w, basis)
+    assert rel_l2(g, o) < TOL
+
+
+# ---------------------------------------------------------------- network
+def test_mlp_forward_matches_oracle(lib):
+    J, K, H, W = 36, 100, 16, 24
+    rng = np.random.default_rng(0)
+    params = {"W1": rng.standard_normal((256, J)) / 6, "b1": rng.standard_normal(256) * 0.1,
+              "W2": rng.standard_normal((256, 256)) / 16, "b2": rng.standard_normal(256) * 0.1,
+              "W3": rng.standard_normal((K, 256)) / 16, "b3": rng.standard_normal(K) * 0.1}
+    params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
+    in_scale = np.ones(J)
+    in_scale[:2] = 0
+    out_scale = rng.uniform(0.5, 2, K)
+    out_shift = rng.standard_normal(K)
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    P = lib.P2S(J, cu(basis))
+    P.set_mlp(*[cu(params[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")], cu(in_scale), cu(out_scale),
+              cu(out_shift))
+    a = synthetic.random_fields(J, H, W, scale=0.5, seed=3)
+    g = lib.p2s_weights(P, lib.P2S_LEARNED, cu(a)).cpu().numpy()
+    o = mlp.predict_weights(params, np.moveaxis(a, 0, -1), in_scale, out_scale, out_shift)
+    assert rel_l2(g, o) < TOL
+
+
+# ------------------------------------------------------------------- frame
+def test_simulate_frame_exact_small_workload(lib):
+    J, K, H, W, N, d = 36, 16, 64, 64, 128, 2.0
+    img = synthetic.smooth_noise(H, W, seed=0)
+    basis = p2s.build_basis(0, J, K, 2000, [d])
+    f = lib.SpectralFactor(J, N, 8.0)
+    P = lib.P2S(J, cu(basis))
+    sim = lib.Simulator(f, P, 1, H, W)
+    g = sim.simulate_frame(cu(img), d, 0, 0, lib.P2S_EXACT).cpu().numpy()
+    o = __import__("oracle.frame", fromlist=["x"]).simulate_frame(img, d, 0, 0, J, basis, 8.0, N)
+    assert rel_l2(g, o["out"]) < TOL
+
+
+def test_bad_arguments_return_einval(lib):
+    f = lib.SpectralFactor(6, 16, 2.0)
+    with pytest.raises(lib.DFP2SError) as e:
+        lib.sample_zernike_fields(f, 1.0, 0, 0, 17, 8)  # larger than the grid
+    assert e.value.code == -1
+    with pytest.raises(lib.DFP2SError):
+        lib.SpectralFactor(6, 100, 2.0)  # not a power of two
+    basis = torch.zeros(4, 33, 33, device="cuda")
+    P = lib.P2S(6, basis)
+    with pytest.raises(lib.DFP2SError):
+        lib.p2s_weights(P, lib.P2S_LEARNED, torch.zeros(6, 4, 4, device="cuda"))  # no network installed
