@@ -117,6 +117,28 @@ int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_byt
 int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
                                 int H, int W, float* fields_dev, void* stream);
 
+/* Same result as dfp2s_sample_zernike_fields, for callers that cannot
+ * allocate device memory while they draw frames (a fixed memory plan made at
+ * start-up, a plug-in whose host framework owns the device allocator, a
+ * latency-bound loop in which an allocation may synchronise the device or
+ * fail).  This call allocates nothing: the FFT scratch is a statically sized
+ * device array inside the library, DFP2S_NOALLOC_SCRATCH_BYTES (48 MiB) on
+ * every GPU that loads the library, held until the process exits.  The paper
+ * has no counterpart; this is a deployment variant of the same computation.
+ *   - Requires J (N/2+1) N * 8 <= DFP2S_NOALLOC_SCRATCH_BYTES (e.g. N = 512
+ *     with J <= 45, N = 256 with J <= 64); larger factors get DFP2S_EINVAL.
+ *   - The factor must live on the current device (DFP2S_EINVAL otherwise).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture begins.
+ *   - Every call on a device shares the one array, and it keeps the previous
+ *     call's contents (nothing in it needs clearing: each call writes all it
+ *     reads).  Calls whose work overlaps on the GPU (different streams, or
+ *     different host threads without ordering) race on the array: order them. */
+#define DFP2S_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+int dfp2s_sample_zernike_fields_noalloc(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                        int H, int W, float* fields_dev, void* stream);
+
 /* Debug/verification: the FP32 Gaussians of one (seed, tag, frame, mode) stream
  * as rows x cols (cols % 4 == 0), into out_dev.  The same values the field
  * sampler generates in registers (tag 0). */

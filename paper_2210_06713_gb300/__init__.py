@@ -44,6 +44,7 @@ SIGNATURES = {
     "dfp2s_factor_copy_cholesky": (_i, [_vp, _vp]),
     "dfp2s_factor_info": (_i, [_vp, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_sz)]),
     "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
     "dfp2s_p2s_create": (_i, [_i, _i, _vp, _c.POINTER(_vp)]),
@@ -172,6 +173,14 @@ def sample_zernike_fields(factor: SpectralFactor, D_over_r0: float, seed: int, f
         out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
     _check(load().dfp2s_sample_zernike_fields(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
                                               _stream(stream)))
+    return out
+
+
+def sample_zernike_fields_noalloc(factor: SpectralFactor, D_over_r0: float, seed: int, frame: int, H: int, W: int,
+                                  out: torch.Tensor, stream=None) -> torch.Tensor:
+    """sample_zernike_fields without any device allocation (static library scratch; see include/dfp2s.h)."""
+    _check(load().dfp2s_sample_zernike_fields_noalloc(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
+                                                      _stream(stream)))
     return out
 
 

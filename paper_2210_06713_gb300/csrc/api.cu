@@ -67,12 +67,6 @@ extern "C" int dfp2s_grid_size(int H, int W, double pix_per_D) {
 }
 
 // ------------------------------------------------------------ spectral factor
-struct dfp2s_factor {
-  dfp2s_factor_dev d;
-  int kind;
-  int device;
-};
-
 static void factor_free(dfp2s_factor* f) {
   if (!f) return;
   cudaFree(f->d.mult);

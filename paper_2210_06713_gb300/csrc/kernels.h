@@ -25,6 +25,13 @@ struct dfp2s_factor_dev {
 };
 int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st);
 
+// The opaque handle of include/dfp2s.h.
+struct dfp2s_factor {
+  dfp2s_factor_dev d;
+  int kind;
+  int device;  // device the factor's memory lives on
+};
+
 // warp.cu
 int dfp2s_launch_tilt_warp(const float* img, int C, int H, int W, const float* a2, const float* a3, float* out,
                            cudaStream_t st);
