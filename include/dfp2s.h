@@ -157,6 +157,10 @@ typedef struct dfp2s_p2s dfp2s_p2s;
  * (K x 33 x 33 float32, device).  Errors: EINVAL, ENOMEM. */
 int dfp2s_p2s_create(int J, int K, const float* basis_dev, dfp2s_p2s** out);
 int dfp2s_p2s_destroy(dfp2s_p2s* p);
+/* Reads (synchronously) and clears the handle's device error word: returns
+ * DFP2S_ETIMEOUT if a tensor-core kernel launched with this handle gave up on
+ * a bounded barrier wait (its output is then invalid), DFP2S_OK otherwise. */
+int dfp2s_p2s_check(dfp2s_p2s* p);
 
 /* Installs surrogate-network weights (all device float32, copied):
  * W1 256 x J, b1 256, W2 256 x 256, b2 256, W3 K x 256, b3 K; in_scale J

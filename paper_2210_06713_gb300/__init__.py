@@ -49,6 +49,7 @@ SIGNATURES = {
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
     "dfp2s_p2s_create": (_i, [_i, _i, _vp, _c.POINTER(_vp)]),
     "dfp2s_p2s_destroy": (_i, [_vp]),
+    "dfp2s_p2s_check": (_i, [_vp]),
     "dfp2s_p2s_set_mlp": (_i, [_vp] + [_vp] * 9),
     "dfp2s_p2s_weights": (_i, [_vp, _i, _vp, _i, _i, _vp, _i, _vp]),
     "dfp2s_tilt_warp": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
@@ -218,6 +219,10 @@ class P2S:
               for t in (W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift)]
         _check(load().dfp2s_p2s_set_mlp(self._h, *[_ptr(t) for t in ts]))
         self.has_mlp = True
+
+    def check(self):
+        """Raises DFP2SError(-4) if a tensor-core kernel of this handle gave up on a bounded wait."""
+        _check(load().dfp2s_p2s_check(self._h))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -170,8 +171,9 @@ struct dfp2s_p2s {
 
 static void p2s_free(dfp2s_p2s* p) {
   if (!p) return;
-  void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt, p->d.mask, p->d.dft, p->d.W1, p->d.b1, p->d.W2,
-                  p->d.b2, p->d.W3, p->d.b3, p->d.in_scale, p->d.out_scale, p->d.out_shift};
+  void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt,    p->d.mask, p->d.dft,       p->d.W1,        p->d.b1,
+                  p->d.W2,    p->d.b2,   p->d.W3,    p->d.b3,   p->d.in_scale, p->d.out_scale, p->d.out_shift,
+                  p->d.bt,    p->d.pad,  p->d.err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -205,6 +207,18 @@ extern "C" int dfp2s_p2s_create(int J, int K, const float* basis, dfp2s_p2s** ou
     return dfp2s_fail_cuda(cudaGetLastError(), "p2s tables");
   }
   *out = p;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_p2s_check(dfp2s_p2s* p) {
+  CHECK_ARG(p, "null handle");
+  if (!p->d.err) return DFP2S_OK;
+  int h = 0;
+  DFP2S_CUDA_TRY(cudaMemcpy(&h, p->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    cudaMemset(p->d.err, 0, sizeof(int));
+    return dfp2s_fail(DFP2S_ETIMEOUT, "a tensor-core kernel gave up waiting on a barrier (device error word %d)", h);
+  }
   return DFP2S_OK;
 }
 
@@ -286,6 +300,13 @@ extern "C" int dfp2s_basis_blur(const dfp2s_p2s* p, const float* img, int C, int
   CHECK_ARG(img != out, "out must not alias img");
   CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 * 4 && W <= (1 << 20), "bad image shape");
   CHECK_ARG(w_dtype == DFP2S_W_F32 || w_dtype == DFP2S_W_BF16, "unknown weight dtype");
+  if (w_dtype == DFP2S_W_BF16) {
+    const int rc = dfp2s_launch_blur_tc(const_cast<dfp2s_p2s_dev*>(&p->d), img, C, H, W,
+                                        static_cast<const __nv_bfloat16*>(w), out, as_stream(stream));
+    if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
+    if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur launch");
+    return DFP2S_OK;
+  }
   CHECK_LAUNCH(dfp2s_launch_blur(&p->d, img, C, H, W, w, w_dtype, out, as_stream(stream)));
   return DFP2S_OK;
 }

@@ -1,0 +1,267 @@
+// Basis blur on the tcgen05 tensor cores (BF16 operands, FP32 accumulation in
+// TMEM), Eq. (varying blur):
+//
+//   out_c(y, x) = sum_k w_k(y, x) conv_k,c(y, x),
+//   conv_k,c(y, x) = sum_{iy, ix} phi_k(iy, ix) I_c(y + 16 - iy, x + 16 - ix)   (clamp to edge)
+//
+// For one output row y and 128 consecutive pixels x0..x0+127, the 33 taps of
+// basis row iy form a dense contraction over kappa = 32 - ix:
+//
+//   D[p][k] += sum_kappa A_iy[p][kappa] B_iy[k][kappa],
+//   A_iy[p][kappa] = I_c(r, x0 - 16 + p + kappa), r = y + 16 - iy   (Hankel in p + kappa)
+//   B_iy[k][kappa] = phi_k(iy, 32 - kappa)                          (kappa padded to 48, k to NP)
+//
+// with M = 128 pixels, N = NP filters and K = 48 (three K = 16 MMAs) per basis
+// row, 99 MMAs per channel per tile.  A needs no im2col: a K-major core matrix
+// (8 rows x 16 bytes) of A at (row group i, K group g) is the 8 x 8 block
+// E_{i+g}[s][t] = I_c(r, x0 - 16 + 8(i+g) + s + t), so one staged image row
+// holds the 21 blocks E_0..E_20 back to back and the operand descriptor uses
+// the same 128-byte stride along M and along K.  B tiles for each iy are laid
+// out once per basis in global memory and streamed with 1-D bulk copies.
+// The epilogue reads D from TMEM (one pixel per thread) and contracts it with
+// the pixel's weights: out = sum_k w_k D[p][k].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "umma.cuh"
+
+namespace {
+
+constexpr int KS = 33;
+constexpr int TM = 128;                // pixels per tile (MMA M)
+constexpr int KP = 48;                 // taps of one basis row padded to three K = 16 steps
+constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
+constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
+constexpr int CMAX = 4;                // channels per pass (TMEM: CMAX * NP <= 512 columns)
+constexpr int THREADS = 128;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+struct Smem {
+  uint8_t A[2][CMAX][ROWB];       // double-buffered staged image rows
+  uint8_t B[2][KP / 8 * 16 * 128];  // double-buffered basis tiles (up to NP = 128)
+  uint64_t b_full[2];
+  uint64_t mma_done[2];
+  uint32_t tmem_base;
+  int abort;
+};
+
+// Replicate-padded BF16 copy of the image: P[c][r + 16][x + 16] = I[c][clamp(r)][clamp(x)].
+__global__ void k_pad_bf16(const float* __restrict__ img, int C, int H, int W, int Wp,
+                           __nv_bfloat16* __restrict__ P) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  const int c = blockIdx.z;
+  if (x >= Wp) return;
+  const int sy = min(max(r - 16, 0), H - 1);
+  const int sx = min(max(x - 16, 0), W - 1);
+  P[((size_t)c * (H + 32) + r) * Wp + x] = __float2bfloat16_rn(img[((size_t)c * H + sy) * W + sx]);
+}
+
+// B tiles: Bt[iy][j][g][n8][k8] = phi_{8j+n8}(iy, 32 - (8g+k8)), zero outside.
+__global__ void k_build_bt(const float* __restrict__ basis, int K, int NP, __nv_bfloat16* __restrict__ Bt) {
+  const int per_iy = NP * KP;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= KS * per_iy) return;
+  const int iy = i / per_iy;
+  int rem = i - iy * per_iy;
+  const int j = rem / (6 * 64);
+  rem -= j * 6 * 64;
+  const int g = rem / 64;
+  rem -= g * 64;
+  const int n8 = rem / 8, k8 = rem - n8 * 8;
+  const int k = 8 * j + n8, kap = 8 * g + k8;
+  float v = 0.f;
+  if (k < K && kap < KS) v = basis[((size_t)k * KS + iy) * KS + (KS - 1 - kap)];
+  Bt[i] = __float2bfloat16_rn(v);
+}
+
+DFP2S_DEV uint32_t shr16(uint32_t lo, uint32_t hi) { return __funnelshift_r(lo, hi, 16); }
+
+__global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __restrict__ P, int C, int H, int W,
+                                                        int Wp, const __nv_bfloat16* __restrict__ Bt, int K, int NP,
+                                                        const __nv_bfloat16* __restrict__ w, float* __restrict__ out,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const uint32_t bt_bytes = (uint32_t)(NP / 8) * 6 * 128;
+  const uint32_t idesc = umma::idesc_bf16(TM, NP);
+  const int nseg = (W + TM - 1) / TM;
+  const int ntiles = H * nseg;
+
+  if (tid == 0) {
+    umma::mbar_init(&s.b_full[0], 1);
+    umma::mbar_init(&s.b_full[1], 1);
+    umma::mbar_init(&s.mma_done[0], 1);
+    umma::mbar_init(&s.mma_done[1], 1);
+    s.abort = 0;
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(&s.tmem_base, 512);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = s.tmem_base;
+
+  uint32_t it = 0;  // staging iterations issued by this CTA (buffer = it & 1)
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int y = tile / nseg;
+    const int x0 = (tile - y * nseg) * TM;
+    for (int iy = 0; iy < KS; ++iy, ++it) {
+      const int buf = it & 1;
+      // buffer `buf` was last read by the MMAs of iteration it - 2
+      if (it >= 2) {
+        if (!umma::mbar_wait(&s.mma_done[buf], ((it - 2) >> 1) & 1, kWaitNs)) s.abort = 1;
+      }
+      __syncthreads();
+      if (s.abort) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        umma::mbar_arrive_expect_tx(&s.b_full[buf], bt_bytes);
+        umma::bulk_g2s(s.B[buf], Bt + (size_t)iy * (NP * KP), bt_bytes, &s.b_full[buf]);
+      }
+      // stage E_0..E_20 of image row r for every channel: item = (channel, block)
+      const int pr = y + 32 - iy;  // padded row of r = y + 16 - iy
+      for (int item = tid; item < C * NBLK; item += THREADS) {
+        const int c = item / NBLK;
+        const int b = item - c * NBLK;
+        const __nv_bfloat16* src = P + ((size_t)c * (H + 32) + pr) * Wp + x0 + 8 * b;
+        const uint4 v0 = *reinterpret_cast<const uint4*>(src);
+        const uint4 v1 = *reinterpret_cast<const uint4*>(src + 8);
+        const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint4* dst = reinterpret_cast<uint4*>(s.A[buf][c] + b * 128);
+#pragma unroll
+        for (int sh = 0; sh < 8; ++sh) {  // row s of the block: elements s .. s+7
+          const int w0 = sh >> 1;
+          uint4 o;
+          if ((sh & 1) == 0) {
+            o = make_uint4(wv[w0], wv[w0 + 1], wv[w0 + 2], wv[w0 + 3]);
+          } else {
+            o = make_uint4(shr16(wv[w0], wv[w0 + 1]), shr16(wv[w0 + 1], wv[w0 + 2]), shr16(wv[w0 + 2], wv[w0 + 3]),
+                           shr16(wv[w0 + 3], wv[w0 + 4]));
+          }
+          dst[sh] = o;
+        }
+      }
+      umma::fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        if (!umma::mbar_wait(&s.b_full[buf], (it >> 1) & 1, kWaitNs)) {
+          s.abort = 1;
+        } else {
+          umma::fence_after_sync();
+          const uint32_t a0 = umma::smem_u32(s.A[buf][0]);
+          const uint32_t b0 = umma::smem_u32(s.B[buf]);
+          for (int c = 0; c < C; ++c) {
+#pragma unroll
+            for (int ks = 0; ks < KP / 16; ++ks) {
+              const uint64_t ad = umma::sdesc(a0 + c * ROWB + ks * 256, 128, 128);
+              // B tile [j][g][8][8]: K-adjacent core matrices 128 B apart, 8-filter groups 768 B apart
+              const uint64_t bd = umma::sdesc(b0 + ks * 256, 128, 768);
+              umma::mma_bf16(tmem + c * NP, ad, bd, idesc, (iy | ks) != 0);
+            }
+          }
+          umma::mma_commit(&s.mma_done[buf]);
+        }
+      }
+    }
+    if (!ok) break;
+    // epilogue: all MMAs of this tile are done once the last commit has arrived
+    {
+      const uint32_t last = it - 1;
+      if (!umma::mbar_wait(&s.mma_done[last & 1], (last >> 1) & 1, kWaitNs)) s.abort = 1;
+    }
+    __syncthreads();
+    if (s.abort) {
+      ok = false;
+      break;
+    }
+    umma::fence_after_sync();
+    {
+      const int x = x0 + warp * 32 + lane;
+      const bool live = x < W;
+      const size_t pix = (size_t)y * W + (live ? x : 0);
+      const __nv_bfloat16* wp = w + pix * K;
+      for (int c = 0; c < C; ++c) {
+        float acc = 0.f;
+        for (int q = 0; q < NP / 16; ++q) {
+          float d[16];
+          umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * NP + q * 16, d);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int k = q * 16 + i;
+            if (k < K) acc = fmaf(__bfloat162float(wp[k]), d[i], acc);
+          }
+        }
+        if (live) out[((size_t)c * H + y) * W + x] = acc;
+      }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+  }
+  // drain: never leave MMAs or copies in flight on an abort path (bounded)
+  if (!ok && tid == 0) {
+    atomicExch(err, 1);
+    if (it >= 1) umma::mbar_wait(&s.mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1, kWaitNs);
+    if (it >= 1) umma::mbar_wait(&s.b_full[(it - 1) & 1], ((it - 1) >> 1) & 1, kWaitNs);
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const __nv_bfloat16* w, float* out,
+                         cudaStream_t st) {
+  const int K = p->K;
+  const int NP = (K + 15) / 16 * 16;
+  if (NP > 128) return DFP2S_EUNSUPPORTED;
+  // basis tiles (once per handle)
+  if (!p->bt) {
+    if (cudaMalloc((void**)&p->bt, (size_t)KS * NP * KP * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
+    const int n = KS * NP * KP;
+    k_build_bt<<<(n + 255) / 256, 256, 0, st>>>(p->basis, K, NP, p->bt);
+  }
+  if (!p->err) {
+    if (cudaMalloc((void**)&p->err, sizeof(int)) != cudaSuccess) return DFP2S_ENOMEM;
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+  }
+  const int nseg = (W + TM - 1) / TM;
+  const int Wp = nseg * TM + 64;
+  const size_t need = (size_t)C * (H + 32) * Wp;
+  if (need > p->pad_cap) {
+    if (p->pad) cudaFree(p->pad);
+    p->pad = nullptr;
+    p->pad_cap = 0;
+    if (cudaMalloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
+    p->pad_cap = need;
+  }
+  k_pad_bf16<<<dim3((Wp + 255) / 256, H + 32, C), 256, 0, st>>>(img, C, H, W, Wp, p->pad);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = H * nseg;
+  const int grid = ntiles < sms ? ntiles : sms;
+  // ask for more shared memory than one tile needs so only one CTA (and one
+  // 512-column TMEM allocation) lives on an SM
+  const size_t sm = 120 * 1024;
+  static_assert(sizeof(Smem) < 120 * 1024, "smem layout");
+  cudaFuncSetAttribute(k_blur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  for (int c0 = 0; c0 < C; c0 += CMAX) {
+    const int nc = C - c0 < CMAX ? C - c0 : CMAX;
+    k_blur_tc<<<grid, THREADS, sm, st>>>(p->pad + (size_t)c0 * (H + 32) * Wp, nc, H, W, Wp, p->bt, K, NP, w,
+                                         out + (size_t)c0 * H * W, p->err);
+  }
+  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+}

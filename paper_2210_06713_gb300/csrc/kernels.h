@@ -2,6 +2,7 @@
 // Every launcher enqueues work on `st` and returns DFP2S_OK or DFP2S_ECUDA.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -47,11 +48,20 @@ struct dfp2s_p2s_dev {
   // surrogate network (optional)
   int has_mlp;
   float *W1, *b1, *W2, *b2, *W3, *b3, *in_scale, *out_scale, *out_shift;
+  // tensor-core blur: basis tiles, padded BF16 image scratch, device error word
+  __nv_bfloat16* bt;
+  __nv_bfloat16* pad;
+  size_t pad_cap;
+  int* err;
 };
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
 int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
                            cudaStream_t st);
 int dfp2s_launch_p2s_mlp(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
+                         cudaStream_t st);
+
+// blur_tc.cu -- BF16 tcgen05 blur (weights in BF16)
+int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const __nv_bfloat16* w, float* out,
                          cudaStream_t st);
 
 // blur.cu

@@ -149,6 +149,27 @@ def test_blur_fp32_matches_oracle(lib, C, H, W, K):
     assert rel_l2(g, o) < TOL
 
 
+def _bf16(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("C,H,W,K", [(3, 64, 130, 100), (1, 33, 200, 16), (5, 20, 128, 112), (2, 17, 19, 128),
+                                     (3, 40, 256, 100)])
+def test_blur_bf16_tensor_cores_match_oracle_on_bf16_operands(lib, C, H, W, K):
+    # the tcgen05 blur rounds image and basis to bfloat16 and accumulates in FP32; against the oracle
+    # evaluated on the same bfloat16 operands it must agree to FP32 accumulation error
+    img = synthetic.blobs(H, W, C, n=6, seed=K)
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=C).reshape(K, 33, 33)
+    w = torch.as_tensor(np.random.default_rng(H).standard_normal((H, W, K)), dtype=torch.bfloat16, device="cuda")
+    P = lib.P2S(36, cu(basis))
+    g = lib.basis_blur(P, cu(img), w).cpu().numpy()
+    P.check()
+    o = image.basis_blur(_bf16(img), w.float().cpu().numpy(), _bf16(basis))
+    assert rel_l2(g, o) < TOL
+    # and stays within bfloat16 rounding of the FP32-operand result
+    assert rel_l2(g, image.basis_blur(img, w.float().cpu().numpy(), basis)) < 2e-2
+
+
 # ---------------------------------------------------------------- network
 def test_mlp_forward_matches_oracle(lib):
     J, K, H, W = 36, 100, 16, 24
