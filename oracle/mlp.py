@@ -39,13 +39,18 @@ def forward(params: dict, x: np.ndarray):
     return y, (x, z1, h1, z2, h2)
 
 
-def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray):
-    """Mean squared error over the B x K outputs and its gradient for every parameter."""
+def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray, lw: np.ndarray | None = None):
+    """Weighted squared error sum_k lw_k (y - t)^2 / (B K) over the B x K outputs and its gradient.
+
+    lw = None is the plain mean squared error; lw_k = var(w_k) / mean var makes the
+    loss the squared error of the PSF (the basis is orthonormal), reading R18.
+    """
     y, (x, z1, h1, z2, h2) = forward(params, x)
     B, K = y.shape
     r = y - np.asarray(t, dtype=np.float64)
-    loss = float(np.mean(r * r))
-    dy = 2.0 * r / (B * K)
+    wk = np.ones(K) if lw is None else np.asarray(lw, dtype=np.float64)
+    loss = float(np.sum(wk * r * r) / (B * K))
+    dy = 2.0 * wk * r / (B * K)
     g = {}
     g["W3"] = dy.T @ h2
     g["b3"] = dy.sum(axis=0)

@@ -134,22 +134,24 @@ def _params(J, Hd, K, seed=0):
             "W3": rng.standard_normal((K, Hd)) / math.sqrt(Hd), "b3": rng.standard_normal(K) * 0.1}
 
 
-def test_mlp_gradients_by_finite_differences():
+@pytest.mark.parametrize("weighted", [False, True])
+def test_mlp_gradients_by_finite_differences(weighted):
     J, Hd, K, B = 5, 7, 4, 6
     P = _params(J, Hd, K)
     rng = np.random.default_rng(1)
     x = rng.standard_normal((B, J))
     t = rng.standard_normal((B, K))
-    _, g = mlp.loss_and_grads(P, x, t)
+    lw = rng.uniform(0.1, 3.0, K) if weighted else None
+    _, g = mlp.loss_and_grads(P, x, t, lw)
     eps = 1e-6
     for name, val in P.items():
         flat = val.ravel()
         for i in range(0, flat.size, max(1, flat.size // 9)):
             old = flat[i]
             flat[i] = old + eps
-            lp, _ = mlp.loss_and_grads(P, x, t)
+            lp, _ = mlp.loss_and_grads(P, x, t, lw)
             flat[i] = old - eps
-            lm, _ = mlp.loss_and_grads(P, x, t)
+            lm, _ = mlp.loss_and_grads(P, x, t, lw)
             flat[i] = old
             assert g[name].ravel()[i] == pytest.approx((lp - lm) / (2 * eps), rel=1e-6, abs=1e-9)
 
