@@ -170,6 +170,41 @@ int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1, const floa
                       const float* W3, const float* b3, const float* in_scale, const float* out_scale,
                       const float* out_shift);
 
+/* Surrogate training on the device.  Draws n_pairs Zernike vectors
+ * a ~ N(0, A_0(D/r0)) (Philox tag 2, D/r0 cycling over D_over_r0[0..n_dr),
+ * tilt fields zeroed), computes their exact P2S weights with the same kernel as
+ * dfp2s_p2s_weights(EXACT), standardises inputs and targets, trains
+ * J -> 256 -> 256 -> K (GELU, erf form) with Adam on a one-cycle schedule
+ * (FP32; one step is a captured CUDA graph), and installs the network in `p`
+ * (as dfp2s_p2s_set_mlp would).  The last val_fraction of the pairs is held out:
+ * report_host[1] receives the relative L2 error of the network's weights on
+ * them, report_host[0] the final training loss, report_host[2] the steps run.
+ * params_out_host (optional) receives the flat FP32 parameters
+ * [W1 (256 x J), b1, W2 (256 x 256), b2, W3 (K x 256), b3] before the
+ * standardisation is folded in.  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct {
+  int n_pairs;            /* training + validation pairs, >= 1024 */
+  int n_dr;               /* 1..8 */
+  double D_over_r0[8];    /* turbulence strengths, pooled evenly */
+  uint64_t seed;          /* Philox key for the data, the batches and the initial weights */
+  int batch;              /* 64..8192 */
+  int steps;              /* Adam steps */
+  float lr;               /* peak learning rate */
+  int psf_weighted_loss;  /* 1: per-k loss weight = variance of w_k / mean variance (error of the PSF);
+                             0: plain MSE of the standardised weights */
+  float val_fraction;     /* 0 <= val_fraction < 0.5 */
+} dfp2s_mlp_train_params;
+int dfp2s_mlp_train(dfp2s_p2s* p, const dfp2s_factor* f, const dfp2s_mlp_train_params* tp, float* report_host,
+                    float* params_out_host, void* stream);
+/* Number of FP32 parameters of the J -> 256 -> 256 -> K network. */
+int dfp2s_mlp_param_count(int J, int K);
+/* One forward/backward pass on a given batch (for gradient checks): X (B x J)
+ * network inputs, T (B x K) targets, lw (K) loss weights, params flat as above;
+ * writes grads (flat, same layout) and loss = sum_k lw_k (y - t)^2 / (B K).
+ * All device pointers.  Synchronous. */
+int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params_dev, const float* X_dev, const float* T_dev,
+                        const float* lw_dev, float* grads_dev, float* loss_dev, void* stream);
+
 /* Sec. II-C: per-pixel basis weights from the fields (J x H x W, device).
  *   EXACT: PSF of Eq. (2) from modes Noll 4..J+1 on a 64 x 64 pupil grid
  *          (aperture 32 samples across, P = 1 inside), |DFT|^2, 33 x 33 centre,

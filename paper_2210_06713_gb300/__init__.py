@@ -34,6 +34,11 @@ class FactorParams(ctypes.Structure):
     _fields_ = [("J", _i), ("N", _i), ("pix_per_D", _d), ("kind", _i)]
 
 
+class TrainParams(ctypes.Structure):
+    _fields_ = [("n_pairs", _i), ("n_dr", _i), ("D_over_r0", _d * 8), ("seed", _u64), ("batch", _i), ("steps", _i),
+                ("lr", _c.c_float), ("psf_weighted_loss", _i), ("val_fraction", _c.c_float)]
+
+
 SIGNATURES = {
     "dfp2s_last_error": (_i, [_c.c_char_p, _sz]),
     "dfp2s_version": (_c.c_char_p, []),
@@ -51,6 +56,9 @@ SIGNATURES = {
     "dfp2s_p2s_destroy": (_i, [_vp]),
     "dfp2s_p2s_check": (_i, [_vp]),
     "dfp2s_p2s_set_mlp": (_i, [_vp] + [_vp] * 9),
+    "dfp2s_mlp_train": (_i, [_vp, _vp, _c.POINTER(TrainParams), _vp, _vp, _vp]),
+    "dfp2s_mlp_param_count": (_i, [_i, _i]),
+    "dfp2s_mlp_loss_grad": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dfp2s_p2s_weights": (_i, [_vp, _i, _vp, _i, _i, _vp, _i, _vp]),
     "dfp2s_tilt_warp": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dfp2s_basis_blur": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
@@ -234,6 +242,46 @@ class P2S:
             self.close()
         except Exception:
             pass
+
+
+def mlp_param_count(J: int, K: int) -> int:
+    n = load().dfp2s_mlp_param_count(J, K)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, T: torch.Tensor, lw: torch.Tensor):
+    """Loss and flat gradient of the surrogate on one batch (device FP32 tensors)."""
+    B, J = X.shape
+    K = T.shape[1]
+    grads = torch.empty_like(params)
+    loss = torch.zeros(1, device="cuda")
+    _check(load().dfp2s_mlp_loss_grad(J, K, B, _ptr(params), _ptr(X), _ptr(T), _ptr(lw), _ptr(grads), _ptr(loss),
+                                      _stream()))
+    return float(loss.item()), grads
+
+
+def mlp_train(p: P2S, factor: SpectralFactor, n_pairs: int = 1 << 20, D_over_r0=(1.0, 2.0, 4.0), seed: int = 0,
+              batch: int = 2048, steps: int = 20000, lr: float = 2e-3, psf_weighted_loss: bool = True,
+              val_fraction: float = 0.05, return_params: bool = False):
+    """Trains the surrogate on the device and installs it in `p`; returns a report dict."""
+    import numpy as np
+    tp = TrainParams()
+    tp.n_pairs, tp.n_dr = n_pairs, len(D_over_r0)
+    for i, dval in enumerate(D_over_r0):
+        tp.D_over_r0[i] = dval
+    tp.seed, tp.batch, tp.steps, tp.lr = seed, batch, steps, lr
+    tp.psf_weighted_loss, tp.val_fraction = int(psf_weighted_loss), val_fraction
+    rep = np.zeros(3, dtype=np.float32)
+    params = np.zeros(mlp_param_count(p.J, p.K), dtype=np.float32) if return_params else None
+    _check(load().dfp2s_mlp_train(p.handle, factor.handle, ctypes.byref(tp), rep.ctypes.data_as(ctypes.c_void_p),
+                                  params.ctypes.data_as(ctypes.c_void_p) if return_params else None, _stream()))
+    p.has_mlp = True
+    out = {"final_loss": float(rep[0]), "val_weight_rel_l2": float(rep[1]), "steps": int(rep[2])}
+    if return_params:
+        out["params"] = params
+    return out
 
 
 def p2s_weights(p: P2S, mode: int, fields: torch.Tensor, w_dtype: int = W_F32, out: torch.Tensor | None = None,

@@ -244,28 +244,65 @@ static cudaError_t copy_vec(float** dst, const float* src, int n) {
   return cudaMemcpy(*dst, src, n * sizeof(float), cudaMemcpyDefault);
 }
 
-extern "C" int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1, const float* W2, const float* b2,
-                                 const float* W3, const float* b3, const float* in_scale, const float* out_scale,
-                                 const float* out_shift) {
-  CHECK_ARG(p && W1 && b1 && W2 && b2 && W3 && b3 && in_scale && out_scale && out_shift, "null argument");
-  const int J = p->d.J, K = p->d.K;
-  float** olds[] = {&p->d.W1, &p->d.b1, &p->d.W2, &p->d.b2, &p->d.W3, &p->d.b3,
-                    &p->d.in_scale, &p->d.out_scale, &p->d.out_shift};
+int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* d, const float* W1, const float* b1, const float* W2, const float* b2,
+                          const float* W3, const float* b3, const float* in_scale, const float* out_scale,
+                          const float* out_shift) {
+  const int J = d->J, K = d->K;
+  float** olds[] = {&d->W1, &d->b1, &d->W2, &d->b2, &d->W3, &d->b3, &d->in_scale, &d->out_scale, &d->out_shift};
   for (float** o : olds)
     if (*o) {
       cudaFree(*o);
       *o = nullptr;
     }
-  p->d.has_mlp = 0;
+  d->has_mlp = 0;
   cudaError_t e;
-  if ((e = copy_transposed(&p->d.W1, W1, 256, J)) != cudaSuccess || (e = copy_vec(&p->d.b1, b1, 256)) != cudaSuccess ||
-      (e = copy_transposed(&p->d.W2, W2, 256, 256)) != cudaSuccess ||
-      (e = copy_vec(&p->d.b2, b2, 256)) != cudaSuccess || (e = copy_transposed(&p->d.W3, W3, K, 256)) != cudaSuccess ||
-      (e = copy_vec(&p->d.b3, b3, K)) != cudaSuccess || (e = copy_vec(&p->d.in_scale, in_scale, J)) != cudaSuccess ||
-      (e = copy_vec(&p->d.out_scale, out_scale, K)) != cudaSuccess ||
-      (e = copy_vec(&p->d.out_shift, out_shift, K)) != cudaSuccess)
+  if ((e = copy_transposed(&d->W1, W1, 256, J)) != cudaSuccess || (e = copy_vec(&d->b1, b1, 256)) != cudaSuccess ||
+      (e = copy_transposed(&d->W2, W2, 256, 256)) != cudaSuccess || (e = copy_vec(&d->b2, b2, 256)) != cudaSuccess ||
+      (e = copy_transposed(&d->W3, W3, K, 256)) != cudaSuccess || (e = copy_vec(&d->b3, b3, K)) != cudaSuccess ||
+      (e = copy_vec(&d->in_scale, in_scale, J)) != cudaSuccess ||
+      (e = copy_vec(&d->out_scale, out_scale, K)) != cudaSuccess ||
+      (e = copy_vec(&d->out_shift, out_shift, K)) != cudaSuccess)
     return dfp2s_fail_cuda(e, "mlp weights");
-  p->d.has_mlp = 1;
+  d->has_mlp = 1;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1, const float* W2, const float* b2,
+                                 const float* W3, const float* b3, const float* in_scale, const float* out_scale,
+                                 const float* out_shift) {
+  CHECK_ARG(p && W1 && b1 && W2 && b2 && W3 && b3 && in_scale && out_scale && out_shift, "null argument");
+  return dfp2s_p2s_install_mlp(&p->d, W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift);
+}
+
+extern "C" int dfp2s_mlp_param_count(int J, int K) {
+  CHECK_ARG(J >= 3 && J <= DFP2S_MAX_J && K >= 1 && K <= DFP2S_MAX_K, "J/K out of range");
+  return (int)dfp2s_mlp_nparams(J, K);
+}
+
+extern "C" int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params, const float* X, const float* T,
+                                   const float* lw, float* grads, float* loss, void* stream) {
+  CHECK_ARG(params && X && T && lw && grads, "null argument");
+  CHECK_ARG(J >= 3 && J <= DFP2S_MAX_J && K >= 1 && K <= DFP2S_MAX_K && B >= 1 && B <= (1 << 20), "bad shape");
+  const int rc = dfp2s_mlp_loss_grad_device(J, K, B, params, X, T, lw, grads, loss, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "mlp scratch allocation");
+  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "mlp loss/grad");
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_mlp_train(dfp2s_p2s* p, const dfp2s_factor* f, const dfp2s_mlp_train_params* tp, float* report,
+                               float* params_out_host, void* stream) {
+  CHECK_ARG(p && f && tp, "null argument");
+  CHECK_ARG(f->d.J == p->d.J, "factor J %d != p2s J %d", f->d.J, p->d.J);
+  CHECK_ARG(tp->n_pairs >= 1024 && tp->n_pairs <= (1 << 24), "n_pairs out of range");
+  CHECK_ARG(tp->n_dr >= 1 && tp->n_dr <= 8, "n_dr out of range");
+  for (int i = 0; i < tp->n_dr; ++i) CHECK_ARG(tp->D_over_r0[i] > 0 && tp->D_over_r0[i] < 1e3, "bad D/r0");
+  CHECK_ARG(tp->batch >= 64 && tp->batch <= 8192, "batch out of range");
+  CHECK_ARG(tp->steps >= 1 && tp->steps <= 10000000, "steps out of range");
+  CHECK_ARG(tp->lr > 0 && tp->lr < 1, "lr out of range");
+  CHECK_ARG(tp->val_fraction >= 0 && tp->val_fraction < 0.5, "val_fraction out of range");
+  const int rc = dfp2s_mlp_train_device(&p->d, f->d.L32, tp, report, params_out_host, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "training allocation");
+  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "mlp training");
   return DFP2S_OK;
 }
 

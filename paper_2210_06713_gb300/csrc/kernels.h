@@ -7,6 +7,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/dfp2s.h"
+
 // fields.cu -- Sec. III-C sampler passes
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
@@ -59,6 +61,20 @@ int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, i
                            cudaStream_t st);
 int dfp2s_launch_p2s_mlp(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
                          cudaStream_t st);
+
+// api.cu -- installs surrogate weights (device pointers, row-major W1 256 x J, W2 256 x 256, W3 K x 256)
+int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* p, const float* W1, const float* b1, const float* W2, const float* b2,
+                          const float* W3, const float* b3, const float* in_scale, const float* out_scale,
+                          const float* out_shift);
+
+// mlp_train.cu
+size_t dfp2s_mlp_nparams(int J, int K);
+int dfp2s_mlp_loss_grad_device(int J, int K, int B, const float* params, const float* X, const float* T,
+                               const float* lw, float* grads, float* loss, cudaStream_t st);
+int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_train_params* tp, float* report,
+                           float* params_out_host, cudaStream_t st);
+int dfp2s_launch_draw_vectors(int n, int J, const float* L, const float* drs, int nd, uint64_t seed, uint32_t tag,
+                              float* out, cudaStream_t st);
 
 // blur_tc.cu -- BF16 tcgen05 blur (weights in BF16)
 int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const __nv_bfloat16* w, float* out,

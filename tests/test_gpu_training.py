@@ -1,0 +1,77 @@
+"""The surrogate network's device training kernels against the FP64 oracle,
+and what the trained network gains over the method without it."""
+import numpy as np
+import pytest
+import torch
+
+from inputs import synthetic
+from oracle import image, mlp, p2s, sampler
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_06713_gb300 as d
+    d.load()
+    return d
+
+
+def _flat_to_dict(flat, J, K):
+    H = 256
+    sizes = [("W1", (H, J)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (K, H)), ("b3", (K,))]
+    out, o = {}, 0
+    for name, shp in sizes:
+        n = int(np.prod(shp))
+        out[name] = flat[o:o + n].reshape(shp).astype(np.float64)
+        o += n
+    assert o == flat.size
+    return out
+
+
+@pytest.mark.parametrize("J,K,B", [(36, 16, 64), (15, 100, 33)])
+def test_loss_and_gradients_match_oracle(lib, J, K, B):
+    n = lib.mlp_param_count(J, K)
+    rng = np.random.default_rng(J + K)
+    flat = (rng.standard_normal(n) * 0.1).astype(np.float32)
+    X = rng.standard_normal((B, J)).astype(np.float32)
+    T = rng.standard_normal((B, K)).astype(np.float32)
+    lw = rng.uniform(0.2, 2.0, K).astype(np.float32)
+    loss, g = lib.mlp_loss_grad(torch.tensor(flat, device="cuda"), torch.tensor(X, device="cuda"),
+                                torch.tensor(T, device="cuda"), torch.tensor(lw, device="cuda"))
+    P = _flat_to_dict(flat, J, K)
+    lo, go = mlp.loss_and_grads(P, X, T, lw)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    gd = _flat_to_dict(g.cpu().numpy(), J, K)
+    for name in P:
+        ref = go[name]
+        err = np.linalg.norm(gd[name] - ref) / np.linalg.norm(ref)
+        assert err < 1e-4, (name, err)
+
+
+def test_training_learns_and_beats_mean_weights(lib):
+    # a short training run: the network must explain most of the weight variation and
+    # its frame must be much closer to the exact-P2S frame than the spatially invariant
+    # blur with the mean weights (the method without a per-pixel P2S)
+    J, K, H, W, N, d = 36, 16, 64, 64, 128, 2.0
+    basis = p2s.build_basis(0, J, K, 600, [d])
+    f = lib.SpectralFactor(J, N, 8.0)
+    P = lib.P2S(J, torch.as_tensor(basis, dtype=torch.float32, device="cuda"))
+    rep = lib.mlp_train(P, f, n_pairs=1 << 16, D_over_r0=(d,), seed=3, batch=1024, steps=3000, lr=2e-3)
+    assert rep["steps"] == 3000
+    assert rep["val_weight_rel_l2"] < 0.05
+    img = torch.as_tensor(synthetic.shapes(H, W, 3, seed=1), device="cuda")
+    sim = lib.Simulator(f, P, 3, H, W)
+    ex = sim.simulate_frame(img, d, 9, 0, lib.P2S_EXACT).double()
+    le = sim.simulate_frame(img, d, 9, 0, lib.P2S_LEARNED).double()
+    P.check()
+    fields = lib.sample_zernike_fields(f, d, 9, 0, H, W)
+    w_ex = lib.p2s_weights(P, lib.P2S_EXACT, fields)
+    w_mean = w_ex.reshape(-1, K).mean(0).expand(H * W, K).reshape(H, W, K).contiguous()
+    warped = lib.tilt_warp(img, fields[0].contiguous(), fields[1].contiguous())
+    mean_frame = lib.basis_blur(P, warped, w_mean).double()
+    e_learned = float((le - ex).norm() / ex.norm())
+    e_mean = float((mean_frame - ex).norm() / ex.norm())
+    assert e_learned < 0.5 * e_mean, (e_learned, e_mean)
