@@ -71,6 +71,10 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # nvidia-smi's start-up briefly stalls the device: wait for its first sample
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
 
@@ -102,7 +106,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def setup_ours(workload: str, mode: str, device):
+def setup_ours(workload: str, mode: str, device, train_steps: int = 20000):
+    """Untimed setup: spectral factor, SVD basis of 2000 exact PSFs and (learned mode) the trained surrogate,
+    all built on the device."""
     import torch
     import paper_2210_06713_gb300 as d
     from inputs import synthetic
@@ -110,29 +116,45 @@ def setup_ours(workload: str, mode: str, device):
     H, W, C, kind, K, dlist, _ = WORKLOADS[workload]
     N = d.grid_size(H, W, PIX_PER_D)
     img = torch.as_tensor(synthetic.image_for(kind, H, W, C, seed=0), device=device).contiguous()
+    t0 = time.perf_counter()
     factor = d.SpectralFactor(J, N, PIX_PER_D)
-    basis_np = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
-    P = d.P2S(J, torch.as_tensor(basis_np, dtype=torch.float32, device=device))
-    rng = np.random.default_rng(0)
-    in_scale = np.ones(J, dtype=np.float32)
-    in_scale[:2] = 0
-    P.set_mlp(rng.standard_normal((256, J)) / 6, np.zeros(256), rng.standard_normal((256, 256)) / 16,
-              np.zeros(256), rng.standard_normal((K, 256)) / 16, np.zeros(K), in_scale,
-              np.full(K, 0.01), np.zeros(K))
+    t_factor = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    basis, sig, sweeps = d.build_basis(factor, K, 2000, tuple(dlist), seed=0)
+    t_basis = time.perf_counter() - t0
+    P = d.P2S(J, basis)
+    info = {"factor_s": t_factor, "basis_s": t_basis, "basis_sweeps": sweeps}
+    if mode == "learned":
+        t0 = time.perf_counter()
+        rep = d.mlp_train(P, factor, n_pairs=1 << 20, D_over_r0=tuple(dlist), seed=1, batch=2048,
+                          steps=train_steps, lr=2e-3)
+        info.update({"train_s": time.perf_counter() - t0, "train_steps": rep["steps"],
+                     "val_weight_rel_l2": rep["val_weight_rel_l2"]})
     sim = d.Simulator(factor, P, C, H, W)
-    return d, dict(H=H, W=W, C=C, K=K, N=N, dlist=dlist, img=img, factor=factor, P=P, sim=sim)
+    return d, dict(H=H, W=W, C=C, K=K, N=N, dlist=dlist, img=img, factor=factor, P=P, sim=sim, info=info)
+
+
+def accuracy_vs_exact(d, S, seed):
+    """rel-L2 of the learned frame against the exact-P2S FP32 frame, one frame per D/r0."""
+    out = {}
+    for dr in S["dlist"]:
+        ex = S["sim"].simulate_frame(S["img"], dr, seed, 0, d.P2S_EXACT).double()
+        le = S["sim"].simulate_frame(S["img"], dr, seed, 0, d.P2S_LEARNED).double()
+        out[str(dr)] = float((le - ex).norm() / ex.norm())
+    S["P"].check()
+    return out
 
 
 def run_ours(args, rank, world, device):
     import torch
-    d, S = setup_ours(args.workload, args.mode, device)
+    d, S = setup_ours(args.workload, args.mode, device, args.train_steps)
     H, W, C, K = S["H"], S["W"], S["C"], S["K"]
     mode = d.P2S_LEARNED if args.mode == "learned" else d.P2S_EXACT
-    wdt = d.W_BF16 if mode == d.P2S_LEARNED else d.W_F32
+    wdt = d.W_F32
     stream = torch.cuda.current_stream()
     fields = torch.empty(J, H, W, device=device)
     warped = torch.empty(C, H, W, device=device)
-    w = torch.empty(H, W, K, device=device, dtype=torch.bfloat16 if wdt == d.W_BF16 else torch.float32)
+    w = torch.empty(H, W, K, device=device, dtype=torch.float32)
     out = torch.empty(C, H, W, device=device)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
     nstage = 4
@@ -151,7 +173,10 @@ def run_ours(args, rank, world, device):
         d.p2s_weights(S["P"], mode, fields, w_dtype=wdt, out=w)
         if ev is not None:
             ev[3].record(stream)
-        d.basis_blur(S["P"], warped, w, out=out)
+        if mode == d.P2S_LEARNED:
+            d.basis_blur_tc(S["P"], warped, w, out=out)
+        else:
+            d.basis_blur(S["P"], warped, w, out=out)
         if ev is not None:
             ev[4].record(stream)
 
@@ -205,12 +230,19 @@ def run_ours(args, rank, world, device):
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
     names = ["fields", "warp", "p2s_" + args.mode, "blur"]
+    acc = None
+    if args.mode == "learned" and not args.no_accuracy:
+        acc = accuracy_vs_exact(d, S, seed_base + 77)
     mean_stage = stage_ms.mean(axis=0)
     peaks, peak_kind = _peaks()
     # dominant kernel roofline
     dom = int(np.argmax(mean_stage))
     npix = H * W
-    if names[dom] == "blur":
+    if names[dom] == "blur" and args.mode == "learned":
+        flops = 2.0 * 1089 * K * C * npix  # Eq. (varying blur) as a dense contraction on the tensor cores
+        roof = {"kernel": "k_blur_tc", "bound": "tensor", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None, "peak_source": peak_kind}
+    elif names[dom] == "blur":
         flops = 2.0 * 1089 * (K + C) * npix  # per-pixel PSF form on FP32 CUDA cores
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -244,10 +276,12 @@ def run_ours(args, rank, world, device):
                    "K": K, "N": S["N"], "l2": "flushed between timed frames (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)},
+        "rel_l2_learned_vs_exact": acc,
         "roofline": roof,
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
-        "gpu_launches": args.steps * 7,
+        "gpu_launches": args.steps * (8 if args.mode == "learned" else 7),
+        "setup": S["info"],
         "clocks": clk,
         "wall_s": wall,
     }
@@ -313,6 +347,8 @@ def main():
     ap.add_argument("--mode", default="learned", choices=["learned", "exact"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

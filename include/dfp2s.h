@@ -162,6 +162,18 @@ int dfp2s_p2s_destroy(dfp2s_p2s* p);
  * a bounded barrier wait (its output is then invalid), DFP2S_OK otherwise. */
 int dfp2s_p2s_check(dfp2s_p2s* p);
 
+/* Sec. II-C (PSF database -> basis; reading: uncentred SVD): draws n_psf
+ * Zernike vectors a ~ N(0, A_0(D/r0)) with Philox tag 1 (D/r0 =
+ * D_over_r0[i % n_dr] for draw i, tilts zeroed), forms their exact 33 x 33 PSFs
+ * and writes the top-K right singular vectors of the n_psf x 1089 PSF matrix
+ * (FP64 one-sided Jacobi on the device) to basis_dev (K x 33 x 33 float32),
+ * each signed so that its largest-magnitude entry is positive.  sigma_host
+ * (optional, 1089 doubles) receives all singular values in descending order;
+ * sweeps_host (optional) the Jacobi sweeps used.  Synchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int dfp2s_build_basis(const dfp2s_factor* f, int K, int n_psf, const double* D_over_r0, int n_dr, uint64_t seed,
+                      float* basis_dev, double* sigma_host, int* sweeps_host, void* stream);
+
 /* Installs surrogate-network weights (all device float32, copied):
  * W1 256 x J, b1 256, W2 256 x 256, b2 256, W3 K x 256, b3 K; in_scale J
  * (multiplies the Zernike vector before the first layer; 0 on the tilt
@@ -225,9 +237,18 @@ int dfp2s_tilt_warp(const float* img_dev, int C, int H, int W, const float* a2_d
 /* Eq. (varying blur): out_c(x) = sum_k w_k(x) sum_u phi_k(u) img_c(x - u),
  * u in [-16, 16]^2, clamp-to-edge borders.  w_dtype F32: FP32 arithmetic;
  * BF16: image and basis rounded to bfloat16, tensor-core products with FP32
- * accumulation.  Errors: EINVAL, ECUDA. */
+ * accumulation (dfp2s_basis_blur_tc).  Errors: EINVAL, ECUDA. */
 int dfp2s_basis_blur(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W, const void* w_dev,
                      int w_dtype, float* out_dev, void* stream);
+
+/* Eq. (varying blur) on the tcgen05 tensor cores: the image enters as
+ * bfloat16(I - 0.5) (the constant 0.5 * sum_u phi_k(u) is added back in FP32),
+ * the basis as bfloat16, products accumulate in FP32 in tensor memory, and the
+ * weights (FP32 or BF16 as stored) are applied in FP32.  Requires K <= 128.
+ * Errors: EINVAL, EUNSUPPORTED, ENOMEM (scratch), ECUDA.  A device-side barrier
+ * timeout is reported by dfp2s_p2s_check. */
+int dfp2s_basis_blur_tc(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W, const void* w_dev,
+                        int w_dtype, float* out_dev, void* stream);
 
 /* ---------------------------------------------------------------- frames
  * A context binds a factor and a P2S handle and owns the per-frame scratch
@@ -238,8 +259,9 @@ int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int max_C, int m
 int dfp2s_ctx_destroy(dfp2s_ctx* c);
 
 /* Fig. dfp2s: one frame.  fields (Sec. III-C) -> tilt warp -> P2S weights
- * (p2s_mode EXACT -> FP32 weights and FP32 blur; LEARNED -> BF16 weights and
- * the BF16 tensor-core blur) -> out (C x H x W, device).
+ * (FP32) -> blur (p2s_mode EXACT: FP32 CUDA-core blur; LEARNED: the network's
+ * weights and the BF16 tensor-core blur, dfp2s_basis_blur_tc) -> out
+ * (C x H x W, device).
  * Errors: EINVAL, ECUDA. */
 int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img_dev, int C, int H, int W, double D_over_r0,
                          uint64_t seed, uint32_t frame, int p2s_mode, float* out_dev, void* stream);

@@ -52,6 +52,7 @@ SIGNATURES = {
     "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
+    "dfp2s_build_basis": (_i, [_vp, _i, _i, _vp, _i, _u64, _vp, _vp, _vp, _vp]),
     "dfp2s_p2s_create": (_i, [_i, _i, _vp, _c.POINTER(_vp)]),
     "dfp2s_p2s_destroy": (_i, [_vp]),
     "dfp2s_p2s_check": (_i, [_vp]),
@@ -62,6 +63,7 @@ SIGNATURES = {
     "dfp2s_p2s_weights": (_i, [_vp, _i, _vp, _i, _i, _vp, _i, _vp]),
     "dfp2s_tilt_warp": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dfp2s_basis_blur": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
+    "dfp2s_basis_blur_tc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_ctx_create": (_i, [_vp, _vp, _i, _i, _i, _c.POINTER(_vp)]),
     "dfp2s_ctx_destroy": (_i, [_vp]),
     "dfp2s_simulate_frame": (_i, [_vp, _vp, _i, _i, _i, _d, _u64, _u32, _i, _vp, _vp]),
@@ -205,6 +207,18 @@ def philox_words(seed: int, sub: int, q0: int, n: int) -> torch.Tensor:
     return out
 
 
+def build_basis(factor: SpectralFactor, K: int, n_psf: int = 2000, D_over_r0=(2.0,), seed: int = 0):
+    """Top-K SVD basis of n_psf exact PSFs (device FP64); returns (basis K x 33 x 33, singular values, sweeps)."""
+    import numpy as np
+    basis = torch.empty(K, KS, KS, dtype=torch.float32, device="cuda")
+    dr = np.asarray(D_over_r0, dtype=np.float64)
+    sig = np.zeros(KS * KS, dtype=np.float64)
+    sweeps = ctypes.c_int(0)
+    _check(load().dfp2s_build_basis(factor.handle, K, n_psf, dr.ctypes.data_as(ctypes.c_void_p), len(dr), seed,
+                                    _ptr(basis), sig.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sweeps), _stream()))
+    return basis, sig, sweeps.value
+
+
 # --------------------------------------------------------------------- P2S
 class P2S:
     """PSF basis (K x 33 x 33) and optional surrogate network."""
@@ -309,6 +323,17 @@ def basis_blur(p: P2S, img: torch.Tensor, w: torch.Tensor, out: torch.Tensor | N
         out = torch.empty_like(img)
     wdt = W_BF16 if w.dtype == torch.bfloat16 else W_F32
     _check(load().dfp2s_basis_blur(p.handle, _ptr(img), C, H, W, _ptr(w), wdt, _ptr(out), _stream(stream)))
+    return out
+
+
+def basis_blur_tc(p: P2S, img: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Tensor-core (BF16 operands, FP32 accumulation) blur with FP32 or BF16 weights."""
+    C, H, W = img.shape
+    if out is None:
+        out = torch.empty_like(img)
+    wdt = W_BF16 if w.dtype == torch.bfloat16 else W_F32
+    _check(load().dfp2s_basis_blur_tc(p.handle, _ptr(img), C, H, W, _ptr(w), wdt, _ptr(out), _stream(stream)))
     return out
 
 

@@ -164,6 +164,20 @@ extern "C" int dfp2s_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int 
   return DFP2S_OK;
 }
 
+extern "C" int dfp2s_build_basis(const dfp2s_factor* f, int K, int n_psf, const double* dr, int n_dr, uint64_t seed,
+                                 float* basis, double* sigma_host, int* sweeps_host, void* stream) {
+  CHECK_ARG(f && dr && basis, "null argument");
+  CHECK_ARG(K >= 1 && K <= DFP2S_MAX_K, "K = %d out of range", K);
+  CHECK_ARG(n_psf >= K && n_psf <= (1 << 16), "n_psf = %d out of range", n_psf);
+  CHECK_ARG(n_dr >= 1 && n_dr <= 8, "n_dr out of range");
+  for (int i = 0; i < n_dr; ++i) CHECK_ARG(dr[i] > 0 && dr[i] < 1e3, "bad D/r0");
+  const int rc = dfp2s_basis_build_device(f->d.J, f->d.L32, K, n_psf, dr, n_dr, seed, basis, sigma_host, sweeps_host,
+                                          as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "basis allocation");
+  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "basis build");
+  return DFP2S_OK;
+}
+
 // ---------------------------------------------------------------------- P2S
 struct dfp2s_p2s {
   dfp2s_p2s_dev d;
@@ -173,7 +187,7 @@ static void p2s_free(dfp2s_p2s* p) {
   if (!p) return;
   void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt,    p->d.mask, p->d.dft,       p->d.W1,        p->d.b1,
                   p->d.W2,    p->d.b2,   p->d.W3,    p->d.b3,   p->d.in_scale, p->d.out_scale, p->d.out_shift,
-                  p->d.bt,    p->d.pad,  p->d.err};
+                  p->d.bt,    p->d.pad,  p->d.err,   p->d.bsum};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -337,14 +351,22 @@ extern "C" int dfp2s_basis_blur(const dfp2s_p2s* p, const float* img, int C, int
   CHECK_ARG(img != out, "out must not alias img");
   CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 * 4 && W <= (1 << 20), "bad image shape");
   CHECK_ARG(w_dtype == DFP2S_W_F32 || w_dtype == DFP2S_W_BF16, "unknown weight dtype");
-  if (w_dtype == DFP2S_W_BF16) {
-    const int rc = dfp2s_launch_blur_tc(const_cast<dfp2s_p2s_dev*>(&p->d), img, C, H, W,
-                                        static_cast<const __nv_bfloat16*>(w), out, as_stream(stream));
-    if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
-    if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur launch");
-    return DFP2S_OK;
-  }
+  if (w_dtype == DFP2S_W_BF16) return dfp2s_basis_blur_tc(p, img, C, H, W, w, w_dtype, out, stream);
   CHECK_LAUNCH(dfp2s_launch_blur(&p->d, img, C, H, W, w, w_dtype, out, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_basis_blur_tc(const dfp2s_p2s* p, const float* img, int C, int H, int W, const void* w,
+                                   int w_dtype, float* out, void* stream) {
+  CHECK_ARG(p && img && w && out, "null argument");
+  CHECK_ARG(img != out, "out must not alias img");
+  CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 - 32 && W <= (1 << 20), "bad image shape");
+  CHECK_ARG(w_dtype == DFP2S_W_F32 || w_dtype == DFP2S_W_BF16, "unknown weight dtype");
+  const int rc = dfp2s_launch_blur_tc(const_cast<dfp2s_p2s_dev*>(&p->d), img, C, H, W, w, w_dtype, out,
+                                      as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
+  if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur launch");
   return DFP2S_OK;
 }
 
@@ -418,8 +440,8 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
   const size_t npix = (size_t)H * W;
   rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
   if (rc) return rc;
-  const int wdt = p2s_mode == DFP2S_P2S_EXACT ? DFP2S_W_F32 : DFP2S_W_BF16;
-  rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, wdt, stream);
+  rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, DFP2S_W_F32, stream);
   if (rc) return rc;
-  return dfp2s_basis_blur(c->p, c->warped, C, H, W, c->w, wdt, out, stream);
+  if (p2s_mode == DFP2S_P2S_EXACT) return dfp2s_basis_blur(c->p, c->warped, C, H, W, c->w, DFP2S_W_F32, out, stream);
+  return dfp2s_basis_blur_tc(c->p, c->warped, C, H, W, c->w, DFP2S_W_F32, out, stream);
 }

@@ -19,7 +19,12 @@
 // the same 128-byte stride along M and along K.  B tiles for each iy are laid
 // out once per basis in global memory and streamed with 1-D bulk copies.
 // The epilogue reads D from TMEM (one pixel per thread) and contracts it with
-// the pixel's weights: out = sum_k w_k D[p][k].
+// the pixel's weights: out = sum_k w_k (D[p][k] + c s_k).
+//
+// Precision: the image enters as bfloat16(I - c) with c = 0.5 (centring halves
+// the magnitudes of [0, 1] images and so the rounding error), and the exact
+// term c s_k, s_k = sum_u bf16(phi_k(u)), is added back in FP32; the weights
+// are read in FP32 or BF16 as stored.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,7 +54,7 @@ struct Smem {
 };
 
 // Replicate-padded BF16 copy of the image: P[c][r + 16][x + 16] = I[c][clamp(r)][clamp(x)].
-__global__ void k_pad_bf16(const float* __restrict__ img, int C, int H, int W, int Wp,
+__global__ void k_pad_bf16(const float* __restrict__ img, int C, int H, int W, int Wp, float centre,
                            __nv_bfloat16* __restrict__ P) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
@@ -57,7 +62,7 @@ __global__ void k_pad_bf16(const float* __restrict__ img, int C, int H, int W, i
   if (x >= Wp) return;
   const int sy = min(max(r - 16, 0), H - 1);
   const int sx = min(max(x - 16, 0), W - 1);
-  P[((size_t)c * (H + 32) + r) * Wp + x] = __float2bfloat16_rn(img[((size_t)c * H + sy) * W + sx]);
+  P[((size_t)c * (H + 32) + r) * Wp + x] = __float2bfloat16_rn(img[((size_t)c * H + sy) * W + sx] - centre);
 }
 
 // B tiles: Bt[iy][j][g][n8][k8] = phi_{8j+n8}(iy, 32 - (8g+k8)), zero outside.
@@ -78,12 +83,42 @@ __global__ void k_build_bt(const float* __restrict__ basis, int K, int NP, __nv_
   Bt[i] = __float2bfloat16_rn(v);
 }
 
+// s_k = sum over the 33 x 33 taps of the bfloat16-rounded basis function k (zero for k >= K)
+__global__ void k_basis_sums(const float* __restrict__ basis, int K, int NP, float* __restrict__ sums) {
+  __shared__ float red[8];
+  const int k = blockIdx.x;
+  float t = 0.f;
+  if (k < K)
+    for (int i = threadIdx.x; i < KS * KS; i += blockDim.x)
+      t += __bfloat162float(__float2bfloat16_rn(basis[(size_t)k * KS * KS + i]));
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
+    sums[k] = a;
+  }
+}
+
+template <typename WT>
+DFP2S_DEV float wload(const WT* p);
+template <>
+DFP2S_DEV float wload<float>(const float* p) { return __ldg(p); }
+template <>
+DFP2S_DEV float wload<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+__global__ void k_scale(float* __restrict__ v, int n, float a) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] *= a;
+}
+
 DFP2S_DEV uint32_t shr16(uint32_t lo, uint32_t hi) { return __funnelshift_r(lo, hi, 16); }
 
+template <typename WT>
 __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __restrict__ P, int C, int H, int W,
                                                         int Wp, const __nv_bfloat16* __restrict__ Bt, int K, int NP,
-                                                        const __nv_bfloat16* __restrict__ w, float* __restrict__ out,
-                                                        int* __restrict__ err) {
+                                                        const float* __restrict__ csum, const WT* __restrict__ w,
+                                                        float* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
@@ -191,7 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
       const int x = x0 + warp * 32 + lane;
       const bool live = x < W;
       const size_t pix = (size_t)y * W + (live ? x : 0);
-      const __nv_bfloat16* wp = w + pix * K;
+      const WT* wp = w + pix * K;
       for (int c = 0; c < C; ++c) {
         float acc = 0.f;
         for (int q = 0; q < NP / 16; ++q) {
@@ -200,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int k = q * 16 + i;
-            if (k < K) acc = fmaf(__bfloat162float(wp[k]), d[i], acc);
+            if (k < K) acc = fmaf(wload<WT>(wp + k), d[i] + csum[k], acc);
           }
         }
         if (live) out[((size_t)c * H + y) * W + x] = acc;
@@ -222,16 +257,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
 
 }  // namespace
 
-int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const __nv_bfloat16* w, float* out,
-                         cudaStream_t st) {
+int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
+                         float* out, cudaStream_t st) {
   const int K = p->K;
   const int NP = (K + 15) / 16 * 16;
+  const float centre = 0.5f;
   if (NP > 128) return DFP2S_EUNSUPPORTED;
-  // basis tiles (once per handle)
+  // basis tiles and centring sums c * s_k (once per handle)
   if (!p->bt) {
     if (cudaMalloc((void**)&p->bt, (size_t)KS * NP * KP * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
+    if (cudaMalloc((void**)&p->bsum, (size_t)NP * sizeof(float)) != cudaSuccess) return DFP2S_ENOMEM;
     const int n = KS * NP * KP;
     k_build_bt<<<(n + 255) / 256, 256, 0, st>>>(p->basis, K, NP, p->bt);
+    k_basis_sums<<<NP, 256, 0, st>>>(p->basis, K, NP, p->bsum);
+    k_scale<<<1, 128, 0, st>>>(p->bsum, NP, centre);
   }
   if (!p->err) {
     if (cudaMalloc((void**)&p->err, sizeof(int)) != cudaSuccess) return DFP2S_ENOMEM;
@@ -247,7 +286,7 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
     if (cudaMalloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
     p->pad_cap = need;
   }
-  k_pad_bf16<<<dim3((Wp + 255) / 256, H + 32, C), 256, 0, st>>>(img, C, H, W, Wp, p->pad);
+  k_pad_bf16<<<dim3((Wp + 255) / 256, H + 32, C), 256, 0, st>>>(img, C, H, W, Wp, centre, p->pad);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -257,11 +296,18 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
   // 512-column TMEM allocation) lives on an SM
   const size_t sm = 120 * 1024;
   static_assert(sizeof(Smem) < 120 * 1024, "smem layout");
-  cudaFuncSetAttribute(k_blur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   for (int c0 = 0; c0 < C; c0 += CMAX) {
     const int nc = C - c0 < CMAX ? C - c0 : CMAX;
-    k_blur_tc<<<grid, THREADS, sm, st>>>(p->pad + (size_t)c0 * (H + 32) * Wp, nc, H, W, Wp, p->bt, K, NP, w,
-                                         out + (size_t)c0 * H * W, p->err);
+    const __nv_bfloat16* pc = p->pad + (size_t)c0 * (H + 32) * Wp;
+    float* oc = out + (size_t)c0 * H * W;
+    if (w_dtype == DFP2S_W_BF16)
+      k_blur_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum,
+                                                         (const __nv_bfloat16*)w, oc, p->err);
+    else
+      k_blur_tc<float><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum, (const float*)w, oc,
+                                                 p->err);
   }
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }

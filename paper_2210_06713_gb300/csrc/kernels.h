@@ -55,8 +55,11 @@ struct dfp2s_p2s_dev {
   __nv_bfloat16* pad;
   size_t pad_cap;
   int* err;
+  float* bsum;  // centre * sum of each bfloat16 basis function (tensor-core blur)
 };
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
+// w_dtype for dfp2s_launch_p2s_exact that writes the normalised 33 x 33 PSFs (npix x 1089 FP32) instead of weights
+#define DFP2S_W_PSF 2
 int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
                            cudaStream_t st);
 int dfp2s_launch_p2s_mlp(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
@@ -76,9 +79,13 @@ int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_t
 int dfp2s_launch_draw_vectors(int n, int J, const float* L, const float* drs, int nd, uint64_t seed, uint32_t tag,
                               float* out, cudaStream_t st);
 
+// basis.cu -- FP64 SVD basis of exact PSFs
+int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const double* dr_host, int n_dr, uint64_t seed,
+                             float* basis_out, double* sigma_host, int* sweeps_out, cudaStream_t st);
+
 // blur_tc.cu -- BF16 tcgen05 blur (weights in BF16)
-int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const __nv_bfloat16* w, float* out,
-                         cudaStream_t st);
+int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
+                         float* out, cudaStream_t st);
 
 // blur.cu
 int dfp2s_launch_blur(const dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,

@@ -73,7 +73,7 @@ DFP2S_DEV void store_w<float>(float* w, size_t idx, float v) { w[idx] = v; }
 template <>
 DFP2S_DEV void store_w<__nv_bfloat16>(__nv_bfloat16* w, size_t idx, float v) { w[idx] = __float2bfloat16_rn(v); }
 
-template <typename WT>
+template <typename WT, bool PSF_OUT>
 __global__ void __launch_bounds__(NT) k_p2s_exact(const float* __restrict__ fields, int J, int npix, int K,
                                                   const float* __restrict__ zt, const float* __restrict__ mask,
                                                   const float2* __restrict__ dft, const float* __restrict__ phiT,
@@ -158,6 +158,14 @@ __global__ void __launch_bounds__(NT) k_p2s_exact(const float* __restrict__ fiel
       }
     }
     __syncthreads();
+    if (PSF_OUT) {  // the normalised PSFs themselves, npix x 1089 FP32
+      float* hout = reinterpret_cast<float*>(w);
+      for (int idx = tid; idx < PB * KS2; idx += NT) {
+        const int p = idx / KS2, q = idx - p * KS2;
+        if (p0 + p < npix) hout[(size_t)(p0 + p) * KS2 + q] = ph[p][q] / hsum[p];
+      }
+      continue;
+    }
     // w[p][k] = sum_q Phi[k][q] h[p][q] / sum h[p]
     {
       const int kk = tid % 128;
@@ -265,13 +273,18 @@ int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, i
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = nbatch < sms * 3 ? nbatch : sms * 3;
   const size_t sm = 3 * KS2 * sizeof(float2) + (PB * KS2 + PB * DFP2S_MAX_J + PB + NT / 32) * sizeof(float);
-  cudaFuncSetAttribute(k_p2s_exact<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_p2s_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (w_dtype == DFP2S_W_BF16)
-    k_p2s_exact<__nv_bfloat16><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft, p->phiT,
-                                                   (__nv_bfloat16*)w);
+  cudaFuncSetAttribute(k_p2s_exact<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_p2s_exact<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_p2s_exact<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (w_dtype == DFP2S_W_PSF)
+    k_p2s_exact<float, true><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft, p->phiT,
+                                                   (float*)w);
+  else if (w_dtype == DFP2S_W_BF16)
+    k_p2s_exact<__nv_bfloat16, false><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft,
+                                                          p->phiT, (__nv_bfloat16*)w);
   else
-    k_p2s_exact<float><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft, p->phiT, (float*)w);
+    k_p2s_exact<float, false><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft, p->phiT,
+                                                    (float*)w);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
 

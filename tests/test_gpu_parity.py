@@ -164,10 +164,17 @@ def test_blur_bf16_tensor_cores_match_oracle_on_bf16_operands(lib, C, H, W, K):
     P = lib.P2S(36, cu(basis))
     g = lib.basis_blur(P, cu(img), w).cpu().numpy()
     P.check()
-    o = image.basis_blur(_bf16(img), w.float().cpu().numpy(), _bf16(basis))
+    # the kernel's operands: bf16(I - 0.5) (the 0.5 added back exactly), bf16 basis, weights as stored
+    img_q = _bf16(img - 0.5) + 0.5
+    o = image.basis_blur(img_q, w.float().cpu().numpy(), _bf16(basis))
     assert rel_l2(g, o) < TOL
     # and stays within bfloat16 rounding of the FP32-operand result
-    assert rel_l2(g, image.basis_blur(img, w.float().cpu().numpy(), basis)) < 2e-2
+    assert rel_l2(g, image.basis_blur(img, w.float().cpu().numpy(), basis)) < 1e-2
+    # FP32 weights through the same tensor-core path
+    wf = torch.as_tensor(np.random.default_rng(H + 1).standard_normal((H, W, K)), dtype=torch.float32, device="cuda")
+    g32 = lib.basis_blur_tc(P, cu(img), wf).cpu().numpy()
+    P.check()
+    assert rel_l2(g32, image.basis_blur(img_q, wf.cpu().numpy(), _bf16(basis))) < TOL
 
 
 # ---------------------------------------------------------------- network

@@ -75,3 +75,26 @@ def test_training_learns_and_beats_mean_weights(lib):
     e_learned = float((le - ex).norm() / ex.norm())
     e_mean = float((mean_frame - ex).norm() / ex.norm())
     assert e_learned < 0.5 * e_mean, (e_learned, e_mean)
+
+
+@pytest.mark.parametrize("K,n_psf,drs", [(16, 300, (2.0,)), (100, 2000, (1.0, 2.0, 4.0))])
+def test_basis_svd_matches_oracle(lib, K, n_psf, drs):
+    J = 36
+    f = lib.SpectralFactor(J, 64, 8.0)
+    basis, sig, sweeps = lib.build_basis(f, K, n_psf, drs, seed=5)
+    assert 1 <= sweeps < 40
+    g = basis.double().cpu().numpy().reshape(K, -1)
+    a = p2s.basis_draws(5, J, n_psf, list(drs))
+    Hm = p2s.psf(a, J).reshape(n_psf, -1)
+    Phi, s = p2s.svd_basis(Hm, K)
+    assert np.allclose(sig[:K], s[:K], rtol=1e-5)
+    # orthonormal rows, same subspace (projector distance), same vectors where the spectrum is not degenerate
+    assert np.allclose(g @ g.T, np.eye(K), atol=1e-6)
+    proj = np.linalg.norm(g.T @ g - Phi.T @ Phi) / np.sqrt(K)
+    gap = (s[K - 1] - s[K]) / s[0]
+    if gap > 1e-4:
+        assert proj < 1e-3
+    for k in range(K):
+        sep = min(abs(s[k] - s[k - 1]) if k > 0 else 1.0, abs(s[k] - s[k + 1])) / s[0]
+        if sep > 1e-3:
+            assert np.dot(g[k], Phi[k]) > 1 - 1e-4, k
