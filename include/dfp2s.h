@@ -54,7 +54,8 @@ extern "C" {
 #define DFP2S_W_BF16 1  /* weight storage: bfloat16 */
 
 #define DFP2S_P2S_EXACT 0    /* pupil-FFT PSF + projection (Eq. 2, Sec. II-C) */
-#define DFP2S_P2S_LEARNED 1  /* the trained surrogate network (Sec. II-C) */
+#define DFP2S_P2S_LEARNED 1  /* the trained surrogate network (Sec. II-C), BF16 tensor cores */
+#define DFP2S_P2S_LEARNED_FP32 2 /* the same network in FP32 on CUDA cores (check mode) */
 
 #define DFP2S_FACTOR_FACTORED 0 /* sqrt(lambda_j(f)) per mode, then mixing by L (Sec. III-C) */
 #define DFP2S_FACTOR_DENSE 1    /* per-frequency J x J symmetric root of L diag(lambda) L^T */
@@ -221,7 +222,10 @@ int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params_dev, const floa
  *   EXACT: PSF of Eq. (2) from modes Noll 4..J+1 on a 64 x 64 pupil grid
  *          (aperture 32 samples across, P = 1 inside), |DFT|^2, 33 x 33 centre,
  *          unit sum, then w = Phi^T h;
- *   LEARNED: w = MLP(a * in_scale) * out_scale + out_shift.
+ *   LEARNED: w = MLP(a * in_scale) * out_scale + out_shift on the tcgen05
+ *          tensor cores (BF16 inputs, weights and hidden activations, FP32
+ *          accumulation), one fused kernel;
+ *   LEARNED_FP32: the same network in FP32 on CUDA cores.
  * Writes w_dev (H x W x K, dtype w_dtype).  Errors: EINVAL (no MLP for
  * LEARNED, sizes), ECUDA. */
 int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fields_dev, int H, int W, void* w_dev,

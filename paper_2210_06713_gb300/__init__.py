@@ -19,7 +19,7 @@ from . import build as _build
 
 OK = 0
 W_F32, W_BF16 = 0, 1
-P2S_EXACT, P2S_LEARNED = 0, 1
+P2S_EXACT, P2S_LEARNED, P2S_LEARNED_FP32 = 0, 1, 2
 FACTOR_FACTORED, FACTOR_DENSE = 0, 1
 KS = 33
 MAX_J = 64

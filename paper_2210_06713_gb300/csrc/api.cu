@@ -187,7 +187,8 @@ static void p2s_free(dfp2s_p2s* p) {
   if (!p) return;
   void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt,    p->d.mask, p->d.dft,       p->d.W1,        p->d.b1,
                   p->d.W2,    p->d.b2,   p->d.W3,    p->d.b3,   p->d.in_scale, p->d.out_scale, p->d.out_shift,
-                  p->d.bt,    p->d.pad,  p->d.err,   p->d.bsum};
+                  p->d.bt,    p->d.pad,  p->d.err,   p->d.bsum,     p->d.tc_w1,     p->d.tc_w2,     p->d.tc_w3,
+                  p->d.tc_c3};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -277,6 +278,14 @@ int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* d, const float* W1, const float* b1, co
       (e = copy_vec(&d->out_scale, out_scale, K)) != cudaSuccess ||
       (e = copy_vec(&d->out_shift, out_shift, K)) != cudaSuccess)
     return dfp2s_fail_cuda(e, "mlp weights");
+  if (!d->err) {
+    if ((e = cudaMalloc((void**)&d->err, sizeof(int))) != cudaSuccess) return dfp2s_fail_cuda(e, "error word");
+    cudaMemset(d->err, 0, sizeof(int));
+  }
+  const int rc = dfp2s_mlp_tc_pack(d, 0);
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "tensor-core weight allocation");
+  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core weight packing");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return dfp2s_fail_cuda(e, "tensor-core weight packing");
   d->has_mlp = 1;
   return DFP2S_OK;
 }
@@ -328,6 +337,9 @@ extern "C" int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fiel
   if (mode == DFP2S_P2S_EXACT) {
     CHECK_LAUNCH(dfp2s_launch_p2s_exact(&p->d, fields, H, W, w, w_dtype, as_stream(stream)));
   } else if (mode == DFP2S_P2S_LEARNED) {
+    CHECK_ARG(p->d.has_mlp, "no surrogate network installed");
+    CHECK_LAUNCH(dfp2s_launch_mlp_tc(&p->d, fields, H * W, w, w_dtype, as_stream(stream)));
+  } else if (mode == DFP2S_P2S_LEARNED_FP32) {
     CHECK_ARG(p->d.has_mlp, "no surrogate network installed");
     CHECK_LAUNCH(dfp2s_launch_p2s_mlp(&p->d, fields, H, W, w, w_dtype, as_stream(stream)));
   } else {
@@ -434,7 +446,8 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
   CHECK_ARG(img != out, "out must not alias img");
   CHECK_ARG(C >= 1 && C <= c->maxC && H >= 1 && H <= c->maxH && W >= 1 && W <= c->maxW,
             "frame %dx%dx%d exceeds the context's %dx%dx%d", C, H, W, c->maxC, c->maxH, c->maxW);
-  CHECK_ARG(p2s_mode == DFP2S_P2S_EXACT || p2s_mode == DFP2S_P2S_LEARNED, "unknown P2S mode");
+  CHECK_ARG(p2s_mode == DFP2S_P2S_EXACT || p2s_mode == DFP2S_P2S_LEARNED || p2s_mode == DFP2S_P2S_LEARNED_FP32,
+            "unknown P2S mode");
   int rc = dfp2s_sample_zernike_fields(c->f, D_over_r0, seed, frame, H, W, c->fields, stream);
   if (rc) return rc;
   const size_t npix = (size_t)H * W;

@@ -56,6 +56,9 @@ struct dfp2s_p2s_dev {
   size_t pad_cap;
   int* err;
   float* bsum;  // centre * sum of each bfloat16 basis function (tensor-core blur)
+  // tensor-core surrogate: packed BF16 weights and the folded output offset
+  __nv_bfloat16 *tc_w1, *tc_w2, *tc_w3;
+  float* tc_c3;
 };
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
 // w_dtype for dfp2s_launch_p2s_exact that writes the normalised 33 x 33 PSFs (npix x 1089 FP32) instead of weights
@@ -78,6 +81,10 @@ int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_t
                            float* params_out_host, cudaStream_t st);
 int dfp2s_launch_draw_vectors(int n, int J, const float* L, const float* drs, int nd, uint64_t seed, uint32_t tag,
                               float* out, cudaStream_t st);
+
+// mlp_tc.cu -- tensor-core surrogate inference
+int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st);
+int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st);
 
 // basis.cu -- FP64 SVD basis of exact PSFs
 int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const double* dr_host, int n_dr, uint64_t seed,

@@ -178,25 +178,45 @@ def test_blur_bf16_tensor_cores_match_oracle_on_bf16_operands(lib, C, H, W, K):
 
 
 # ---------------------------------------------------------------- network
-def test_mlp_forward_matches_oracle(lib):
-    J, K, H, W = 36, 100, 16, 24
-    rng = np.random.default_rng(0)
+def _bf(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+@pytest.mark.parametrize("K,H,W", [(100, 16, 24), (16, 9, 31), (128, 130, 3)])
+def test_mlp_forward_matches_oracle(lib, K, H, W):
+    J = 36
+    rng = np.random.default_rng(K)
     params = {"W1": rng.standard_normal((256, J)) / 6, "b1": rng.standard_normal(256) * 0.1,
               "W2": rng.standard_normal((256, 256)) / 16, "b2": rng.standard_normal(256) * 0.1,
               "W3": rng.standard_normal((K, 256)) / 16, "b3": rng.standard_normal(K) * 0.1}
     params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
-    in_scale = np.ones(J)
+    in_scale = rng.uniform(0.5, 2.0, J).astype(np.float32).astype(np.float64)
     in_scale[:2] = 0
-    out_scale = rng.uniform(0.5, 2, K)
-    out_shift = rng.standard_normal(K)
+    out_scale = rng.uniform(0.5, 2, K).astype(np.float32).astype(np.float64)
+    out_shift = rng.standard_normal(K).astype(np.float32).astype(np.float64)
     basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
     P = lib.P2S(J, cu(basis))
     P.set_mlp(*[cu(params[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")], cu(in_scale), cu(out_scale),
               cu(out_shift))
     a = synthetic.random_fields(J, H, W, scale=0.5, seed=3)
+    av = np.moveaxis(a, 0, -1).reshape(-1, J).astype(np.float64)
+    o = mlp.predict_weights(params, av, in_scale, out_scale, out_shift).reshape(H, W, K)
+    # FP32 CUDA-core form against the FP64 oracle
+    g32 = lib.p2s_weights(P, lib.P2S_LEARNED_FP32, cu(a)).cpu().numpy()
+    assert rel_l2(g32, o) < TOL
+    # tensor-core form against the oracle evaluated with the kernel's bfloat16 roundings
     g = lib.p2s_weights(P, lib.P2S_LEARNED, cu(a)).cpu().numpy()
-    o = mlp.predict_weights(params, np.moveaxis(a, 0, -1), in_scale, out_scale, out_shift)
-    assert rel_l2(g, o) < TOL
+    P.check()
+    z1 = _bf(av) @ _bf(params["W1"] * in_scale[None, :]).T + params["b1"]
+    h1 = _bf(mlp.gelu(z1))
+    z2 = h1 @ _bf(params["W2"]).T + params["b2"]
+    h2 = _bf(mlp.gelu(z2))
+    y = h2 @ _bf(params["W3"]).T
+    ob = (y * out_scale + (params["b3"] * out_scale + out_shift)).reshape(H, W, K)
+    assert rel_l2(g, ob) < 1e-3
+    assert rel_l2(g, o) < 2e-2
+    gb = lib.p2s_weights(P, lib.P2S_LEARNED, cu(a), w_dtype=lib.W_BF16).float().cpu().numpy()
+    assert rel_l2(gb, ob) < 4e-3
 
 
 # ------------------------------------------------------------------- frame
