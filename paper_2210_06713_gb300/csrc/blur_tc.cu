@@ -41,14 +41,19 @@ constexpr int KP = 48;                 // taps of one basis row padded to three 
 constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
 constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
 constexpr int CMAX = 4;                // channels per pass (TMEM: CMAX * NP <= 512 columns)
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;
+constexpr int NB = 4;                  // depth of the A/B ring (one slot per basis row iy)
+constexpr int PREF = 2;                // basis tiles are requested PREF rows ahead
+constexpr int RAWW = TM + KP;          // 176 staged image columns per row
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 struct Smem {
-  uint8_t A[2][CMAX][ROWB];       // double-buffered staged image rows
-  uint8_t B[2][KP / 8 * 16 * 128];  // double-buffered basis tiles (up to NP = 128)
-  uint64_t b_full[2];
-  uint64_t mma_done[2];
+  uint8_t raw[2][CMAX][KS][RAWW * 2];  // image rows of a tile (bulk copies, prefetched one tile ahead)
+  uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows, one slot per basis row
+  uint8_t B[NB][KP / 8 * 16 * 128];    // basis tiles (up to NP = 128)
+  uint64_t raw_full[2];
+  uint64_t b_full[NB];
+  uint64_t mma_done[NB];
   uint32_t tmem_base;
   int abort;
 };
@@ -127,12 +132,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   const uint32_t idesc = umma::idesc_bf16(TM, NP);
   const int nseg = (W + TM - 1) / TM;
   const int ntiles = H * nseg;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const uint32_t total_iters = (uint32_t)my_tiles * KS;
 
   if (tid == 0) {
-    umma::mbar_init(&s.b_full[0], 1);
-    umma::mbar_init(&s.b_full[1], 1);
-    umma::mbar_init(&s.mma_done[0], 1);
-    umma::mbar_init(&s.mma_done[1], 1);
+    for (int i = 0; i < 2; ++i) umma::mbar_init(&s.raw_full[i], 1);
+    for (int i = 0; i < NB; ++i) {
+      umma::mbar_init(&s.b_full[i], 1);
+      umma::mbar_init(&s.mma_done[i], 1);
+    }
     s.abort = 0;
     umma::fence_mbar_init();
   }
@@ -145,58 +153,76 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   umma::fence_after_sync();
   const uint32_t tmem = s.tmem_base;
 
-  uint32_t it = 0;  // staging iterations issued by this CTA (buffer = it & 1)
+  // thread 0's copy engine: image rows of a tile, basis tiles of an iteration
+  auto issue_raw = [&](int t_local) {
+    const int tile = blockIdx.x + t_local * gridDim.x;
+    const int y = tile / nseg, x0 = (tile - y * nseg) * TM;
+    const int rb = t_local & 1;
+    umma::mbar_arrive_expect_tx(&s.raw_full[rb], (uint32_t)(C * KS * RAWW * 2));
+    for (int c = 0; c < C; ++c)
+      for (int ri = 0; ri < KS; ++ri)
+        umma::bulk_g2s(s.raw[rb][c][ri], P + ((size_t)c * (H + 32) + y + ri) * Wp + x0, RAWW * 2, &s.raw_full[rb]);
+  };
+  uint32_t b_issued = 0;
+  auto issue_b = [&](uint32_t v) {
+    const int b = v % NB;
+    if (v >= NB && !umma::mbar_wait(&s.mma_done[b], ((v / NB) - 1) & 1, kWaitNs)) s.abort = 1;
+    umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
+    umma::bulk_g2s(s.B[b], Bt + (size_t)(v % KS) * (NP * KP), bt_bytes, &s.b_full[b]);
+  };
+  if (tid == 0 && my_tiles > 0) issue_raw(0);
+
+  uint32_t it = 0;
   bool ok = true;
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  for (int t_local = 0; t_local < my_tiles && ok; ++t_local) {
+    const int tile = blockIdx.x + t_local * gridDim.x;
     const int y = tile / nseg;
     const int x0 = (tile - y * nseg) * TM;
+    const int rb = t_local & 1;
+    // the other raw buffer was fully staged by the previous tile: prefetch the next tile into it
+    if (tid == 0 && t_local + 1 < my_tiles) issue_raw(t_local + 1);
+    if (!umma::mbar_wait(&s.raw_full[rb], (t_local >> 1) & 1, kWaitNs)) s.abort = 1;
     for (int iy = 0; iy < KS; ++iy, ++it) {
-      const int buf = it & 1;
-      // buffer `buf` was last read by the MMAs of iteration it - 2
-      if (it >= 2) {
-        if (!umma::mbar_wait(&s.mma_done[buf], ((it - 2) >> 1) & 1, kWaitNs)) s.abort = 1;
+      const int sb = it % NB;
+      if (tid == 0)
+        while (b_issued < total_iters && b_issued <= it + PREF) issue_b(b_issued++);
+      // slot sb was last read by the MMAs of iteration it - NB
+      if (it >= NB && !umma::mbar_wait(&s.mma_done[sb], ((it / NB) - 1) & 1, kWaitNs)) s.abort = 1;
+      // stage the Hankel blocks of image row ri = 32 - iy: item = (channel, block, half of the 8 shifts)
+      const int ri = KS - 1 - iy;
+      for (int item = tid; item < C * NBLK * 2; item += THREADS) {
+        const int c = item / (NBLK * 2);
+        const int rem = item - c * NBLK * 2;
+        const int b = rem >> 1;
+        const uint4* src = reinterpret_cast<const uint4*>(s.raw[rb][c][ri] + b * 16);
+        const uint4 v0 = src[0], v1 = src[1];
+        const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint4* dst = reinterpret_cast<uint4*>(s.A[sb][c] + b * 128);
+        if ((rem & 1) == 0) {
+          dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+          dst[1] = make_uint4(shr16(wv[0], wv[1]), shr16(wv[1], wv[2]), shr16(wv[2], wv[3]), shr16(wv[3], wv[4]));
+          dst[2] = make_uint4(wv[1], wv[2], wv[3], wv[4]);
+          dst[3] = make_uint4(shr16(wv[1], wv[2]), shr16(wv[2], wv[3]), shr16(wv[3], wv[4]), shr16(wv[4], wv[5]));
+        } else {
+          dst[4] = make_uint4(wv[2], wv[3], wv[4], wv[5]);
+          dst[5] = make_uint4(shr16(wv[2], wv[3]), shr16(wv[3], wv[4]), shr16(wv[4], wv[5]), shr16(wv[5], wv[6]));
+          dst[6] = make_uint4(wv[3], wv[4], wv[5], wv[6]);
+          dst[7] = make_uint4(shr16(wv[3], wv[4]), shr16(wv[4], wv[5]), shr16(wv[5], wv[6]), shr16(wv[6], wv[7]));
+        }
       }
+      umma::fence_proxy_async_smem();
       __syncthreads();
       if (s.abort) {
         ok = false;
         break;
       }
       if (tid == 0) {
-        umma::mbar_arrive_expect_tx(&s.b_full[buf], bt_bytes);
-        umma::bulk_g2s(s.B[buf], Bt + (size_t)iy * (NP * KP), bt_bytes, &s.b_full[buf]);
-      }
-      // stage E_0..E_20 of image row r for every channel: item = (channel, block)
-      const int pr = y + 32 - iy;  // padded row of r = y + 16 - iy
-      for (int item = tid; item < C * NBLK; item += THREADS) {
-        const int c = item / NBLK;
-        const int b = item - c * NBLK;
-        const __nv_bfloat16* src = P + ((size_t)c * (H + 32) + pr) * Wp + x0 + 8 * b;
-        const uint4 v0 = *reinterpret_cast<const uint4*>(src);
-        const uint4 v1 = *reinterpret_cast<const uint4*>(src + 8);
-        const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        uint4* dst = reinterpret_cast<uint4*>(s.A[buf][c] + b * 128);
-#pragma unroll
-        for (int sh = 0; sh < 8; ++sh) {  // row s of the block: elements s .. s+7
-          const int w0 = sh >> 1;
-          uint4 o;
-          if ((sh & 1) == 0) {
-            o = make_uint4(wv[w0], wv[w0 + 1], wv[w0 + 2], wv[w0 + 3]);
-          } else {
-            o = make_uint4(shr16(wv[w0], wv[w0 + 1]), shr16(wv[w0 + 1], wv[w0 + 2]), shr16(wv[w0 + 2], wv[w0 + 3]),
-                           shr16(wv[w0 + 3], wv[w0 + 4]));
-          }
-          dst[sh] = o;
-        }
-      }
-      umma::fence_proxy_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        if (!umma::mbar_wait(&s.b_full[buf], (it >> 1) & 1, kWaitNs)) {
+        if (!umma::mbar_wait(&s.b_full[sb], (it / NB) & 1, kWaitNs)) {
           s.abort = 1;
         } else {
           umma::fence_after_sync();
-          const uint32_t a0 = umma::smem_u32(s.A[buf][0]);
-          const uint32_t b0 = umma::smem_u32(s.B[buf]);
+          const uint32_t a0 = umma::smem_u32(s.A[sb][0]);
+          const uint32_t b0 = umma::smem_u32(s.B[sb]);
           for (int c = 0; c < C; ++c) {
 #pragma unroll
             for (int ks = 0; ks < KP / 16; ++ks) {
@@ -206,15 +232,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
               umma::mma_bf16(tmem + c * NP, ad, bd, idesc, (iy | ks) != 0);
             }
           }
-          umma::mma_commit(&s.mma_done[buf]);
+          umma::mma_commit(&s.mma_done[sb]);
         }
       }
     }
     if (!ok) break;
-    // epilogue: all MMAs of this tile are done once the last commit has arrived
+    // epilogue: the tile's MMAs are done once the last commit has arrived
     {
       const uint32_t last = it - 1;
-      if (!umma::mbar_wait(&s.mma_done[last & 1], (last >> 1) & 1, kWaitNs)) s.abort = 1;
+      if (!umma::mbar_wait(&s.mma_done[last % NB], (last / NB) & 1, kWaitNs)) s.abort = 1;
     }
     __syncthreads();
     if (s.abort) {
@@ -223,32 +249,49 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
     }
     umma::fence_after_sync();
     {
-      const int x = x0 + warp * 32 + lane;
+      // warps w and w + 4 read TMEM lanes 32 (w % 4) ..: the first takes the even channels, the second the odd
+      const int q4 = warp & 3;
+      const int x = x0 + q4 * 32 + lane;
       const bool live = x < W;
       const size_t pix = (size_t)y * W + (live ? x : 0);
       const WT* wp = w + pix * K;
-      for (int c = 0; c < C; ++c) {
-        float acc = 0.f;
-        for (int q = 0; q < NP / 16; ++q) {
-          float d[16];
-          umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * NP + q * 16, d);
+      float acc[2] = {0.f, 0.f};
+      const int cfirst = warp >> 2;
+      for (int q = 0; q < NP / 16; ++q) {
+        float wk[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int k = q * 16 + i;
-            if (k < K) acc = fmaf(wload<WT>(wp + k), d[i] + csum[k], acc);
+        for (int i = 0; i < 16; ++i) {
+          const int k = q * 16 + i;
+          wk[i] = k < K ? wload<WT>(wp + k) : 0.f;
+        }
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = cfirst + 2 * cc;
+          if (c < C) {
+            float d[16];
+            umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + c * NP + q * 16, d);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[cc] = fmaf(wk[i], d[i] + csum[q * 16 + i], acc[cc]);
           }
         }
-        if (live) out[((size_t)c * H + y) * W + x] = acc;
+      }
+      if (live) {
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = cfirst + 2 * cc;
+          if (c < C) out[((size_t)c * H + y) * W + x] = acc[cc];
+        }
       }
     }
     umma::fence_before_sync();
     __syncthreads();
   }
-  // drain: never leave MMAs or copies in flight on an abort path (bounded)
-  if (!ok && tid == 0) {
-    atomicExch(err, 1);
-    if (it >= 1) umma::mbar_wait(&s.mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1, kWaitNs);
-    if (it >= 1) umma::mbar_wait(&s.b_full[(it - 1) & 1], ((it - 1) >> 1) & 1, kWaitNs);
+  // drain: never leave MMAs or copies in flight (bounded waits)
+  if (tid == 0) {
+    if (!ok) atomicExch(err, 1);
+    for (uint32_t v = (it >= NB ? it - NB : 0); v < b_issued; ++v)
+      umma::mbar_wait(&s.b_full[v % NB], (v / NB) & 1, kWaitNs);
+    if (it >= 1) umma::mbar_wait(&s.mma_done[(it - 1) % NB], ((it - 1) / NB) & 1, kWaitNs);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -292,10 +335,10 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ntiles = H * nseg;
   const int grid = ntiles < sms ? ntiles : sms;
-  // ask for more shared memory than one tile needs so only one CTA (and one
-  // 512-column TMEM allocation) lives on an SM
-  const size_t sm = 120 * 1024;
-  static_assert(sizeof(Smem) < 120 * 1024, "smem layout");
+  // more than half of an SM's shared memory: one CTA (and one 512-column TMEM
+  // allocation) per SM
+  const size_t sm = sizeof(Smem) + 1024;
+  static_assert(sizeof(Smem) + 1024 > 116 * 1024 && sizeof(Smem) + 1024 < 227 * 1024, "smem layout");
   cudaFuncSetAttribute(k_blur_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   for (int c0 = 0; c0 < C; c0 += CMAX) {
