@@ -41,7 +41,8 @@ constexpr int KP = 48;                 // taps of one basis row padded to three 
 constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
 constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
 constexpr int CMAX = 4;                // channels per pass (TMEM: CMAX * NP <= 512 columns)
-constexpr int THREADS = 256;
+constexpr int THREADS = 256;           // warp 0: copies + MMA issue; warps 1-3: staging; warps 4-7: epilogue
+constexpr int NSTAGE_WARPS = 3;
 constexpr int NB = 4;                  // depth of the A/B ring (one slot per basis row iy)
 constexpr int PREF = 2;                // basis tiles are requested PREF rows ahead
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
@@ -52,8 +53,8 @@ struct Smem {
   uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows, one slot per basis row
   uint8_t B[NB][KP / 8 * 16 * 128];    // basis tiles (up to NP = 128)
   uint64_t raw_full[2];
-  uint64_t b_full[NB];
-  uint64_t mma_done[NB];
+  uint64_t a_full[NB], b_full[NB], slot_free[NB];
+  uint64_t tile_done, tmem_empty;
   uint32_t tmem_base;
   int abort;
 };
@@ -138,9 +139,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) umma::mbar_init(&s.raw_full[i], 1);
     for (int i = 0; i < NB; ++i) {
+      umma::mbar_init(&s.a_full[i], NSTAGE_WARPS);
       umma::mbar_init(&s.b_full[i], 1);
-      umma::mbar_init(&s.mma_done[i], 1);
+      umma::mbar_init(&s.slot_free[i], 1);
     }
+    umma::mbar_init(&s.tile_done, 1);
+    umma::mbar_init(&s.tmem_empty, 4);
     s.abort = 0;
     umma::fence_mbar_init();
   }
@@ -153,73 +157,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   umma::fence_after_sync();
   const uint32_t tmem = s.tmem_base;
 
-  // thread 0's copy engine: image rows of a tile, basis tiles of an iteration
-  auto issue_raw = [&](int t_local) {
-    const int tile = blockIdx.x + t_local * gridDim.x;
-    const int y = tile / nseg, x0 = (tile - y * nseg) * TM;
-    const int rb = t_local & 1;
-    umma::mbar_arrive_expect_tx(&s.raw_full[rb], (uint32_t)(C * KS * RAWW * 2));
-    for (int c = 0; c < C; ++c)
-      for (int ri = 0; ri < KS; ++ri)
-        umma::bulk_g2s(s.raw[rb][c][ri], P + ((size_t)c * (H + 32) + y + ri) * Wp + x0, RAWW * 2, &s.raw_full[rb]);
-  };
-  uint32_t b_issued = 0;
-  auto issue_b = [&](uint32_t v) {
-    const int b = v % NB;
-    if (v >= NB && !umma::mbar_wait(&s.mma_done[b], ((v / NB) - 1) & 1, kWaitNs)) s.abort = 1;
-    umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
-    umma::bulk_g2s(s.B[b], Bt + (size_t)(v % KS) * (NP * KP), bt_bytes, &s.b_full[b]);
-  };
-  if (tid == 0 && my_tiles > 0) issue_raw(0);
-
-  uint32_t it = 0;
-  bool ok = true;
-  for (int t_local = 0; t_local < my_tiles && ok; ++t_local) {
-    const int tile = blockIdx.x + t_local * gridDim.x;
-    const int y = tile / nseg;
-    const int x0 = (tile - y * nseg) * TM;
-    const int rb = t_local & 1;
-    // the other raw buffer was fully staged by the previous tile: prefetch the next tile into it
-    if (tid == 0 && t_local + 1 < my_tiles) issue_raw(t_local + 1);
-    if (!umma::mbar_wait(&s.raw_full[rb], (t_local >> 1) & 1, kWaitNs)) s.abort = 1;
-    for (int iy = 0; iy < KS; ++iy, ++it) {
-      const int sb = it % NB;
-      if (tid == 0)
-        while (b_issued < total_iters && b_issued <= it + PREF) issue_b(b_issued++);
-      // slot sb was last read by the MMAs of iteration it - NB
-      if (it >= NB && !umma::mbar_wait(&s.mma_done[sb], ((it / NB) - 1) & 1, kWaitNs)) s.abort = 1;
-      // stage the Hankel blocks of image row ri = 32 - iy: item = (channel, block, half of the 8 shifts)
-      const int ri = KS - 1 - iy;
-      for (int item = tid; item < C * NBLK * 2; item += THREADS) {
-        const int c = item / (NBLK * 2);
-        const int rem = item - c * NBLK * 2;
-        const int b = rem >> 1;
-        const uint4* src = reinterpret_cast<const uint4*>(s.raw[rb][c][ri] + b * 16);
-        const uint4 v0 = src[0], v1 = src[1];
-        const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        uint4* dst = reinterpret_cast<uint4*>(s.A[sb][c] + b * 128);
-        if ((rem & 1) == 0) {
-          dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-          dst[1] = make_uint4(shr16(wv[0], wv[1]), shr16(wv[1], wv[2]), shr16(wv[2], wv[3]), shr16(wv[3], wv[4]));
-          dst[2] = make_uint4(wv[1], wv[2], wv[3], wv[4]);
-          dst[3] = make_uint4(shr16(wv[1], wv[2]), shr16(wv[2], wv[3]), shr16(wv[3], wv[4]), shr16(wv[4], wv[5]));
-        } else {
-          dst[4] = make_uint4(wv[2], wv[3], wv[4], wv[5]);
-          dst[5] = make_uint4(shr16(wv[2], wv[3]), shr16(wv[3], wv[4]), shr16(wv[4], wv[5]), shr16(wv[5], wv[6]));
-          dst[6] = make_uint4(wv[3], wv[4], wv[5], wv[6]);
-          dst[7] = make_uint4(shr16(wv[3], wv[4]), shr16(wv[4], wv[5]), shr16(wv[5], wv[6]), shr16(wv[6], wv[7]));
-        }
-      }
-      umma::fence_proxy_async_smem();
-      __syncthreads();
-      if (s.abort) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        if (!umma::mbar_wait(&s.b_full[sb], (it / NB) & 1, kWaitNs)) {
-          s.abort = 1;
-        } else {
+  if (warp == 0) {
+    // ---------------------------------------------------------- copies + MMA issue (one lane)
+    if (lane == 0) {
+      auto issue_raw = [&](int t_local) {
+        const int tile = blockIdx.x + t_local * gridDim.x;
+        const int y = tile / nseg, x0 = (tile - y * nseg) * TM;
+        const int rb = t_local & 1;
+        umma::mbar_arrive_expect_tx(&s.raw_full[rb], (uint32_t)(C * KS * RAWW * 2));
+        for (int c = 0; c < C; ++c)
+          for (int ri = 0; ri < KS; ++ri)
+            umma::bulk_g2s(s.raw[rb][c][ri], P + ((size_t)c * (H + 32) + y + ri) * Wp + x0, RAWW * 2,
+                           &s.raw_full[rb]);
+      };
+      uint32_t b_issued = 0;
+      bool ok = true;
+      auto issue_b = [&](uint32_t v) {
+        const int b = v % NB;
+        if (v >= NB && !umma::mbar_wait(&s.slot_free[b], ((v / NB) - 1) & 1, kWaitNs)) ok = false;
+        umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
+        umma::bulk_g2s(s.B[b], Bt + (size_t)(v % KS) * (NP * KP), bt_bytes, &s.b_full[b]);
+      };
+      if (my_tiles > 0) issue_raw(0);
+      uint32_t it = 0;
+      for (int t = 0; t < my_tiles && ok; ++t) {
+        // raw buffer (t+1)&1 was last read by the staging of tile t-1, all of whose slots were consumed
+        if (t + 1 < my_tiles) issue_raw(t + 1);
+        for (int iy = 0; iy < KS && ok; ++iy, ++it) {
+          while (b_issued < total_iters && b_issued <= it + PREF && ok) issue_b(b_issued++);
+          const int sb = it % NB;
+          if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs) ||
+              !umma::mbar_wait(&s.b_full[sb], (it / NB) & 1, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          if (iy == 0 && t > 0 && !umma::mbar_wait(&s.tmem_empty, (t - 1) & 1, kWaitNs)) {
+            ok = false;
+            break;
+          }
           umma::fence_after_sync();
           const uint32_t a0 = umma::smem_u32(s.A[sb][0]);
           const uint32_t b0 = umma::smem_u32(s.B[sb]);
@@ -232,31 +207,64 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
               umma::mma_bf16(tmem + c * NP, ad, bd, idesc, (iy | ks) != 0);
             }
           }
-          umma::mma_commit(&s.mma_done[sb]);
+          umma::mma_commit(&s.slot_free[sb]);
+          if (iy == KS - 1) umma::mma_commit(&s.tile_done);
         }
       }
+      if (!ok) {
+        s.abort = 1;
+        atomicExch(err, 1);
+      }
+      // drain: wait (bounded) for every bulk copy issued and for the last MMAs
+      for (uint32_t v = (it >= NB ? it - NB : 0); v < b_issued; ++v)
+        if (v >= it) umma::mbar_wait(&s.b_full[v % NB], (v / NB) & 1, kWaitNs);
+      if (it >= 1) umma::mbar_wait(&s.slot_free[(it - 1) % NB], ((it - 1) / NB) & 1, kWaitNs);
     }
-    if (!ok) break;
-    // epilogue: the tile's MMAs are done once the last commit has arrived
-    {
-      const uint32_t last = it - 1;
-      if (!umma::mbar_wait(&s.mma_done[last % NB], (last / NB) & 1, kWaitNs)) s.abort = 1;
+  } else if (warp <= NSTAGE_WARPS) {
+    // ---------------------------------------------------------- staging: Hankel blocks from raw rows
+    const int st_tid = tid - 32;
+    uint32_t it = 0;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int rb = t & 1;
+      if (!umma::mbar_wait(&s.raw_full[rb], (t >> 1) & 1, kWaitNs)) s.abort = 1;
+      if (s.abort) break;
+      for (int iy = 0; iy < KS; ++iy, ++it) {
+        const int sb = it % NB;
+        if (it >= NB && !umma::mbar_wait(&s.slot_free[sb], ((it / NB) - 1) & 1, kWaitNs)) s.abort = 1;
+        if (s.abort) break;
+        const int ri = KS - 1 - iy;
+        // item = (channel, block, row s of the block), s fastest: 8 lanes write one 128-byte block
+        for (int item = st_tid; item < C * NBLK * 8; item += NSTAGE_WARPS * 32) {
+          const int sr = item & 7;
+          const int cb = item >> 3;
+          const int c = cb / NBLK, b = cb - c * NBLK;
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(s.raw[rb][c][ri]) + 4 * b + (sr >> 1);
+          const uint32_t w0 = src[0], w1 = src[1], w2 = src[2], w3 = src[3], w4 = src[4];
+          const uint32_t sh = (sr & 1) * 16;
+          const uint4 o = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                                     __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+          *reinterpret_cast<uint4*>(s.A[sb][c] + b * 128 + sr * 16) = o;
+        }
+        umma::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&s.a_full[sb]);
+      }
+      if (s.abort) break;
     }
-    __syncthreads();
-    if (s.abort) {
-      ok = false;
-      break;
-    }
-    umma::fence_after_sync();
-    {
-      // warps w and w + 4 read TMEM lanes 32 (w % 4) ..: the first takes the even channels, the second the odd
-      const int q4 = warp & 3;
+  } else {
+    // ---------------------------------------------------------- epilogue: TMEM -> weighted sums
+    const int q4 = warp & 3;
+    for (int t = 0; t < my_tiles; ++t) {
+      if (!umma::mbar_wait(&s.tile_done, t & 1, kWaitNs)) s.abort = 1;
+      if (s.abort) break;
+      umma::fence_after_sync();
+      const int tile = blockIdx.x + t * gridDim.x;
+      const int y = tile / nseg, x0 = (tile - y * nseg) * TM;
       const int x = x0 + q4 * 32 + lane;
       const bool live = x < W;
       const size_t pix = (size_t)y * W + (live ? x : 0);
       const WT* wp = w + pix * K;
-      float acc[2] = {0.f, 0.f};
-      const int cfirst = warp >> 2;
+      float acc[CMAX] = {0.f, 0.f, 0.f, 0.f};
       for (int q = 0; q < NP / 16; ++q) {
         float wk[16];
 #pragma unroll
@@ -265,33 +273,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
           wk[i] = k < K ? wload<WT>(wp + k) : 0.f;
         }
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int c = cfirst + 2 * cc;
+        for (int c = 0; c < CMAX; ++c) {
           if (c < C) {
             float d[16];
             umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + c * NP + q * 16, d);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[cc] = fmaf(wk[i], d[i] + csum[q * 16 + i], acc[cc]);
+            for (int i = 0; i < 16; ++i) acc[c] = fmaf(wk[i], d[i] + csum[q * 16 + i], acc[c]);
           }
         }
       }
       if (live) {
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int c = cfirst + 2 * cc;
-          if (c < C) out[((size_t)c * H + y) * W + x] = acc[cc];
-        }
+        for (int c = 0; c < CMAX; ++c)
+          if (c < C) out[((size_t)c * H + y) * W + x] = acc[c];
       }
+      umma::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&s.tmem_empty);
     }
-    umma::fence_before_sync();
-    __syncthreads();
-  }
-  // drain: never leave MMAs or copies in flight (bounded waits)
-  if (tid == 0) {
-    if (!ok) atomicExch(err, 1);
-    for (uint32_t v = (it >= NB ? it - NB : 0); v < b_issued; ++v)
-      umma::mbar_wait(&s.b_full[v % NB], (v / NB) & 1, kWaitNs);
-    if (it >= 1) umma::mbar_wait(&s.mma_done[(it - 1) % NB], ((it - 1) / NB) & 1, kWaitNs);
   }
   umma::fence_before_sync();
   __syncthreads();
