@@ -40,11 +40,12 @@ constexpr int TM = 128;                // pixels per tile (MMA M)
 constexpr int KP = 48;                 // taps of one basis row padded to three K = 16 steps
 constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
 constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
-constexpr int CMAX = 4;                // channels per pass (TMEM: CMAX * NP <= 512 columns)
+constexpr int CMAX = 3;                // channels per pass
+constexpr int NSLOT = 4;               // TMEM accumulator slots of NP <= 128 columns (512 in all)
 constexpr int THREADS = 256;           // warp 0: copies + MMA issue; warps 1-3: staging; warps 4-7: epilogue
 constexpr int NSTAGE_WARPS = 3;
 constexpr int NB = 4;                  // depth of the A/B ring (one slot per basis row iy)
-constexpr int PREF = 2;                // basis tiles are requested PREF rows ahead
+constexpr int PREF = 3;                // basis tiles are requested PREF rows ahead
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
@@ -52,9 +53,11 @@ struct Smem {
   uint8_t raw[2][CMAX][KS][RAWW * 2];  // image rows of a tile (bulk copies, prefetched one tile ahead)
   uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows, one slot per basis row
   uint8_t B[NB][KP / 8 * 16 * 128];    // basis tiles (up to NP = 128)
+  float wt[TM * 100];                  // FP32 weights of the current tile (K <= 100, K % 4 == 0)
   uint64_t raw_full[2];
   uint64_t a_full[NB], b_full[NB], slot_free[NB];
-  uint64_t tile_done, tmem_empty;
+  uint64_t acc_full[NSLOT], acc_empty[NSLOT];
+  uint64_t w_full, w_empty;
   uint32_t tmem_base;
   int abort;
 };
@@ -124,7 +127,7 @@ template <typename WT>
 __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __restrict__ P, int C, int H, int W,
                                                         int Wp, const __nv_bfloat16* __restrict__ Bt, int K, int NP,
                                                         const float* __restrict__ csum, const WT* __restrict__ w,
-                                                        float* __restrict__ out, int* __restrict__ err) {
+                                                        int w_smem, float* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
@@ -143,8 +146,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
       umma::mbar_init(&s.b_full[i], 1);
       umma::mbar_init(&s.slot_free[i], 1);
     }
-    umma::mbar_init(&s.tile_done, 1);
-    umma::mbar_init(&s.tmem_empty, 4);
+    for (int i = 0; i < NSLOT; ++i) {
+      umma::mbar_init(&s.acc_full[i], 1);
+      umma::mbar_init(&s.acc_empty[i], 4);
+    }
+    umma::mbar_init(&s.w_full, 1);
+    umma::mbar_init(&s.w_empty, 4);
     s.abort = 0;
     umma::fence_mbar_init();
   }
@@ -156,13 +163,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = s.tmem_base;
+  auto tile_xy = [&](int t_local, int& y, int& x0) {
+    const int tile = blockIdx.x + t_local * gridDim.x;
+    y = tile / nseg;
+    x0 = (tile - y * nseg) * TM;
+  };
 
   if (warp == 0) {
     // ---------------------------------------------------------- copies + MMA issue (one lane)
     if (lane == 0) {
       auto issue_raw = [&](int t_local) {
-        const int tile = blockIdx.x + t_local * gridDim.x;
-        const int y = tile / nseg, x0 = (tile - y * nseg) * TM;
+        int y, x0;
+        tile_xy(t_local, y, x0);
         const int rb = t_local & 1;
         umma::mbar_arrive_expect_tx(&s.raw_full[rb], (uint32_t)(C * KS * RAWW * 2));
         for (int c = 0; c < C; ++c)
@@ -191,24 +203,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
             ok = false;
             break;
           }
-          if (iy == 0 && t > 0 && !umma::mbar_wait(&s.tmem_empty, (t - 1) & 1, kWaitNs)) {
-            ok = false;
-            break;
-          }
           umma::fence_after_sync();
           const uint32_t a0 = umma::smem_u32(s.A[sb][0]);
           const uint32_t b0 = umma::smem_u32(s.B[sb]);
           for (int c = 0; c < C; ++c) {
+            const uint32_t g = (uint32_t)(t * C + c);  // accumulator use number; slot g % NSLOT
+            const int slot = g % NSLOT;
+            if (iy == 0 && g >= NSLOT && !umma::mbar_wait(&s.acc_empty[slot], ((g / NSLOT) - 1) & 1, kWaitNs)) {
+              ok = false;
+              break;
+            }
+            if (iy == 0) umma::fence_after_sync();
 #pragma unroll
             for (int ks = 0; ks < KP / 16; ++ks) {
               const uint64_t ad = umma::sdesc(a0 + c * ROWB + ks * 256, 128, 128);
               // B tile [j][g][8][8]: K-adjacent core matrices 128 B apart, 8-filter groups 768 B apart
               const uint64_t bd = umma::sdesc(b0 + ks * 256, 128, 768);
-              umma::mma_bf16(tmem + c * NP, ad, bd, idesc, (iy | ks) != 0);
+              umma::mma_bf16(tmem + slot * NP, ad, bd, idesc, (iy | ks) != 0);
             }
           }
+          if (!ok) break;
           umma::mma_commit(&s.slot_free[sb]);
-          if (iy == KS - 1) umma::mma_commit(&s.tile_done);
+          if (iy == KS - 1)
+            for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
         }
       }
       if (!ok) {
@@ -254,42 +271,75 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   } else {
     // ---------------------------------------------------------- epilogue: TMEM -> weighted sums
     const int q4 = warp & 3;
+    const int etid = tid - 128;
+    // weights of a tile: one contiguous run of nlive * K floats (issued one tile ahead)
+    auto issue_w = [&](int t_local) {
+      int y, x0;
+      tile_xy(t_local, y, x0);
+      const int nlive = min(TM, W - x0);
+      const uint32_t bytes = (uint32_t)(nlive * K * 4);
+      umma::mbar_arrive_expect_tx(&s.w_full, bytes);
+      umma::bulk_g2s(s.wt, reinterpret_cast<const float*>(w) + ((size_t)y * W + x0) * K, bytes, &s.w_full);
+    };
+    if (w_smem && etid == 0 && my_tiles > 0) issue_w(0);
     for (int t = 0; t < my_tiles; ++t) {
-      if (!umma::mbar_wait(&s.tile_done, t & 1, kWaitNs)) s.abort = 1;
-      if (s.abort) break;
-      umma::fence_after_sync();
-      const int tile = blockIdx.x + t * gridDim.x;
-      const int y = tile / nseg, x0 = (tile - y * nseg) * TM;
+      int y, x0;
+      tile_xy(t, y, x0);
       const int x = x0 + q4 * 32 + lane;
       const bool live = x < W;
       const size_t pix = (size_t)y * W + (live ? x : 0);
-      const WT* wp = w + pix * K;
-      float acc[CMAX] = {0.f, 0.f, 0.f, 0.f};
-      for (int q = 0; q < NP / 16; ++q) {
-        float wk[16];
+      if (w_smem && !umma::mbar_wait(&s.w_full, t & 1, kWaitNs)) s.abort = 1;
+      const float* wrow = s.wt + (size_t)(q4 * 32 + lane) * K;
+      const WT* wg = w + pix * K;
+      float acc[CMAX] = {0.f, 0.f, 0.f};
+      for (int c = 0; c < C; ++c) {
+        const uint32_t g = (uint32_t)(t * C + c);
+        const int slot = g % NSLOT;
+        if (!umma::mbar_wait(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
+        if (s.abort) break;
+        umma::fence_after_sync();
+        float a = 0.f;
+        for (int q = 0; q < NP / 16; ++q) {
+          float d[16];
+          umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + slot * NP + q * 16, d);
+          if (w_smem) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int k = q * 16 + i;
-          wk[i] = k < K ? wload<WT>(wp + k) : 0.f;
-        }
+            for (int i4 = 0; i4 < 4; ++i4) {
+              const int k = q * 16 + 4 * i4;
+              if (k < K) {
+                const float4 wk = live ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                a = fmaf(wk.x, d[4 * i4 + 0] + csum[k + 0], a);
+                a = fmaf(wk.y, d[4 * i4 + 1] + csum[k + 1], a);
+                a = fmaf(wk.z, d[4 * i4 + 2] + csum[k + 2], a);
+                a = fmaf(wk.w, d[4 * i4 + 3] + csum[k + 3], a);
+              }
+            }
+          } else {
 #pragma unroll
-        for (int c = 0; c < CMAX; ++c) {
-          if (c < C) {
-            float d[16];
-            umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + c * NP + q * 16, d);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) acc[c] = fmaf(wk[i], d[i] + csum[q * 16 + i], acc[c]);
+            for (int i = 0; i < 16; ++i) {
+              const int k = q * 16 + i;
+              if (k < K) a = fmaf(wload<WT>(wg + k), d[i] + csum[k], a);
+            }
           }
+        }
+        acc[c] = a;
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&s.acc_empty[slot]);
+      }
+      if (s.abort) break;
+      // this warp is done with the tile's weights; once all four are, fetch the next tile's
+      if (w_smem) {
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&s.w_empty);
+        if (etid == 0 && t + 1 < my_tiles) {
+          if (!umma::mbar_wait(&s.w_empty, t & 1, kWaitNs)) s.abort = 1;
+          else issue_w(t + 1);
         }
       }
       if (live) {
-#pragma unroll
-        for (int c = 0; c < CMAX; ++c)
-          if (c < C) out[((size_t)c * H + y) * W + x] = acc[c];
+        for (int c = 0; c < C; ++c) out[((size_t)c * H + y) * W + x] = acc[c];
       }
-      umma::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&s.tmem_empty);
     }
   }
   umma::fence_before_sync();
@@ -340,16 +390,18 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
   static_assert(sizeof(Smem) + 1024 > 116 * 1024 && sizeof(Smem) + 1024 < 227 * 1024, "smem layout");
   cudaFuncSetAttribute(k_blur_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // weights through shared memory when a tile's run of FP32 weights fits and is 16-byte aligned
+  const int w_smem = (w_dtype == DFP2S_W_F32) && K <= 100 && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
   for (int c0 = 0; c0 < C; c0 += CMAX) {
     const int nc = C - c0 < CMAX ? C - c0 : CMAX;
     const __nv_bfloat16* pc = p->pad + (size_t)c0 * (H + 32) * Wp;
     float* oc = out + (size_t)c0 * H * W;
     if (w_dtype == DFP2S_W_BF16)
       k_blur_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum,
-                                                         (const __nv_bfloat16*)w, oc, p->err);
+                                                         (const __nv_bfloat16*)w, 0, oc, p->err);
     else
-      k_blur_tc<float><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum, (const float*)w, oc,
-                                                 p->err);
+      k_blur_tc<float><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum, (const float*)w, w_smem,
+                                                 oc, p->err);
   }
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
