@@ -42,8 +42,9 @@ constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
 constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
 constexpr int CMAX = 3;                // channels per pass
 constexpr int NSLOT = 4;               // TMEM accumulator slots of NP <= 128 columns (512 in all)
-constexpr int THREADS = 256;           // warp 0: copies + MMA issue; warps 1-3: staging; warps 4-7: epilogue
-constexpr int NSTAGE_WARPS = 3;
+constexpr int NSTAGE_WARPS = 7;        // warp 0: copies + MMA issue; warps 1-7: staging; warps 8-11: epilogue
+constexpr int EPI_WARP0 = 1 + NSTAGE_WARPS;
+constexpr int THREADS = (EPI_WARP0 + 4) * 32;
 constexpr int NB = 4;                  // depth of the A/B ring (one slot per basis row iy)
 constexpr int PREF = 3;                // basis tiles are requested PREF rows ahead
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
@@ -57,6 +58,7 @@ struct Smem {
   uint64_t raw_full[2];
   uint64_t a_full[NB], b_full[NB], slot_free[NB];
   uint64_t acc_full[NSLOT], acc_empty[NSLOT];
+  float csum[128];
   uint64_t w_full, w_empty;
   uint32_t tmem_base;
   int abort;
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
     s.abort = 0;
     umma::fence_mbar_init();
   }
+  for (int i = tid; i < 128; i += THREADS) s.csum[i] = i < NP ? csum[i] : 0.f;
   if (warp == 0) {
     umma::tmem_alloc(&s.tmem_base, 512);
     umma::tmem_relinquish();
@@ -270,8 +273,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
     }
   } else {
     // ---------------------------------------------------------- epilogue: TMEM -> weighted sums
-    const int q4 = warp & 3;
-    const int etid = tid - 128;
+    const int q4 = warp & 3;  // warp w reads TMEM lanes 32 (w % 4) ..
+    const int etid = tid - EPI_WARP0 * 32;
     // weights of a tile: one contiguous run of nlive * K floats (issued one tile ahead)
     auto issue_w = [&](int t_local) {
       int y, x0;
@@ -308,17 +311,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
               const int k = q * 16 + 4 * i4;
               if (k < K) {
                 const float4 wk = live ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-                a = fmaf(wk.x, d[4 * i4 + 0] + csum[k + 0], a);
-                a = fmaf(wk.y, d[4 * i4 + 1] + csum[k + 1], a);
-                a = fmaf(wk.z, d[4 * i4 + 2] + csum[k + 2], a);
-                a = fmaf(wk.w, d[4 * i4 + 3] + csum[k + 3], a);
+                a = fmaf(wk.x, d[4 * i4 + 0] + s.csum[k + 0], a);
+                a = fmaf(wk.y, d[4 * i4 + 1] + s.csum[k + 1], a);
+                a = fmaf(wk.z, d[4 * i4 + 2] + s.csum[k + 2], a);
+                a = fmaf(wk.w, d[4 * i4 + 3] + s.csum[k + 3], a);
               }
             }
           } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               const int k = q * 16 + i;
-              if (k < K) a = fmaf(wload<WT>(wg + k), d[i] + csum[k], a);
+              if (k < K) a = fmaf(wload<WT>(wg + k), d[i] + s.csum[k], a);
             }
           }
         }
