@@ -45,8 +45,8 @@ constexpr int NSLOT = 4;               // TMEM accumulator slots of NP <= 128 co
 constexpr int NSTAGE_WARPS = 7;        // warp 0: copies + MMA issue; warps 1-7: staging; warps 8-11: epilogue
 constexpr int EPI_WARP0 = 1 + NSTAGE_WARPS;
 constexpr int THREADS = (EPI_WARP0 + 4) * 32;
-constexpr int NB = 4;                  // depth of the A/B ring (one slot per basis row iy)
-constexpr int PREF = 3;                // basis tiles are requested PREF rows ahead
+constexpr int NB = 5;                  // depth of the A/B ring (one slot per basis row iy)
+constexpr int PREF = 2;                // basis tiles are requested PREF rows ahead (PREF < NB - 1 keeps two MMA batches queued)
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
