@@ -45,21 +45,21 @@ constexpr int NSLOT = 4;               // TMEM accumulator slots of NP <= 128 co
 constexpr int NSTAGE_WARPS = 7;        // warp 0: copies + MMA issue; warps 1-7: staging; warps 8-11: epilogue
 constexpr int EPI_WARP0 = 1 + NSTAGE_WARPS;
 constexpr int THREADS = (EPI_WARP0 + 4) * 32;
-constexpr int NB = 5;                  // depth of the A/B ring (one slot per basis row iy)
-constexpr int PREF = 2;                // basis tiles are requested PREF rows ahead (PREF < NB - 1 keeps two MMA batches queued)
+constexpr int NB = 5;                  // staged-row ring (one slot per basis row iy)
+constexpr int NBB = 8;                 // basis-tile ring: copies run PREF_B rows ahead to hide L2 latency
+constexpr int PREF_B = NBB - 2;
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 struct Smem {
   uint8_t raw[2][CMAX][KS][RAWW * 2];  // image rows of a tile (bulk copies, prefetched one tile ahead)
-  uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows, one slot per basis row
-  uint8_t B[NB][KP / 8 * 16 * 128];    // basis tiles (up to NP = 128)
-  float wt[TM * 100];                  // FP32 weights of the current tile (K <= 100, K % 4 == 0)
-  uint64_t raw_full[2];
-  uint64_t a_full[NB], b_full[NB], slot_free[NB];
-  uint64_t acc_full[NSLOT], acc_empty[NSLOT];
+  uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows
+  uint8_t B[NBB][KP / 8 * 16 * 128];   // basis tiles (up to NP = 128)
   float csum[128];
-  uint64_t w_full, w_empty;
+  uint64_t raw_full[2];
+  uint64_t a_full[NB], slot_free[NB];
+  uint64_t b_full[NBB], b_free[NBB];
+  uint64_t acc_full[NSLOT], acc_empty[NSLOT];
   uint32_t tmem_base;
   int abort;
 };
@@ -145,15 +145,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
     for (int i = 0; i < 2; ++i) umma::mbar_init(&s.raw_full[i], 1);
     for (int i = 0; i < NB; ++i) {
       umma::mbar_init(&s.a_full[i], NSTAGE_WARPS);
-      umma::mbar_init(&s.b_full[i], 1);
       umma::mbar_init(&s.slot_free[i], 1);
+    }
+    for (int i = 0; i < NBB; ++i) {
+      umma::mbar_init(&s.b_full[i], 1);
+      umma::mbar_init(&s.b_free[i], 1);
     }
     for (int i = 0; i < NSLOT; ++i) {
       umma::mbar_init(&s.acc_full[i], 1);
       umma::mbar_init(&s.acc_empty[i], 4);
     }
-    umma::mbar_init(&s.w_full, 1);
-    umma::mbar_init(&s.w_empty, 4);
     s.abort = 0;
     umma::fence_mbar_init();
   }
@@ -188,8 +189,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
       uint32_t b_issued = 0;
       bool ok = true;
       auto issue_b = [&](uint32_t v) {
-        const int b = v % NB;
-        if (v >= NB && !umma::mbar_wait(&s.slot_free[b], ((v / NB) - 1) & 1, kWaitNs)) ok = false;
+        const int b = v % NBB;
+        if (v >= NBB && !umma::mbar_wait(&s.b_free[b], ((v / NBB) - 1) & 1, kWaitNs)) ok = false;
         umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
         umma::bulk_g2s(s.B[b], Bt + (size_t)(v % KS) * (NP * KP), bt_bytes, &s.b_full[b]);
       };
@@ -199,16 +200,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
         // raw buffer (t+1)&1 was last read by the staging of tile t-1, all of whose slots were consumed
         if (t + 1 < my_tiles) issue_raw(t + 1);
         for (int iy = 0; iy < KS && ok; ++iy, ++it) {
-          while (b_issued < total_iters && b_issued <= it + PREF && ok) issue_b(b_issued++);
+          while (b_issued < total_iters && b_issued <= it + PREF_B && ok) issue_b(b_issued++);
           const int sb = it % NB;
+          const int bb = it % NBB;
           if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs) ||
-              !umma::mbar_wait(&s.b_full[sb], (it / NB) & 1, kWaitNs)) {
+              !umma::mbar_wait(&s.b_full[bb], (it / NBB) & 1, kWaitNs)) {
             ok = false;
             break;
           }
           umma::fence_after_sync();
           const uint32_t a0 = umma::smem_u32(s.A[sb][0]);
-          const uint32_t b0 = umma::smem_u32(s.B[sb]);
+          const uint32_t b0 = umma::smem_u32(s.B[bb]);
           for (int c = 0; c < C; ++c) {
             const uint32_t g = (uint32_t)(t * C + c);  // accumulator use number; slot g % NSLOT
             const int slot = g % NSLOT;
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
           }
           if (!ok) break;
           umma::mma_commit(&s.slot_free[sb]);
+          umma::mma_commit(&s.b_free[bb]);
           if (iy == KS - 1)
             for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
         }
@@ -236,8 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
         atomicExch(err, 1);
       }
       // drain: wait (bounded) for every bulk copy issued and for the last MMAs
-      for (uint32_t v = (it >= NB ? it - NB : 0); v < b_issued; ++v)
-        if (v >= it) umma::mbar_wait(&s.b_full[v % NB], (v / NB) & 1, kWaitNs);
+      for (uint32_t v = it; v < b_issued; ++v) umma::mbar_wait(&s.b_full[v % NBB], (v / NBB) & 1, kWaitNs);
       if (it >= 1) umma::mbar_wait(&s.slot_free[(it - 1) % NB], ((it - 1) / NB) & 1, kWaitNs);
     }
   } else if (warp <= NSTAGE_WARPS) {
@@ -274,74 +276,59 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   } else {
     // ---------------------------------------------------------- epilogue: TMEM -> weighted sums
     const int q4 = warp & 3;  // warp w reads TMEM lanes 32 (w % 4) ..
-    const int etid = tid - EPI_WARP0 * 32;
-    // weights of a tile: one contiguous run of nlive * K floats (issued one tile ahead)
-    auto issue_w = [&](int t_local) {
-      int y, x0;
-      tile_xy(t_local, y, x0);
-      const int nlive = min(TM, W - x0);
-      const uint32_t bytes = (uint32_t)(nlive * K * 4);
-      umma::mbar_arrive_expect_tx(&s.w_full, bytes);
-      umma::bulk_g2s(s.wt, reinterpret_cast<const float*>(w) + ((size_t)y * W + x0) * K, bytes, &s.w_full);
-    };
-    if (w_smem && etid == 0 && my_tiles > 0) issue_w(0);
     for (int t = 0; t < my_tiles; ++t) {
       int y, x0;
       tile_xy(t, y, x0);
       const int x = x0 + q4 * 32 + lane;
       const bool live = x < W;
       const size_t pix = (size_t)y * W + (live ? x : 0);
-      if (w_smem && !umma::mbar_wait(&s.w_full, t & 1, kWaitNs)) s.abort = 1;
-      const float* wrow = s.wt + (size_t)(q4 * 32 + lane) * K;
       const WT* wg = w + pix * K;
-      float acc[CMAX] = {0.f, 0.f, 0.f};
+      int slot[CMAX];
       for (int c = 0; c < C; ++c) {
         const uint32_t g = (uint32_t)(t * C + c);
-        const int slot = g % NSLOT;
-        if (!umma::mbar_wait(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
-        if (s.abort) break;
-        umma::fence_after_sync();
-        float a = 0.f;
-        for (int q = 0; q < NP / 16; ++q) {
-          float d[16];
-          umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + slot * NP + q * 16, d);
-          if (w_smem) {
-#pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4) {
-              const int k = q * 16 + 4 * i4;
-              if (k < K) {
-                const float4 wk = live ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-                a = fmaf(wk.x, d[4 * i4 + 0] + s.csum[k + 0], a);
-                a = fmaf(wk.y, d[4 * i4 + 1] + s.csum[k + 1], a);
-                a = fmaf(wk.z, d[4 * i4 + 2] + s.csum[k + 2], a);
-                a = fmaf(wk.w, d[4 * i4 + 3] + s.csum[k + 3], a);
-              }
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int k = q * 16 + i;
-              if (k < K) a = fmaf(wload<WT>(wg + k), d[i] + s.csum[k], a);
-            }
-          }
-        }
-        acc[c] = a;
-        umma::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&s.acc_empty[slot]);
+        slot[c] = g % NSLOT;
+        if (!umma::mbar_wait(&s.acc_full[slot[c]], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
       }
       if (s.abort) break;
-      // this warp is done with the tile's weights; once all four are, fetch the next tile's
-      if (w_smem) {
-        __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&s.w_empty);
-        if (etid == 0 && t + 1 < my_tiles) {
-          if (!umma::mbar_wait(&s.w_empty, t & 1, kWaitNs)) s.abort = 1;
-          else issue_w(t + 1);
+      umma::fence_after_sync();
+      float acc[CMAX] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < NP / 16; ++q) {
+        float wk[16];
+        if (w_smem) {  // 16-byte aligned FP32 rows: four vector loads
+#pragma unroll
+          for (int i4 = 0; i4 < 4; ++i4) {
+            const int k = q * 16 + 4 * i4;
+            const float4 v = k < K ? __ldg(reinterpret_cast<const float4*>(wg) + (k >> 2)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            wk[4 * i4 + 0] = v.x;
+            wk[4 * i4 + 1] = v.y;
+            wk[4 * i4 + 2] = v.z;
+            wk[4 * i4 + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int k = q * 16 + i;
+            wk[i] = k < K ? wload<WT>(wg + k) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c) {
+          if (c < C) {
+            float d[16];
+            umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + slot[c] * NP + q * 16, d);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[c] = fmaf(wk[i], d[i] + s.csum[q * 16 + i], acc[c]);
+          }
         }
       }
+      umma::fence_before_sync();
+      __syncwarp();
+      if (lane == 0)
+        for (int c = 0; c < C; ++c) umma::mbar_arrive(&s.acc_empty[slot[c]]);
       if (live) {
-        for (int c = 0; c < C; ++c) out[((size_t)c * H + y) * W + x] = acc[c];
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c)
+          if (c < C) out[((size_t)c * H + y) * W + x] = acc[c];
       }
     }
   }
@@ -393,8 +380,8 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
   static_assert(sizeof(Smem) + 1024 > 116 * 1024 && sizeof(Smem) + 1024 < 227 * 1024, "smem layout");
   cudaFuncSetAttribute(k_blur_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  // weights through shared memory when a tile's run of FP32 weights fits and is 16-byte aligned
-  const int w_smem = (w_dtype == DFP2S_W_F32) && K <= 100 && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
+  // FP32 weights in 16-byte aligned rows are read with vector loads
+  const int w_smem = (w_dtype == DFP2S_W_F32) && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
   for (int c0 = 0; c0 < C; c0 += CMAX) {
     const int nc = C - c0 < CMAX ? C - c0 : CMAX;
     const __nv_bfloat16* pc = p->pad + (size_t)c0 * (H + 32) * Wp;
