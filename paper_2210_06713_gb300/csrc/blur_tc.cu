@@ -42,19 +42,20 @@ constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
 constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
 constexpr int CMAX = 3;                // channels per pass
 constexpr int NSLOT = 4;               // TMEM accumulator slots of NP <= 128 columns (512 in all)
-constexpr int NSTAGE_WARPS = 7;        // warp 0: copies + MMA issue; warps 1-7: staging; warps 8-11: epilogue
+constexpr int NSTAGE_WARPS = 3;        // warp 0: copies + MMA issue; warps 1-3: staging; warps 4-7: epilogue
 constexpr int EPI_WARP0 = 1 + NSTAGE_WARPS;
 constexpr int THREADS = (EPI_WARP0 + 4) * 32;
-constexpr int NB = 5;                  // staged-row ring (one slot per basis row iy)
-constexpr int NBB = 8;                 // basis-tile ring: copies run PREF_B rows ahead to hide L2 latency
+constexpr int NB = 4;                  // staged-row ring (one slot per basis row iy)
+constexpr int NBB = 4;                 // basis-tile ring: copies run PREF_B rows ahead
 constexpr int PREF_B = NBB - 2;
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
+constexpr int B_SLOT = KP / 8 * 16 * 128;  // bytes of one basis-tile slot
 
 struct Smem {
   uint8_t raw[2][CMAX][KS][RAWW * 2];  // image rows of a tile (bulk copies, prefetched one tile ahead)
   uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows
-  uint8_t B[NBB][KP / 8 * 16 * 128];   // basis tiles (up to NP = 128)
+  uint8_t B[NBB][B_SLOT];              // basis tiles (up to NP = 128)
   float csum[128];
   uint64_t raw_full[2];
   uint64_t a_full[NB], slot_free[NB];
@@ -195,6 +196,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
         umma::bulk_g2s(s.B[b], Bt + (size_t)(v % KS) * (NP * KP), bt_bytes, &s.b_full[b]);
       };
       if (my_tiles > 0) issue_raw(0);
+      // A tile (slot 0, channel 0): core matrices 128 B apart along M and K (Hankel blocks);
+      // B tile [j][g][8][8]: K-adjacent core matrices 128 B apart, 8-filter groups 768 B apart
+      const uint64_t a_base = umma::sdesc(umma::smem_u32(s.A[0][0]), 128, 128);
+      const uint64_t b_base = umma::sdesc(umma::smem_u32(s.B[0]), 128, 768);
       uint32_t it = 0;
       for (int t = 0; t < my_tiles && ok; ++t) {
         // raw buffer (t+1)&1 was last read by the staging of tile t-1, all of whose slots were consumed
@@ -209,9 +214,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
             break;
           }
           umma::fence_after_sync();
-          const uint32_t a0 = umma::smem_u32(s.A[sb][0]);
-          const uint32_t b0 = umma::smem_u32(s.B[bb]);
-          for (int c = 0; c < C; ++c) {
+          // descriptors = base descriptor + (byte offset >> 4): forming each one from scratch in the
+          // issue loop costs more than the MMA itself
+          const uint64_t a_it = a_base + (uint64_t)(((uint32_t)sb * (CMAX * ROWB)) >> 4);
+          const uint64_t b_it = b_base + (uint64_t)(((uint32_t)bb * B_SLOT) >> 4);
+#pragma unroll
+          for (int c = 0; c < CMAX; ++c) {
+            if (c >= C) break;
             const uint32_t g = (uint32_t)(t * C + c);  // accumulator use number; slot g % NSLOT
             const int slot = g % NSLOT;
             if (iy == 0 && g >= NSLOT && !umma::mbar_wait(&s.acc_empty[slot], ((g / NSLOT) - 1) & 1, kWaitNs)) {
@@ -219,13 +228,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
               break;
             }
             if (iy == 0) umma::fence_after_sync();
-#pragma unroll
-            for (int ks = 0; ks < KP / 16; ++ks) {
-              const uint64_t ad = umma::sdesc(a0 + c * ROWB + ks * 256, 128, 128);
-              // B tile [j][g][8][8]: K-adjacent core matrices 128 B apart, 8-filter groups 768 B apart
-              const uint64_t bd = umma::sdesc(b0 + ks * 256, 128, 768);
-              umma::mma_bf16(tmem + slot * NP, ad, bd, idesc, (iy | ks) != 0);
-            }
+            const uint32_t d = tmem + slot * NP;
+            const uint64_t a_c = a_it + (uint64_t)((c * ROWB) >> 4);
+            umma::mma_bf16(d, a_c, b_it, idesc, iy != 0);
+            umma::mma_bf16(d, a_c + 16, b_it + 16, idesc, 1);
+            umma::mma_bf16(d, a_c + 32, b_it + 32, idesc, 1);
           }
           if (!ok) break;
           umma::mma_commit(&s.slot_free[sb]);

@@ -123,6 +123,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     umma::mbar_arrive_expect_tx(&s.w1_full, HID * KX * 2);
     umma::bulk_g2s(s.W1, w1t, HID * KX * 2, &s.w1_full);
   }
+  // operand descriptors (K-major, no swizzle): X and W1 with 6 K groups per 8-row group,
+  // H with 32, weight chunks with 8; per-MMA descriptors add (byte offset >> 4)
+  const uint64_t x_desc = umma::sdesc(umma::smem_u32(s.X), 128, 768);
+  const uint64_t w1_desc = umma::sdesc(umma::smem_u32(s.W1), 128, 768);
+  const uint64_t h_desc = umma::sdesc(umma::smem_u32(s.H), 128, 4096);
+  const uint64_t ring_desc = umma::sdesc(umma::smem_u32(s.ring[0]), 128, 1024);
   const uint32_t idesc1 = umma::idesc_bf16(TM, HID);
   const uint32_t idesc3 = umma::idesc_bf16(TM, NP3);
   uint32_t u_issue = 0;  // weight chunks issued (bulk copies)
@@ -170,10 +176,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         s.abort = 1;
       } else {
         umma::fence_after_sync();
-        const uint32_t xa = umma::smem_u32(s.X), wa = umma::smem_u32(s.W1);
-        for (int ks = 0; ks < KX / 16; ++ks)
-          umma::mma_bf16(tmem, umma::sdesc(xa + ks * 256, 128, 768), umma::sdesc(wa + ks * 256, 128, 768), idesc1,
-                         ks != 0);
+#pragma unroll
+        for (int ks = 0; ks < KX / 16; ++ks) umma::mma_bf16(tmem, x_desc + 16 * ks, w1_desc + 16 * ks, idesc1, ks != 0);
         umma::mma_commit(&s.layer_done);
       }
     }
@@ -192,7 +196,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int layer = 2; layer <= 3; ++layer) {
       if (tid == 0) {
         umma::fence_after_sync();
-        const uint32_t ha = umma::smem_u32(s.H);
         for (int c = 0; c < 4; ++c) {
           const uint32_t u = u_use++;
           const int b = u % NRING;
@@ -200,13 +203,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             s.abort = 1;
             break;
           }
-          const uint32_t ba = umma::smem_u32(s.ring[b]);
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint64_t ad = umma::sdesc(ha + (c * 8 + ks * 2) * 128, 128, 4096);
-            const uint64_t bd = umma::sdesc(ba + ks * 256, 128, 1024);
-            if (layer == 2) umma::mma_bf16(tmem + 256, ad, bd, idesc1, (c | ks) != 0);
-            else umma::mma_bf16(tmem, ad, bd, idesc3, (c | ks) != 0);
-          }
+          // descriptors = base + (byte offset >> 4)
+          const uint64_t a_c = h_desc + (uint64_t)(c * 8 * 8);
+          const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
+          const uint32_t d = layer == 2 ? tmem + 256 : tmem;
+          const uint32_t id = layer == 2 ? idesc1 : idesc3;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, (c | ks) != 0);
           umma::mma_commit(&s.empty[b]);
           // keep the ring full (the next tile's chunks too)
           while (u_issue < u_use + NRING && !s.abort) issue(u_issue++);
