@@ -42,12 +42,13 @@ constexpr int NBLK = TM / 8 + KP / 8 - 1;  // 21 staged 8x8 blocks per image row
 constexpr int ROWB = NBLK * 128;       // 2688 bytes per staged row
 constexpr int CMAX = 3;                // channels per pass
 constexpr int NSLOT = 4;               // TMEM accumulator slots of NP <= 128 columns (512 in all)
-constexpr int NSTAGE_WARPS = 3;        // warp 0: copies + MMA issue; warps 1-3: staging; warps 4-7: epilogue
-constexpr int EPI_WARP0 = 1 + NSTAGE_WARPS;
+// warp 0: bulk copies; warp 1: MMA issue; warps 2-7: staging; warps 8-11: epilogue (TMEM lane quarters 0-3)
+constexpr int STAGE_WARP0 = 2;
+constexpr int NSTAGE_WARPS = 6;
+constexpr int EPI_WARP0 = STAGE_WARP0 + NSTAGE_WARPS;
 constexpr int THREADS = (EPI_WARP0 + 4) * 32;
 constexpr int NB = 4;                  // staged-row ring (one slot per basis row iy)
-constexpr int NBB = 4;                 // basis-tile ring: copies run PREF_B rows ahead
-constexpr int PREF_B = NBB - 2;
+constexpr int NBB = 4;                 // basis-tile ring
 constexpr int RAWW = TM + KP;          // 176 staged image columns per row
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 constexpr int B_SLOT = KP / 8 * 16 * 128;  // bytes of one basis-tile slot
@@ -57,7 +58,7 @@ struct Smem {
   uint8_t A[NB][CMAX][ROWB];           // Hankel-blocked rows
   uint8_t B[NBB][B_SLOT];              // basis tiles (up to NP = 128)
   float csum[128];
-  uint64_t raw_full[2];
+  uint64_t raw_full[2], raw_empty[2];
   uint64_t a_full[NB], slot_free[NB];
   uint64_t b_full[NBB], b_free[NBB];
   uint64_t acc_full[NSLOT], acc_empty[NSLOT];
@@ -124,10 +125,8 @@ __global__ void k_scale(float* __restrict__ v, int n, float a) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] *= a;
 }
 
-DFP2S_DEV uint32_t shr16(uint32_t lo, uint32_t hi) { return __funnelshift_r(lo, hi, 16); }
-
-template <typename WT>
-__global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __restrict__ P, int C, int H, int W,
+template <typename WT, int C>
+__global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __restrict__ P, int H, int W,
                                                         int Wp, const __nv_bfloat16* __restrict__ Bt, int K, int NP,
                                                         const float* __restrict__ csum, const WT* __restrict__ w,
                                                         int w_smem, float* __restrict__ out, int* __restrict__ err) {
@@ -140,10 +139,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   const int nseg = (W + TM - 1) / TM;
   const int ntiles = H * nseg;
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const uint32_t total_iters = (uint32_t)my_tiles * KS;
 
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) umma::mbar_init(&s.raw_full[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      umma::mbar_init(&s.raw_full[i], 1);
+      umma::mbar_init(&s.raw_empty[i], NSTAGE_WARPS);
+    }
     for (int i = 0; i < NB; ++i) {
       umma::mbar_init(&s.a_full[i], NSTAGE_WARPS);
       umma::mbar_init(&s.slot_free[i], 1);
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   };
 
   if (warp == 0) {
-    // ---------------------------------------------------------- copies + MMA issue (one lane)
+    // ---------------------------------------------------------- bulk copies (one lane)
     if (lane == 0) {
       auto issue_raw = [&](int t_local) {
         int y, x0;
@@ -187,25 +188,54 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
             umma::bulk_g2s(s.raw[rb][c][ri], P + ((size_t)c * (H + 32) + y + ri) * Wp + x0, RAWW * 2,
                            &s.raw_full[rb]);
       };
-      uint32_t b_issued = 0;
       bool ok = true;
-      auto issue_b = [&](uint32_t v) {
-        const int b = v % NBB;
-        if (v >= NBB && !umma::mbar_wait(&s.b_free[b], ((v / NBB) - 1) & 1, kWaitNs)) ok = false;
-        umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
-        umma::bulk_g2s(s.B[b], Bt + (size_t)(v % KS) * (NP * KP), bt_bytes, &s.b_full[b]);
-      };
-      if (my_tiles > 0) issue_raw(0);
+      uint32_t v = 0;  // basis tiles issued
+      int raw_issued = 0;
+      if (my_tiles > 0) {
+        issue_raw(0);
+        raw_issued = 1;
+      }
+      for (int t = 0; t < my_tiles && ok; ++t) {
+        for (int iy = 0; iy < KS && ok; ++iy, ++v) {
+          // the next tile's image rows go out a quarter of the way into this tile, into the raw buffer
+          // whose previous tile (t - 1) finished staging before the MMAs of this tile began
+          if (iy == KS / 4 && t + 1 < my_tiles) {
+            if (t >= 1 && !umma::mbar_wait(&s.raw_empty[(t + 1) & 1], ((t - 1) >> 1) & 1, kWaitNs)) {
+              ok = false;
+              break;
+            }
+            issue_raw(t + 1);
+            raw_issued = t + 2;
+          }
+          const int b = v % NBB;
+          if (v >= NBB && !umma::mbar_wait(&s.b_free[b], ((v / NBB) - 1) & 1, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
+          umma::bulk_g2s(s.B[b], Bt + (size_t)iy * (NP * KP), bt_bytes, &s.b_full[b]);
+        }
+      }
+      if (!ok) {
+        s.abort = 1;
+        atomicExch(err, 1);
+      }
+      // every issued copy must land before the CTA exits (bounded)
+      for (uint32_t u = (v >= NBB ? v - NBB : 0); u < v; ++u) umma::mbar_wait(&s.b_full[u % NBB], (u / NBB) & 1, kWaitNs);
+      for (int t = (raw_issued >= 2 ? raw_issued - 2 : 0); t < raw_issued; ++t)
+        umma::mbar_wait(&s.raw_full[t & 1], (t >> 1) & 1, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issue (one lane)
+    if (lane == 0) {
       // A tile (slot 0, channel 0): core matrices 128 B apart along M and K (Hankel blocks);
       // B tile [j][g][8][8]: K-adjacent core matrices 128 B apart, 8-filter groups 768 B apart
       const uint64_t a_base = umma::sdesc(umma::smem_u32(s.A[0][0]), 128, 128);
       const uint64_t b_base = umma::sdesc(umma::smem_u32(s.B[0]), 128, 768);
+      bool ok = true;
       uint32_t it = 0;
       for (int t = 0; t < my_tiles && ok; ++t) {
-        // raw buffer (t+1)&1 was last read by the staging of tile t-1, all of whose slots were consumed
-        if (t + 1 < my_tiles) issue_raw(t + 1);
-        for (int iy = 0; iy < KS && ok; ++iy, ++it) {
-          while (b_issued < total_iters && b_issued <= it + PREF_B && ok) issue_b(b_issued++);
+        for (int iy = 0; iy < KS; ++iy, ++it) {
           const int sb = it % NB;
           const int bb = it % NBB;
           if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs) ||
@@ -213,31 +243,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
             ok = false;
             break;
           }
+          if (iy == 0) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const uint32_t g = (uint32_t)(t * C + c);
+              if (g >= NSLOT && !umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) ok = false;
+            }
+            if (!ok) break;
+          }
           umma::fence_after_sync();
           // descriptors = base descriptor + (byte offset >> 4): forming each one from scratch in the
           // issue loop costs more than the MMA itself
           const uint64_t a_it = a_base + (uint64_t)(((uint32_t)sb * (CMAX * ROWB)) >> 4);
           const uint64_t b_it = b_base + (uint64_t)(((uint32_t)bb * B_SLOT) >> 4);
+          const uint32_t acc = iy != 0;
 #pragma unroll
-          for (int c = 0; c < CMAX; ++c) {
-            if (c >= C) break;
-            const uint32_t g = (uint32_t)(t * C + c);  // accumulator use number; slot g % NSLOT
-            const int slot = g % NSLOT;
-            if (iy == 0 && g >= NSLOT && !umma::mbar_wait(&s.acc_empty[slot], ((g / NSLOT) - 1) & 1, kWaitNs)) {
-              ok = false;
-              break;
-            }
-            if (iy == 0) umma::fence_after_sync();
-            const uint32_t d = tmem + slot * NP;
+          for (int c = 0; c < C; ++c) {
+            const uint32_t d = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
             const uint64_t a_c = a_it + (uint64_t)((c * ROWB) >> 4);
-            umma::mma_bf16(d, a_c, b_it, idesc, iy != 0);
+            umma::mma_bf16(d, a_c, b_it, idesc, acc);
             umma::mma_bf16(d, a_c + 16, b_it + 16, idesc, 1);
             umma::mma_bf16(d, a_c + 32, b_it + 32, idesc, 1);
           }
-          if (!ok) break;
           umma::mma_commit(&s.slot_free[sb]);
           umma::mma_commit(&s.b_free[bb]);
           if (iy == KS - 1)
+#pragma unroll
             for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
         }
       }
@@ -245,13 +276,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
         s.abort = 1;
         atomicExch(err, 1);
       }
-      // drain: wait (bounded) for every bulk copy issued and for the last MMAs
-      for (uint32_t v = it; v < b_issued; ++v) umma::mbar_wait(&s.b_full[v % NBB], (v / NBB) & 1, kWaitNs);
       if (it >= 1) umma::mbar_wait(&s.slot_free[(it - 1) % NB], ((it - 1) / NB) & 1, kWaitNs);
     }
-  } else if (warp <= NSTAGE_WARPS) {
+  } else if (warp < EPI_WARP0) {
     // ---------------------------------------------------------- staging: Hankel blocks from raw rows
-    const int st_tid = tid - 32;
+    const int st_tid = tid - STAGE_WARP0 * 32;
     uint32_t it = 0;
     for (int t = 0; t < my_tiles; ++t) {
       const int rb = t & 1;
@@ -279,6 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
         if (lane == 0) umma::mbar_arrive(&s.a_full[sb]);
       }
       if (s.abort) break;
+      if (lane == 0) umma::mbar_arrive(&s.raw_empty[rb]);
     }
   } else {
     // ---------------------------------------------------------- epilogue: TMEM -> weighted sums
@@ -385,20 +415,32 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
   // allocation) per SM
   const size_t sm = sizeof(Smem) + 1024;
   static_assert(sizeof(Smem) + 1024 > 116 * 1024 && sizeof(Smem) + 1024 < 227 * 1024, "smem layout");
-  cudaFuncSetAttribute(k_blur_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   // FP32 weights in 16-byte aligned rows are read with vector loads
   const int w_smem = (w_dtype == DFP2S_W_F32) && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
   for (int c0 = 0; c0 < C; c0 += CMAX) {
     const int nc = C - c0 < CMAX ? C - c0 : CMAX;
     const __nv_bfloat16* pc = p->pad + (size_t)c0 * (H + 32) * Wp;
     float* oc = out + (size_t)c0 * H * W;
-    if (w_dtype == DFP2S_W_BF16)
-      k_blur_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum,
-                                                         (const __nv_bfloat16*)w, 0, oc, p->err);
-    else
-      k_blur_tc<float><<<grid, THREADS, sm, st>>>(pc, nc, H, W, Wp, p->bt, K, NP, p->bsum, (const float*)w, w_smem,
-                                                 oc, p->err);
+#define DFP2S_BLUR_LAUNCH(WT, NC, WPTR, WSM) \
+  k_blur_tc<WT, NC><<<grid, THREADS, sm, st>>>(pc, H, W, Wp, p->bt, K, NP, p->bsum, WPTR, WSM, oc, p->err)
+    if (w_dtype == DFP2S_W_BF16) {
+      const __nv_bfloat16* wb = (const __nv_bfloat16*)w;
+      if (nc == 1) DFP2S_BLUR_LAUNCH(__nv_bfloat16, 1, wb, 0);
+      else if (nc == 2) DFP2S_BLUR_LAUNCH(__nv_bfloat16, 2, wb, 0);
+      else DFP2S_BLUR_LAUNCH(__nv_bfloat16, 3, wb, 0);
+    } else {
+      const float* wf = (const float*)w;
+      if (nc == 1) DFP2S_BLUR_LAUNCH(float, 1, wf, w_smem);
+      else if (nc == 2) DFP2S_BLUR_LAUNCH(float, 2, wf, w_smem);
+      else DFP2S_BLUR_LAUNCH(float, 3, wf, w_smem);
+    }
+#undef DFP2S_BLUR_LAUNCH
   }
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
