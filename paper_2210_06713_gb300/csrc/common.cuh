@@ -5,8 +5,7 @@
 //    so that every value is reproducible bit for bit on any IEEE FP32 machine:
 //    each step is one correctly rounded operation (__fmul_rn, __fadd_rn, ...),
 //    so no multiply-add is ever contracted.
-//  * complex helpers and a shared-memory Stockham FFT in which every thread
-//    keeps 8 complex values in registers (radix-8/4/2 stages).
+//  * complex helpers and fixed DFTs of length 2, 4 and 8 in registers.
 //  * status codes and launch-error checks used by the host code.
 #pragma once
 
@@ -177,73 +176,6 @@ DFP2S_DEV void dft8(float2* v) {
   v[6] = csub(e2, o2);
   v[3] = cadd(e3, o3);
   v[7] = csub(e3, o3);
-}
-
-// Shared-memory index with one pad slot every 8 entries (breaks the stride-8
-// bank conflicts of the Stockham scatter).
-DFP2S_DEV int fpad(int i) { return i + (i >> 3); }
-__host__ __device__ constexpr int fpad_size(int n) { return n + (n >> 3); }
-
-// One Stockham autosort stage (Govindaraju et al., SC 2008) of an FFT of
-// length N held in shared memory `buf` (padded with fpad): with sub-transform
-// length Ns and radix R it reads x[j + r N/R], multiplies by the twiddles
-// w^(r k), k = j mod Ns, w = exp(-+2 pi i / (Ns R)), does a DFT-R and writes
-// y[(j - k) R + k + r Ns].  The NT = N/8 threads of the group each own 8 values
-// (8/R butterflies), so a stage is load -> barrier -> compute -> store ->
-// barrier and runs in place.  `tw` holds exp(-2 pi i m / N), m in [0, N),
-// rounded from FP64.
-template <int R, bool INV, typename Sync>
-DFP2S_DEV void fft_stage(float2* buf, int N, int Ns, int t, const float2* __restrict__ tw, Sync sync) {
-  constexpr int PER = 8 / R;
-  const int nb = N >> 3;
-  const int nbutter = N / R;
-  float2 v[8];
-#pragma unroll
-  for (int bi = 0; bi < PER; ++bi)
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[bi * R + r] = buf[fpad(t + bi * nb + r * nbutter)];
-  sync();
-#pragma unroll
-  for (int bi = 0; bi < PER; ++bi) {
-    const int j = t + bi * nb;
-    const int k = j & (Ns - 1);
-    if (Ns > 1) {
-      const int step = N / (Ns * R);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const float2 w = __ldg(tw + r * k * step);
-        v[bi * R + r] = INV ? cmulc(v[bi * R + r], w) : cmul(v[bi * R + r], w);
-      }
-    }
-    if (R == 8) dft8<INV>(v + bi * R);
-    else if (R == 4) dft4<INV>(v[bi * R], v[bi * R + 1], v[bi * R + 2], v[bi * R + 3]);
-    else dft2<INV>(v[bi * R], v[bi * R + 1]);
-  }
-#pragma unroll
-  for (int bi = 0; bi < PER; ++bi) {
-    const int j = t + bi * nb;
-    const int k = j & (Ns - 1);
-    const int base = (j - k) * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) buf[fpad(base + r * Ns)] = v[bi * R + r];
-  }
-  sync();
-}
-
-// Full FFT of length N (power of two, 8 <= N <= 4096), unnormalised: radix-8
-// stages, then one radix-4 or radix-2 stage for the rest.  The caller must have
-// made `buf` visible to the group (barrier) before the call.
-template <bool INV, typename Sync>
-DFP2S_DEV void fft_smem(float2* buf, int N, int t, const float2* __restrict__ tw, Sync sync) {
-  int Ns = 1;
-  int rem = N;
-  while (rem >= 8) {
-    fft_stage<8, INV>(buf, N, Ns, t, tw, sync);
-    Ns *= 8;
-    rem >>= 3;
-  }
-  if (rem == 4) fft_stage<4, INV>(buf, N, Ns, t, tw, sync);
-  else if (rem == 2) fft_stage<2, INV>(buf, N, Ns, t, tw, sync);
 }
 
 // ------------------------------------------------------------- host helpers

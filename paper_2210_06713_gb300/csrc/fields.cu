@@ -3,155 +3,197 @@
 // -> crop -> pixel-wise mixing by L.
 //
 // Three passes over a per-factor scratch spectrum S[j][kx][y] (complex FP32,
-// kx in [0, N/2], y in [0, N); column-major in the sense that a frequency
-// column is contiguous):
-//   k_rowfft_noise  Philox noise made in registers, two real rows packed as one
-//                   complex FFT, split into the two half spectra, written
-//                   transposed so the column pass reads contiguous columns;
-//   k_colfilter     column FFT, multiply by sqrt(lambda_j)/N^2, inverse column
-//                   FFT, keep rows y < H (written in place);
-//   k_rowifft       rows y < H: Hermitian completion of two rows packed as one
-//                   complex spectrum, inverse FFT, crop to W, write fields;
+// kx in [0, N/2], y in [0, N); a frequency column is contiguous), each FFT
+// done in registers by a group of threads (fft_reg.cuh):
+//   k_rowfft_noise  Philox noise for two real rows, packed as one complex row
+//                   z = a + i b, forward FFT, split into the two half spectra;
+//                   a block of G groups covers 2G consecutive rows and writes
+//                   them through a shared-memory tile, 16 G bytes per column;
+//   k_colfilter     one column per group: forward FFT, multiply by
+//                   sqrt(lambda_j)/N^2, inverse FFT straight from the forward
+//                   FFT's register layout, keep rows y < H (in place);
+//   k_rowifft       2G rows per block read through a tile; per row pair the
+//                   Hermitian completion of Ga + i Gb, inverse FFT, rows to the
+//                   fields, cropped to W;
 // and k_mix applies a(x) = L a~(x) in place.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "fft_reg.cuh"
 #include "kernels.h"
 
 namespace {
 
-struct BlockSync {
-  DFP2S_DEV void operator()() const { __syncthreads(); }
+using fftr::OutIndex;
+using fftr::pad32;
+using fftr::Plan;
+
+// FFT groups per block: 8 up to N = 1024, then enough for 256 threads.
+template <int N>
+struct Groups {
+  static constexpr int G = N >= 4096 ? 2 : (N >= 2048 ? 4 : 8);
+  static constexpr int THREADS = G * Plan<N>::T;
+  static constexpr int BUFE = (Plan<N>::BUF + 1) / 2 * 2;  // even: 16-byte aligned group buffers
+  static constexpr int TS = 2 * G + 1;                     // tile row stride (complex), odd against conflicts
+  static constexpr size_t smem_fft = (size_t)G * BUFE * sizeof(float2);
+  static constexpr size_t smem_tile = (size_t)(N / 2 + 1) * TS * sizeof(float2);
+  static constexpr size_t smem = smem_fft > smem_tile ? smem_fft : smem_tile;
 };
 
-// FFTs per CTA so that one CTA holds 8192 complex values (1024 threads at N/8
-// threads per FFT).
-inline int ffts_per_cta(int N) {
-  int f = 8192 / N;
-  return f > 8 ? 8 : (f < 1 ? 1 : f);
-}
-
 // -------------------------------------------------------------- pass 1
-__global__ void __launch_bounds__(1024) k_rowfft_noise(float2* __restrict__ S, const float2* __restrict__ tw, int N,
-                                                       int nfft, uint64_t seed, uint32_t frame) {
-  extern __shared__ float2 smem[];
-  const int nb = N >> 3;
-  const int g = threadIdx.x / nb;  // which FFT of this CTA
-  const int t = threadIdx.x - g * nb;
+template <int N>
+__global__ void __launch_bounds__(Groups<N>::THREADS) k_rowfft_noise(float2* __restrict__ S,
+                                                                     const float2* __restrict__ tw, uint64_t seed,
+                                                                     uint32_t frame) {
+  using P = Plan<N>;
+  using GR = Groups<N>;
+  constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
+  extern __shared__ __align__(16) float2 smem[];
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x - g * T;
   const int j = blockIdx.y;
-  const int rows = 2 * nfft;
-  const int y0 = blockIdx.x * rows;
-  float2* buf = smem + g * fpad_size(N);
+  const int y0 = blockIdx.x * 2 * G;
+  const int ya = y0 + 2 * g, yb = ya + 1;
+  float2* buf = smem + g * GR::BUFE;
   const uint64_t sub = dfp2s_subsequence(0u, frame, (uint32_t)j);
   {
-    // this thread makes positions 8t .. 8t+7 of rows ya = y0 + 2g and yb = ya + 1
-    const int ya = y0 + 2 * g, yb = ya + 1;
-    const uint64_t qa = ((uint64_t)ya * N + 8 * t) >> 2;
-    const uint64_t qb = ((uint64_t)yb * N + 8 * t) >> 2;
-    const float4 a0 = dfp2s_gauss4(seed, sub, qa), a1 = dfp2s_gauss4(seed, sub, qa + 1);
-    const float4 b0 = dfp2s_gauss4(seed, sub, qb), b1 = dfp2s_gauss4(seed, sub, qb + 1);
-    const int x = 8 * t;
-    buf[fpad(x + 0)] = make_float2(a0.x, b0.x);
-    buf[fpad(x + 1)] = make_float2(a0.y, b0.y);
-    buf[fpad(x + 2)] = make_float2(a0.z, b0.z);
-    buf[fpad(x + 3)] = make_float2(a0.w, b0.w);
-    buf[fpad(x + 4)] = make_float2(a1.x, b1.x);
-    buf[fpad(x + 5)] = make_float2(a1.y, b1.y);
-    buf[fpad(x + 6)] = make_float2(a1.z, b1.z);
-    buf[fpad(x + 7)] = make_float2(a1.w, b1.w);
+    // noise: chunk i of a row is positions 4i..4i+3 (one Philox block); staged as two float rows
+    float* bf = reinterpret_cast<float*>(buf);
+    const uint64_t qa = ((uint64_t)ya * N) >> 2, qb = ((uint64_t)yb * N) >> 2;
+#pragma unroll
+    for (int c = 0; c < V / 4; ++c) {
+      const int i = t + T * c;
+      *reinterpret_cast<float4*>(bf + 4 * i) = dfp2s_gauss4(seed, sub, qa + i);
+      *reinterpret_cast<float4*>(bf + N + 4 * i) = dfp2s_gauss4(seed, sub, qb + i);
+    }
+  }
+  fftr::group_sync<T>();
+  float2 v[V];
+  {
+    const float* bf = reinterpret_cast<const float*>(buf);
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = make_float2(bf[t + T * m], bf[N + t + T * m]);
+  }
+  fftr::group_sync<T>();
+  fftr::fft<N, false>(v, buf, t, tw);
+  // Z in natural order, then split Z = X_a + i X_b:
+  //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
+  fftr::group_sync<T>();
+#pragma unroll
+  for (int m = 0; m < V; ++m) buf[pad32(t + T * m)] = v[OutIndex<N>::reg(m)];
+  fftr::group_sync<T>();
+  constexpr int NK = V / 2 + 1;  // k = t + T m for m < V / 2, and k = N / 2 on thread 0
+  float2 xa[NK], xb[NK];
+#pragma unroll
+  for (int m = 0; m < NK; ++m) {
+    const int k = t + T * m;
+    if (m < V / 2 || t == 0) {
+      const float2 zk = buf[pad32(k)];
+      const float2 zn = buf[pad32((N - k) & (N - 1))];
+      xa[m] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+      xb[m] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+    }
+  }
+  __syncthreads();  // the tile overlays every group's buffer
+#pragma unroll
+  for (int m = 0; m < NK; ++m) {
+    const int k = t + T * m;
+    if (m < V / 2 || t == 0) {
+      smem[k * GR::TS + 2 * g] = xa[m];
+      smem[k * GR::TS + 2 * g + 1] = xb[m];
+    }
   }
   __syncthreads();
-  fft_smem<false>(buf, N, t, tw, BlockSync());
-  // split Z = X_a + i X_b:  X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
-  const int half = N / 2 + 1;
-  const int total = half * rows;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int k = idx / rows;
-    const int r = idx - k * rows;
-    const float2* zb = smem + (r >> 1) * fpad_size(N);
-    const float2 zk = zb[fpad(k)];
-    const float2 zn = zb[fpad((N - k) & (N - 1))];
-    float2 x;
-    if ((r & 1) == 0) {
-      x = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-    } else {
-      x = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
-    }
-    S[((size_t)j * half + k) * N + y0 + r] = x;
+  float2* Sj = S + (size_t)j * HALF * N;
+  for (int i = threadIdx.x; i < HALF * 2 * G; i += GR::THREADS) {
+    const int k = i / (2 * G), r = i - k * (2 * G);
+    Sj[(size_t)k * N + y0 + r] = smem[k * GR::TS + r];
   }
 }
 
 // -------------------------------------------------------------- pass 2
-__global__ void __launch_bounds__(1024) k_colfilter(float2* __restrict__ S, const float* __restrict__ mult,
-                                                    const float2* __restrict__ tw, int N, int ncol, int H) {
-  extern __shared__ float2 smem[];
-  const int nb = N >> 3;
-  const int g = threadIdx.x / nb;
-  const int t = threadIdx.x - g * nb;
+template <int N>
+__global__ void __launch_bounds__(Groups<N>::THREADS) k_colfilter(float2* __restrict__ S, const float* __restrict__ mult,
+                                                                  const float2* __restrict__ tw, int H) {
+  using P = Plan<N>;
+  using GR = Groups<N>;
+  constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
+  extern __shared__ __align__(16) float2 smem[];
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x - g * T;
   const int j = blockIdx.y;
-  const int half = N / 2 + 1;
-  const int kx = blockIdx.x * ncol + g;
-  const bool live = kx < half;
-  float2* buf = smem + g * fpad_size(N);
-  float2* col = S + ((size_t)j * half + (live ? kx : 0)) * N;
-  const float* m = mult + ((size_t)j * half + (live ? kx : 0)) * N;
-  for (int i = t; i < N; i += nb) buf[fpad(i)] = live ? col[i] : make_float2(0.f, 0.f);
-  __syncthreads();
-  fft_smem<false>(buf, N, t, tw, BlockSync());
-  for (int i = t; i < N; i += nb) {
-    const float s = live ? m[i] : 0.f;
-    buf[fpad(i)] = cscale(buf[fpad(i)], s);
+  const int kx = blockIdx.x * G + g;
+  const bool live = kx < HALF;  // dead groups still join the block-wide exchanges when T > 32
+  float2* buf = smem + g * GR::BUFE;
+  float2* col = S + ((size_t)j * HALF + (live ? kx : 0)) * N;
+  const float* mc = mult + ((size_t)j * HALF + (live ? kx : 0)) * N;
+  float2 v[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) v[m] = live ? col[t + T * m] : make_float2(0.f, 0.f);
+  fftr::fft<N, false>(v, buf, t, tw);
+  float2 u[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const float s = live ? __ldg(mc + t + T * m) : 0.f;
+    u[m] = cscale(v[OutIndex<N>::reg(m)], s);
   }
-  __syncthreads();
-  fft_smem<true>(buf, N, t, tw, BlockSync());
-  if (live)
-    for (int i = t; i < H; i += nb) col[i] = buf[fpad(i)];
+  fftr::group_sync<T>();
+  fftr::fft<N, true>(u, buf, t, tw);
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+      const int y = t + T * m;
+      if (y < H) col[y] = u[OutIndex<N>::reg(m)];
+    }
+  }
 }
 
 // -------------------------------------------------------------- pass 3
-__global__ void __launch_bounds__(1024) k_rowifft(const float2* __restrict__ S, float* __restrict__ out,
-                                                  const float2* __restrict__ tw, int N, int nfft, int H, int W) {
-  extern __shared__ float2 smem[];
-  const int nb = N >> 3;
-  const int g = threadIdx.x / nb;
-  const int t = threadIdx.x - g * nb;
+template <int N>
+__global__ void __launch_bounds__(Groups<N>::THREADS) k_rowifft(const float2* __restrict__ S, float* __restrict__ out,
+                                                                const float2* __restrict__ tw, int H, int W) {
+  using P = Plan<N>;
+  using GR = Groups<N>;
+  constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
+  extern __shared__ __align__(16) float2 smem[];
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x - g * T;
   const int j = blockIdx.y;
-  const int half = N / 2 + 1;
-  const int rows = 2 * nfft;
-  const int y0 = blockIdx.x * rows;
-  // gather: (k, pair) with the pair index fastest; each thread reads rows ya, yb of column k (16 bytes)
-  const int total = half * nfft;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int k = idx / nfft;
-    const int p = idx - k * nfft;
-    const int ya = y0 + 2 * p;
-    const float2* colp = S + ((size_t)j * half + k) * N;
-    float2 ga = make_float2(0.f, 0.f), gb = make_float2(0.f, 0.f);
-    if (ya + 1 < H) {
-      const float4 v = *reinterpret_cast<const float4*>(colp + ya);
-      ga = make_float2(v.x, v.y);
-      gb = make_float2(v.z, v.w);
-    } else if (ya < H) {
-      ga = colp[ya];
-    }
-    if (k == 0 || k == N / 2) {  // C2R convention: DC and Nyquist bins are real
-      ga.y = 0.f;
-      gb.y = 0.f;
-    }
-    float2* zb = smem + p * fpad_size(N);
-    zb[fpad(k)] = make_float2(ga.x - gb.y, ga.y + gb.x);  // Z[k] = Ga + i Gb
-    if (k > 0 && k < N / 2) zb[fpad(N - k)] = make_float2(ga.x + gb.y, gb.x - ga.y);  // conj Ga + i conj Gb
+  const int y0 = blockIdx.x * 2 * G;
+  const float2* Sj = S + (size_t)j * HALF * N;
+  for (int i = threadIdx.x; i < HALF * 2 * G; i += GR::THREADS) {
+    const int k = i / (2 * G), r = i - k * (2 * G);
+    float2 x = y0 + r < H ? Sj[(size_t)k * N + y0 + r] : make_float2(0.f, 0.f);
+    if (k == 0 || k == N / 2) x.y = 0.f;  // C2R convention: DC and Nyquist bins are real
+    smem[k * GR::TS + r] = x;
   }
   __syncthreads();
-  fft_smem<true>(smem + g * fpad_size(N), N, t, tw, BlockSync());
-  const int outs = rows * W;
-  for (int idx = threadIdx.x; idx < outs; idx += blockDim.x) {
-    const int r = idx / W;
-    const int x = idx - r * W;
-    const int y = y0 + r;
-    if (y >= H) continue;
-    const float2 z = smem[(r >> 1) * fpad_size(N) + fpad(x)];
-    out[((size_t)j * H + y) * W + x] = (r & 1) ? z.y : z.x;
+  // Z[n] = Ga[n] + i Gb[n] for n <= N/2, conj Ga[N-n] + i conj Gb[N-n] above
+  float2 v[V];
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int n = t + T * m;
+    if (n <= N / 2) {
+      const float2 ga = smem[n * GR::TS + 2 * g], gb = smem[n * GR::TS + 2 * g + 1];
+      v[m] = make_float2(ga.x - gb.y, ga.y + gb.x);
+    } else {
+      const float2 ga = smem[(N - n) * GR::TS + 2 * g], gb = smem[(N - n) * GR::TS + 2 * g + 1];
+      v[m] = make_float2(ga.x + gb.y, gb.x - ga.y);
+    }
+  }
+  __syncthreads();  // the groups' FFT buffers overlay the tile
+  fftr::fft<N, true>(v, smem + g * GR::BUFE, t, tw);
+  const int ya = y0 + 2 * g, yb = ya + 1;
+  float* oa = out + ((size_t)j * H + ya) * W;
+  float* ob = oa + W;
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int x = t + T * m;
+    if (x < W) {
+      const float2 z = v[OutIndex<N>::reg(m)];
+      if (ya < H) oa[x] = z.x;
+      if (yb < H) ob[x] = z.y;
+    }
   }
 }
 
@@ -199,21 +241,37 @@ __global__ void k_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* __rest
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
+template <int N>
+void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H, int W, uint64_t seed,
+                   uint32_t frame, float* fields, cudaStream_t st) {
+  using GR = Groups<N>;
+  constexpr int G = GR::G, HALF = N / 2 + 1;
+  const size_t sm = GR::smem;
+  if (sm > 48 * 1024) {
+    cudaFuncSetAttribute(k_rowfft_noise<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_colfilter<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_rowifft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  }
+  k_rowfft_noise<N><<<dim3(N / (2 * G), J), GR::THREADS, sm, st>>>(S, tw, seed, frame);
+  k_colfilter<N><<<dim3((HALF + G - 1) / G, J), GR::THREADS, sm, st>>>(S, mult, tw, H);
+  k_rowifft<N><<<dim3((H + 2 * G - 1) / (2 * G), J), GR::THREADS, sm, st>>>(S, fields, tw, H, W);
+}
+
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
                                cudaStream_t st) {
-  const int nfft = ffts_per_cta(N);
-  const int threads = nfft * (N / 8);
-  const size_t sm = (size_t)nfft * fpad_size(N) * sizeof(float2);
-  if (sm > 48 * 1024) {
-    cudaFuncSetAttribute(k_rowfft_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_colfilter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_rowifft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  switch (N) {
+    case 16: launch_passes<16>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 32: launch_passes<32>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 64: launch_passes<64>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 128: launch_passes<128>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 256: launch_passes<256>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 512: launch_passes<512>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 1024: launch_passes<1024>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 2048: launch_passes<2048>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 4096: launch_passes<4096>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    default: return DFP2S_EINVAL;
   }
-  const int half = N / 2 + 1;
-  k_rowfft_noise<<<dim3(N / (2 * nfft), J), threads, sm, st>>>(S, tw, N, nfft, seed, frame);
-  k_colfilter<<<dim3((half + nfft - 1) / nfft, J), threads, sm, st>>>(S, mult, tw, N, nfft, H);
-  k_rowifft<<<dim3((H + 2 * nfft - 1) / (2 * nfft), J), threads, sm, st>>>(S, fields, tw, N, nfft, H, W);
   const size_t npix = (size_t)H * W;
   const int blocks = (int)((npix + 255) / 256);
   if (J <= 16) k_mix<16><<<blocks, 256, 0, st>>>(fields, L, scale, J, npix);

@@ -74,6 +74,9 @@ def test_spectral_factor_matches_oracle(lib, J, N, ppd):
     (36, 50, 37, 128, 8.0, 3.0, 5, 9),      # ragged crop, odd height
     (15, 16, 16, 64, 2.0, 1.0, 1, 1),       # J = 15
     (36, 256, 256, 512, 8.0, 3.0, 0, 3),    # 256 x 256 workload
+    (6, 16, 9, 16, 2.0, 1.0, 4, 0),         # smallest grid: one thread per FFT
+    (10, 30, 17, 32, 2.0, 2.0, 8, 6),       # N = 32: one radix-32 pass
+    (4, 700, 1500, 2048, 8.0, 2.0, 2, 1),   # three passes (32 x 32 x 2), block-wide exchanges
 ])
 def test_fields_match_oracle(lib, J, H, W, N, ppd, d, seed, frame):
     f = lib.SpectralFactor(J, N, ppd)
@@ -90,6 +93,16 @@ def test_fields_full_size_512(lib):
     f = lib.SpectralFactor(J, N, 8.0)
     g = lib.sample_zernike_fields(f, 4.0, 11, 2, H, W).cpu().numpy()
     o = sampler.sample_fields(11, 2, J, H, W, 4.0, 8.0, N)
+    assert rel_l2(g, o) < TOL
+
+
+@pytest.mark.slow
+def test_fields_grid_4096(lib):
+    # the 3840 x 2160 workload's grid (32 x 32 x 4 passes), few modes to bound the oracle's cost
+    J, H, W, N = 3, 2160, 3840, 4096
+    f = lib.SpectralFactor(J, N, 8.0)
+    g = lib.sample_zernike_fields(f, 4.0, 1, 0, H, W).cpu().numpy()
+    o = sampler.sample_fields(1, 0, J, H, W, 4.0, 8.0, N)
     assert rel_l2(g, o) < TOL
 
 
