@@ -198,12 +198,52 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_rowifft(const float2* __
 }
 
 // ------------------------------------------------------------------- mix
-// a_i = sum_{j <= i} L_ij a~_j at every pixel, in place; JB >= J is the
-// register bucket.
+// a_i = sum_{j <= i} L_ij a~_j at every pixel, in place; JB >= J (a multiple of
+// 4) is the register bucket.  Each thread mixes a pair of adjacent pixels
+// (8-byte loads and stores; needs an even pixel count) and reads four
+// coefficients of L per shared-memory load.
 template <int JB>
-__global__ void __launch_bounds__(256) k_mix(float* __restrict__ fields, const float* __restrict__ L, float scale,
+__global__ void __launch_bounds__(128, 4) k_mix_pairs(float* __restrict__ fields, const float* __restrict__ L,
+                                                   float scale, int J, size_t npix) {
+  __shared__ __align__(16) float Ls[JB * JB];
+  for (int i = threadIdx.x; i < JB * JB; i += blockDim.x) {
+    const int r = i / JB, c = i - r * JB;
+    Ls[i] = (r < J && c < J && c <= r) ? L[r * J + c] * scale : 0.f;
+  }
+  __syncthreads();
+  const size_t p = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (p >= npix) return;
+  float2 v[JB];
+#pragma unroll
+  for (int j = 0; j < JB; ++j)
+    v[j] = j < J ? *reinterpret_cast<const float2*>(fields + (size_t)j * npix + p) : make_float2(0.f, 0.f);
+  // rows in a runtime loop (so the compiler does not hoist L into registers), the
+  // triangle's columns as uniform branches over an unrolled loop
+  for (int i = 0; i < J; ++i) {
+    float ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int j4 = 0; j4 < JB / 4; ++j4) {
+      if (4 * j4 <= i) {
+        const float4 l = *reinterpret_cast<const float4*>(Ls + i * JB + 4 * j4);
+        ax = fmaf(l.x, v[4 * j4].x, ax);
+        ay = fmaf(l.x, v[4 * j4].y, ay);
+        ax = fmaf(l.y, v[4 * j4 + 1].x, ax);
+        ay = fmaf(l.y, v[4 * j4 + 1].y, ay);
+        ax = fmaf(l.z, v[4 * j4 + 2].x, ax);
+        ay = fmaf(l.z, v[4 * j4 + 2].y, ay);
+        ax = fmaf(l.w, v[4 * j4 + 3].x, ax);
+        ay = fmaf(l.w, v[4 * j4 + 3].y, ay);
+      }
+    }
+    *reinterpret_cast<float2*>(fields + (size_t)i * npix + p) = make_float2(ax, ay);
+  }
+}
+
+// One pixel per thread (odd pixel counts).
+template <int JB>
+__global__ void __launch_bounds__(128, 4) k_mix(float* __restrict__ fields, const float* __restrict__ L, float scale,
                                              int J, size_t npix) {
-  __shared__ float Ls[JB * JB];
+  __shared__ __align__(16) float Ls[JB * JB];
   for (int i = threadIdx.x; i < JB * JB; i += blockDim.x) {
     const int r = i / JB, c = i - r * JB;
     Ls[i] = (r < J && c < J && c <= r) ? L[r * J + c] * scale : 0.f;
@@ -214,15 +254,32 @@ __global__ void __launch_bounds__(256) k_mix(float* __restrict__ fields, const f
   float v[JB];
 #pragma unroll
   for (int j = 0; j < JB; ++j) v[j] = j < J ? fields[(size_t)j * npix + p] : 0.f;
+  for (int i = 0; i < J; ++i) {
+    float acc = 0.f;
 #pragma unroll
-  for (int i = JB - 1; i >= 0; --i) {
-    if (i < J) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j <= i; ++j) acc = fmaf(Ls[i * JB + j], v[j], acc);
-      fields[(size_t)i * npix + p] = acc;
+    for (int j4 = 0; j4 < JB / 4; ++j4) {
+      if (4 * j4 <= i) {
+        const float4 l = *reinterpret_cast<const float4*>(Ls + i * JB + 4 * j4);
+        acc = fmaf(l.x, v[4 * j4], acc);
+        acc = fmaf(l.y, v[4 * j4 + 1], acc);
+        acc = fmaf(l.z, v[4 * j4 + 2], acc);
+        acc = fmaf(l.w, v[4 * j4 + 3], acc);
+      }
+    }
+    fields[(size_t)i * npix + p] = acc;
+  }
+}
+
+template <int JB>
+void launch_mix(float* fields, const float* L, float scale, int J, size_t npix, cudaStream_t st) {
+  if constexpr (JB <= 40) {
+    if (npix % 2 == 0) {
+      const size_t pairs = npix / 2;
+      k_mix_pairs<JB><<<(unsigned)((pairs + 127) / 128), 128, 0, st>>>(fields, L, scale, J, npix);
+      return;
     }
   }
+  k_mix<JB><<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(fields, L, scale, J, npix);
 }
 
 __global__ void k_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* __restrict__ out) {
@@ -273,10 +330,9 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
     default: return DFP2S_EINVAL;
   }
   const size_t npix = (size_t)H * W;
-  const int blocks = (int)((npix + 255) / 256);
-  if (J <= 16) k_mix<16><<<blocks, 256, 0, st>>>(fields, L, scale, J, npix);
-  else if (J <= 40) k_mix<40><<<blocks, 256, 0, st>>>(fields, L, scale, J, npix);
-  else k_mix<64><<<blocks, 256, 0, st>>>(fields, L, scale, J, npix);
+  if (J <= 16) launch_mix<16>(fields, L, scale, J, npix, st);
+  else if (J <= 40) launch_mix<40>(fields, L, scale, J, npix, st);
+  else launch_mix<64>(fields, L, scale, J, npix, st);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
 

@@ -2,15 +2,22 @@
 // kernel per frame, BF16 operands, FP32 accumulation in tensor memory.
 //
 // A tile is 128 consecutive pixels (MMA M = 128):
-//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T -> TMEM columns [0, 256)
+//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T -> TMEM columns A = [0, 256)
 //            (W1' = W1 diag(in_scale), resident in shared memory)
 //   GELU(z + b1) -> H [128 x 256] BF16 in shared memory (K-major core matrices)
-//   layer 2: H x W2^T -> TMEM [256, 512), W2 streamed in four 64-wide K chunks
+//   layer 2: H x W2^T -> TMEM B = [256, 512), W2 streamed in four 64-wide K chunks
 //   GELU(z + b2) -> H
-//   layer 3: H x W3^T -> TMEM [0, NP3), W3 streamed in four K chunks
+//   layer 3: H x W3^T -> TMEM A[0, NP3), W3 streamed in four K chunks
 //   w = y * out_scale + (b3 * out_scale + out_shift) -> global (FP32 or BF16)
-// Weight chunks arrive by 1-D bulk copies into a three-deep ring; the MMAs of a
-// chunk release its buffer through tcgen05.commit.  All waits are bounded.
+//
+// Warp roles: warps 0-7 run the epilogues (warps w and w + 4 read TMEM lanes
+// 32 (w % 4) .., one half of the columns each), warp 8 issues the weight copies
+// and the MMAs.  The epilogues hand H over in 64-column chunks (one mbarrier
+// per chunk), so the MMAs of the next layer start on chunk c while the
+// epilogue is still working on chunk c + 1.  Weight chunks arrive by 1-D bulk
+// copies into a three-deep ring; their MMAs release a slot through
+// tcgen05.commit.  All waits are bounded; a wait that runs out sets the
+// kernel's error word.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -24,29 +31,94 @@ namespace {
 constexpr int TM = 128;
 constexpr int HID = 256;
 constexpr int KX = 48;           // J padded to three K = 16 steps
-constexpr int THREADS = 256;     // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) ..
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int THREADS = EPI_THREADS + 32;  // + the producer warp
 constexpr int NRING = 3;
 constexpr int CHUNK_BYTES = HID * 64 * 2;  // one 64-wide K chunk of W2 (the largest)
+constexpr int STAGE_BYTES = TM * 132 * 4;  // FP32 output rows of up to 128 (+4) weights
+constexpr int HS_BYTES = STAGE_BYTES > TM * HID * 2 ? STAGE_BYTES : TM * HID * 2;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct Smem {
   uint8_t ring[NRING][CHUNK_BYTES];  // 96 KB
-  uint8_t H[TM * HID * 2];           // 64 KB
+  uint8_t H[HS_BYTES];               // hidden activations, then the output staging rows
   uint8_t W1[HID * KX * 2];          // 24 KB
   uint8_t X[TM * KX * 2];            // 12 KB
   float b1[HID], b2[HID];
   float c3[128], s3[128];            // output bias and scale
   uint64_t full[NRING], empty[NRING];
-  uint64_t w1_full, layer_done;
+  uint64_t w1_full, x_ready, l1_done, l2_done, l3_done;
+  uint64_t h_ready[4];
   uint32_t tmem_base;
   int abort;
 };
 
-DFP2S_DEV float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the
+// rational-exponential approximation 7.1.26 of Abramowitz and Stegun
+// (|error| <= 1.5e-7): erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2),
+// t = 1 / (1 + p x), x >= 0.  exp and the reciprocal use the hardware
+// approximations (ex2.approx, rcp.approx); the activations are rounded to
+// bfloat16 afterwards, far above these errors.
+DFP2S_DEV float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+DFP2S_DEV float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+DFP2S_DEV float gelu(float z) {
+  const float az = fabsf(z);
+  const float t = rcp_approx(fmaf(0.3275911f * 0.70710678118654752f, az, 1.0f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  q *= t;
+  // exp(-z^2 / 2) = 2^(-z^2 log2(e) / 2)
+  const float e = ex2_approx((z * -0.72134752044448170f) * z);
+  const float erf_abs = fmaf(-q, e, 1.0f);
+  const float phi = fmaf(0.5f, copysignf(erf_abs, z), 0.5f);
+  return z * phi;
+}
 
 // byte offset of element (row, k) in a K-major no-swizzle tile with `kgroups` 8-element K groups per row group
 DFP2S_DEV uint32_t kmajor_off(int row, int k, int kgroups) {
   return (uint32_t)(((row >> 3) * kgroups + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane (warp-wide).
+DFP2S_DEV void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Barrier of the epilogue warps (named barrier 1) that also ORs a flag over
+// them, so that every epilogue thread takes the same abort decision.
+DFP2S_DEV bool bar_epi_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(EPI_THREADS)
+      : "memory");
+  return r != 0;
 }
 
 template <typename WT>
@@ -56,25 +128,32 @@ DFP2S_DEV void wstore<float>(float* p, float v) { *p = v; }
 template <>
 DFP2S_DEV void wstore<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-// TMEM columns [col0, col0 + 128) of this thread's pixel -> GELU(z + b) -> H row (K = col - col0 + kbase)
-DFP2S_DEV void epilogue_gelu(uint32_t tmem, int warp, int lane, int col0, int kbase, const float* bias, uint8_t* H) {
-  const int p = (warp & 3) * 32 + lane;
-  for (int q = 0; q < 8; ++q) {
-    float d[16];
-    umma::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0 + q * 16, d);
-    uint32_t packed[8];
+// Hidden-layer epilogue of one epilogue warp: for each 64-column chunk c, this
+// warp's 32 columns [64 c + 32 h, +32) of TMEM region `col0` -> GELU(z + b) ->
+// H (K-major, K = column - col0), then the chunk is handed to the MMA warp.
+DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col0, const float* bias) {
+  const int q4 = warp & 3, h = warp >> 2;
+  const int p = q4 * 32 + lane;
+  for (int c = 0; c < 4; ++c) {
+    const int k0 = 64 * c + 32 * h;
+    float d[32];
+    tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + col0 + k0, d);
+    uint32_t packed[16];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int k = kbase + q * 16 + 2 * i;
-      const float g0 = gelu(d[2 * i] + bias[k]);
-      const float g1 = gelu(d[2 * i + 1] + bias[k + 1]);
+    for (int i = 0; i < 16; ++i) {
+      const float g0 = gelu(d[2 * i] + bias[k0 + 2 * i]);
+      const float g1 = gelu(d[2 * i + 1] + bias[k0 + 2 * i + 1]);
       __nv_bfloat162 h2 = __floats2bfloat162_rn(g0, g1);
       packed[i] = *reinterpret_cast<uint32_t*>(&h2);
     }
-    const int k0 = kbase + q * 16;
-    *reinterpret_cast<uint4*>(H + kmajor_off(p, k0, HID / 8)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    *reinterpret_cast<uint4*>(H + kmajor_off(p, k0 + 8, HID / 8)) =
-        make_uint4(packed[4], packed[5], packed[6], packed[7]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      *reinterpret_cast<uint4*>(s.H + kmajor_off(p, k0 + 8 * m, HID / 8)) =
+          make_uint4(packed[4 * m], packed[4 * m + 1], packed[4 * m + 2], packed[4 * m + 3]);
+    umma::fence_proxy_async_smem();  // H stores -> visible to the tensor cores
+    umma::fence_before_sync();       // TMEM reads ordered before the hand-over
+    __syncwarp();
+    if (lane == 0) umma::mbar_arrive(&s.h_ready[c]);
   }
 }
 
@@ -83,13 +162,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_mlp_tc(const float* __restrict__ fields, int J, int npix, int K, int NP3, const __nv_bfloat16* __restrict__ w1t,
              const __nv_bfloat16* __restrict__ w2c, const __nv_bfloat16* __restrict__ w3c, const float* __restrict__ b1,
              const float* __restrict__ b2, const float* __restrict__ c3, const float* __restrict__ s3,
-             WT* __restrict__ wout, int* __restrict__ err) {
+             WT* __restrict__ wout, int KS, int vec_out, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t w2_bytes = (uint32_t)CHUNK_BYTES;
-  const uint32_t w3_bytes = (uint32_t)(NP3 * 64 * 2);
   const int ntiles = (npix + TM - 1) / TM;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (tid == 0) {
     for (int i = 0; i < NRING; ++i) {
@@ -97,7 +175,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       umma::mbar_init(&s.empty[i], 1);
     }
     umma::mbar_init(&s.w1_full, 1);
-    umma::mbar_init(&s.layer_done, 1);
+    umma::mbar_init(&s.x_ready, EPI_WARPS);
+    umma::mbar_init(&s.l1_done, 1);
+    umma::mbar_init(&s.l2_done, 1);
+    umma::mbar_init(&s.l3_done, 1);
+    for (int c = 0; c < 4; ++c) umma::mbar_init(&s.h_ready[c], EPI_WARPS);
     s.abort = 0;
     umma::fence_mbar_init();
   }
@@ -119,146 +201,167 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = s.tmem_base;
-  if (tid == 0) {
-    umma::mbar_arrive_expect_tx(&s.w1_full, HID * KX * 2);
-    umma::bulk_g2s(s.W1, w1t, HID * KX * 2, &s.w1_full);
-  }
-  // operand descriptors (K-major, no swizzle): X and W1 with 6 K groups per 8-row group,
-  // H with 32, weight chunks with 8; per-MMA descriptors add (byte offset >> 4)
-  const uint64_t x_desc = umma::sdesc(umma::smem_u32(s.X), 128, 768);
-  const uint64_t w1_desc = umma::sdesc(umma::smem_u32(s.W1), 128, 768);
-  const uint64_t h_desc = umma::sdesc(umma::smem_u32(s.H), 128, 4096);
-  const uint64_t ring_desc = umma::sdesc(umma::smem_u32(s.ring[0]), 128, 1024);
-  const uint32_t idesc1 = umma::idesc_bf16(TM, HID);
-  const uint32_t idesc3 = umma::idesc_bf16(TM, NP3);
-  uint32_t u_issue = 0;  // weight chunks issued (bulk copies)
-  uint32_t u_use = 0;    // weight chunks consumed by MMAs
-  uint32_t ndone = 0;    // completions of layer_done
-  bool ok = true;
 
-  // issue the copy of weight chunk number u (8 per tile: 4 of W2 then 4 of W3)
-  auto issue = [&](uint32_t u) {
-    const int b = u % NRING;
-    if (u >= NRING) {
-      if (!umma::mbar_wait(&s.empty[b], ((u / NRING) - 1) & 1, kWaitNs)) s.abort = 1;
-    }
-    const int c = u % 8;
-    if (c < 4) {
-      umma::mbar_arrive_expect_tx(&s.full[b], w2_bytes);
-      umma::bulk_g2s(s.ring[b], w2c + (size_t)c * (HID * 64), w2_bytes, &s.full[b]);
-    } else {
-      umma::mbar_arrive_expect_tx(&s.full[b], w3_bytes);
-      umma::bulk_g2s(s.ring[b], w3c + (size_t)(c - 4) * (NP3 * 64), w3_bytes, &s.full[b]);
-    }
-  };
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int p0 = tile * TM;
-    // prefetch the first chunks of this tile
-    if (tid == 0) {
-      while (u_issue < u_use + NRING && !s.abort) issue(u_issue++);
-    }
-    // X tile: fields[j][p0 + p] -> bf16 at (p, j)
-    for (int idx = tid; idx < J * TM; idx += THREADS) {
-      const int j = idx / TM, p = idx - j * TM;
-      const float v = (p0 + p < npix) ? __ldg(fields + (size_t)j * npix + p0 + p) : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(s.X + kmajor_off(p, j, KX / 8)) = __float2bfloat16_rn(v);
-    }
-    umma::fence_proxy_async_smem();
-    __syncthreads();
-    if (s.abort) {
-      ok = false;
-      break;
-    }
-    // layer 1
-    if (tid == 0) {
-      if (!umma::mbar_wait(&s.w1_full, 0, kWaitNs)) {
-        s.abort = 1;
-      } else {
+  if (warp == EPI_WARPS) {
+    // ------------------------------------------------------------ producer: copies and MMAs
+    if (lane == 0) {
+      const uint32_t w2_bytes = (uint32_t)CHUNK_BYTES;
+      const uint32_t w3_bytes = (uint32_t)(NP3 * 64 * 2);
+      // K-major no-swizzle descriptors: X and W1 with 6 K groups per 8-row group, H with 32,
+      // weight chunks with 8; per-MMA descriptors add (byte offset >> 4)
+      const uint64_t x_desc = umma::sdesc(umma::smem_u32(s.X), 128, 768);
+      const uint64_t w1_desc = umma::sdesc(umma::smem_u32(s.W1), 128, 768);
+      const uint64_t h_desc = umma::sdesc(umma::smem_u32(s.H), 128, 4096);
+      const uint64_t ring_desc = umma::sdesc(umma::smem_u32(s.ring[0]), 128, 1024);
+      const uint32_t idesc1 = umma::idesc_bf16(TM, HID);
+      const uint32_t idesc3 = umma::idesc_bf16(TM, NP3);
+      const uint32_t total_chunks = (uint32_t)my_tiles * 8;  // 4 of W2 then 4 of W3 per tile
+      uint32_t u_issue = 0, u_use = 0;
+      bool ok = true;
+      auto issue_copy = [&](uint32_t u) {
+        const int b = u % NRING;
+        const int c = u % 8;
+        if (c < 4) {
+          umma::mbar_arrive_expect_tx(&s.full[b], w2_bytes);
+          umma::bulk_g2s(s.ring[b], w2c + (size_t)c * (HID * 64), w2_bytes, &s.full[b]);
+        } else {
+          umma::mbar_arrive_expect_tx(&s.full[b], w3_bytes);
+          umma::bulk_g2s(s.ring[b], w3c + (size_t)(c - 4) * (NP3 * 64), w3_bytes, &s.full[b]);
+        }
+      };
+      // issue every copy whose ring slot is already free (no waiting)
+      auto top_up = [&]() {
+        while (u_issue < total_chunks && u_issue < u_use + NRING) {
+          if (u_issue >= NRING && !umma::mbar_test(&s.empty[u_issue % NRING], ((u_issue / NRING) - 1) & 1)) break;
+          issue_copy(u_issue++);
+        }
+      };
+      // make sure chunk u has been issued (waiting for its slot if needed)
+      auto ensure = [&](uint32_t u) {
+        while (ok && u_issue <= u) {
+          if (u_issue >= NRING &&
+              !umma::mbar_wait(&s.empty[u_issue % NRING], ((u_issue / NRING) - 1) & 1, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          issue_copy(u_issue++);
+        }
+      };
+      umma::mbar_arrive_expect_tx(&s.w1_full, HID * KX * 2);
+      umma::bulk_g2s(s.W1, w1t, HID * KX * 2, &s.w1_full);
+      top_up();
+      if (my_tiles > 0 && !umma::mbar_wait(&s.w1_full, 0, kWaitNs)) ok = false;
+      for (int t = 0; t < my_tiles && ok; ++t) {
+        // layer 1 (X of this tile written; TMEM A free: the previous tile's epilogues are done)
+        if (!umma::mbar_wait(&s.x_ready, t & 1, kWaitNs)) {
+          ok = false;
+          break;
+        }
         umma::fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < KX / 16; ++ks) umma::mma_bf16(tmem, x_desc + 16 * ks, w1_desc + 16 * ks, idesc1, ks != 0);
-        umma::mma_commit(&s.layer_done);
-      }
-    }
-    if (!umma::mbar_wait(&s.layer_done, ndone & 1, kWaitNs)) s.abort = 1;
-    ++ndone;
-    umma::fence_after_sync();
-    epilogue_gelu(tmem, warp, lane, (warp >> 2) * 128, (warp >> 2) * 128, s.b1, s.H);
-    umma::fence_proxy_async_smem();
-    umma::fence_before_sync();
-    __syncthreads();
-    if (s.abort) {
-      ok = false;
-      break;
-    }
-    // layers 2 and 3: 8 weight chunks
-    for (int layer = 2; layer <= 3; ++layer) {
-      if (tid == 0) {
-        umma::fence_after_sync();
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t u = u_use++;
-          const int b = u % NRING;
-          if (!umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
-            s.abort = 1;
-            break;
-          }
-          // descriptors = base + (byte offset >> 4)
-          const uint64_t a_c = h_desc + (uint64_t)(c * 8 * 8);
-          const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
+        umma::mma_commit(&s.l1_done);
+        // layers 2 and 3, chunk by chunk as the epilogue hands H over
+        for (int layer = 2; layer <= 3 && ok; ++layer) {
           const uint32_t d = layer == 2 ? tmem + 256 : tmem;
           const uint32_t id = layer == 2 ? idesc1 : idesc3;
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t u = u_use;
+            ensure(u);
+            const int b = u % NRING;
+            if (!ok || !umma::mbar_wait(&s.h_ready[c], layer == 2 ? 0 : 1, kWaitNs) ||
+                !umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
+              ok = false;
+              break;
+            }
+            umma::fence_after_sync();
+            const uint64_t a_c = h_desc + (uint64_t)(c * 8 * 8);
+            const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, (c | ks) != 0);
-          umma::mma_commit(&s.empty[b]);
-          // keep the ring full (the next tile's chunks too)
-          while (u_issue < u_use + NRING && !s.abort) issue(u_issue++);
+            for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, (c | ks) != 0);
+            umma::mma_commit(&s.empty[b]);
+            ++u_use;
+            top_up();
+          }
+          if (ok) umma::mma_commit(layer == 2 ? &s.l2_done : &s.l3_done);
         }
-        umma::mma_commit(&s.layer_done);
       }
-      if (!umma::mbar_wait(&s.layer_done, ndone & 1, kWaitNs)) s.abort = 1;
-      ++ndone;
+      if (!ok) {
+        s.abort = 1;
+        atomicExch(err, 2);
+      }
+      // outstanding copies and MMAs finish before the CTA exits (bounded)
+      for (uint32_t u = u_use; u < u_issue; ++u) umma::mbar_wait(&s.full[u % NRING], (u / NRING) & 1, kWaitNs);
+      if (u_use > 0) umma::mbar_wait(&s.empty[(u_use - 1) % NRING], ((u_use - 1) / NRING) & 1, kWaitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    const int q4 = warp & 3, h = warp >> 2;
+    const int p = q4 * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int tile = blockIdx.x + t * gridDim.x;
+      const int p0 = tile * TM;
+      // X tile: fields[j][p0 + p] -> bf16 at (p, j); TMEM and H of the previous tile are free
+      for (int idx = tid; idx < J * TM; idx += EPI_THREADS) {
+        const int j = idx / TM, pp = idx - j * TM;
+        const float v = (p0 + pp < npix) ? __ldg(fields + (size_t)j * npix + p0 + pp) : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(s.X + kmajor_off(pp, j, KX / 8)) = __float2bfloat16_rn(v);
+      }
+      umma::fence_proxy_async_smem();
+      umma::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&s.x_ready);
+      if (!umma::mbar_wait(&s.l1_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
-      if (layer == 2) {
-        epilogue_gelu(tmem, warp, lane, 256 + (warp >> 2) * 128, (warp >> 2) * 128, s.b2, s.H);
-        umma::fence_proxy_async_smem();
-      } else {
-        // stage this tile's outputs in H (free now), then one contiguous coalesced copy
-        float* stage = reinterpret_cast<float*>(s.H);
-        if (warp < 4) {
-          const int p = warp * 32 + lane;
-          for (int q = 0; q < NP3 / 16; ++q) {
-            float d[16];
-            umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + q * 16, d);
+      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, s.b1);
+      if (!umma::mbar_wait(&s.l2_done, t & 1, kWaitNs)) s.abort = 1;
+      umma::fence_after_sync();
+      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, s.b2);
+      if (!umma::mbar_wait(&s.l3_done, t & 1, kWaitNs)) s.abort = 1;
+      umma::fence_after_sync();
+      // outputs: TMEM A[0, NP3) -> FP32 rows of stride KS in the staging area (H is free now)
+      float* stage = reinterpret_cast<float*>(s.H);
+      if (!s.abort) {
+        const int ngrp = NP3 / 16;
+        for (int q = h; q < ngrp; q += 2) {
+          float d[16];
+          umma::tmem_ld16(tmem + lane_base + q * 16, d);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int k = q * 16 + i;
-              if (k < K) stage[p * K + k] = fmaf(d[i], s.s3[k], s.c3[k]);
+          for (int i4 = 0; i4 < 4; ++i4) {
+            const int k = q * 16 + 4 * i4;
+            if (k < K) {
+              float4 o;
+              o.x = fmaf(d[4 * i4 + 0], s.s3[k + 0], s.c3[k + 0]);
+              o.y = fmaf(d[4 * i4 + 1], s.s3[k + 1], s.c3[k + 1]);
+              o.z = fmaf(d[4 * i4 + 2], s.s3[k + 2], s.c3[k + 2]);
+              o.w = fmaf(d[4 * i4 + 3], s.s3[k + 3], s.c3[k + 3]);
+              *reinterpret_cast<float4*>(stage + p * KS + k) = o;
             }
           }
         }
-        __syncthreads();
-        const int nlive = min(TM, npix - p0);
-        WT* dst = wout + (size_t)p0 * K;
-        for (int i = tid; i < nlive * K; i += THREADS) wstore<WT>(dst + i, stage[i]);
       }
       umma::fence_before_sync();
-      __syncthreads();
-      if (s.abort) {
-        ok = false;
-        break;
+      if (bar_epi_any(s.abort != 0)) break;
+      const int nlive = min(TM, npix - p0);
+      WT* dst = wout + (size_t)p0 * K;
+      if (vec_out) {  // FP32 with K % 4 == 0 and 16-byte aligned rows
+        const int n4 = nlive * K / 4;
+        for (int i = tid; i < n4; i += EPI_THREADS) {
+          const int e = 4 * i;
+          const int pp = e / K, k = e - pp * K;
+          reinterpret_cast<float4*>(dst)[i] = *reinterpret_cast<const float4*>(stage + pp * KS + k);
+        }
+      } else {
+        for (int i = tid; i < nlive * K; i += EPI_THREADS) {
+          const int pp = i / K, k = i - pp * K;
+          wstore<WT>(dst + i, stage[pp * KS + k]);
+        }
       }
+      // the next tile's epilogue writes H only after every warp's x_ready arrival, which
+      // follows this copy in each warp's program order
     }
-    if (!ok) break;
-  }
-  if (!ok && tid == 0) atomicExch(err, 2);
-  // drain outstanding copies (bounded) before the CTA exits
-  if (tid == 0) {
-    for (uint32_t u = u_use; u < u_issue; ++u) umma::mbar_wait(&s.full[u % NRING], (u / NRING) & 1, kWaitNs);
-    if (u_use > 0) {
-      const uint32_t u = u_use - 1;
-      umma::mbar_wait(&s.empty[u % NRING], (u / NRING) & 1, kWaitNs);
-    }
+    if (s.abort && tid == 0) atomicExch(err, 2);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -323,14 +426,19 @@ int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, v
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = ntiles < sms ? ntiles : sms;
+  // staging row stride: a multiple of 4 floats with an odd number of 16-byte units (no bank conflicts)
+  int KS = (K + 3) / 4 * 4;
+  if ((KS / 4) % 2 == 0) KS += 4;
+  const int vec_out = (w_dtype == DFP2S_W_F32) && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
   const size_t sm = sizeof(Smem) + 1024;
+  static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory layout");
   cudaFuncSetAttribute(k_mlp_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_mlp_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (w_dtype == DFP2S_W_BF16)
     k_mlp_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3, p->b1,
-                                                      p->b2, p->tc_c3, p->out_scale, (__nv_bfloat16*)w, p->err);
+                                                      p->b2, p->tc_c3, p->out_scale, (__nv_bfloat16*)w, KS, 0, p->err);
   else
     k_mlp_tc<float><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3, p->b1, p->b2,
-                                              p->tc_c3, p->out_scale, (float*)w, p->err);
+                                              p->tc_c3, p->out_scale, (float*)w, KS, vec_out, p->err);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }

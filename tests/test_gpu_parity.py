@@ -77,6 +77,8 @@ def test_spectral_factor_matches_oracle(lib, J, N, ppd):
     (6, 16, 9, 16, 2.0, 1.0, 4, 0),         # smallest grid: one thread per FFT
     (10, 30, 17, 32, 2.0, 2.0, 8, 6),       # N = 32: one radix-32 pass
     (4, 700, 1500, 2048, 8.0, 2.0, 2, 1),   # three passes (32 x 32 x 2), block-wide exchanges
+    (36, 33, 21, 128, 8.0, 2.0, 3, 2),      # odd pixel count: one pixel per mixing thread
+    (45, 31, 29, 128, 8.0, 2.0, 1, 0),      # J > 40: the 64-wide mixing bucket
 ])
 def test_fields_match_oracle(lib, J, H, W, N, ppd, d, seed, frame):
     f = lib.SpectralFactor(J, N, ppd)
@@ -195,7 +197,7 @@ def _bf(a):
     return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
 
 
-@pytest.mark.parametrize("K,H,W", [(100, 16, 24), (16, 9, 31), (128, 130, 3)])
+@pytest.mark.parametrize("K,H,W", [(100, 16, 24), (16, 9, 31), (128, 130, 3), (100, 256, 160)])
 def test_mlp_forward_matches_oracle(lib, K, H, W):
     J = 36
     rng = np.random.default_rng(K)
