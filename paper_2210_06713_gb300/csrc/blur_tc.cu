@@ -17,18 +17,24 @@
 // 69 MMAs per channel per tile, the fewest K = 16 steps that hold 1089 taps.
 // A_iy needs no im2col: its K-major core matrix (8 rows x 16 bytes) at (row
 // group i, K group g) is the 8 x 8 block E_{i+g}[s][t] = I_c(r, x0 - 16 +
-// 8(i+g) + s + t), so a staged image row holds the 19 blocks E_0..E_18 back to
-// back and the operand descriptor takes the same 128-byte stride along M and K.
-// L is gathered once per tile from the same image rows.  B tiles for each iy
-// are laid out once per basis in global memory and streamed with 1-D bulk
-// copies; C stays in shared memory.  The epilogue reads D from TMEM (one pixel
-// per thread, one warp group per channel) and contracts it with the pixel's
-// weights: out = sum_k w_k (D[p][k] + c s_k).
+// 8(i+g) + s + t), so the blocks E_0..E_19 of an image row, back to back,
+// serve as A_iy with the same 128-byte stride along M and K.  Row s of E_b is
+// the 16-byte run at x0 - 16 + 8b + s, which is 16-byte aligned in the image
+// copy shifted left by s columns; with eight shifted copies of the padded image
+// in global memory one TMA tile load (box 8 x 8 shifts x 20 blocks) writes the
+// blocks of one row and channel straight into shared memory.  L is gathered
+// from those blocks (E_b[s][0], 8b + s = p + 32) row by row as they arrive.
+// The row tiles of B for each iy are laid out once per basis in global memory
+// and streamed with 1-D bulk copies; C stays in shared memory, and so do the
+// tile's weights (one bulk copy per tile).  The epilogue reads D from TMEM (one
+// pixel per thread, one warp group per channel) and contracts it with the
+// pixel's weights: out = sum_k w_k (D[p][k] + c s_k).
 //
 // Precision: the image enters as bfloat16(I - c) with c = 0.5 (centring halves
 // the magnitudes of [0, 1] images and so the rounding error), and the exact
 // term c s_k, s_k = sum_u bf16(phi_k(u)), is added back in FP32; the weights
 // are read in FP32 or BF16 as stored.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,55 +46,70 @@
 namespace {
 
 constexpr int KS = 33;
-constexpr int TM = 128;                    // pixels per tile (MMA M)
-constexpr int KM = 32;                     // row taps ix = 1..32 (two K = 16 steps)
-constexpr int KL = 48;                     // column taps iy = 0..32 padded to three K = 16 steps
-constexpr int NBLK = TM / 8 + KM / 8 - 1;  // 19 staged 8x8 blocks per image row
-constexpr int ROWB = NBLK * 128;           // 2432 bytes per staged row
-constexpr int RAWW = TM + KM;              // 160 staged image columns per row (cols p + kappa <= 159)
-constexpr int RAWB = RAWW * 2;             // 320 bytes
-constexpr int CMAX = 3;                    // channels per pass
-constexpr int NSLOT = 4;                   // TMEM accumulator slots of NP <= 128 columns (512 in all)
-// warp 0: bulk copies; warp 1: MMA issue; warps 2-7: staging; warps 8-19: epilogue,
-// one group of four per channel (warp w reads TMEM lanes 32 (w % 4) ..)
-constexpr int STAGE_WARP0 = 2;
-constexpr int NSTAGE_WARPS = 6;
-constexpr int EPI_WARP0 = STAGE_WARP0 + NSTAGE_WARPS;
-constexpr int EPI_WARPS = 4 * CMAX;
-constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;
-constexpr int NB = 4;                      // staged-row ring (one slot per basis row iy)
-constexpr int NBB = 4;                     // basis-tile ring
+constexpr int TM = 128;              // pixels per tile (MMA M)
+constexpr int KM = 32;               // row taps ix = 1..32 (two K = 16 steps)
+constexpr int KL = 48;               // column taps iy = 0..32 padded to three K = 16 steps
+constexpr int NBLK = 20;             // blocks E_0..E_19 per image row (the MMAs use E_0..E_18)
+constexpr int ROWB = NBLK * 128;     // 2560 bytes per row and channel
+constexpr int NSHIFT = 8;            // shifted image copies
+constexpr int CMAX = 3;              // channels per pass
+constexpr int NSLOT = 4;             // TMEM accumulator slots of NP <= 128 columns (512 in all)
+// warp 0: copies; warp 1: MMA issue; warps 2-3: column operand; warps 4-15:
+// epilogue, one group of four per channel (warp w reads TMEM lanes 32 (w % 4) ..)
+constexpr int L_WARP0 = 2;
+constexpr int NL_WARPS = 2;
+constexpr int EPI_WARP0 = 4;
+constexpr int THREADS = (EPI_WARP0 + 4 * CMAX) * 32;
+constexpr int NB = 4;                // row-block ring (one slot per basis row iy)
+constexpr int NBB = 4;               // basis-tile ring
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
-constexpr int B_SLOT = 128 * KM * 2;       // bytes of one basis-tile slot (NP <= 128)
-constexpr int L_BYTES = TM * KL * 2;       // column operand of one channel
-constexpr int C_BYTES = 128 * KL * 2;      // column taps of the basis
+constexpr int B_SLOT = 128 * KM * 2;         // bytes of one basis-tile slot (NP <= 128)
+constexpr int L_BYTES = TM * KL * 2;         // column operand of one channel
+constexpr int C_BYTES = 128 * KL * 2;        // column taps of the basis
 
 struct Smem {
-  uint8_t raw[2][CMAX][KS][RAWB];  // image rows of a tile (bulk copies, prefetched one tile ahead)
-  uint8_t A[NB][CMAX][ROWB];       // Hankel-blocked rows
-  uint8_t L[CMAX][L_BYTES];        // column operand of the tile
+  uint8_t A[NB][CMAX][ROWB];       // Hankel blocks of one image row per channel (TMA)
   uint8_t B[NBB][B_SLOT];          // basis tiles of one row each
+  uint8_t L[2][CMAX][L_BYTES];     // column operand, double-buffered over tiles
   uint8_t Cb[C_BYTES];             // column taps (resident)
+  float Wt[TM * 128];              // the tile's weights (FP32, K per pixel)
   float csum[128];
-  uint64_t raw_full[2], raw_empty[2];
-  uint64_t a_full[NB], slot_free[NB];
+  uint64_t a_full[NB], a_free[NB];
   uint64_t b_full[NBB], b_free[NBB];
-  uint64_t l_full, l_free, c_full;
+  uint64_t l_full[2], l_free[2];
+  uint64_t c_full, w_full, w_empty;
   uint64_t acc_full[NSLOT], acc_empty[NSLOT];
   uint32_t tmem_base;
   int abort;
 };
 
-// Replicate-padded BF16 copy of the image: P[c][r + 16][x + 16] = I[c][clamp(r)][clamp(x)].
-__global__ void k_pad_bf16(const float* __restrict__ img, int C, int H, int W, int Wp, float centre,
-                           __nv_bfloat16* __restrict__ P) {
+// TMA tile load of a rank-5 box into shared memory, completion counted in bytes on `bar`.
+DFP2S_DEV void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(umma::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(umma::smem_u32(bar))
+      : "memory");
+}
+
+// Replicate-padded, shifted BF16 copies of the image:
+// P[c][sh][r][x] = I[c][clamp(r - 16)][clamp(x + sh - 16)] - centre, sh = 0..7, r < H + 32, x < Wq.
+__global__ void k_pad_shifted(const float* __restrict__ img, int C, int H, int W, int Wq, float centre,
+                              __nv_bfloat16* __restrict__ P) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   const int c = blockIdx.z;
-  if (x >= Wp) return;
+  if (x >= Wq) return;
+  const int R = H + 32;
   const int sy = min(max(r - 16, 0), H - 1);
-  const int sx = min(max(x - 16, 0), W - 1);
-  P[((size_t)c * (H + 32) + r) * Wp + x] = __float2bfloat16_rn(img[((size_t)c * H + sy) * W + sx] - centre);
+  const float* row = img + ((size_t)c * H + sy) * W;
+  const size_t plane = (size_t)R * Wq;
+  __nv_bfloat16* dst = P + (size_t)c * NSHIFT * plane + (size_t)r * Wq + x;
+#pragma unroll
+  for (int sh = 0; sh < NSHIFT; ++sh) {
+    const int sx = min(max(x + sh - 16, 0), W - 1);
+    dst[sh * plane] = __float2bfloat16_rn(row[sx] - centre);
+  }
 }
 
 // Row tiles: Bt[iy][j][g][n8][k8] = phi_{8j+n8}(iy, 32 - (8g+k8)), g < 4 (taps ix = 1..32),
@@ -152,12 +173,14 @@ __global__ void k_scale(float* __restrict__ v, int n, float a) {
 }
 
 template <typename WT, int C>
-__global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __restrict__ P, int H, int W,
-                                                        int Wp, const __nv_bfloat16* __restrict__ Bt, int K, int NP,
-                                                        const float* __restrict__ csum, const WT* __restrict__ w,
-                                                        int w_vec, float* __restrict__ out, int* __restrict__ err) {
+__global__ void __launch_bounds__(THREADS, 1)
+    k_blur_tc(const __grid_constant__ CUtensorMap tmap, int H, int W, const __nv_bfloat16* __restrict__ Bt, int K,
+              int NP, const float* __restrict__ csum, const WT* __restrict__ w, int w_vec, float* __restrict__ out,
+              int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  // 1024-byte aligned base in the shared window (the launch adds 1024 bytes of slack)
+  uint8_t* sbase = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
+  Smem& s = *reinterpret_cast<Smem*>(sbase);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const uint32_t bt_bytes = (uint32_t)NP * KM * 2;
@@ -169,21 +192,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
-      umma::mbar_init(&s.raw_full[i], 1);
-      umma::mbar_init(&s.raw_empty[i], NSTAGE_WARPS);
-    }
     for (int i = 0; i < NB; ++i) {
-      umma::mbar_init(&s.a_full[i], NSTAGE_WARPS);
-      umma::mbar_init(&s.slot_free[i], 1);
+      umma::mbar_init(&s.a_full[i], 1);
+      umma::mbar_init(&s.a_free[i], 1 + NL_WARPS);  // the MMAs' commit and the column-operand warps
     }
     for (int i = 0; i < NBB; ++i) {
       umma::mbar_init(&s.b_full[i], 1);
       umma::mbar_init(&s.b_free[i], 1);
     }
-    umma::mbar_init(&s.l_full, NSTAGE_WARPS);
-    umma::mbar_init(&s.l_free, 1);
+    for (int i = 0; i < 2; ++i) {
+      umma::mbar_init(&s.l_full[i], NL_WARPS);
+      umma::mbar_init(&s.l_free[i], 1);
+    }
     umma::mbar_init(&s.c_full, 1);
+    umma::mbar_init(&s.w_full, 1);
+    umma::mbar_init(&s.w_empty, 4 * C);
     for (int i = 0; i < NSLOT; ++i) {
       umma::mbar_init(&s.acc_full[i], 1);
       umma::mbar_init(&s.acc_empty[i], 4);
@@ -192,10 +215,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
     umma::fence_mbar_init();
   }
   for (int i = tid; i < 128; i += THREADS) s.csum[i] = i < NP ? csum[i] : 0.f;
+  // the column operand's padding K columns (iy = 33..47) stay zero
+  for (int i = tid; i < 2 * CMAX * L_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(&s.L[0][0][0])[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
     umma::tmem_alloc(&s.tmem_base, 512);
     umma::tmem_relinquish();
   }
+  umma::fence_proxy_async_smem();
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -207,45 +233,55 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   };
 
   if (warp == 0) {
-    // ---------------------------------------------------------- bulk copies (one lane)
+    // ---------------------------------------------------------- copies (one lane)
     if (lane == 0) {
-      auto issue_raw = [&](int t_local) {
-        int y, x0;
-        tile_xy(t_local, y, x0);
-        const int rb = t_local & 1;
-        umma::mbar_arrive_expect_tx(&s.raw_full[rb], (uint32_t)(C * KS * RAWB));
-        for (int c = 0; c < C; ++c)
-          for (int ri = 0; ri < KS; ++ri)
-            umma::bulk_g2s(s.raw[rb][c][ri], P + ((size_t)c * (H + 32) + y + ri) * Wp + x0, RAWB, &s.raw_full[rb]);
-      };
       bool ok = true;
-      uint32_t v = 0;  // row tiles issued
-      int raw_issued = 0;
+      uint32_t it = 0;                    // rows handled
+      uint32_t a_issued = 0, b_issued = 0;  // row-block and basis-tile copies issued
+      int w_issued = 0;                   // weight tiles issued
       umma::mbar_arrive_expect_tx(&s.c_full, ct_bytes);
       umma::bulk_g2s(s.Cb, Ct, ct_bytes, &s.c_full);
-      if (my_tiles > 0) {
-        issue_raw(0);
-        raw_issued = 1;
-      }
+      auto issue_w = [&](int t) {
+        int y, x0;
+        tile_xy(t, y, x0);
+        const int nlive = min(TM, W - x0);
+        const uint32_t bytes = (uint32_t)(nlive * K * 4);
+        umma::mbar_arrive_expect_tx(&s.w_full, bytes);
+        umma::bulk_g2s(s.Wt, w + ((size_t)y * W + x0) * K, bytes, &s.w_full);
+        w_issued = t + 1;
+      };
       for (int t = 0; t < my_tiles && ok; ++t) {
-        for (int iy = 0; iy < KS && ok; ++iy, ++v) {
-          // the next tile's image rows go out a quarter of the way into this tile, into the raw buffer
-          // whose previous tile (t - 1) finished staging before the MMAs of this tile began
-          if (iy == KS / 4 && t + 1 < my_tiles) {
-            if (t >= 1 && !umma::mbar_wait(&s.raw_empty[(t + 1) & 1], ((t - 1) >> 1) & 1, kWaitNs)) {
-              ok = false;
-              break;
-            }
-            issue_raw(t + 1);
-            raw_issued = t + 2;
-          }
-          const int b = v % NBB;
-          if (v >= NBB && !umma::mbar_wait(&s.b_free[b], ((v / NBB) - 1) & 1, kWaitNs)) {
+        int y, x0;
+        tile_xy(t, y, x0);
+        for (int iy = 0; iy < KS; ++iy, ++it) {
+          const int sb = it % NB, bb = it % NBB;
+          if (it >= NB && !umma::mbar_wait(&s.a_free[sb], ((it / NB) - 1) & 1, kWaitNs)) {
             ok = false;
             break;
           }
-          umma::mbar_arrive_expect_tx(&s.b_full[b], bt_bytes);
-          umma::bulk_g2s(s.B[b], Bt + (size_t)iy * (NP * KM), bt_bytes, &s.b_full[b]);
+          umma::mbar_arrive_expect_tx(&s.a_full[sb], (uint32_t)(C * ROWB));
+#pragma unroll
+          for (int c = 0; c < C; ++c) tma_load_5d(s.A[sb][c], &tmap, 0, 0, x0 >> 3, y + (KS - 1 - iy), c, &s.a_full[sb]);
+          ++a_issued;
+          if (it >= NBB && !umma::mbar_wait(&s.b_free[bb], ((it / NBB) - 1) & 1, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          umma::mbar_arrive_expect_tx(&s.b_full[bb], bt_bytes);
+          umma::bulk_g2s(s.B[bb], Bt + (size_t)iy * (NP * KM), bt_bytes, &s.b_full[bb]);
+          ++b_issued;
+          // this tile's weights, once the epilogue of the previous tile has released the buffer
+          if (w_vec && w_issued == t && iy >= 2) {
+            if (t == 0 || umma::mbar_test(&s.w_empty, (t - 1) & 1)) {
+              issue_w(t);
+            } else if (iy == KS - 1) {
+              if (!umma::mbar_wait(&s.w_empty, (t - 1) & 1, kWaitNs)) {
+                ok = false;
+                break;
+              }
+              issue_w(t);
+            }
+          }
         }
       }
       if (!ok) {
@@ -254,154 +290,139 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
       }
       // every issued copy must land before the CTA exits (bounded)
       umma::mbar_wait(&s.c_full, 0, kWaitNs);
-      for (uint32_t u = (v >= NBB ? v - NBB : 0); u < v; ++u) umma::mbar_wait(&s.b_full[u % NBB], (u / NBB) & 1, kWaitNs);
-      for (int t = (raw_issued >= 2 ? raw_issued - 2 : 0); t < raw_issued; ++t)
-        umma::mbar_wait(&s.raw_full[t & 1], (t >> 1) & 1, kWaitNs);
+      for (uint32_t u = (a_issued >= NB ? a_issued - NB : 0); u < a_issued; ++u)
+        umma::mbar_wait(&s.a_full[u % NB], (u / NB) & 1, kWaitNs);
+      for (uint32_t u = (b_issued >= NBB ? b_issued - NBB : 0); u < b_issued; ++u)
+        umma::mbar_wait(&s.b_full[u % NBB], (u / NBB) & 1, kWaitNs);
+      if (w_issued > 0) umma::mbar_wait(&s.w_full, (w_issued - 1) & 1, kWaitNs);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issue (one lane)
     if (lane == 0) {
-      // row operand (slot 0, channel 0): core matrices 128 B apart along M and K (Hankel blocks);
-      // row tiles [j][g][8][8]: K-adjacent core matrices 128 B apart, 8-filter groups 512 B apart;
-      // column operand [p/8][g][8][8] and column taps [j][g][8][8]: 128 B along K, 768 B along M/N
+      // row blocks: core matrices 128 B apart along M and K (Hankel); row tiles [j][g][8][8]: K-adjacent
+      // core matrices 128 B apart, 8-filter groups 512 B apart; column operand [p/8][g][8][8] and
+      // column taps [j][g][8][8]: 128 B along K, 768 B along M/N
       const uint64_t a_base = umma::sdesc(umma::smem_u32(s.A[0][0]), 128, 128);
       const uint64_t b_base = umma::sdesc(umma::smem_u32(s.B[0]), 128, KM / 8 * 128);
-      const uint64_t l_base = umma::sdesc(umma::smem_u32(s.L[0]), 128, KL / 8 * 128);
+      const uint64_t l_base = umma::sdesc(umma::smem_u32(s.L[0][0]), 128, KL / 8 * 128);
       const uint64_t c_desc = umma::sdesc(umma::smem_u32(s.Cb), 128, KL / 8 * 128);
       bool ok = my_tiles == 0 || umma::mbar_wait(&s.c_full, 0, kWaitNs);
       uint32_t it = 0;
       for (int t = 0; t < my_tiles && ok; ++t) {
         for (int iy = 0; iy < KS; ++iy, ++it) {
-          const int sb = it % NB;
-          const int bb = it % NBB;
+          const int sb = it % NB, bb = it % NBB;
           if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs) ||
               !umma::mbar_wait(&s.b_full[bb], (it / NBB) & 1, kWaitNs)) {
             ok = false;
             break;
           }
-          if (iy == 0 && !umma::mbar_wait(&s.l_full, t & 1, kWaitNs)) {
-            ok = false;
-            break;
+          if (iy == 0) {
+            // fresh accumulators: wait until the epilogue has emptied their slots
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const uint32_t g = (uint32_t)(t * C + c);
+              if (g >= NSLOT && !umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) ok = false;
+            }
+            if (!ok) break;
           }
           umma::fence_after_sync();
-          // descriptors = base descriptor + (byte offset >> 4): forming each one from scratch in the
-          // issue loop costs more than the MMA itself
+          // descriptors = base descriptor + (byte offset >> 4)
           const uint64_t a_it = a_base + (uint64_t)(((uint32_t)sb * (CMAX * ROWB)) >> 4);
           const uint64_t b_it = b_base + (uint64_t)(((uint32_t)bb * B_SLOT) >> 4);
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            const uint32_t g = (uint32_t)(t * C + c);
-            const uint32_t d = tmem + (g % NSLOT) * NP;
-            if (iy == 0) {
-              // a fresh accumulator: wait until the epilogue has emptied this slot, then the column taps
-              if (g >= NSLOT && !umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) {
-                ok = false;
-                break;
-              }
-              umma::fence_after_sync();
-              const uint64_t l_c = l_base + (uint64_t)((c * L_BYTES) >> 4);
-              umma::mma_bf16(d, l_c, c_desc, idesc, 0);
+            const uint32_t d = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
+            const uint64_t a_c = a_it + (uint64_t)((c * ROWB) >> 4);
+            umma::mma_bf16(d, a_c, b_it, idesc, iy != 0);
+            umma::mma_bf16(d, a_c + 16, b_it + 16, idesc, 1);
+          }
+          umma::mma_commit(&s.a_free[sb]);
+          umma::mma_commit(&s.b_free[bb]);
+          if (iy == KS - 1) {
+            // the column taps, once the tile's column operand is complete
+            const int lb = t & 1;
+            if (!umma::mbar_wait(&s.l_full[lb], (t >> 1) & 1, kWaitNs)) {
+              ok = false;
+              break;
+            }
+            umma::fence_after_sync();
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const uint32_t d = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
+              const uint64_t l_c = l_base + (uint64_t)(((lb * CMAX + c) * L_BYTES) >> 4);
+              umma::mma_bf16(d, l_c, c_desc, idesc, 1);
               umma::mma_bf16(d, l_c + 16, c_desc + 16, idesc, 1);
               umma::mma_bf16(d, l_c + 32, c_desc + 32, idesc, 1);
             }
-            const uint64_t a_c = a_it + (uint64_t)((c * ROWB) >> 4);
-            umma::mma_bf16(d, a_c, b_it, idesc, 1);
-            umma::mma_bf16(d, a_c + 16, b_it + 16, idesc, 1);
-          }
-          if (!ok) break;
-          umma::mma_commit(&s.slot_free[sb]);
-          umma::mma_commit(&s.b_free[bb]);
-          if (iy == 0) umma::mma_commit(&s.l_free);
-          if (iy == KS - 1)
+            umma::mma_commit(&s.l_free[lb]);
 #pragma unroll
             for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
+          }
         }
       }
       if (!ok) {
         s.abort = 1;
         atomicExch(err, 1);
+      } else if (my_tiles > 0) {
+        const int t = my_tiles - 1;  // the last MMAs have completed before the CTA exits
+        umma::mbar_wait(&s.l_free[t & 1], (t >> 1) & 1, kWaitNs);
       }
-      if (it >= 1) umma::mbar_wait(&s.slot_free[(it - 1) % NB], ((it - 1) / NB) & 1, kWaitNs);
     }
   } else if (warp < EPI_WARP0) {
-    // ---------------------------------------------------------- staging: Hankel blocks and column operand
-    const int st_tid = tid - STAGE_WARP0 * 32;
+    // ---------------------------------------------------------- column operand L from the row blocks
+    const int lt = tid - L_WARP0 * 32;
     uint32_t it = 0;
     for (int t = 0; t < my_tiles; ++t) {
-      const int rb = t & 1;
-      if (!umma::mbar_wait(&s.raw_full[rb], (t >> 1) & 1, kWaitNs)) s.abort = 1;
-      // the column operand of the previous tile has been consumed by its first MMAs
-      if (t >= 1 && !umma::mbar_wait(&s.l_free, (t - 1) & 1, kWaitNs)) s.abort = 1;
+      const int lb = t & 1;
+      // buffer lb was last read by the column MMAs of tile t - 2
+      if (t >= 2 && !umma::mbar_wait(&s.l_free[lb], ((t - 2) >> 1) & 1, kWaitNs)) s.abort = 1;
       if (s.abort) break;
-      // L[p][iy] = raw row 32 - iy, column p + 32 (iy < 33; zero up to 48), K-major [p/8][iy/8][8][8]
-      for (int item = st_tid; item < C * (KL / 8) * TM; item += NSTAGE_WARPS * 32) {
-        const int p = item & (TM - 1);
-        const int cg = item >> 7;
-        const int c = cg / (KL / 8), g = cg - c * (KL / 8);
-        uint32_t wv[4];
-#pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          uint32_t lo = 0, hi = 0;
-          const int iy0 = 8 * g + 2 * e2;
-          if (iy0 < KS) lo = *reinterpret_cast<const uint16_t*>(s.raw[rb][c][KS - 1 - iy0] + 2 * (p + 32));
-          if (iy0 + 1 < KS) hi = *reinterpret_cast<const uint16_t*>(s.raw[rb][c][KS - 2 - iy0] + 2 * (p + 32));
-          wv[e2] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4*>(s.L[c] + ((p >> 3) * (KL / 8) + g) * 128 + (p & 7) * 16) =
-            make_uint4(wv[0], wv[1], wv[2], wv[3]);
-      }
-      umma::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&s.l_full);
       for (int iy = 0; iy < KS; ++iy, ++it) {
         const int sb = it % NB;
-        if (it >= NB && !umma::mbar_wait(&s.slot_free[sb], ((it / NB) - 1) & 1, kWaitNs)) s.abort = 1;
+        if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs)) s.abort = 1;
         if (s.abort) break;
-        const int ri = KS - 1 - iy;
-        // item = (channel, block, row s of the block), s fastest: 8 lanes write one 128-byte block
-        for (int item = st_tid; item < C * NBLK * 8; item += NSTAGE_WARPS * 32) {
-          const int sr = item & 7;
-          const int cb = item >> 3;
-          const int c = cb / NBLK, b = cb - c * NBLK;
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(s.raw[rb][c][ri]) + 4 * b + (sr >> 1);
-          const uint32_t w0 = src[0], w1 = src[1], w2 = src[2], w3 = src[3], w4 = src[4];
-          const uint32_t sh = (sr & 1) * 16;
-          const uint4 o = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                                     __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
-          *reinterpret_cast<uint4*>(s.A[sb][c] + b * 128 + sr * 16) = o;
+        // L[p][iy] = E_b[sh][0] with 8 b + sh = p + 32; K-major [p/8][iy/8][p%8][iy%8]
+        for (int item = lt; item < C * TM; item += NL_WARPS * 32) {
+          const int c = item >> 7, p = item & (TM - 1);
+          const int e = p + 32;
+          const uint16_t v = *reinterpret_cast<const uint16_t*>(s.A[sb][c] + (e >> 3) * 128 + (e & 7) * 16);
+          *reinterpret_cast<uint16_t*>(s.L[lb][c] + ((p >> 3) * (KL / 8) + (iy >> 3)) * 128 + (p & 7) * 16 + (iy & 7) * 2) = v;
         }
-        umma::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&s.a_full[sb]);
+        if (lane == 0) umma::mbar_arrive(&s.a_free[sb]);
       }
       if (s.abort) break;
-      if (lane == 0) umma::mbar_arrive(&s.raw_empty[rb]);
+      umma::fence_proxy_async_smem();  // L stores -> visible to the tensor cores
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&s.l_full[lb]);
     }
   } else {
     // ---------------------------------------------------------- epilogue: TMEM -> weighted sums, one channel per group
     const int c = (warp - EPI_WARP0) >> 2;
     const int q4 = warp & 3;  // warp w reads TMEM lanes 32 (w % 4) ..
+    const int p = q4 * 32 + lane;
     if (c < C) {
       for (int t = 0; t < my_tiles; ++t) {
         int y, x0;
         tile_xy(t, y, x0);
-        const int x = x0 + q4 * 32 + lane;
+        const int x = x0 + p;
         const bool live = x < W;
-        const size_t pix = (size_t)y * W + (live ? x : 0);
-        const WT* wg = w + pix * K;
         const uint32_t g = (uint32_t)(t * C + c);
         const uint32_t slot = g % NSLOT;
         if (!umma::mbar_wait(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
+        if (w_vec && !umma::mbar_wait(&s.w_full, t & 1, kWaitNs)) s.abort = 1;
         if (s.abort) break;
         umma::fence_after_sync();
         float acc = 0.f;
+        const float* ws = s.Wt + p * K;
+        const WT* wg = w + ((size_t)y * W + (live ? x : 0)) * K;
         for (int q = 0; q < NP / 16; ++q) {
           float wk[16];
-          if (w_vec) {  // 16-byte aligned FP32 rows: four vector loads
+          if (w_vec) {  // the tile's FP32 weights in shared memory
 #pragma unroll
             for (int i4 = 0; i4 < 4; ++i4) {
               const int k = q * 16 + 4 * i4;
-              const float4 v4 = k < K ? __ldg(reinterpret_cast<const float4*>(wg) + (k >> 2)) : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float4 v4 = (k < K && live) ? *reinterpret_cast<const float4*>(ws + k) : make_float4(0.f, 0.f, 0.f, 0.f);
               wk[4 * i4 + 0] = v4.x;
               wk[4 * i4 + 1] = v4.y;
               wk[4 * i4 + 2] = v4.z;
@@ -421,7 +442,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
         }
         umma::fence_before_sync();
         __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&s.acc_empty[slot]);
+        if (lane == 0) {
+          umma::mbar_arrive(&s.acc_empty[slot]);
+          if (w_vec) umma::mbar_arrive(&s.w_empty);
+        }
         if (live) out[((size_t)c * H + y) * W + x] = acc;
       }
     }
@@ -429,6 +453,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_blur_tc(const __nv_bfloat16* __r
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, 512);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)ptr;
+  }
+  return fn;
 }
 
 }  // namespace
@@ -453,8 +493,10 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
   }
   const int nseg = (W + TM - 1) / TM;
-  const int Wp = nseg * TM + 64;
-  const size_t need = (size_t)C * (H + 32) * Wp;
+  const int Wq = nseg * TM + 64;  // >= x0 + 160 for every tile; a multiple of 8 (16-byte rows)
+  const int R = H + 32;
+  const size_t plane = (size_t)R * Wq;
+  const size_t need = (size_t)C * NSHIFT * plane;
   if (need > p->pad_cap) {
     if (p->pad) cudaFree(p->pad);
     p->pad = nullptr;
@@ -462,7 +504,9 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
     if (cudaMalloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
     p->pad_cap = need;
   }
-  k_pad_bf16<<<dim3((Wp + 255) / 256, H + 32, C), 256, 0, st>>>(img, C, H, W, Wp, centre, p->pad);
+  EncodeTiledFn encode = encode_tiled();
+  if (!encode) return DFP2S_EUNSUPPORTED;
+  k_pad_shifted<<<dim3((Wq + 255) / 256, R, C), 256, 0, st>>>(img, C, H, W, Wq, centre, p->pad);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -478,14 +522,23 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
   cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_blur_tc<__nv_bfloat16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  // FP32 weights in 16-byte aligned rows are read with vector loads
+  // FP32 weights whose tile rows are 16-byte multiples come in by one bulk copy per tile
   const int w_vec = (w_dtype == DFP2S_W_F32) && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
   for (int c0 = 0; c0 < C; c0 += CMAX) {
     const int nc = C - c0 < CMAX ? C - c0 : CMAX;
-    const __nv_bfloat16* pc = p->pad + (size_t)c0 * (H + 32) * Wp;
+    // rank-5 view of the shifted copies: (t: 8 columns, sh: shift, b: 8-column block, r: row, c: channel)
+    CUtensorMap tmap;
+    const cuuint64_t dims[5] = {8, NSHIFT, (cuuint64_t)(Wq / 8), (cuuint64_t)R, (cuuint64_t)nc};
+    const cuuint64_t strides[4] = {plane * 2, 16, (cuuint64_t)Wq * 2, NSHIFT * plane * 2};
+    const cuuint32_t box[5] = {8, NSHIFT, NBLK, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p->pad + (size_t)c0 * NSHIFT * plane, dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return DFP2S_EUNSUPPORTED;
     float* oc = out + (size_t)c0 * H * W;
-#define DFP2S_BLUR_LAUNCH(WT, NC, WPTR, WSM) \
-  k_blur_tc<WT, NC><<<grid, THREADS, sm, st>>>(pc, H, W, Wp, p->bt, K, NP, p->bsum, WPTR, WSM, oc, p->err)
+#define DFP2S_BLUR_LAUNCH(WT, NC, WPTR, WV) \
+  k_blur_tc<WT, NC><<<grid, THREADS, sm, st>>>(tmap, H, W, p->bt, K, NP, p->bsum, WPTR, WV, oc, p->err)
     if (w_dtype == DFP2S_W_BF16) {
       const __nv_bfloat16* wb = (const __nv_bfloat16*)w;
       if (nc == 1) DFP2S_BLUR_LAUNCH(__nv_bfloat16, 1, wb, 0);
