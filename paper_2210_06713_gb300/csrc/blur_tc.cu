@@ -83,6 +83,27 @@ struct Smem {
   int abort;
 };
 
+// Warp-wide load of 16 TMEM columns without waiting; tmem_wait_ld waits for all
+// outstanding loads and ties the destination registers to the wait, so that no
+// use of them is scheduled before it.
+DFP2S_DEV void tmem_ld16_async(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+DFP2S_DEV void tmem_wait_ld(float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
 // TMA tile load of a rank-5 box into shared memory, completion counted in bytes on `bar`.
 DFP2S_DEV void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4, uint64_t* bar) {
   asm volatile(
@@ -316,26 +337,28 @@ __global__ void __launch_bounds__(THREADS, 1)
             ok = false;
             break;
           }
-          if (iy == 0) {
-            // fresh accumulators: wait until the epilogue has emptied their slots
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              const uint32_t g = (uint32_t)(t * C + c);
-              if (g >= NSLOT && !umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) ok = false;
-            }
-            if (!ok) break;
-          }
           umma::fence_after_sync();
           // descriptors = base descriptor + (byte offset >> 4)
           const uint64_t a_it = a_base + (uint64_t)(((uint32_t)sb * (CMAX * ROWB)) >> 4);
           const uint64_t b_it = b_base + (uint64_t)(((uint32_t)bb * B_SLOT) >> 4);
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            const uint32_t d = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
+            const uint32_t g = (uint32_t)(t * C + c);
+            if (iy == 0 && g >= NSLOT) {
+              // a fresh accumulator: wait until the epilogue has emptied the slot (the previous
+              // channels' MMAs are already running meanwhile)
+              if (!umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) {
+                ok = false;
+                break;
+              }
+              umma::fence_after_sync();
+            }
+            const uint32_t d = tmem + (g % NSLOT) * NP;
             const uint64_t a_c = a_it + (uint64_t)((c * ROWB) >> 4);
             umma::mma_bf16(d, a_c, b_it, idesc, iy != 0);
             umma::mma_bf16(d, a_c + 16, b_it + 16, idesc, 1);
           }
+          if (!ok) break;
           umma::mma_commit(&s.a_free[sb]);
           umma::mma_commit(&s.b_free[bb]);
           if (iy == KS - 1) {
@@ -370,26 +393,47 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp < EPI_WARP0) {
     // ---------------------------------------------------------- column operand L from the row blocks
+    // Thread (c, m) keeps, for eight consecutive basis rows iy = 8 g + e, the pixels p = 8 m .. 8 m + 7
+    // of row 0 of block E_{m+4} (8 b + t = p + 32, one 16-byte load per row), then transposes the
+    // 8 x 8 tile in registers and writes the core matrix L[8 m .. 8 m + 7][8 g .. 8 g + 7].
     const int lt = tid - L_WARP0 * 32;
+    const int lc = lt >> 4, m = lt & 15;
+    const bool active = lc < C;
     uint32_t it = 0;
-    for (int t = 0; t < my_tiles; ++t) {
+    for (int t = 0; t < my_tiles && !s.abort; ++t) {
       const int lb = t & 1;
       // buffer lb was last read by the column MMAs of tile t - 2
       if (t >= 2 && !umma::mbar_wait(&s.l_free[lb], ((t - 2) >> 1) & 1, kWaitNs)) s.abort = 1;
-      if (s.abort) break;
-      for (int iy = 0; iy < KS; ++iy, ++it) {
-        const int sb = it % NB;
-        if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs)) s.abort = 1;
-        if (s.abort) break;
-        // L[p][iy] = E_b[sh][0] with 8 b + sh = p + 32; K-major [p/8][iy/8][p%8][iy%8]
-        for (int item = lt; item < C * TM; item += NL_WARPS * 32) {
-          const int c = item >> 7, p = item & (TM - 1);
-          const int e = p + 32;
-          const uint16_t v = *reinterpret_cast<const uint16_t*>(s.A[sb][c] + (e >> 3) * 128 + (e & 7) * 16);
-          *reinterpret_cast<uint16_t*>(s.L[lb][c] + ((p >> 3) * (KL / 8) + (iy >> 3)) * 128 + (p & 7) * 16 + (iy & 7) * 2) = v;
+      for (int g = 0; g < (KS + 7) / 8 && !s.abort; ++g) {
+        uint4 win[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          win[e] = make_uint4(0, 0, 0, 0);
+          if (8 * g + e < KS) {
+            const int sb = it % NB;
+            if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs)) {
+              s.abort = 1;
+              break;
+            }
+            if (active) win[e] = *reinterpret_cast<const uint4*>(s.A[sb][lc] + (m + 4) * 128);
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&s.a_free[sb]);
+            ++it;
+          }
         }
-        __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&s.a_free[sb]);
+        if (active) {
+          // out[j] = column j of the 8 x 8 bf16 tile: rows 2k and 2k + 1 in word k
+          uint8_t* dst = s.L[lb][lc] + (m * (KL / 8) + g) * 128;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;
+            const int wj = j >> 1;
+            auto word = [&](const uint4& v) { return wj == 0 ? v.x : (wj == 1 ? v.y : (wj == 2 ? v.z : v.w)); };
+            const uint4 o = make_uint4(__byte_perm(word(win[0]), word(win[1]), sel), __byte_perm(word(win[2]), word(win[3]), sel),
+                                       __byte_perm(word(win[4]), word(win[5]), sel), __byte_perm(word(win[6]), word(win[7]), sel));
+            *reinterpret_cast<uint4*>(dst + j * 16) = o;
+          }
+        }
       }
       if (s.abort) break;
       umma::fence_proxy_async_smem();  // L stores -> visible to the tensor cores
@@ -416,29 +460,38 @@ __global__ void __launch_bounds__(THREADS, 1)
         float acc = 0.f;
         const float* ws = s.Wt + p * K;
         const WT* wg = w + ((size_t)y * W + (live ? x : 0)) * K;
-        for (int q = 0; q < NP / 16; ++q) {
-          float wk[16];
-          if (w_vec) {  // the tile's FP32 weights in shared memory
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + slot * NP;
+        const int nq = NP / 16;
+        // two register buffers: the load of group q + 1 overlaps the arithmetic of group q
+        float d0[16], d1[16];
+        tmem_ld16_async(taddr, d0);
 #pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4) {
-              const int k = q * 16 + 4 * i4;
-              const float4 v4 = (k < K && live) ? *reinterpret_cast<const float4*>(ws + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-              wk[4 * i4 + 0] = v4.x;
-              wk[4 * i4 + 1] = v4.y;
-              wk[4 * i4 + 2] = v4.z;
-              wk[4 * i4 + 3] = v4.w;
-            }
-          } else {
+        for (int q = 0; q < 8; ++q) {
+          if (q < nq) {
+            float* dq = (q & 1) ? d1 : d0;
+            tmem_wait_ld(dq);
+            if (q + 1 < nq) tmem_ld16_async(taddr + (q + 1) * 16, (q & 1) ? d0 : d1);
+            float wk[16];
+            if (w_vec) {  // the tile's FP32 weights in shared memory
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int k = q * 16 + i;
-              wk[i] = k < K ? wload<WT>(wg + k) : 0.f;
+              for (int i4 = 0; i4 < 4; ++i4) {
+                const int k = q * 16 + 4 * i4;
+                const float4 v4 = (k < K && live) ? *reinterpret_cast<const float4*>(ws + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                wk[4 * i4 + 0] = v4.x;
+                wk[4 * i4 + 1] = v4.y;
+                wk[4 * i4 + 2] = v4.z;
+                wk[4 * i4 + 3] = v4.w;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int k = q * 16 + i;
+                wk[i] = k < K ? wload<WT>(wg + k) : 0.f;
+              }
             }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc = fmaf(wk[i], dq[i] + s.csum[q * 16 + i], acc);
           }
-          float d[16];
-          umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + slot * NP + q * 16, d);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) acc = fmaf(wk[i], d[i] + s.csum[q * 16 + i], acc);
         }
         umma::fence_before_sync();
         __syncwarp();
