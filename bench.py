@@ -157,7 +157,7 @@ def run_ours(args, rank, world, device):
     w = torch.empty(H, W, K, device=device, dtype=torch.float32)
     out = torch.empty(C, H, W, device=device)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
-    nstage = 4
+    nstage = 5
     seed_base = 1000 * rank
 
     def step(i, ev=None):
@@ -174,11 +174,17 @@ def run_ours(args, rank, world, device):
         if ev is not None:
             ev[3].record(stream)
         if mode == d.P2S_LEARNED:
-            d.basis_blur_tc(S["P"], warped, w, out=out)
+            # the two steps of the tensor-core blur, so that its contraction kernel is timed alone
+            d.basis_blur_tc_prepare(S["P"], warped)
+            if ev is not None:
+                ev[4].record(stream)
+            d.basis_blur_tc_run(S["P"], (C, H, W), w, out=out)
         else:
+            if ev is not None:
+                ev[4].record(stream)
             d.basis_blur(S["P"], warped, w, out=out)
         if ev is not None:
-            ev[4].record(stream)
+            ev[5].record(stream)
 
     for i in range(args.warmup):
         step(i)
@@ -229,19 +235,24 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    names = ["fields", "warp", "p2s_" + args.mode, "blur"]
+    names = ["fields", "warp", "p2s_" + args.mode, "blur_prepare", "blur"]
     acc = None
     if args.mode == "learned" and not args.no_accuracy:
         acc = accuracy_vs_exact(d, S, seed_base + 77)
     mean_stage = stage_ms.mean(axis=0)
     peaks, peak_kind = _peaks()
-    # dominant kernel roofline
-    dom = int(np.argmax(mean_stage))
+    # dominant kernel roofline: among the stages that are one kernel launch each (warp, P2S weights, blur
+    # contraction); the field stage is four launches, each shorter than the blur contraction (ncu launch list)
+    single = [1, 2, 4]
+    dom = single[int(np.argmax(mean_stage[single]))]
     npix = H * W
     if names[dom] == "blur" and args.mode == "learned":
-        flops = 2.0 * 1089 * K * C * npix  # Eq. (varying blur) as a dense contraction on the tensor cores
+        # Eq. (varying blur) as a dense contraction on the tensor cores: 2 x 33^2 x K MACs per pixel and
+        # channel; the events bracket the one k_blur_tc launch of the frame (C <= 3)
+        flops = 2.0 * 1089 * K * C * npix
         roof = {"kernel": "k_blur_tc", "bound": "tensor", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None, "peak_source": peak_kind}
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
+                "peak_source": peak_kind + " (burst bf16 GEMM)"}
     elif names[dom] == "blur":
         flops = 2.0 * 1089 * (K + C) * npix  # per-pixel PSF form on FP32 CUDA cores
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -249,22 +260,31 @@ def run_ours(args, rank, world, device):
         roof = {"kernel": "k_blur_psf", "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    elif names[dom].startswith("p2s") and args.mode == "learned":
+        # the surrogate MLP on the tensor cores: 2 (256 J + 256^2 + 256 K) FLOP per pixel, one k_mlp_tc launch
+        flops = npix * 2.0 * (J * 256 + 256 * 256 + 256 * K)
+        roof = {"kernel": "k_mlp_tc", "bound": "tensor", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
+                "peak_source": peak_kind + " (burst bf16 GEMM)"}
     elif names[dom].startswith("p2s"):
-        if args.mode == "exact":
-            flops = npix * (2.0 * 1089 * (J - 2) + 2 * 8.0 * 33 ** 3 + 2.0 * 1089 * K)
-        else:
-            flops = npix * 2.0 * (J * 256 + 256 * 256 + 256 * K)
+        flops = npix * (2.0 * 1089 * (J - 2) + 2 * 8.0 * 33 ** 3 + 2.0 * 1089 * K)
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "k_p2s_" + args.mode, "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+        roof = {"kernel": "k_p2s_exact", "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     else:
-        N = S["N"]
-        half = N // 2 + 1
-        byt = 16.0 * J * N * half + 16.0 * J * H * half + 4.0 * J * npix + 4.0 * J * N * half + 8.0 * J * npix
-        roof = {"kernel": "fields (4 kernels)", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
+        byt = 4.0 * npix * (2 + 2 * C)  # tilt fields a2, a3 and the image in, the warped image out
+        roof = {"kernel": "k_tilt_warp", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
+    # the field sampler's four launches as one HBM-bound stage: spectrum written and read (16 J N (N/2+1)),
+    # multiplier (4 J N (N/2+1)), cropped columns written and read (16 J H (N/2+1)), fields and mixing (12 J H W)
+    N = S["N"]
+    half = N // 2 + 1
+    fbytes = 16.0 * J * N * half + 16.0 * J * H * half + 4.0 * J * npix + 4.0 * J * N * half + 8.0 * J * npix
+    fields_roof = {"kernels": "k_rowfft_noise + k_colfilter + k_rowifft + k_mix", "bound": "hbm",
+                   "achieved": fbytes / (mean_stage[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    fields_roof["frac"] = fields_roof["achieved"] / fields_roof["peak"]
     roof["frac"] = roof["achieved"] / roof["peak"]
     value = world * args.steps / (total_ms * 1e-3)
     line = {
@@ -278,6 +298,7 @@ def run_ours(args, rank, world, device):
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)},
         "rel_l2_learned_vs_exact": acc,
         "roofline": roof,
+        "fields_roofline": fields_roof,
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
         "gpu_launches": args.steps * (8 if args.mode == "learned" else 7),

@@ -254,6 +254,20 @@ int dfp2s_basis_blur(const dfp2s_p2s* p, const float* img_dev, int C, int H, int
 int dfp2s_basis_blur_tc(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W, const void* w_dev,
                         int w_dtype, float* out_dev, void* stream);
 
+/* dfp2s_basis_blur_tc in its two steps, for callers that time or overlap
+ * them separately.  _prepare writes the image's BF16 operand (eight copies of
+ * bfloat16(I - 0.5), edge-padded by 16 and shifted by 0..7 columns, so that
+ * the tensor-core operand tiles of Eq. (varying blur) are 16-byte aligned
+ * runs) into scratch owned by the handle; _run contracts the prepared image
+ * with the basis and the weights w_dev.  A handle holds one prepared image:
+ * issue _prepare and then _run, with the same C, H, W, on one stream; _run on
+ * a handle without a prepared image of that shape returns EINVAL.
+ * dfp2s_basis_blur_tc(...) is _prepare followed by _run.
+ * Errors: EINVAL, EUNSUPPORTED (K > 128), ENOMEM (scratch), ECUDA. */
+int dfp2s_basis_blur_tc_prepare(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W, void* stream);
+int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void* w_dev, int w_dtype, float* out_dev,
+                            void* stream);
+
 /* ---------------------------------------------------------------- frames
  * A context binds a factor and a P2S handle and owns the per-frame scratch
  * (fields, warped image, weights) for frames up to max_C x max_H x max_W. */

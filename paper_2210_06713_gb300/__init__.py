@@ -64,6 +64,8 @@ SIGNATURES = {
     "dfp2s_tilt_warp": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dfp2s_basis_blur": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_basis_blur_tc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
+    "dfp2s_basis_blur_tc_prepare": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "dfp2s_basis_blur_tc_run": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_ctx_create": (_i, [_vp, _vp, _i, _i, _i, _c.POINTER(_vp)]),
     "dfp2s_ctx_destroy": (_i, [_vp]),
     "dfp2s_simulate_frame": (_i, [_vp, _vp, _i, _i, _i, _d, _u64, _u32, _i, _vp, _vp]),
@@ -334,6 +336,22 @@ def basis_blur_tc(p: P2S, img: torch.Tensor, w: torch.Tensor, out: torch.Tensor 
         out = torch.empty_like(img)
     wdt = W_BF16 if w.dtype == torch.bfloat16 else W_F32
     _check(load().dfp2s_basis_blur_tc(p.handle, _ptr(img), C, H, W, _ptr(w), wdt, _ptr(out), _stream(stream)))
+    return out
+
+
+def basis_blur_tc_prepare(p: P2S, img: torch.Tensor, stream=None) -> None:
+    """First step of basis_blur_tc: the image's shifted BF16 operand, kept in the handle."""
+    C, H, W = img.shape
+    _check(load().dfp2s_basis_blur_tc_prepare(p.handle, _ptr(img), C, H, W, _stream(stream)))
+
+
+def basis_blur_tc_run(p: P2S, shape, w: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Second step of basis_blur_tc: the contraction on the image prepared for `shape` = (C, H, W)."""
+    C, H, W = shape
+    if out is None:
+        out = torch.empty(C, H, W, device=w.device, dtype=torch.float32)
+    wdt = W_BF16 if w.dtype == torch.bfloat16 else W_F32
+    _check(load().dfp2s_basis_blur_tc_run(p.handle, C, H, W, _ptr(w), wdt, _ptr(out), _stream(stream)))
     return out
 
 

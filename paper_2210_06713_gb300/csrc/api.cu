@@ -382,6 +382,28 @@ extern "C" int dfp2s_basis_blur_tc(const dfp2s_p2s* p, const float* img, int C, 
   return DFP2S_OK;
 }
 
+extern "C" int dfp2s_basis_blur_tc_prepare(const dfp2s_p2s* p, const float* img, int C, int H, int W, void* stream) {
+  CHECK_ARG(p && img, "null argument");
+  CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 - 32 && W <= (1 << 20), "bad image shape");
+  const int rc = dfp2s_launch_blur_tc_prepare(const_cast<dfp2s_p2s_dev*>(&p->d), img, C, H, W, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
+  if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur image preparation");
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void* w, int w_dtype, float* out,
+                                       void* stream) {
+  CHECK_ARG(p && w && out, "null argument");
+  CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 - 32 && W <= (1 << 20), "bad image shape");
+  CHECK_ARG(w_dtype == DFP2S_W_F32 || w_dtype == DFP2S_W_BF16, "unknown weight dtype");
+  const int rc = dfp2s_launch_blur_tc_run(const_cast<dfp2s_p2s_dev*>(&p->d), C, H, W, w, w_dtype, out, as_stream(stream));
+  if (rc == DFP2S_EINVAL) return dfp2s_fail(rc, "no prepared image of shape %dx%dx%d on this handle", C, H, W);
+  if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128 (and needs TMA)");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur launch");
+  return DFP2S_OK;
+}
+
 // ------------------------------------------------------------------ frames
 struct dfp2s_ctx {
   const dfp2s_factor* f;

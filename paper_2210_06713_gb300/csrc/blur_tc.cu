@@ -526,8 +526,8 @@ EncodeTiledFn encode_tiled() {
 
 }  // namespace
 
-int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
-                         float* out, cudaStream_t st) {
+// Shifted BF16 planes of the image in the handle's scratch (k_pad_shifted).
+int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, cudaStream_t st) {
   const int K = p->K;
   const int NP = (K + 15) / 16 * 16;
   const float centre = 0.5f;
@@ -557,9 +557,26 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
     if (cudaMalloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
     p->pad_cap = need;
   }
+  k_pad_shifted<<<dim3((Wq + 255) / 256, R, C), 256, 0, st>>>(img, C, H, W, Wq, centre, p->pad);
+  p->prep_C = C;
+  p->prep_H = H;
+  p->prep_W = W;
+  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+}
+
+// The tensor-core contraction on the prepared planes.
+int dfp2s_launch_blur_tc_run(dfp2s_p2s_dev* p, int C, int H, int W, const void* w, int w_dtype, float* out,
+                             cudaStream_t st) {
+  const int K = p->K;
+  const int NP = (K + 15) / 16 * 16;
+  if (NP > 128) return DFP2S_EUNSUPPORTED;
+  if (!p->pad || !p->bt || p->prep_C != C || p->prep_H != H || p->prep_W != W) return DFP2S_EINVAL;
+  const int nseg = (W + TM - 1) / TM;
+  const int Wq = nseg * TM + 64;
+  const int R = H + 32;
+  const size_t plane = (size_t)R * Wq;
   EncodeTiledFn encode = encode_tiled();
   if (!encode) return DFP2S_EUNSUPPORTED;
-  k_pad_shifted<<<dim3((Wq + 255) / 256, R, C), 256, 0, st>>>(img, C, H, W, Wq, centre, p->pad);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -606,4 +623,11 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
 #undef DFP2S_BLUR_LAUNCH
   }
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+}
+
+int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
+                         float* out, cudaStream_t st) {
+  const int rc = dfp2s_launch_blur_tc_prepare(p, img, C, H, W, st);
+  if (rc != DFP2S_OK) return rc;
+  return dfp2s_launch_blur_tc_run(p, C, H, W, w, w_dtype, out, st);
 }

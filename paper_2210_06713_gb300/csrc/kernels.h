@@ -56,6 +56,7 @@ struct dfp2s_p2s_dev {
   size_t pad_cap;
   int* err;
   float* bsum;  // centre * sum of each bfloat16 basis function (tensor-core blur)
+  int prep_C, prep_H, prep_W;  // image shape whose shifted planes `pad` holds (tensor-core blur)
   // tensor-core surrogate: packed BF16 weights and the folded output offset
   __nv_bfloat16 *tc_w1, *tc_w2, *tc_w3;
   float* tc_c3;
@@ -91,6 +92,9 @@ int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const do
                              float* basis_out, double* sigma_host, int* sweeps_out, cudaStream_t st);
 
 // blur_tc.cu -- BF16 tcgen05 blur (weights in BF16)
+int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, cudaStream_t st);
+int dfp2s_launch_blur_tc_run(dfp2s_p2s_dev* p, int C, int H, int W, const void* w, int w_dtype, float* out,
+                             cudaStream_t st);
 int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
                          float* out, cudaStream_t st);
 

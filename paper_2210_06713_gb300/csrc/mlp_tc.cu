@@ -2,20 +2,23 @@
 // kernel per frame, BF16 operands, FP32 accumulation in tensor memory.
 //
 // A tile is 128 consecutive pixels (MMA M = 128):
-//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T -> TMEM columns A = [0, 256)
+//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T -> TMEM A = columns [0, 256)
 //            (W1' = W1 diag(in_scale), resident in shared memory)
 //   GELU(z + b1) -> H [128 x 256] BF16 in shared memory (K-major core matrices)
 //   layer 2: H x W2^T -> TMEM B = [256, 512), W2 streamed in four 64-wide K chunks
 //   GELU(z + b2) -> H
-//   layer 3: H x W3^T -> TMEM A[0, NP3), W3 streamed in four K chunks
+//   layer 3: H x W3^T -> TMEM [384, 384 + NP3), W3 streamed in four K chunks
 //   w = y * out_scale + (b3 * out_scale + out_shift) -> global (FP32 or BF16)
 //
-// Warp roles: warps 0-7 run the epilogues (warps w and w + 4 read TMEM lanes
-// 32 (w % 4) .., one half of the columns each), warp 8 issues the weight copies
-// and the MMAs.  The epilogues hand H over in 64-column chunks (one mbarrier
-// per chunk), so the MMAs of the next layer start on chunk c while the
-// epilogue is still working on chunk c + 1.  Weight chunks arrive by 1-D bulk
-// copies into a three-deep ring; their MMAs release a slot through
+// Warp roles: warps 0-15 run the epilogues (warp w reads TMEM lanes 32 (w % 4)
+// .. and a quarter of the columns), warp 16 issues the weight copies and the
+// MMAs, warp 17 converts the next tile's fields into X.  The epilogues hand H
+// over in 64-column chunks (one mbarrier per chunk), so the MMAs of the next
+// layer start on a chunk while the epilogue works on the following one; the
+// second epilogue walks its chunks from the top so that layer 3's columns
+// [384, 512) are free first.  Layer 1 of the next tile runs on the tensor
+// cores while the epilogues finish the current tile.  Weight chunks arrive by
+// 1-D bulk copies into a three-deep ring; their MMAs release a slot through
 // tcgen05.commit.  All waits are bounded; a wait that runs out sets the
 // kernel's error word.
 #include <cuda_bf16.h>
@@ -31,9 +34,12 @@ namespace {
 constexpr int TM = 128;
 constexpr int HID = 256;
 constexpr int KX = 48;           // J padded to three K = 16 steps
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
-constexpr int THREADS = EPI_THREADS + 32;  // + the producer warp
+constexpr int PRODUCER_WARP = EPI_WARPS;
+constexpr int LOADER_WARP = EPI_WARPS + 1;
+constexpr int THREADS = EPI_THREADS + 64;  // + producer and loader warps
+constexpr int L3_COL = 384;                // layer-3 accumulator columns [384, 384 + NP3)
 constexpr int NRING = 3;
 constexpr int CHUNK_BYTES = HID * 64 * 2;  // one 64-wide K chunk of W2 (the largest)
 constexpr int STAGE_BYTES = TM * 132 * 4;  // FP32 output rows of up to 128 (+4) weights
@@ -90,22 +96,6 @@ DFP2S_DEV uint32_t kmajor_off(int row, int k, int kgroups) {
   return (uint32_t)(((row >> 3) * kgroups + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// 32 consecutive 32-bit TMEM columns of this thread's lane (warp-wide).
-DFP2S_DEV void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // Barrier of the epilogue warps (named barrier 1) that also ORs a flag over
 // them, so that every epilogue thread takes the same abort decision.
 DFP2S_DEV bool bar_epi_any(bool v) {
@@ -128,28 +118,29 @@ DFP2S_DEV void wstore<float>(float* p, float v) { *p = v; }
 template <>
 DFP2S_DEV void wstore<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-// Hidden-layer epilogue of one epilogue warp: for each 64-column chunk c, this
-// warp's 32 columns [64 c + 32 h, +32) of TMEM region `col0` -> GELU(z + b) ->
-// H (K-major, K = column - col0), then the chunk is handed to the MMA warp.
-DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col0, const float* bias) {
-  const int q4 = warp & 3, h = warp >> 2;
+// Hidden-layer epilogue of one epilogue warp: for each 64-column chunk c
+// (ascending, or descending if `reverse`), this warp's 16 columns
+// [64 c + 16 sl, +16) of TMEM region `col0` -> GELU(z + b) -> H (K-major,
+// K = column - col0), then the chunk is handed to the MMA warp.
+DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col0, const float* bias, bool reverse) {
+  const int q4 = warp & 3, sl = warp >> 2;
   const int p = q4 * 32 + lane;
-  for (int c = 0; c < 4; ++c) {
-    const int k0 = 64 * c + 32 * h;
-    float d[32];
-    tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + col0 + k0, d);
-    uint32_t packed[16];
+  for (int i = 0; i < 4; ++i) {
+    const int c = reverse ? 3 - i : i;
+    const int k0 = 64 * c + 16 * sl;
+    float d[16];
+    umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + col0 + k0, d);
+    uint32_t packed[8];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float g0 = gelu(d[2 * i] + bias[k0 + 2 * i]);
-      const float g1 = gelu(d[2 * i + 1] + bias[k0 + 2 * i + 1]);
+    for (int e = 0; e < 8; ++e) {
+      const float g0 = gelu(d[2 * e] + bias[k0 + 2 * e]);
+      const float g1 = gelu(d[2 * e + 1] + bias[k0 + 2 * e + 1]);
       __nv_bfloat162 h2 = __floats2bfloat162_rn(g0, g1);
-      packed[i] = *reinterpret_cast<uint32_t*>(&h2);
+      packed[e] = *reinterpret_cast<uint32_t*>(&h2);
     }
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-      *reinterpret_cast<uint4*>(s.H + kmajor_off(p, k0 + 8 * m, HID / 8)) =
-          make_uint4(packed[4 * m], packed[4 * m + 1], packed[4 * m + 2], packed[4 * m + 3]);
+    *reinterpret_cast<uint4*>(s.H + kmajor_off(p, k0, HID / 8)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    *reinterpret_cast<uint4*>(s.H + kmajor_off(p, k0 + 8, HID / 8)) =
+        make_uint4(packed[4], packed[5], packed[6], packed[7]);
     umma::fence_proxy_async_smem();  // H stores -> visible to the tensor cores
     umma::fence_before_sync();       // TMEM reads ordered before the hand-over
     __syncwarp();
@@ -175,7 +166,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       umma::mbar_init(&s.empty[i], 1);
     }
     umma::mbar_init(&s.w1_full, 1);
-    umma::mbar_init(&s.x_ready, EPI_WARPS);
+    umma::mbar_init(&s.x_ready, 1);
     umma::mbar_init(&s.l1_done, 1);
     umma::mbar_init(&s.l2_done, 1);
     umma::mbar_init(&s.l3_done, 1);
@@ -202,7 +193,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   umma::fence_after_sync();
   const uint32_t tmem = s.tmem_base;
 
-  if (warp == EPI_WARPS) {
+  if (warp == PRODUCER_WARP) {
     // ------------------------------------------------------------ producer: copies and MMAs
     if (lane == 0) {
       const uint32_t w2_bytes = (uint32_t)CHUNK_BYTES;
@@ -218,6 +209,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t total_chunks = (uint32_t)my_tiles * 8;  // 4 of W2 then 4 of W3 per tile
       uint32_t u_issue = 0, u_use = 0;
       bool ok = true;
+      // weight chunk u: W2 chunk u % 8 for u % 8 < 4, else W3 chunk in the order layer 3 uses them
       auto issue_copy = [&](uint32_t u) {
         const int b = u % NRING;
         const int c = u % 8;
@@ -225,8 +217,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           umma::mbar_arrive_expect_tx(&s.full[b], w2_bytes);
           umma::bulk_g2s(s.ring[b], w2c + (size_t)c * (HID * 64), w2_bytes, &s.full[b]);
         } else {
+          const int c3 = 7 - c;  // layer 3 takes its K chunks 3, 2, 1, 0
           umma::mbar_arrive_expect_tx(&s.full[b], w3_bytes);
-          umma::bulk_g2s(s.ring[b], w3c + (size_t)(c - 4) * (NP3 * 64), w3_bytes, &s.full[b]);
+          umma::bulk_g2s(s.ring[b], w3c + (size_t)c3 * (NP3 * 64), w3_bytes, &s.full[b]);
         }
       };
       // issue every copy whose ring slot is already free (no waiting)
@@ -247,12 +240,29 @@ __global__ void __launch_bounds__(THREADS, 1)
           issue_copy(u_issue++);
         }
       };
+      // MMAs of one 64-wide K chunk (weight chunk u in the ring, H chunk c)
+      auto chunk_mmas = [&](uint32_t u, int c, uint32_t d, uint32_t id, bool first) {
+        ensure(u);
+        const int b = u % NRING;
+        if (!ok || !umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
+          ok = false;
+          return;
+        }
+        umma::fence_after_sync();
+        const uint64_t a_c = h_desc + (uint64_t)(c * 8 * 8);
+        const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, !(first && ks == 0));
+        umma::mma_commit(&s.empty[b]);
+        top_up();
+      };
       umma::mbar_arrive_expect_tx(&s.w1_full, HID * KX * 2);
       umma::bulk_g2s(s.W1, w1t, HID * KX * 2, &s.w1_full);
       top_up();
       if (my_tiles > 0 && !umma::mbar_wait(&s.w1_full, 0, kWaitNs)) ok = false;
       for (int t = 0; t < my_tiles && ok; ++t) {
-        // layer 1 (X of this tile written; TMEM A free: the previous tile's epilogues are done)
+        // layer 1: X of this tile written by the loader; TMEM A free since the previous
+        // tile's first epilogue handed over all four chunks (waited on below for that tile)
         if (!umma::mbar_wait(&s.x_ready, t & 1, kWaitNs)) {
           ok = false;
           break;
@@ -261,30 +271,32 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int ks = 0; ks < KX / 16; ++ks) umma::mma_bf16(tmem, x_desc + 16 * ks, w1_desc + 16 * ks, idesc1, ks != 0);
         umma::mma_commit(&s.l1_done);
-        // layers 2 and 3, chunk by chunk as the epilogue hands H over
-        for (int layer = 2; layer <= 3 && ok; ++layer) {
-          const uint32_t d = layer == 2 ? tmem + 256 : tmem;
-          const uint32_t id = layer == 2 ? idesc1 : idesc3;
-          for (int c = 0; c < 4; ++c) {
-            const uint32_t u = u_use;
-            ensure(u);
-            const int b = u % NRING;
-            if (!ok || !umma::mbar_wait(&s.h_ready[c], layer == 2 ? 0 : 1, kWaitNs) ||
-                !umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
-              ok = false;
-              break;
-            }
-            umma::fence_after_sync();
-            const uint64_t a_c = h_desc + (uint64_t)(c * 8 * 8);
-            const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, (c | ks) != 0);
-            umma::mma_commit(&s.empty[b]);
-            ++u_use;
-            top_up();
+        // layer 2 on the first epilogue's chunks (h_ready completion 2t)
+        for (int c = 0; c < 4 && ok; ++c) {
+          if (!umma::mbar_wait(&s.h_ready[c], 0, kWaitNs)) {
+            ok = false;
+            break;
           }
-          if (ok) umma::mma_commit(layer == 2 ? &s.l2_done : &s.l3_done);
+          chunk_mmas(u_use++, c, tmem + 256, idesc1, c == 0);
         }
+        if (!ok) break;
+        umma::mma_commit(&s.l2_done);
+        // layer 3 on the second epilogue's chunks (completion 2t + 1, chunks 3, 2, 1, 0); its
+        // accumulator [384, 384 + NP3) is free once chunks 3 and 2 of layer 2 have been read
+        if (!umma::mbar_wait(&s.h_ready[3], 1, kWaitNs) || !umma::mbar_wait(&s.h_ready[2], 1, kWaitNs)) {
+          ok = false;
+          break;
+        }
+        for (int i = 0; i < 4 && ok; ++i) {
+          const int c = 3 - i;
+          if (!umma::mbar_wait(&s.h_ready[c], 1, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          chunk_mmas(u_use++, c, tmem + L3_COL, idesc3, i == 0);
+        }
+        if (!ok) break;
+        umma::mma_commit(&s.l3_done);
       }
       if (!ok) {
         s.abort = 1;
@@ -294,39 +306,49 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (uint32_t u = u_use; u < u_issue; ++u) umma::mbar_wait(&s.full[u % NRING], (u / NRING) & 1, kWaitNs);
       if (u_use > 0) umma::mbar_wait(&s.empty[(u_use - 1) % NRING], ((u_use - 1) / NRING) & 1, kWaitNs);
     }
+  } else if (warp == LOADER_WARP) {
+    // ------------------------------------------------------------ loader: fields -> X (bf16, K-major)
+    for (int t = 0; t < my_tiles; ++t) {
+      // X is free once layer 1 of the previous tile has completed
+      if (t >= 1 && !umma::mbar_wait(&s.l1_done, (t - 1) & 1, kWaitNs)) s.abort = 1;
+      if (s.abort) break;
+      const int p0 = (blockIdx.x + t * gridDim.x) * TM;
+      for (int j = 0; j < J; ++j) {
+        const float* src = fields + (size_t)j * npix + p0;
+#pragma unroll
+        for (int r = 0; r < TM / 32; ++r) {
+          const int pp = r * 32 + lane;
+          const float v = (p0 + pp < npix) ? __ldg(src + pp) : 0.f;
+          *reinterpret_cast<__nv_bfloat16*>(s.X + kmajor_off(pp, j, KX / 8)) = __float2bfloat16_rn(v);
+        }
+      }
+      umma::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&s.x_ready);
+    }
   } else {
     // ------------------------------------------------------------ epilogue warps
-    const int q4 = warp & 3, h = warp >> 2;
+    const int q4 = warp & 3, sl = warp >> 2;
     const int p = q4 * 32 + lane;
     const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
     for (int t = 0; t < my_tiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
       const int p0 = tile * TM;
-      // X tile: fields[j][p0 + p] -> bf16 at (p, j); TMEM and H of the previous tile are free
-      for (int idx = tid; idx < J * TM; idx += EPI_THREADS) {
-        const int j = idx / TM, pp = idx - j * TM;
-        const float v = (p0 + pp < npix) ? __ldg(fields + (size_t)j * npix + p0 + pp) : 0.f;
-        *reinterpret_cast<__nv_bfloat16*>(s.X + kmajor_off(pp, j, KX / 8)) = __float2bfloat16_rn(v);
-      }
-      umma::fence_proxy_async_smem();
-      umma::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&s.x_ready);
       if (!umma::mbar_wait(&s.l1_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
-      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, s.b1);
+      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, s.b1, false);
       if (!umma::mbar_wait(&s.l2_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
-      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, s.b2);
+      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, s.b2, true);
       if (!umma::mbar_wait(&s.l3_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
-      // outputs: TMEM A[0, NP3) -> FP32 rows of stride KS in the staging area (H is free now)
+      // outputs: TMEM [384, 384 + NP3) -> FP32 rows of stride KS in the staging area (H is free now)
       float* stage = reinterpret_cast<float*>(s.H);
       if (!s.abort) {
         const int ngrp = NP3 / 16;
-        for (int q = h; q < ngrp; q += 2) {
+        for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
           float d[16];
-          umma::tmem_ld16(tmem + lane_base + q * 16, d);
+          umma::tmem_ld16(tmem + lane_base + L3_COL + q * 16, d);
 #pragma unroll
           for (int i4 = 0; i4 < 4; ++i4) {
             const int k = q * 16 + 4 * i4;
@@ -358,8 +380,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           wstore<WT>(dst + i, stage[pp * KS + k]);
         }
       }
-      // the next tile's epilogue writes H only after every warp's x_ready arrival, which
-      // follows this copy in each warp's program order
+      // the next tile's first epilogue overwrites the staging area
+      if (bar_epi_any(s.abort != 0)) break;
     }
     if (s.abort && tid == 0) atomicExch(err, 2);
   }

@@ -190,6 +190,23 @@ def test_blur_bf16_tensor_cores_match_oracle_on_bf16_operands(lib, C, H, W, K):
     g32 = lib.basis_blur_tc(P, cu(img), wf).cpu().numpy()
     P.check()
     assert rel_l2(g32, image.basis_blur(img_q, wf.cpu().numpy(), _bf16(basis))) < TOL
+    # the two public steps give the same result bit for bit
+    lib.basis_blur_tc_prepare(P, cu(img))
+    g2 = lib.basis_blur_tc_run(P, (C, H, W), wf).cpu().numpy()
+    assert np.array_equal(g2, g32)
+
+
+def test_blur_tc_run_needs_a_prepared_image(lib):
+    basis = synthetic.random_orthonormal_rows(16, 33 * 33, seed=3).reshape(16, 33, 33)
+    P = lib.P2S(36, cu(basis))
+    w = torch.zeros(20, 30, 16, device="cuda")
+    with pytest.raises(lib.DFP2SError) as e:
+        lib.basis_blur_tc_run(P, (1, 20, 30), w)  # nothing prepared yet
+    assert e.value.code == -1
+    lib.basis_blur_tc_prepare(P, torch.zeros(1, 20, 30, device="cuda"))
+    with pytest.raises(lib.DFP2SError):
+        lib.basis_blur_tc_run(P, (1, 20, 31), torch.zeros(20, 31, 16, device="cuda"))  # another shape
+    lib.basis_blur_tc_run(P, (1, 20, 30), w)
 
 
 # ---------------------------------------------------------------- network
