@@ -453,8 +453,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool live = x < W;
         const uint32_t g = (uint32_t)(t * C + c);
         const uint32_t slot = g % NSLOT;
-        if (!umma::mbar_wait(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
-        if (w_vec && !umma::mbar_wait(&s.w_full, t & 1, kWaitNs)) s.abort = 1;
+        if (!umma::mbar_wait_backoff(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
+        if (w_vec && !umma::mbar_wait_backoff(&s.w_full, t & 1, kWaitNs)) s.abort = 1;
         if (s.abort) break;
         umma::fence_after_sync();
         float acc = 0.f;

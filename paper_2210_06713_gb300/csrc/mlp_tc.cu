@@ -334,13 +334,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = 0; t < my_tiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
       const int p0 = tile * TM;
-      if (!umma::mbar_wait(&s.l1_done, t & 1, kWaitNs)) s.abort = 1;
+      if (!umma::mbar_wait_backoff(&s.l1_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
       if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, s.b1, false);
-      if (!umma::mbar_wait(&s.l2_done, t & 1, kWaitNs)) s.abort = 1;
+      if (!umma::mbar_wait_backoff(&s.l2_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
       if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, s.b2, true);
-      if (!umma::mbar_wait(&s.l3_done, t & 1, kWaitNs)) s.abort = 1;
+      if (!umma::mbar_wait_backoff(&s.l3_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
       // outputs: TMEM [384, 384 + NP3) -> FP32 rows of stride KS in the staging area (H is free now)
       float* stage = reinterpret_cast<float*>(s.H);
