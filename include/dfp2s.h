@@ -204,19 +204,32 @@ typedef struct {
   int steps;              /* Adam steps */
   float lr;               /* peak learning rate */
   int psf_weighted_loss;  /* 1: per-k loss weight = variance of w_k / mean variance (error of the PSF);
-                             0: plain MSE of the standardised weights */
+                             0: plain MSE of the standardised weights (both only if image_prior_loss = 0) */
   float val_fraction;     /* 0 <= val_fraction < 0.5 */
+  int image_prior_loss;   /* 1: loss r^T G r / K per pair, G = dfp2s_mlp_image_prior_gram of the targets'
+                             standard deviations (the expected error of the blurred image); 0: per-k weights */
 } dfp2s_mlp_train_params;
 int dfp2s_mlp_train(dfp2s_p2s* p, const dfp2s_factor* f, const dfp2s_mlp_train_params* tp, float* report_host,
                     float* params_out_host, void* stream);
 /* Number of FP32 parameters of the J -> 256 -> 256 -> K network. */
 int dfp2s_mlp_param_count(int J, int K);
 /* One forward/backward pass on a given batch (for gradient checks): X (B x J)
- * network inputs, T (B x K) targets, lw (K) loss weights, params flat as above;
- * writes grads (flat, same layout) and loss = sum_k lw_k (y - t)^2 / (B K).
- * All device pointers.  Synchronous. */
+ * network inputs, T (B x K) targets, params flat as above; the loss is
+ * sum_b r_b^T G r_b / (B K), r = y - t, if G_dev (K x K, symmetric) is given,
+ * else sum_k lw_k r_k^2 / (B K) with lw_dev (K).  Writes grads (flat, same
+ * layout) and loss.  All device pointers.  Synchronous. */
 int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params_dev, const float* X_dev, const float* T_dev,
-                        const float* lw_dev, float* grads_dev, float* loss_dev, void* stream);
+                        const float* lw_dev, const float* G_dev, float* grads_dev, float* loss_dev, void* stream);
+/* The training loss's quadratic form for this handle's basis (reading of the
+ * training objective, Sec. II-C): G_kl = sum_f S(f) Re(Phi_k(f) conj Phi_l(f)),
+ * Phi_k the 64 x 64 DFT of basis function k (33 x 33 at the origin),
+ * S(f) = 1 / (fx^2 + fy^2 + 1) for integer frequencies in [-32, 32) -- the
+ * expected energy a weight error puts into the blurred image of Eq. (varying
+ * blur) for images with that power spectrum -- then G^ = diag(sd) G diag(sd)
+ * scaled to a unit mean diagonal.  sd_dev (K): standard deviations of the
+ * weights; writes G_dev (K x K float32).  FP64 on the device.  Synchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int dfp2s_mlp_image_prior_gram(const dfp2s_p2s* p, const float* sd_dev, float* G_dev, void* stream);
 
 /* Sec. II-C: per-pixel basis weights from the fields (J x H x W, device).
  *   EXACT: PSF of Eq. (2) from modes Noll 4..J+1 on a 64 x 64 pupil grid

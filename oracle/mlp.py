@@ -5,8 +5,11 @@ Test infrastructure only (see the package docstring).
 Sec. II-C: the paper (after Mao et al. 2021) maps each pixel's Zernike vector
 a_x to the basis coefficients beta_x with a small neural network.  The
 network's shape and training are not given (reading R18): J -> 256 -> 256 -> K
-with the erf form of GELU, trained with the mean squared error on per-k
-standardised weights and Adam (Kingma & Ba 2015).  Input features are
+with the erf form of GELU, trained with Adam (Kingma & Ba 2015) on per-k
+standardised weights, with the loss of reading R25: the expected squared error
+that a weight error causes in the blurred image under a 1/(|f|^2 + 1) image
+spectrum (`image_prior_gram`); the flat spectrum gives the squared error of
+the PSF, and lw = 1 the plain mean squared error.  Input features are
 x = a * in_scale (in_scale is 0 on the two tilt fields, reading R9); the output
 is w = y * out_scale + out_shift.
 """
@@ -39,18 +42,50 @@ def forward(params: dict, x: np.ndarray):
     return y, (x, z1, h1, z2, h2)
 
 
-def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray, lw: np.ndarray | None = None):
-    """Weighted squared error sum_k lw_k (y - t)^2 / (B K) over the B x K outputs and its gradient.
+def image_prior_gram(basis: np.ndarray, sd: np.ndarray, M: int = 64, flat: bool = False) -> np.ndarray:
+    """Quadratic form of the training loss, reading R25.
 
-    lw = None is the plain mean squared error; lw_k = var(w_k) / mean var makes the
-    loss the squared error of the PSF (the basis is orthonormal), reading R18.
+    A weight error dw at a pixel changes the blurred image (Eq. varying blur) by
+    e = sum_k dw_k (phi_k (*) I).  For images with power spectrum S(f) its expected
+    energy is dw^T G dw, G_kl = sum_f S(f) Re(Phi_k(f) conj Phi_l(f)), Phi_k the DFT
+    of phi_k (33 x 33, placed at the origin of an M x M torus), S(f) =
+    1 / (fx^2 + fy^2 + 1) with integer frequencies (or S = 1 if `flat`).  In the
+    network's standardised outputs dw = diag(sd) r, so the loss matrix is
+    G^ = diag(sd) G diag(sd), scaled to a unit mean diagonal.
+    """
+    b = np.asarray(basis, dtype=np.float64)
+    K = b.shape[0]
+    pad = np.zeros((K, M, M))
+    pad[:, :b.shape[1], :b.shape[2]] = b
+    F = np.fft.fft2(pad).reshape(K, -1)
+    f = np.fft.fftfreq(M) * M
+    S = np.ones((M, M)) if flat else 1.0 / (f[:, None] ** 2 + f[None, :] ** 2 + 1.0)
+    G = np.real((F * S.reshape(1, -1)) @ F.conj().T)
+    D = np.asarray(sd, dtype=np.float64)
+    Gh = D[:, None] * G * D[None, :]
+    return Gh / np.mean(np.diag(Gh))
+
+
+def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray, lw: np.ndarray | None = None,
+                   G: np.ndarray | None = None):
+    """Training loss over the B x K outputs and its gradient.
+
+    With G (K x K, symmetric): sum_b r_b^T G r_b / (B K), r = y - t (reading R25).
+    Otherwise the weighted squared error sum_k lw_k r_k^2 / (B K): lw = None is the
+    plain mean squared error, lw_k = var(w_k) / mean var the squared error of the
+    PSF (the basis is orthonormal; G^ of a flat spectrum), reading R18.
     """
     y, (x, z1, h1, z2, h2) = forward(params, x)
     B, K = y.shape
     r = y - np.asarray(t, dtype=np.float64)
-    wk = np.ones(K) if lw is None else np.asarray(lw, dtype=np.float64)
-    loss = float(np.sum(wk * r * r) / (B * K))
-    dy = 2.0 * wk * r / (B * K)
+    if G is not None:
+        rg = r @ np.asarray(G, dtype=np.float64)
+        loss = float(np.sum(rg * r) / (B * K))
+        dy = 2.0 * rg / (B * K)
+    else:
+        wk = np.ones(K) if lw is None else np.asarray(lw, dtype=np.float64)
+        loss = float(np.sum(wk * r * r) / (B * K))
+        dy = 2.0 * wk * r / (B * K)
     g = {}
     g["W3"] = dy.T @ h2
     g["b3"] = dy.sum(axis=0)

@@ -36,7 +36,8 @@ class FactorParams(ctypes.Structure):
 
 class TrainParams(ctypes.Structure):
     _fields_ = [("n_pairs", _i), ("n_dr", _i), ("D_over_r0", _d * 8), ("seed", _u64), ("batch", _i), ("steps", _i),
-                ("lr", _c.c_float), ("psf_weighted_loss", _i), ("val_fraction", _c.c_float)]
+                ("lr", _c.c_float), ("psf_weighted_loss", _i), ("val_fraction", _c.c_float),
+                ("image_prior_loss", _i)]
 
 
 SIGNATURES = {
@@ -59,7 +60,8 @@ SIGNATURES = {
     "dfp2s_p2s_set_mlp": (_i, [_vp] + [_vp] * 9),
     "dfp2s_mlp_train": (_i, [_vp, _vp, _c.POINTER(TrainParams), _vp, _vp, _vp]),
     "dfp2s_mlp_param_count": (_i, [_i, _i]),
-    "dfp2s_mlp_loss_grad": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dfp2s_mlp_loss_grad": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dfp2s_mlp_image_prior_gram": (_i, [_vp, _vp, _vp, _vp]),
     "dfp2s_p2s_weights": (_i, [_vp, _i, _vp, _i, _i, _vp, _i, _vp]),
     "dfp2s_tilt_warp": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dfp2s_basis_blur": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
@@ -267,20 +269,29 @@ def mlp_param_count(J: int, K: int) -> int:
     return n
 
 
-def mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, T: torch.Tensor, lw: torch.Tensor):
-    """Loss and flat gradient of the surrogate on one batch (device FP32 tensors)."""
+def mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, T: torch.Tensor, lw: torch.Tensor | None = None,
+                  G: torch.Tensor | None = None):
+    """Loss and flat gradient of the surrogate on one batch (device FP32 tensors); G (K x K) selects the
+    quadratic-form loss, else the per-k weights lw."""
     B, J = X.shape
     K = T.shape[1]
     grads = torch.empty_like(params)
     loss = torch.zeros(1, device="cuda")
-    _check(load().dfp2s_mlp_loss_grad(J, K, B, _ptr(params), _ptr(X), _ptr(T), _ptr(lw), _ptr(grads), _ptr(loss),
-                                      _stream()))
+    _check(load().dfp2s_mlp_loss_grad(J, K, B, _ptr(params), _ptr(X), _ptr(T), _ptr(lw) if lw is not None else None,
+                                      _ptr(G) if G is not None else None, _ptr(grads), _ptr(loss), _stream()))
     return float(loss.item()), grads
+
+
+def mlp_image_prior_gram(p: P2S, sd: torch.Tensor) -> torch.Tensor:
+    """The training loss's K x K form for the basis of `p` and weight standard deviations `sd` (device)."""
+    G = torch.empty(p.K, p.K, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_mlp_image_prior_gram(p.handle, _ptr(sd), _ptr(G), _stream()))
+    return G
 
 
 def mlp_train(p: P2S, factor: SpectralFactor, n_pairs: int = 1 << 20, D_over_r0=(1.0, 2.0, 4.0), seed: int = 0,
               batch: int = 2048, steps: int = 20000, lr: float = 2e-3, psf_weighted_loss: bool = True,
-              val_fraction: float = 0.05, return_params: bool = False):
+              val_fraction: float = 0.05, return_params: bool = False, image_prior_loss: bool = True):
     """Trains the surrogate on the device and installs it in `p`; returns a report dict."""
     import numpy as np
     tp = TrainParams()
@@ -289,6 +300,7 @@ def mlp_train(p: P2S, factor: SpectralFactor, n_pairs: int = 1 << 20, D_over_r0=
         tp.D_over_r0[i] = dval
     tp.seed, tp.batch, tp.steps, tp.lr = seed, batch, steps, lr
     tp.psf_weighted_loss, tp.val_fraction = int(psf_weighted_loss), val_fraction
+    tp.image_prior_loss = int(image_prior_loss)
     rep = np.zeros(3, dtype=np.float32)
     params = np.zeros(mlp_param_count(p.J, p.K), dtype=np.float32) if return_params else None
     _check(load().dfp2s_mlp_train(p.handle, factor.handle, ctypes.byref(tp), rep.ctypes.data_as(ctypes.c_void_p),

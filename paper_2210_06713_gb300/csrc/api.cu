@@ -303,12 +303,20 @@ extern "C" int dfp2s_mlp_param_count(int J, int K) {
 }
 
 extern "C" int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params, const float* X, const float* T,
-                                   const float* lw, float* grads, float* loss, void* stream) {
-  CHECK_ARG(params && X && T && lw && grads, "null argument");
+                                   const float* lw, const float* G, float* grads, float* loss, void* stream) {
+  CHECK_ARG(params && X && T && (lw || G) && grads, "null argument");
   CHECK_ARG(J >= 3 && J <= DFP2S_MAX_J && K >= 1 && K <= DFP2S_MAX_K && B >= 1 && B <= (1 << 20), "bad shape");
-  const int rc = dfp2s_mlp_loss_grad_device(J, K, B, params, X, T, lw, grads, loss, as_stream(stream));
+  const int rc = dfp2s_mlp_loss_grad_device(J, K, B, params, X, T, lw, G, grads, loss, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "mlp scratch allocation");
   if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "mlp loss/grad");
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_mlp_image_prior_gram(const dfp2s_p2s* p, const float* sd, float* G, void* stream) {
+  CHECK_ARG(p && sd && G, "null argument");
+  const int rc = dfp2s_prior_gram_device(p->d.basis, p->d.K, sd, G, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "gram scratch allocation");
+  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "image-prior loss form");
   return DFP2S_OK;
 }
 
@@ -323,6 +331,7 @@ extern "C" int dfp2s_mlp_train(dfp2s_p2s* p, const dfp2s_factor* f, const dfp2s_
   CHECK_ARG(tp->steps >= 1 && tp->steps <= 10000000, "steps out of range");
   CHECK_ARG(tp->lr > 0 && tp->lr < 1, "lr out of range");
   CHECK_ARG(tp->val_fraction >= 0 && tp->val_fraction < 0.5, "val_fraction out of range");
+  CHECK_ARG(tp->image_prior_loss == 0 || tp->image_prior_loss == 1, "image_prior_loss must be 0 or 1");
   const int rc = dfp2s_mlp_train_device(&p->d, f->d.L32, tp, report, params_out_host, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "training allocation");
   if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "mlp training");

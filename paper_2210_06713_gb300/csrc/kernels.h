@@ -77,7 +77,8 @@ int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* p, const float* W1, const float* b1, co
 // mlp_train.cu
 size_t dfp2s_mlp_nparams(int J, int K);
 int dfp2s_mlp_loss_grad_device(int J, int K, int B, const float* params, const float* X, const float* T,
-                               const float* lw, float* grads, float* loss, cudaStream_t st);
+                               const float* lw, const float* G, float* grads, float* loss, cudaStream_t st);
+int dfp2s_prior_gram_device(const float* basis, int K, const float* sd, float* Gh, cudaStream_t st);
 int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_train_params* tp, float* report,
                            float* params_out_host, cudaStream_t st);
 int dfp2s_launch_draw_vectors(int n, int J, const float* L, const float* drs, int nd, uint64_t seed, uint32_t tag,

@@ -8,9 +8,11 @@
 // Data: n Zernike vectors a ~ N(0, A_0(D/r0)) (Philox tag 2, D/r0 cycling over a
 // list, tilt fields zeroed), targets w = exact P2S weights from the same kernel
 // that serves frames.  Inputs are scaled per field by 1/std, targets
-// standardised per k; the loss is sum_k lw_k (y_k - t_k)^2 / (B K) with lw_k = 1
-// (plain MSE on standardised weights) or lw_k = var_k / mean(var) (MSE of the
-// PSF, since the basis is orthonormal).
+// standardised per k.  The loss is either sum_b r_b^T G r_b / (B K), r = y - t,
+// with G the expected blurred-image error per weight error under a
+// 1 / (|f|^2 + 1) image spectrum (k_prior_*), or sum_k lw_k r_k^2 / (B K) with
+// lw_k = 1 (plain MSE on standardised weights) or lw_k = var_k / mean(var) (MSE
+// of the PSF, since the basis is orthonormal: G of a flat spectrum).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -135,6 +137,118 @@ __global__ void k_loss_grad(const float* __restrict__ Y, const float* __restrict
   }
   for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
   if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+// dY = R (the residual Y - T), overwritten below by the gradient
+__global__ void k_residual(const float* __restrict__ Y, const float* __restrict__ T, size_t n, float* __restrict__ R) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) R[i] = Y[i] - T[i];
+}
+
+// with RG = R G (G symmetric): loss += sum RG * R / (B K); dY = 2 RG / (B K), in place over R
+__global__ void k_gram_loss_grad(const float* __restrict__ RG, float* __restrict__ RdY, int B, int K,
+                                 float* __restrict__ loss) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const float inv = 1.f / ((float)B * (float)K);
+  float l = 0.f;
+  if (i < (size_t)B * K) {
+    const float r = RdY[i], rg = RG[i];
+    l = rg * r * inv;
+    RdY[i] = 2.f * rg * inv;
+  }
+  for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+// ------------------------------------------------------- image-prior loss form
+// G_kl = sum_f S(f) Re(Phi_k(f) conj Phi_l(f)), Phi_k the DFT of the 33 x 33 basis
+// function k at the origin of a 64 x 64 torus, S(f) = 1 / (fx^2 + fy^2 + 1) with
+// integer frequencies in [-32, 32): the expected energy that a weight error puts
+// into the blurred image (Eq. varying blur) for images with that spectrum.
+// FP64 throughout; the twiddles exp(-2 pi i m / 64) come from sincospi of exact
+// multiples of 1/32.
+constexpr int PM = 64;
+constexpr int PS = 33;
+
+__device__ void prior_twiddles(double2* tw) {
+  for (int m = threadIdx.x; m < PM; m += blockDim.x) {
+    double sn, cs;
+    sincospi(-(double)m / (PM / 2), &sn, &cs);
+    tw[m] = make_double2(cs, sn);
+  }
+  __syncthreads();
+}
+
+// rows: T[k][u][fx] = sum_v phi_k(u, v) e^{-2 pi i fx v / 64}
+__global__ void k_prior_dft_rows(const float* __restrict__ basis, double2* __restrict__ Tm) {
+  __shared__ double2 tw[PM];
+  prior_twiddles(tw);
+  const int k = blockIdx.x;
+  for (int i = threadIdx.x; i < PS * PM; i += blockDim.x) {
+    const int u = i / PM, fx = i - u * PM;
+    double re = 0.0, im = 0.0;
+    for (int v = 0; v < PS; ++v) {
+      const double b = basis[((size_t)k * PS + u) * PS + v];
+      const double2 w = tw[(fx * v) & (PM - 1)];
+      re += b * w.x;
+      im += b * w.y;
+    }
+    Tm[((size_t)k * PS + u) * PM + fx] = make_double2(re, im);
+  }
+}
+
+// columns: Phi[k][fy][fx] = sum_u T[k][u][fx] e^{-2 pi i fy u / 64}
+__global__ void k_prior_dft_cols(const double2* __restrict__ Tm, double2* __restrict__ Phi) {
+  __shared__ double2 tw[PM];
+  prior_twiddles(tw);
+  const int k = blockIdx.x;
+  for (int i = threadIdx.x; i < PM * PM; i += blockDim.x) {
+    const int fy = i / PM, fx = i - fy * PM;
+    double re = 0.0, im = 0.0;
+    for (int u = 0; u < PS; ++u) {
+      const double2 t = Tm[((size_t)k * PS + u) * PM + fx];
+      const double2 w = tw[(fy * u) & (PM - 1)];
+      re += t.x * w.x - t.y * w.y;
+      im += t.x * w.y + t.y * w.x;
+    }
+    Phi[(size_t)k * PM * PM + i] = make_double2(re, im);
+  }
+}
+
+__global__ void k_prior_gram(const double2* __restrict__ Phi, int K, double* __restrict__ G) {
+  const int k = blockIdx.x, l = blockIdx.y;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < PM * PM; i += blockDim.x) {
+    int fy = i / PM, fx = i - fy * PM;
+    if (fy >= PM / 2) fy -= PM;
+    if (fx >= PM / 2) fx -= PM;
+    const double S = 1.0 / ((double)(fx * fx + fy * fy) + 1.0);
+    const double2 a = Phi[(size_t)k * PM * PM + i], b = Phi[(size_t)l * PM * PM + i];
+    acc += S * (a.x * b.x + a.y * b.y);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) G[(size_t)k * K + l] = red[0];
+}
+
+// G^ = diag(sd) G diag(sd) / mean_k(sd_k^2 G_kk)
+__global__ void k_prior_scale(const double* __restrict__ G, const float* __restrict__ sd, int K, float* __restrict__ Gh) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < K; ++k) t += (double)sd[k] * sd[k] * G[(size_t)k * K + k];
+    mean = t / K;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
+    const int k = i / K, l = i - k * K;
+    Gh[i] = (float)((double)sd[k] * G[i] * sd[l] / mean);
+  }
 }
 
 struct TrainState {
@@ -283,17 +397,25 @@ Net carve(float* base, int J, int K) {
 }
 
 struct Act {
-  float *Z1, *H1, *Z2, *H2, *Y, *dY, *dH2, *dH1;
+  float *Z1, *H1, *Z2, *H2, *Y, *dY, *dH2, *dH1, *RG;
 };
 
 // forward and backward of one batch (X: B x J, T: B x K) into the flat gradient buffer g
+// (G, K x K symmetric, selects the quadratic-form loss; otherwise the per-k weights lw)
 void fwd_bwd(cudaStream_t st, const Net& p, const Net& g, const Act& a, const float* X, const float* T,
-             const float* lw, int B, float* loss) {
+             const float* lw, const float* G, int B, float* loss) {
   const int J = p.J, K = p.K;
   gemm<false, true, EPI_BIAS_GELU>(st, B, HID, J, X, J, p.W1, J, a.H1, HID, p.b1, a.Z1);
   gemm<false, true, EPI_BIAS_GELU>(st, B, HID, HID, a.H1, HID, p.W2, HID, a.H2, HID, p.b2, a.Z2);
   gemm<false, true, EPI_BIAS>(st, B, K, HID, a.H2, HID, p.W3, HID, a.Y, K, p.b3);
-  k_loss_grad<<<(unsigned)(((size_t)B * K + 255) / 256), 256, 0, st>>>(a.Y, T, lw, B, K, a.dY, loss);
+  const unsigned nb = (unsigned)(((size_t)B * K + 255) / 256);
+  if (G) {
+    k_residual<<<nb, 256, 0, st>>>(a.Y, T, (size_t)B * K, a.dY);
+    gemm<false, false, EPI_NONE>(st, B, K, K, a.dY, K, G, K, a.RG, K);
+    k_gram_loss_grad<<<nb, 256, 0, st>>>(a.RG, a.dY, B, K, loss);
+  } else {
+    k_loss_grad<<<nb, 256, 0, st>>>(a.Y, T, lw, B, K, a.dY, loss);
+  }
   gemm<true, false, EPI_NONE>(st, K, HID, B, a.dY, K, a.H2, HID, g.W3, HID);
   k_colsum<<<(K + 31) / 32, 256, 0, st>>>(a.dY, B, K, g.b3);
   gemm<false, false, EPI_GELU_GRAD>(st, B, HID, K, a.dY, K, p.W3, HID, a.dH2, HID, nullptr, nullptr, a.Z2);
@@ -328,24 +450,39 @@ Act make_act(Pool& pool, int B, int K) {
   a.dY = pool.get<float>((size_t)B * K);
   a.dH2 = pool.get<float>((size_t)B * HID);
   a.dH1 = pool.get<float>((size_t)B * HID);
+  a.RG = pool.get<float>((size_t)B * K);
   return a;
 }
 
-bool act_ok(const Act& a) { return a.Z1 && a.H1 && a.Z2 && a.H2 && a.Y && a.dY && a.dH2 && a.dH1; }
+bool act_ok(const Act& a) { return a.Z1 && a.H1 && a.Z2 && a.H2 && a.Y && a.dY && a.dH2 && a.dH1 && a.RG; }
 
 }  // namespace
 
 size_t dfp2s_mlp_nparams(int J, int K) { return carve(nullptr, J, K).n; }
 
+int dfp2s_prior_gram_device(const float* basis, int K, const float* sd, float* Gh, cudaStream_t st) {
+  Pool pool;
+  double2* Tm = pool.get<double2>((size_t)K * PS * PM);
+  double2* Phi = pool.get<double2>((size_t)K * PM * PM);
+  double* G = pool.get<double>((size_t)K * K);
+  if (!Tm || !Phi || !G) return DFP2S_ENOMEM;
+  k_prior_dft_rows<<<K, 256, 0, st>>>(basis, Tm);
+  k_prior_dft_cols<<<K, 256, 0, st>>>(Tm, Phi);
+  k_prior_gram<<<dim3(K, K), 256, 0, st>>>(Phi, K, G);
+  k_prior_scale<<<1, 256, 0, st>>>(G, sd, K, Gh);
+  if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;  // before the pool frees
+}
+
 int dfp2s_mlp_loss_grad_device(int J, int K, int B, const float* params, const float* X, const float* T,
-                               const float* lw, float* grads, float* loss, cudaStream_t st) {
+                               const float* lw, const float* G, float* grads, float* loss, cudaStream_t st) {
   Pool pool;
   Act a = make_act(pool, B, K);
   if (!act_ok(a)) return DFP2S_ENOMEM;
   const Net p = carve(const_cast<float*>(params), J, K);
   const Net g = carve(grads, J, K);
   if (loss) cudaMemsetAsync(loss, 0, sizeof(float), st);
-  fwd_bwd(st, p, g, a, X, T, lw, B, loss);
+  fwd_bwd(st, p, g, a, X, T, lw, G, B, loss);
   if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
@@ -401,13 +538,14 @@ int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_t
   float* mu = pool.get<float>(K);
   float* sd = pool.get<float>(K);
   float* lw = pool.get<float>(K);
+  float* Gh = tp->image_prior_loss ? pool.get<float>((size_t)K * K) : nullptr;
   float* X = pool.get<float>((size_t)B * J);
   float* T = pool.get<float>((size_t)B * K);
   TrainState* state = pool.get<TrainState>(1);
   double* eacc = pool.get<double>(2);
   Act a = make_act(pool, B, K);
   if (!Af || !Wt || !drs || !params || !grads || !m1 || !m2 || !in_mu || !in_sd || !in_scale || !mu || !sd || !lw ||
-      !X || !T || !state || !eacc || !act_ok(a))
+      !X || !T || !state || !eacc || !act_ok(a) || (tp->image_prior_loss && !Gh))
     return DFP2S_ENOMEM;
   float hdr[8];
   for (int i = 0; i < tp->n_dr; ++i) hdr[i] = (float)tp->D_over_r0[i];
@@ -421,6 +559,7 @@ int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_t
   k_col_stats<<<K, 256, 0, st>>>(Wt, ntrain, K, 0, mu, sd);
   k_inscale<<<1, 64, 0, st>>>(in_sd, J, in_scale);
   k_loss_weights<<<1, 128, 0, st>>>(sd, K, tp->psf_weighted_loss, lw);
+  if (tp->image_prior_loss && (rc = dfp2s_prior_gram_device(p->basis, K, sd, Gh, st))) return rc;
   // parameters
   const Net pn = carve(params, J, K);
   const Net gn = carve(grads, J, K);
@@ -450,7 +589,7 @@ int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_t
   cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   k_step_begin<<<1, 1, 0, cs>>>(state, tp->steps, tp->lr);
   k_gather<<<B, 128, 0, cs>>>(Af, n, ntrain, J, Wt, K, in_scale, mu, sd, B, tp->seed, state, X, T);
-  fwd_bwd(cs, pn, gn, a, X, T, lw, B, &state->loss);
+  fwd_bwd(cs, pn, gn, a, X, T, lw, Gh, B, &state->loss);
   k_adam<<<(unsigned)((np + 255) / 256), 256, 0, cs>>>(params, grads, m1, m2, np, state);
   cudaError_t ce = cudaStreamEndCapture(cs, &graph);
   if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);

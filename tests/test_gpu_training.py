@@ -31,24 +31,42 @@ def _flat_to_dict(flat, J, K):
     return out
 
 
-@pytest.mark.parametrize("J,K,B", [(36, 16, 64), (15, 100, 33)])
-def test_loss_and_gradients_match_oracle(lib, J, K, B):
+@pytest.mark.parametrize("J,K,B,gram", [(36, 16, 64, False), (15, 100, 33, False), (36, 100, 70, True),
+                                        (36, 16, 5, True)])
+def test_loss_and_gradients_match_oracle(lib, J, K, B, gram):
     n = lib.mlp_param_count(J, K)
     rng = np.random.default_rng(J + K)
     flat = (rng.standard_normal(n) * 0.1).astype(np.float32)
     X = rng.standard_normal((B, J)).astype(np.float32)
     T = rng.standard_normal((B, K)).astype(np.float32)
     lw = rng.uniform(0.2, 2.0, K).astype(np.float32)
+    G = None
+    if gram:  # a symmetric positive definite form (the image-prior form has this shape)
+        Q = rng.standard_normal((K, K))
+        G = ((Q @ Q.T) / K + 0.1 * np.eye(K)).astype(np.float32)
     loss, g = lib.mlp_loss_grad(torch.tensor(flat, device="cuda"), torch.tensor(X, device="cuda"),
-                                torch.tensor(T, device="cuda"), torch.tensor(lw, device="cuda"))
+                                torch.tensor(T, device="cuda"), None if gram else torch.tensor(lw, device="cuda"),
+                                torch.tensor(G, device="cuda") if gram else None)
     P = _flat_to_dict(flat, J, K)
-    lo, go = mlp.loss_and_grads(P, X, T, lw)
+    lo, go = mlp.loss_and_grads(P, X, T, None if gram else lw, G)
     assert loss == pytest.approx(lo, rel=1e-5)
     gd = _flat_to_dict(g.cpu().numpy(), J, K)
     for name in P:
         ref = go[name]
         err = np.linalg.norm(gd[name] - ref) / np.linalg.norm(ref)
         assert err < 1e-4, (name, err)
+
+
+@pytest.mark.parametrize("K", [16, 100])
+def test_image_prior_gram_matches_oracle(lib, K):
+    basis = p2s.build_basis(0, 36, K, 300, [2.0]) if K == 16 else \
+        synthetic.random_orthonormal_rows(K, 33 * 33, seed=4).reshape(K, 33, 33)
+    sd = np.random.default_rng(K).uniform(0.1, 2.0, K)
+    P = lib.P2S(36, torch.as_tensor(basis, dtype=torch.float32, device="cuda"))
+    G = lib.mlp_image_prior_gram(P, torch.as_tensor(sd, dtype=torch.float32, device="cuda")).cpu().numpy()
+    # the oracle on the same float32-rounded basis and scales
+    Go = mlp.image_prior_gram(basis.astype(np.float32), sd.astype(np.float32))
+    assert np.linalg.norm(G - Go) / np.linalg.norm(Go) < 1e-5
 
 
 def test_training_learns_and_beats_mean_weights(lib):

@@ -134,26 +134,70 @@ def _params(J, Hd, K, seed=0):
             "W3": rng.standard_normal((K, Hd)) / math.sqrt(Hd), "b3": rng.standard_normal(K) * 0.1}
 
 
-@pytest.mark.parametrize("weighted", [False, True])
-def test_mlp_gradients_by_finite_differences(weighted):
+@pytest.mark.parametrize("kind", ["plain", "weighted", "gram"])
+def test_mlp_gradients_by_finite_differences(kind):
     J, Hd, K, B = 5, 7, 4, 6
     P = _params(J, Hd, K)
     rng = np.random.default_rng(1)
     x = rng.standard_normal((B, J))
     t = rng.standard_normal((B, K))
-    lw = rng.uniform(0.1, 3.0, K) if weighted else None
-    _, g = mlp.loss_and_grads(P, x, t, lw)
+    lw = rng.uniform(0.1, 3.0, K) if kind == "weighted" else None
+    G = None
+    if kind == "gram":
+        Q = rng.standard_normal((K, K))
+        G = Q @ Q.T + 0.1 * np.eye(K)
+    _, g = mlp.loss_and_grads(P, x, t, lw, G)
     eps = 1e-6
     for name, val in P.items():
         flat = val.ravel()
         for i in range(0, flat.size, max(1, flat.size // 9)):
             old = flat[i]
             flat[i] = old + eps
-            lp, _ = mlp.loss_and_grads(P, x, t, lw)
+            lp, _ = mlp.loss_and_grads(P, x, t, lw, G)
             flat[i] = old - eps
-            lm, _ = mlp.loss_and_grads(P, x, t, lw)
+            lm, _ = mlp.loss_and_grads(P, x, t, lw, G)
             flat[i] = old
             assert g[name].ravel()[i] == pytest.approx((lp - lm) / (2 * eps), rel=1e-6, abs=1e-9)
+
+
+def test_image_prior_gram_is_the_blurred_error_energy():
+    # r^T G r = sum_f S |Phi_r|^2 = M^2 sum_x |(phi_r (*) g)(x)|^2 with DFT(g) = sqrt(S): the circular
+    # convolution is done directly, shift by shift, so the DFT convention and the embedding are pinned
+    M, K = 64, 3
+    rng = np.random.default_rng(5)
+    basis = rng.standard_normal((K, 33, 33))
+    sd = np.ones(K)
+    f = np.fft.fftfreq(M) * M
+    S = 1.0 / (f[:, None] ** 2 + f[None, :] ** 2 + 1.0)
+    g = np.real(np.fft.ifft2(np.sqrt(S)))
+    G = mlp.image_prior_gram(basis, sd, M)
+    scale = None
+    for trial in range(3):
+        r = rng.standard_normal(K)
+        phi = np.tensordot(r, basis, axes=1)
+        conv = np.zeros((M, M))
+        for u in range(33):
+            for v in range(33):
+                conv += phi[u, v] * np.roll(np.roll(g, u, axis=0), v, axis=1)
+        energy = M * M * np.sum(conv ** 2)
+        # G^ carries the unit-mean-diagonal scale; recover it from the unscaled form
+        Fb = np.fft.fft2(np.pad(basis, ((0, 0), (0, M - 33), (0, M - 33)))).reshape(K, -1)
+        G_raw = np.real((Fb * S.reshape(1, -1)) @ Fb.conj().T)
+        scale = np.mean(np.diag(G_raw))
+        assert r @ G @ r * scale == pytest.approx(energy, rel=1e-10)
+
+
+def test_image_prior_gram_flat_spectrum_is_the_psf_weighted_loss():
+    # an orthonormal basis and a flat spectrum: G = M^2 I (Parseval), so G^ = diag(sd^2) / mean(sd^2) = lw
+    K = 6
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=2).reshape(K, 33, 33)
+    sd = np.random.default_rng(3).uniform(0.2, 2.0, K)
+    G = mlp.image_prior_gram(basis, sd, flat=True)
+    assert np.allclose(G, np.diag(sd ** 2 / np.mean(sd ** 2)), atol=1e-12)
+    # with the image spectrum the form stays symmetric positive definite
+    G2 = mlp.image_prior_gram(basis, sd)
+    assert np.allclose(G2, G2.T, atol=1e-14)
+    assert np.linalg.eigvalsh(G2).min() > 0
 
 
 def test_gelu_and_adam_closed_forms():
