@@ -237,10 +237,10 @@ int dfp2s_mlp_image_prior_gram(const dfp2s_p2s* p, const float* sd_dev, float* G
  *          unit sum, then w = Phi^T h;
  *   LEARNED: w = MLP(a * in_scale) * out_scale + out_shift on the tcgen05
  *          tensor cores (BF16 inputs, weights and hidden activations, FP32
- *          accumulation), one fused kernel;
+ *          accumulation), one fused kernel; J <= 48, K <= 128;
  *   LEARNED_FP32: the same network in FP32 on CUDA cores.
  * Writes w_dev (H x W x K, dtype w_dtype).  Errors: EINVAL (no MLP for
- * LEARNED, sizes), ECUDA. */
+ * LEARNED, J > 48 for LEARNED, sizes), ECUDA. */
 int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fields_dev, int H, int W, void* w_dev,
                       int w_dtype, void* stream);
 

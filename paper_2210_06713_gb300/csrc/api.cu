@@ -347,6 +347,7 @@ extern "C" int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fiel
     CHECK_LAUNCH(dfp2s_launch_p2s_exact(&p->d, fields, H, W, w, w_dtype, as_stream(stream)));
   } else if (mode == DFP2S_P2S_LEARNED) {
     CHECK_ARG(p->d.has_mlp, "no surrogate network installed");
+    CHECK_ARG(p->d.J <= 48, "the tensor-core surrogate takes J <= 48 fields (J = %d); use LEARNED_FP32", p->d.J);
     CHECK_LAUNCH(dfp2s_launch_mlp_tc(&p->d, fields, H * W, w, w_dtype, as_stream(stream)));
   } else if (mode == DFP2S_P2S_LEARNED_FP32) {
     CHECK_ARG(p->d.has_mlp, "no surrogate network installed");

@@ -313,13 +313,28 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (t >= 1 && !umma::mbar_wait(&s.l1_done, (t - 1) & 1, kWaitNs)) s.abort = 1;
       if (s.abort) break;
       const int p0 = (blockIdx.x + t * gridDim.x) * TM;
-      for (int j = 0; j < J; ++j) {
-        const float* src = fields + (size_t)j * npix + p0;
+      // eight fields at a time for this lane's four pixels (32 loads in flight), packed into the
+      // 16-byte rows of the K-major core matrices (fields j..j+7 of one pixel)
+      for (int jg = 0; jg < (J + 7) / 8 && jg < KX / 8; ++jg) {
+        float v[4][8];
 #pragma unroll
-        for (int r = 0; r < TM / 32; ++r) {
-          const int pp = r * 32 + lane;
-          const float v = (p0 + pp < npix) ? __ldg(src + pp) : 0.f;
-          *reinterpret_cast<__nv_bfloat16*>(s.X + kmajor_off(pp, j, KX / 8)) = __float2bfloat16_rn(v);
+        for (int e = 0; e < 8; ++e) {
+          const int j = jg * 8 + e;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int pp = r * 32 + lane;
+            v[r][e] = (j < J && p0 + pp < npix) ? __ldg(fields + (size_t)j * npix + p0 + pp) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          uint32_t wd[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[r][2 * e2], v[r][2 * e2 + 1]);
+            wd[e2] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+          *reinterpret_cast<uint4*>(s.X + kmajor_off(r * 32 + lane, jg * 8, KX / 8)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
         }
       }
       umma::fence_proxy_async_smem();
@@ -442,6 +457,7 @@ int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st) {
 
 int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st) {
   const int K = p->K;
+  if (p->J > KX) return DFP2S_EUNSUPPORTED;  // the input tile holds at most 48 fields
   const int NP3 = (K + 15) / 16 * 16;
   const int ntiles = (npix + TM - 1) / TM;
   int dev = 0, sms = 148;
