@@ -1,5 +1,6 @@
 // Surrogate P2S network (Sec. II-C) on the tcgen05 tensor cores: one fused
-// kernel per frame, BF16 operands, FP32 accumulation in tensor memory.
+// kernel per frame, BF16 operands, FP32 accumulation in tensor memory, GELU by a
+// logistic fit accurate far beyond the BF16 rounding of the activations.
 //
 // A tile is 128 consecutive pixels (MMA M = 128):
 //   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T -> TMEM A = columns [0, 256)
@@ -26,6 +27,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "gelu_fit.h"
 #include "kernels.h"
 #include "umma.cuh"
 
@@ -60,12 +62,10 @@ struct Smem {
   int abort;
 };
 
-// GELU(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the
-// rational-exponential approximation 7.1.26 of Abramowitz and Stegun
-// (|error| <= 1.5e-7): erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2),
-// t = 1 / (1 + p x), x >= 0.  exp and the reciprocal use the hardware
-// approximations (ex2.approx, rcp.approx); the activations are rounded to
-// bfloat16 afterwards, far above these errors.
+// GELU(z) = z Phi(z) with the logistic fit of Phi in gelu_fit.h (max error
+// 1.9e-5 in Phi); 2^x and the reciprocal use the hardware approximations
+// (ex2.approx, rcp.approx).  For z -> -inf the exponent overflows to +inf and the
+// reciprocal gives 0; the activations are rounded to bfloat16 afterwards.
 DFP2S_DEV float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -77,18 +77,10 @@ DFP2S_DEV float rcp_approx(float x) {
   return y;
 }
 DFP2S_DEV float gelu(float z) {
-  const float az = fabsf(z);
-  const float t = rcp_approx(fmaf(0.3275911f * 0.70710678118654752f, az, 1.0f));
-  float q = fmaf(1.061405429f, t, -1.453152027f);
-  q = fmaf(q, t, 1.421413741f);
-  q = fmaf(q, t, -0.284496736f);
-  q = fmaf(q, t, 0.254829592f);
-  q *= t;
-  // exp(-z^2 / 2) = 2^(-z^2 log2(e) / 2)
-  const float e = ex2_approx((z * -0.72134752044448170f) * z);
-  const float erf_abs = fmaf(-q, e, 1.0f);
-  const float phi = fmaf(0.5f, copysignf(erf_abs, z), 0.5f);
-  return z * phi;
+  const float s = fminf(z * z, DFP2S_GELU_Z2MAX);
+  const float q = fmaf(fmaf(DFP2S_GELU_C2, s, DFP2S_GELU_C1), s, DFP2S_GELU_C0);
+  const float e = ex2_approx(-(z * q));
+  return z * rcp_approx(1.0f + e);
 }
 
 // byte offset of element (row, k) in a K-major no-swizzle tile with `kgroups` 8-element K groups per row group
