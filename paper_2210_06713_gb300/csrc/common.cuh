@@ -72,9 +72,10 @@ DFP2S_DEV float dfp2s_log(float u) {
 // q = round(v) and r = v - q in [-1/2, 1/2] exactly in integers; Taylor series of
 // sin((pi/2) r) to r^9 and cos((pi/2) r) to r^10, then the quadrant.
 DFP2S_DEV void dfp2s_sincos_2pi(uint32_t k, float* cs, float* sn) {
-  const int64_t num = 2 * (int64_t)k + 1;
-  const int64_t q = (num + (1 << 21)) >> 22;
-  const int64_t rnum = num - (q << 22);
+  // k < 2^23, so num < 2^24 and every step is exact in 32-bit integers
+  const int32_t num = 2 * (int32_t)k + 1;
+  const int32_t q = (num + (1 << 21)) >> 22;
+  const int32_t rnum = num - (q << 22);
   const float r = __fmul_rn((float)rnum, 0x1.0p-22f);
   const float r2 = __fmul_rn(r, r);
   float sp = 0x1.507834p-13f;

@@ -161,11 +161,27 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_rowifft(const float2* __
   const int j = blockIdx.y;
   const int y0 = blockIdx.x * 2 * G;
   const float2* Sj = S + (size_t)j * HALF * N;
-  for (int i = threadIdx.x; i < HALF * 2 * G; i += GR::THREADS) {
-    const int k = i / (2 * G), r = i - k * (2 * G);
-    float2 x = y0 + r < H ? Sj[(size_t)k * N + y0 + r] : make_float2(0.f, 0.f);
-    if (k == 0 || k == N / 2) x.y = 0.f;  // C2R convention: DC and Nyquist bins are real
-    smem[k * GR::TS + r] = x;
+  // the tile, eight loads in flight per thread
+  constexpr int TOT = HALF * 2 * G;
+  constexpr int PER = (TOT + GR::THREADS - 1) / GR::THREADS;
+#pragma unroll
+  for (int b0 = 0; b0 < PER; b0 += 8) {
+    float2 x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = threadIdx.x + (b0 + q) * GR::THREADS;
+      const int k = i / (2 * G), r = i - k * (2 * G);
+      x[q] = (b0 + q < PER && i < TOT && y0 + r < H) ? Sj[(size_t)k * N + y0 + r] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = threadIdx.x + (b0 + q) * GR::THREADS;
+      const int k = i / (2 * G), r = i - k * (2 * G);
+      if (b0 + q < PER && i < TOT) {
+        if (k == 0 || k == N / 2) x[q].y = 0.f;  // C2R convention: DC and Nyquist bins are real
+        smem[k * GR::TS + r] = x[q];
+      }
+    }
   }
   __syncthreads();
   // Z[n] = Ga[n] + i Gb[n] for n <= N/2, conj Ga[N-n] + i conj Gb[N-n] above
