@@ -60,8 +60,8 @@ constexpr int L_WARP0 = 2;
 constexpr int NL_WARPS = 2;
 constexpr int EPI_WARP0 = 4;
 constexpr int THREADS = (EPI_WARP0 + 4 * CMAX) * 32;
-constexpr int NB = 4;                // row-block ring (one slot per basis row iy)
-constexpr int NBB = 4;               // basis-tile ring
+constexpr int NB = 6;                // row-block ring (one slot per basis row iy)
+constexpr int NBB = 6;               // basis-tile ring
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 constexpr int B_SLOT = 128 * KM * 2;         // bytes of one basis-tile slot (NP <= 128)
 constexpr int L_BYTES = TM * KL * 2;         // column operand of one channel
@@ -70,20 +70,20 @@ constexpr int C_BYTES = 128 * KL * 2;        // column taps of the basis
 struct Smem {
   uint8_t A[NB][CMAX][ROWB];       // Hankel blocks of one image row per channel (TMA)
   uint8_t B[NBB][B_SLOT];          // basis tiles of one row each
-  uint8_t L[2][CMAX][L_BYTES];     // column operand, double-buffered over tiles
+  uint8_t L[CMAX][L_BYTES];        // column operand of the tile
   uint8_t Cb[C_BYTES];             // column taps (resident)
   float Wt[TM * 128];              // the tile's weights (FP32, K per pixel)
   float csum[128];
   uint64_t a_full[NB], a_free[NB];
   uint64_t b_full[NBB], b_free[NBB];
-  uint64_t l_full[2], l_free[2];
+  uint64_t l_full, l_free;
   uint64_t c_full, w_full, w_empty;
   uint64_t acc_full[NSLOT], acc_empty[NSLOT];
   uint32_t tmem_base;
   int abort;
 };
 
-// Warp-wide load of 16 TMEM columns without waiting; tmem_wait_ld waits for all
+// Warp-wide load of 16 TMEM columns without waiting; tmem_wait_ld4 waits for all
 // outstanding loads and ties the destination registers to the wait, so that no
 // use of them is scheduled before it.
 DFP2S_DEV void tmem_ld16_async(uint32_t taddr, float* v) {
@@ -95,11 +95,17 @@ DFP2S_DEV void tmem_ld16_async(uint32_t taddr, float* v) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-DFP2S_DEV void tmem_wait_ld(float* v) {
-  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+DFP2S_DEV void tmem_wait_ld4(float (&d)[4][16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(&d[0][0]);
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                 "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]),
+                 "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]),
+                 "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]),
+                 "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]),
+                 "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
                :
                : "memory");
 }
@@ -221,10 +227,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       umma::mbar_init(&s.b_full[i], 1);
       umma::mbar_init(&s.b_free[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
-      umma::mbar_init(&s.l_full[i], NL_WARPS);
-      umma::mbar_init(&s.l_free[i], 1);
-    }
+    umma::mbar_init(&s.l_full, NL_WARPS);
+    umma::mbar_init(&s.l_free, 1);
     umma::mbar_init(&s.c_full, 1);
     umma::mbar_init(&s.w_full, 1);
     umma::mbar_init(&s.w_empty, 4 * C);
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   for (int i = tid; i < 128; i += THREADS) s.csum[i] = i < NP ? csum[i] : 0.f;
   // the column operand's padding K columns (iy = 33..47) stay zero
-  for (int i = tid; i < 2 * CMAX * L_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(&s.L[0][0][0])[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < CMAX * L_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(&s.L[0][0])[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
     umma::tmem_alloc(&s.tmem_base, 512);
     umma::tmem_relinquish();
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // column taps [j][g][8][8]: 128 B along K, 768 B along M/N
       const uint64_t a_base = umma::sdesc(umma::smem_u32(s.A[0][0]), 128, 128);
       const uint64_t b_base = umma::sdesc(umma::smem_u32(s.B[0]), 128, KM / 8 * 128);
-      const uint64_t l_base = umma::sdesc(umma::smem_u32(s.L[0][0]), 128, KL / 8 * 128);
+      const uint64_t l_base = umma::sdesc(umma::smem_u32(s.L[0]), 128, KL / 8 * 128);
       const uint64_t c_desc = umma::sdesc(umma::smem_u32(s.Cb), 128, KL / 8 * 128);
       bool ok = my_tiles == 0 || umma::mbar_wait(&s.c_full, 0, kWaitNs);
       uint32_t it = 0;
@@ -363,8 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           umma::mma_commit(&s.b_free[bb]);
           if (iy == KS - 1) {
             // the column taps, once the tile's column operand is complete
-            const int lb = t & 1;
-            if (!umma::mbar_wait(&s.l_full[lb], (t >> 1) & 1, kWaitNs)) {
+            if (!umma::mbar_wait(&s.l_full, t & 1, kWaitNs)) {
               ok = false;
               break;
             }
@@ -372,12 +375,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
               const uint32_t d = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
-              const uint64_t l_c = l_base + (uint64_t)(((lb * CMAX + c) * L_BYTES) >> 4);
+              const uint64_t l_c = l_base + (uint64_t)((c * L_BYTES) >> 4);
               umma::mma_bf16(d, l_c, c_desc, idesc, 1);
               umma::mma_bf16(d, l_c + 16, c_desc + 16, idesc, 1);
               umma::mma_bf16(d, l_c + 32, c_desc + 32, idesc, 1);
             }
-            umma::mma_commit(&s.l_free[lb]);
+            umma::mma_commit(&s.l_free);
 #pragma unroll
             for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
           }
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         atomicExch(err, 1);
       } else if (my_tiles > 0) {
         const int t = my_tiles - 1;  // the last MMAs have completed before the CTA exits
-        umma::mbar_wait(&s.l_free[t & 1], (t >> 1) & 1, kWaitNs);
+        umma::mbar_wait(&s.l_free, t & 1, kWaitNs);
       }
     }
   } else if (warp < EPI_WARP0) {
@@ -401,9 +404,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool active = lc < C;
     uint32_t it = 0;
     for (int t = 0; t < my_tiles && !s.abort; ++t) {
-      const int lb = t & 1;
-      // buffer lb was last read by the column MMAs of tile t - 2
-      if (t >= 2 && !umma::mbar_wait(&s.l_free[lb], ((t - 2) >> 1) & 1, kWaitNs)) s.abort = 1;
+      // the column operand was last read by the column MMAs of tile t - 1
+      if (t >= 1 && !umma::mbar_wait(&s.l_free, (t - 1) & 1, kWaitNs)) s.abort = 1;
       for (int g = 0; g < (KS + 7) / 8 && !s.abort; ++g) {
         uint4 win[8];
 #pragma unroll
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (active) {
           // out[j] = column j of the 8 x 8 bf16 tile: rows 2k and 2k + 1 in word k
-          uint8_t* dst = s.L[lb][lc] + (m * (KL / 8) + g) * 128;
+          uint8_t* dst = s.L[lc] + (m * (KL / 8) + g) * 128;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (s.abort) break;
       umma::fence_proxy_async_smem();  // L stores -> visible to the tensor cores
       __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&s.l_full[lb]);
+      if (lane == 0) umma::mbar_arrive(&s.l_full);
     }
   } else {
     // ---------------------------------------------------------- epilogue: TMEM -> weighted sums, one channel per group
@@ -462,35 +464,42 @@ __global__ void __launch_bounds__(THREADS, 1)
         const WT* wg = w + ((size_t)y * W + (live ? x : 0)) * K;
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + slot * NP;
         const int nq = NP / 16;
-        // two register buffers: the load of group q + 1 overlaps the arithmetic of group q
-        float d0[16], d1[16];
-        tmem_ld16_async(taddr, d0);
+        // up to 64 accumulator columns per TMEM round trip (two for NP <= 128)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (q < nq) {
-            float* dq = (q & 1) ? d1 : d0;
-            tmem_wait_ld(dq);
-            if (q + 1 < nq) tmem_ld16_async(taddr + (q + 1) * 16, (q & 1) ? d0 : d1);
-            float wk[16];
-            if (w_vec) {  // the tile's FP32 weights in shared memory
+        for (int h = 0; h < 2; ++h) {
+          if (4 * h < nq) {
+            float d[4][16];
 #pragma unroll
-              for (int i4 = 0; i4 < 4; ++i4) {
-                const int k = q * 16 + 4 * i4;
-                const float4 v4 = (k < K && live) ? *reinterpret_cast<const float4*>(ws + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-                wk[4 * i4 + 0] = v4.x;
-                wk[4 * i4 + 1] = v4.y;
-                wk[4 * i4 + 2] = v4.z;
-                wk[4 * i4 + 3] = v4.w;
-              }
-            } else {
+            for (int qq = 0; qq < 4; ++qq)
+              if (4 * h + qq < nq) tmem_ld16_async(taddr + (4 * h + qq) * 16, d[qq]);
+            tmem_wait_ld4(d);
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int k = q * 16 + i;
-                wk[i] = k < K ? wload<WT>(wg + k) : 0.f;
+            for (int qq = 0; qq < 4; ++qq) {
+              const int q = 4 * h + qq;
+              if (q < nq) {
+                float wk[16];
+                if (w_vec) {  // the tile's FP32 weights in shared memory
+#pragma unroll
+                  for (int i4 = 0; i4 < 4; ++i4) {
+                    const int k = q * 16 + 4 * i4;
+                    const float4 v4 =
+                        (k < K && live) ? *reinterpret_cast<const float4*>(ws + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    wk[4 * i4 + 0] = v4.x;
+                    wk[4 * i4 + 1] = v4.y;
+                    wk[4 * i4 + 2] = v4.z;
+                    wk[4 * i4 + 3] = v4.w;
+                  }
+                } else {
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) {
+                    const int k = q * 16 + i;
+                    wk[i] = k < K ? wload<WT>(wg + k) : 0.f;
+                  }
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc = fmaf(wk[i], d[qq][i] + s.csum[q * 16 + i], acc);
               }
             }
-#pragma unroll
-            for (int i = 0; i < 16; ++i) acc = fmaf(wk[i], dq[i] + s.csum[q * 16 + i], acc);
           }
         }
         umma::fence_before_sync();
