@@ -235,6 +235,43 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
+    # the other P2S form on the same GPU (the metric compares them): whole frames through simulate_frame
+    other = d.P2S_EXACT if mode == d.P2S_LEARNED else (d.P2S_LEARNED if S["P"].has_mlp else None)
+    other_line = None
+    if other is not None:
+        n_other = 3 if other == d.P2S_EXACT else 10
+        S["sim"].simulate_frame(S["img"], S["dlist"][0], seed_base + 2, 0, other, out=out)
+        torch.cuda.synchronize()
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for i in range(n_other):
+            S["sim"].simulate_frame(S["img"], S["dlist"][i % len(S["dlist"])], seed_base + 2, i, other, out=out)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        oms = o0.elapsed_time(o1) / n_other
+        other_line = {"p2s": "exact" if other == d.P2S_EXACT else "learned", "frames_per_s": 1e3 / oms,
+                      "ms_per_frame": oms, "frames": n_other}
+    # cuFFT (through torch.fft) on the field sampler's transforms, as a comparison: J real N x N noise planes ->
+    # R2C 2-D FFT -> spectral multiply -> C2R 2-D inverse FFT, cropped to H x W (no noise, no mixing)
+    cufft = None
+    try:
+        N = S["N"]
+        noise_t = torch.randn(J, N, N, device=device)
+        mult_t = torch.rand(J, N, N // 2 + 1, device=device)
+        for _ in range(2):
+            torch.fft.irfft2(torch.fft.rfft2(noise_t) * mult_t, s=(N, N))[:, :H, :W].contiguous()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(5):
+            torch.fft.irfft2(torch.fft.rfft2(noise_t) * mult_t, s=(N, N))[:, :H, :W].contiguous()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cufft = {"what": "torch.fft rfft2 -> multiply -> irfft2 -> crop, J x N x N FP32", "ms": c0.elapsed_time(c1) / 5}
+        del noise_t, mult_t
+    except RuntimeError as exc:  # out of memory at the largest grids
+        cufft = {"unavailable": str(exc).splitlines()[0][:120]}
+
     names = ["fields", "warp", "p2s_" + args.mode, "blur_prepare", "blur"]
     acc = None
     if args.mode == "learned" and not args.no_accuracy:
@@ -302,6 +339,8 @@ def run_ours(args, rank, world, device):
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
         "gpu_launches": args.steps * (8 if args.mode == "learned" else 7),
+        "other_p2s": other_line,
+        "cufft_fields_comparison": cufft,
         "setup": S["info"],
         "clocks": clk,
         "wall_s": wall,
