@@ -58,7 +58,9 @@ extern "C" {
 #define DFP2S_P2S_LEARNED_FP32 2 /* the same network in FP32 on CUDA cores (check mode) */
 
 #define DFP2S_FACTOR_FACTORED 0 /* sqrt(lambda_j(f)) per mode, then mixing by L (Sec. III-C) */
-#define DFP2S_FACTOR_DENSE 1    /* per-frequency J x J symmetric root of L diag(lambda) L^T */
+#define DFP2S_FACTOR_DENSE 1    /* per-frequency J x J symmetric root of L diag(lambda) L^T: not built in
+                                   this version (DFP2S_EUNSUPPORTED); FACTORED applies the J x J root
+                                   L diag(sqrt(lambda(f))) of the same spectral density */
 
 #define DFP2S_KS 33       /* PSF / basis support is 33 x 33 pixels */
 #define DFP2S_MAX_J 64    /* at most 64 Zernike fields (Noll 2..65) */
@@ -93,7 +95,7 @@ typedef struct {
   int J;            /* number of fields, Noll modes 2..J+1; 3 <= J <= DFP2S_MAX_J */
   int N;            /* FFT grid side, power of two, 16 <= N <= 4096 */
   double pix_per_D; /* image pixels per aperture diameter of displacement s */
-  int kind;         /* DFP2S_FACTOR_FACTORED or DFP2S_FACTOR_DENSE (N <= 2048) */
+  int kind;         /* DFP2S_FACTOR_FACTORED (DFP2S_FACTOR_DENSE returns DFP2S_EUNSUPPORTED) */
 } dfp2s_factor_params;
 
 /* Builds the factor (allocates device memory, synchronises `stream` before
@@ -117,6 +119,19 @@ int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_byt
  * Errors: EINVAL, ECUDA. */
 int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
                                 int H, int W, float* fields_dev, void* stream);
+
+/* Temporally correlated fields (Sec. III, spatio-temporally correlated
+ * fields: the paper enforces the temporal correlation with an auto-regressive
+ * process).  Reading: the white noise of every mode follows
+ * e_t = alpha e_{t-1} + sqrt(1 - alpha^2) n_t, n_t the noise of frame t; the
+ * sampler is linear and time-invariant, so for a fixed D/r0 this is
+ *   fields_dev = alpha * prev_dev + sqrt(1 - alpha^2) * (the fields of `frame`),
+ * which is what the call computes.  prev_dev (J x H x W, the previous output)
+ * may be NULL for the first frame; it must not alias fields_dev.
+ * 0 <= alpha < 1.  Errors: EINVAL, ECUDA. */
+int dfp2s_sample_zernike_fields_ar1(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                    double alpha, int H, int W, const float* prev_dev, float* fields_dev,
+                                    void* stream);
 
 /* Same result as dfp2s_sample_zernike_fields, for callers that cannot
  * allocate device memory while they draw frames (a fixed memory plan made at

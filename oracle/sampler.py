@@ -46,6 +46,27 @@ def sample_fields(seed: int, frame: int, J: int, H: int, W: int, D_over_r0: floa
     return mix(zernike.noll_cholesky(J, D_over_r0), a_unit)
 
 
+def sample_fields_ar1(seed: int, frames: int, alpha: float, J: int, H: int, W: int, D_over_r0: float,
+                      pix_per_D: float = 8.0, N: int | None = None) -> list[np.ndarray]:
+    """Temporally correlated fields (Sec. III, spatio-temporally correlated fields; reading R26).
+
+    The paper enforces temporal correlation by an auto-regressive process; here the white noise of every
+    mode and torus position follows e_0 = n_0, e_t = alpha e_{t-1} + sqrt(1 - alpha^2) n_t, n_t the noise
+    of frame t, and each frame's fields are the FFT sampler applied to e_t.  Returns frames 0..frames-1.
+    """
+    if N is None:
+        N = grid_size(H, W, pix_per_D)
+    lam = spectrum.lambdas(J, N, pix_per_D)
+    L = zernike.noll_cholesky(J, D_over_r0)
+    beta = np.sqrt(1.0 - alpha * alpha)
+    out, e = [], None
+    for t in range(frames):
+        n = noise.field_noise(seed, t, J, N).astype(np.float64)
+        e = n if e is None else alpha * e + beta * n
+        out.append(mix(L, unit_fields(e, lam)[:, :H, :W]))
+    return out
+
+
 def dense_root(lam: np.ndarray, L: np.ndarray) -> np.ndarray:
     """Per-frequency symmetric square root F(f) of S~(f) = L diag(lambda(f)) L^T, shape (N, N, J, J).
 

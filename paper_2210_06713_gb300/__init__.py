@@ -50,6 +50,7 @@ SIGNATURES = {
     "dfp2s_factor_copy_cholesky": (_i, [_vp, _vp]),
     "dfp2s_factor_info": (_i, [_vp, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_sz)]),
     "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_sample_zernike_fields_ar1": (_i, [_vp, _d, _u64, _u32, _d, _i, _i, _vp, _vp, _vp]),
     "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
@@ -188,6 +189,19 @@ def sample_zernike_fields(factor: SpectralFactor, D_over_r0: float, seed: int, f
         out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
     _check(load().dfp2s_sample_zernike_fields(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
                                               _stream(stream)))
+    return out
+
+
+def sample_zernike_fields_ar1(factor: SpectralFactor, D_over_r0: float, seed: int, frame: int, alpha: float,
+                              H: int, W: int, prev: torch.Tensor | None, out: torch.Tensor | None = None,
+                              stream=None) -> torch.Tensor:
+    """Temporally correlated fields: alpha * prev + sqrt(1 - alpha^2) * (this frame's fields); prev None for
+    the first frame."""
+    if out is None:
+        out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_sample_zernike_fields_ar1(factor.handle, D_over_r0, seed, frame, alpha, H, W,
+                                                  _ptr(prev) if prev is not None else None, _ptr(out),
+                                                  _stream(stream)))
     return out
 
 

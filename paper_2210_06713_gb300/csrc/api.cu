@@ -149,6 +149,20 @@ extern "C" int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_
   return DFP2S_OK;
 }
 
+extern "C" int dfp2s_sample_zernike_fields_ar1(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                               double alpha, int H, int W, const float* prev, float* fields,
+                                               void* stream) {
+  CHECK_ARG(f && fields, "null argument");
+  CHECK_ARG(H >= 1 && W >= 1 && H <= f->d.N && W <= f->d.N, "frame %dx%d does not fit the %d grid", H, W, f->d.N);
+  CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
+  CHECK_ARG(alpha >= 0 && alpha < 1, "alpha = %g out of [0, 1)", alpha);
+  CHECK_ARG(prev != fields, "prev must not alias fields");
+  const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+  CHECK_LAUNCH(dfp2s_launch_sample_fields(f->d.scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame,
+                                          f->d.L32, scale, fields, as_stream(stream), prev, (float)alpha));
+  return DFP2S_OK;
+}
+
 extern "C" int dfp2s_gaussian_noise(uint64_t seed, uint32_t tag, uint32_t frame, uint32_t mode, int rows, int cols,
                                     float* out, void* stream) {
   CHECK_ARG(out && rows >= 1 && cols >= 4 && cols % 4 == 0, "bad noise shape %dx%d", rows, cols);

@@ -218,9 +218,10 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_rowifft(const float2* __
 // 4) is the register bucket.  Each thread mixes a pair of adjacent pixels
 // (8-byte loads and stores; needs an even pixel count) and reads four
 // coefficients of L per shared-memory load.
-template <int JB>
+template <int JB, bool AR>
 __global__ void __launch_bounds__(128, 4) k_mix_pairs(float* __restrict__ fields, const float* __restrict__ L,
-                                                   float scale, int J, size_t npix) {
+                                                   float scale, int J, size_t npix, const float* __restrict__ prev,
+                                                   float alpha) {
   __shared__ __align__(16) float Ls[JB * JB];
   for (int i = threadIdx.x; i < JB * JB; i += blockDim.x) {
     const int r = i / JB, c = i - r * JB;
@@ -251,14 +252,19 @@ __global__ void __launch_bounds__(128, 4) k_mix_pairs(float* __restrict__ fields
         ay = fmaf(l.w, v[4 * j4 + 3].y, ay);
       }
     }
+    if (AR) {  // a_t = alpha a_{t-1} + sqrt(1 - alpha^2) (L a~)_t, the root folded into `scale`
+      const float2 q = *reinterpret_cast<const float2*>(prev + (size_t)i * npix + p);
+      ax = fmaf(alpha, q.x, ax);
+      ay = fmaf(alpha, q.y, ay);
+    }
     *reinterpret_cast<float2*>(fields + (size_t)i * npix + p) = make_float2(ax, ay);
   }
 }
 
 // One pixel per thread (odd pixel counts).
-template <int JB>
+template <int JB, bool AR>
 __global__ void __launch_bounds__(128, 4) k_mix(float* __restrict__ fields, const float* __restrict__ L, float scale,
-                                             int J, size_t npix) {
+                                             int J, size_t npix, const float* __restrict__ prev, float alpha) {
   __shared__ __align__(16) float Ls[JB * JB];
   for (int i = threadIdx.x; i < JB * JB; i += blockDim.x) {
     const int r = i / JB, c = i - r * JB;
@@ -282,20 +288,30 @@ __global__ void __launch_bounds__(128, 4) k_mix(float* __restrict__ fields, cons
         acc = fmaf(l.w, v[4 * j4 + 3], acc);
       }
     }
+    if (AR) acc = fmaf(alpha, prev[(size_t)i * npix + p], acc);
     fields[(size_t)i * npix + p] = acc;
   }
 }
 
-template <int JB>
-void launch_mix(float* fields, const float* L, float scale, int J, size_t npix, cudaStream_t st) {
+template <int JB, bool AR>
+void launch_mix(float* fields, const float* L, float scale, int J, size_t npix, const float* prev, float alpha,
+                cudaStream_t st) {
   if constexpr (JB <= 40) {
     if (npix % 2 == 0) {
       const size_t pairs = npix / 2;
-      k_mix_pairs<JB><<<(unsigned)((pairs + 127) / 128), 128, 0, st>>>(fields, L, scale, J, npix);
+      k_mix_pairs<JB, AR><<<(unsigned)((pairs + 127) / 128), 128, 0, st>>>(fields, L, scale, J, npix, prev, alpha);
       return;
     }
   }
-  k_mix<JB><<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(fields, L, scale, J, npix);
+  k_mix<JB, AR><<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(fields, L, scale, J, npix, prev, alpha);
+}
+
+template <bool AR>
+void launch_mix_any(float* fields, const float* L, float scale, int J, size_t npix, const float* prev, float alpha,
+                    cudaStream_t st) {
+  if (J <= 16) launch_mix<16, AR>(fields, L, scale, J, npix, prev, alpha, st);
+  else if (J <= 40) launch_mix<40, AR>(fields, L, scale, J, npix, prev, alpha, st);
+  else launch_mix<64, AR>(fields, L, scale, J, npix, prev, alpha, st);
 }
 
 __global__ void k_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* __restrict__ out) {
@@ -332,7 +348,7 @@ void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H,
 
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st) {
+                               cudaStream_t st, const float* prev, float alpha) {
   switch (N) {
     case 16: launch_passes<16>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
     case 32: launch_passes<32>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
@@ -346,9 +362,8 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
     default: return DFP2S_EINVAL;
   }
   const size_t npix = (size_t)H * W;
-  if (J <= 16) launch_mix<16>(fields, L, scale, J, npix, st);
-  else if (J <= 40) launch_mix<40>(fields, L, scale, J, npix, st);
-  else launch_mix<64>(fields, L, scale, J, npix, st);
+  if (prev) launch_mix_any<true>(fields, L, scale * sqrtf(1.f - alpha * alpha), J, npix, prev, alpha, st);
+  else launch_mix_any<false>(fields, L, scale, J, npix, nullptr, 0.f, st);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
 

@@ -10,9 +10,10 @@
 #include "../../include/dfp2s.h"
 
 // fields.cu -- Sec. III-C sampler passes
+// prev != nullptr: fields = alpha prev + sqrt(1 - alpha^2) (this frame's fields), the auto-regressive form
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st);
+                               cudaStream_t st, const float* prev = nullptr, float alpha = 0.f);
 int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st);
 int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cudaStream_t st);
 

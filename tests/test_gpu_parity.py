@@ -108,6 +108,19 @@ def test_fields_grid_4096(lib):
     assert rel_l2(g, o) < TOL
 
 
+@pytest.mark.parametrize("J,H,W,N,alpha", [(36, 40, 33, 128, 0.8), (15, 64, 64, 128, 0.3)])
+def test_ar1_fields_match_oracle(lib, J, H, W, N, alpha):
+    f = lib.SpectralFactor(J, N, 8.0)
+    o = sampler.sample_fields_ar1(5, 3, alpha, J, H, W, 2.0, 8.0, N)
+    prev = None
+    for t in range(3):
+        g = lib.sample_zernike_fields_ar1(f, 2.0, 5, t, alpha, H, W, prev)
+        assert rel_l2(g.cpu().numpy(), o[t]) < TOL
+        prev = g
+    with pytest.raises(lib.DFP2SError):
+        lib.sample_zernike_fields_ar1(f, 2.0, 5, 3, alpha, H, W, prev, out=prev)  # aliasing
+
+
 def test_fields_are_deterministic_and_frame_dependent(lib):
     f = lib.SpectralFactor(36, 128, 8.0)
     a = lib.sample_zernike_fields(f, 2.0, 3, 4, 64, 64).cpu()

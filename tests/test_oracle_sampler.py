@@ -97,3 +97,38 @@ def test_brute_force_full_tensor_8x8x6(small):
     # report its size (informational, not a gate: reading R17)
     rel = np.linalg.norm(A - At) / np.linalg.norm(A)
     assert 0.0 < rel < 1.0
+
+
+def test_ar1_fields_special_cases_and_field_recursion():
+    # alpha = 0: independent frames; any alpha: because the sampler is linear and time-invariant the noise
+    # recursion equals a_t = alpha a_{t-1} + sqrt(1 - alpha^2) s_t on the fields (the form the kernels use)
+    J, H, W, N, d = 6, 8, 8, 16, 2.0
+    frames0 = sampler.sample_fields_ar1(4, 3, 0.0, J, H, W, d, PPD, N)
+    for t in range(3):
+        assert np.array_equal(frames0[t], sampler.sample_fields(4, t, J, H, W, d, PPD, N))
+    alpha = 0.7
+    frames = sampler.sample_fields_ar1(4, 4, alpha, J, H, W, d, PPD, N)
+    assert np.array_equal(frames[0], frames0[0])
+    for t in range(1, 4):
+        rec = alpha * frames[t - 1] + math.sqrt(1 - alpha ** 2) * sampler.sample_fields(4, t, J, H, W, d, PPD, N)
+        assert np.allclose(frames[t], rec, atol=1e-12 * np.abs(rec).max())
+
+
+def test_ar1_fields_are_stationary_with_lag_one_correlation_alpha(small):
+    # many independent chains (one Philox key each): Cov(a_1, a_1) = A tilde and Cov(a_1, a_0) = alpha A tilde
+    lam, L, At = small
+    alpha, nc = 0.6, 1500
+    n = N8 * N8
+    idx = np.array([j * n + p for j in range(J6) for p in (0, 9)])
+    a0 = np.empty((nc, idx.size))
+    a1 = np.empty((nc, idx.size))
+    for c in range(nc):
+        f = sampler.sample_fields_ar1(1000 + c, 2, alpha, J6, N8, N8, 2.0, PPD, N8)
+        a0[c] = f[0].ravel()[idx]
+        a1[c] = f[1].ravel()[idx]
+    T = At[np.ix_(idx, idx)]
+    assert _wishart_ok(a1.T @ a1 / nc, T, nc)
+    lag = a1.T @ a0 / nc
+    d = np.sqrt(np.diag(T))
+    sd = np.sqrt((np.outer(d, d) ** 2 + (alpha * T) ** 2) / nc)
+    assert np.all(np.abs(lag - alpha * T) <= 5 * sd + 1e-15)
