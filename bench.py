@@ -157,7 +157,7 @@ def run_ours(args, rank, world, device):
     w = torch.empty(H, W, K, device=device, dtype=torch.float32)
     out = torch.empty(C, H, W, device=device)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
-    nstage = 5
+    nstage = 4
     seed_base = 1000 * rank
 
     def step(i, ev=None):
@@ -167,24 +167,22 @@ def run_ours(args, rank, world, device):
         d.sample_zernike_fields(S["factor"], dr, seed_base, i, H, W, out=fields)
         if ev is not None:
             ev[1].record(stream)
-        d.tilt_warp(S["img"], fields[0], fields[1], out=warped)
+        if mode == d.P2S_LEARNED:
+            # the warp fused with the tensor-core blur's operand; the contraction kernel is timed alone
+            d.tilt_warp_blur_tc_prepare(S["P"], S["img"], fields[0], fields[1])
+        else:
+            d.tilt_warp(S["img"], fields[0], fields[1], out=warped)
         if ev is not None:
             ev[2].record(stream)
         d.p2s_weights(S["P"], mode, fields, w_dtype=wdt, out=w)
         if ev is not None:
             ev[3].record(stream)
         if mode == d.P2S_LEARNED:
-            # the two steps of the tensor-core blur, so that its contraction kernel is timed alone
-            d.basis_blur_tc_prepare(S["P"], warped)
-            if ev is not None:
-                ev[4].record(stream)
             d.basis_blur_tc_run(S["P"], (C, H, W), w, out=out)
         else:
-            if ev is not None:
-                ev[4].record(stream)
             d.basis_blur(S["P"], warped, w, out=out)
         if ev is not None:
-            ev[5].record(stream)
+            ev[4].record(stream)
 
     for i in range(args.warmup):
         step(i)
@@ -272,7 +270,7 @@ def run_ours(args, rank, world, device):
     except RuntimeError as exc:  # out of memory at the largest grids
         cufft = {"unavailable": str(exc).splitlines()[0][:120]}
 
-    names = ["fields", "warp", "p2s_" + args.mode, "blur_prepare", "blur"]
+    names = ["fields", "warp_and_blur_operand" if args.mode == "learned" else "warp", "p2s_" + args.mode, "blur"]
     acc = None
     if args.mode == "learned" and not args.no_accuracy:
         acc = accuracy_vs_exact(d, S, seed_base + 77)
@@ -280,7 +278,7 @@ def run_ours(args, rank, world, device):
     peaks, peak_kind = _peaks()
     # dominant kernel roofline: among the stages that are one kernel launch each (warp, P2S weights, blur
     # contraction); the field stage is four launches, each shorter than the blur contraction (ncu launch list)
-    single = [1, 2, 4]
+    single = [1, 2, 3]
     dom = single[int(np.argmax(mean_stage[single]))]
     npix = H * W
     if names[dom] == "blur" and args.mode == "learned":
@@ -310,6 +308,11 @@ def run_ours(args, rank, world, device):
         roof = {"kernel": "k_p2s_exact", "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    elif args.mode == "learned":
+        wq = (W + 127) // 128 * 128 + 64
+        byt = 4.0 * npix * (2 + C) + 16.0 * C * (H + 32) * wq  # tilts and image in, eight BF16 planes out
+        roof = {"kernel": "k_warp_pad_shifted", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
     else:
         byt = 4.0 * npix * (2 + 2 * C)  # tilt fields a2, a3 and the image in, the warped image out
         roof = {"kernel": "k_tilt_warp", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
@@ -338,7 +341,7 @@ def run_ours(args, rank, world, device):
         "fields_roofline": fields_roof,
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
-        "gpu_launches": args.steps * (8 if args.mode == "learned" else 7),
+        "gpu_launches": args.steps * 7,  # 4 field launches, warp (+operand), P2S, blur
         "other_p2s": other_line,
         "cufft_fields_comparison": cufft,
         "setup": S["info"],

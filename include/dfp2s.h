@@ -293,6 +293,13 @@ int dfp2s_basis_blur_tc(const dfp2s_p2s* p, const float* img_dev, int C, int H, 
  * dfp2s_basis_blur_tc(...) is _prepare followed by _run.
  * Errors: EINVAL, EUNSUPPORTED (K > 128), ENOMEM (scratch), ECUDA. */
 int dfp2s_basis_blur_tc_prepare(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W, void* stream);
+/* dfp2s_tilt_warp (Eq. 2's linear phase as a shift) fused with
+ * dfp2s_basis_blur_tc_prepare: prepares the blur operand of the tilt-warped
+ * image, bit for bit the one _prepare makes from dfp2s_tilt_warp's output,
+ * without writing the FP32 warped image.  a2/a3: H x W tilt fields.  Follow
+ * it with dfp2s_basis_blur_tc_run.  Errors as _prepare. */
+int dfp2s_tilt_warp_blur_tc_prepare(const dfp2s_p2s* p, const float* img_dev, int C, int H, int W,
+                                    const float* a2_dev, const float* a3_dev, void* stream);
 int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void* w_dev, int w_dtype, float* out_dev,
                             void* stream);
 
@@ -306,13 +313,15 @@ int dfp2s_ctx_destroy(dfp2s_ctx* c);
 
 /* Fig. dfp2s: one frame.  fields (Sec. III-C) -> tilt warp -> P2S weights
  * (FP32) -> blur (p2s_mode EXACT: FP32 CUDA-core blur; LEARNED: the network's
- * weights and the BF16 tensor-core blur, dfp2s_basis_blur_tc) -> out
+ * weights and the BF16 tensor-core blur, with the warp fused into the blur's
+ * operand, dfp2s_tilt_warp_blur_tc_prepare + dfp2s_basis_blur_tc_run) -> out
  * (C x H x W, device).
  * Errors: EINVAL, ECUDA. */
 int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img_dev, int C, int H, int W, double D_over_r0,
                          uint64_t seed, uint32_t frame, int p2s_mode, float* out_dev, void* stream);
 /* Device pointers of the context's last fields / warped image / weights
- * (valid until the next call on the context). */
+ * (valid until the next call on the context; LEARNED frames do not write the
+ * FP32 warped image). */
 int dfp2s_ctx_buffers(const dfp2s_ctx* c, float** fields_dev, float** warped_dev, void** w_dev);
 
 #ifdef __cplusplus

@@ -68,6 +68,7 @@ SIGNATURES = {
     "dfp2s_basis_blur": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_basis_blur_tc": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_basis_blur_tc_prepare": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "dfp2s_tilt_warp_blur_tc_prepare": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "dfp2s_basis_blur_tc_run": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_ctx_create": (_i, [_vp, _vp, _i, _i, _i, _c.POINTER(_vp)]),
     "dfp2s_ctx_destroy": (_i, [_vp]),
@@ -369,6 +370,13 @@ def basis_blur_tc_prepare(p: P2S, img: torch.Tensor, stream=None) -> None:
     """First step of basis_blur_tc: the image's shifted BF16 operand, kept in the handle."""
     C, H, W = img.shape
     _check(load().dfp2s_basis_blur_tc_prepare(p.handle, _ptr(img), C, H, W, _stream(stream)))
+
+
+def tilt_warp_blur_tc_prepare(p: P2S, img: torch.Tensor, a2: torch.Tensor, a3: torch.Tensor, stream=None) -> None:
+    """tilt_warp fused with basis_blur_tc_prepare (the warped image itself is not written)."""
+    C, H, W = img.shape
+    _check(load().dfp2s_tilt_warp_blur_tc_prepare(p.handle, _ptr(img), C, H, W, _ptr(a2), _ptr(a3),
+                                                  _stream(stream)))
 
 
 def basis_blur_tc_run(p: P2S, shape, w: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

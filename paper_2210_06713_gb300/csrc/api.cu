@@ -416,6 +416,18 @@ extern "C" int dfp2s_basis_blur_tc_prepare(const dfp2s_p2s* p, const float* img,
   return DFP2S_OK;
 }
 
+extern "C" int dfp2s_tilt_warp_blur_tc_prepare(const dfp2s_p2s* p, const float* img, int C, int H, int W,
+                                               const float* a2, const float* a3, void* stream) {
+  CHECK_ARG(p && img && a2 && a3, "null argument");
+  CHECK_ARG(C >= 1 && C <= 64 && H >= 1 && W >= 1 && H <= 65535 - 32 && W <= (1 << 20), "bad image shape");
+  const int rc = dfp2s_launch_blur_tc_prepare_warp(const_cast<dfp2s_p2s_dev*>(&p->d), img, C, H, W, a2, a3,
+                                                   as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
+  if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "warp + tensor-core blur preparation");
+  return DFP2S_OK;
+}
+
 extern "C" int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void* w, int w_dtype, float* out,
                                        void* stream) {
   CHECK_ARG(p && w && out, "null argument");
@@ -497,6 +509,14 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
   int rc = dfp2s_sample_zernike_fields(c->f, D_over_r0, seed, frame, H, W, c->fields, stream);
   if (rc) return rc;
   const size_t npix = (size_t)H * W;
+  if (p2s_mode == DFP2S_P2S_LEARNED) {
+    // warp fused with the tensor-core blur's operand (the FP32 warped image is not needed)
+    rc = dfp2s_tilt_warp_blur_tc_prepare(c->p, img, C, H, W, c->fields, c->fields + npix, stream);
+    if (rc) return rc;
+    rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, DFP2S_W_F32, stream);
+    if (rc) return rc;
+    return dfp2s_basis_blur_tc_run(c->p, C, H, W, c->w, DFP2S_W_F32, out, stream);
+  }
   rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
   if (rc) return rc;
   rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, DFP2S_W_F32, stream);

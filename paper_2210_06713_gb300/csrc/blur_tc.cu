@@ -41,6 +41,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tilt.cuh"
 #include "umma.cuh"
 
 namespace {
@@ -136,6 +137,40 @@ __global__ void k_pad_shifted(const float* __restrict__ img, int C, int H, int W
   for (int sh = 0; sh < NSHIFT; ++sh) {
     const int sx = min(max(x + sh - 16, 0), W - 1);
     dst[sh * plane] = __float2bfloat16_rn(row[sx] - centre);
+  }
+}
+
+// The same planes for the tilt-warped image, without the FP32 warped image: the
+// value at padded (r, x) of shift sh is the warped pixel (clamp(r - 16),
+// clamp(x + sh - 16)) (tilt_sample, as in the warp kernel).  A thread covers
+// columns 8u .. 8u + 7 of padded row r: per channel it warps the 15 clamped
+// columns 8u - 16 .. 8u - 2 and writes one 16-byte run per shift.
+__global__ void __launch_bounds__(128, 6)
+    k_warp_pad_shifted(const float* __restrict__ img, int C, int H, int W, const float* __restrict__ a2,
+                       const float* __restrict__ a3, int Wq, float centre, __nv_bfloat16* __restrict__ P) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (8 * u >= Wq) return;
+  const int R = H + 32;
+  const int yp = min(max(r - 16, 0), H - 1);
+  const size_t plane = (size_t)R * Wq;
+  const float* t2 = a2 + (size_t)yp * W;
+  const float* t3 = a3 + (size_t)yp * W;
+  for (int c = 0; c < C; ++c) {
+    const float* I = img + (size_t)c * H * W;
+    uint32_t h[15];  // bf16 bits of the 15 warped samples
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+      const int x = min(max(8 * u - 16 + i, 0), W - 1);
+      const float v = tilt_sample(I, H, W, x, yp, __ldg(t2 + x), __ldg(t3 + x));
+      h[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - centre));
+    }
+    __nv_bfloat16* dst = P + ((size_t)c * NSHIFT) * plane + (size_t)r * Wq + 8 * u;
+#pragma unroll
+    for (int sh = 0; sh < NSHIFT; ++sh)
+      *reinterpret_cast<uint4*>(dst + sh * plane) =
+          make_uint4(h[sh] | (h[sh + 1] << 16), h[sh + 2] | (h[sh + 3] << 16), h[sh + 4] | (h[sh + 5] << 16),
+                     h[sh + 6] | (h[sh + 7] << 16));
   }
 }
 
@@ -535,13 +570,12 @@ EncodeTiledFn encode_tiled() {
 
 }  // namespace
 
-// Shifted BF16 planes of the image in the handle's scratch (k_pad_shifted).
-int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, cudaStream_t st) {
+// Basis tiles, centring sums and the plane scratch for a C x H x W image (once per handle / size).
+static int blur_tc_scratch(dfp2s_p2s_dev* p, int C, int H, int W, cudaStream_t st) {
   const int K = p->K;
   const int NP = (K + 15) / 16 * 16;
   const float centre = 0.5f;
   if (NP > 128) return DFP2S_EUNSUPPORTED;
-  // basis tiles and centring sums c * s_k (once per handle)
   if (!p->bt) {
     const int n = KS * NP * KM + NP * KL;  // row tiles, then the column taps
     if (cudaMalloc((void**)&p->bt, (size_t)n * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
@@ -556,9 +590,7 @@ int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int 
   }
   const int nseg = (W + TM - 1) / TM;
   const int Wq = nseg * TM + 64;  // >= x0 + 160 for every tile; a multiple of 8 (16-byte rows)
-  const int R = H + 32;
-  const size_t plane = (size_t)R * Wq;
-  const size_t need = (size_t)C * NSHIFT * plane;
+  const size_t need = (size_t)C * NSHIFT * (H + 32) * Wq;
   if (need > p->pad_cap) {
     if (p->pad) cudaFree(p->pad);
     p->pad = nullptr;
@@ -566,7 +598,28 @@ int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int 
     if (cudaMalloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
     p->pad_cap = need;
   }
-  k_pad_shifted<<<dim3((Wq + 255) / 256, R, C), 256, 0, st>>>(img, C, H, W, Wq, centre, p->pad);
+  return DFP2S_OK;
+}
+
+// Shifted BF16 planes of the image in the handle's scratch (k_pad_shifted).
+int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, cudaStream_t st) {
+  const int rc = blur_tc_scratch(p, C, H, W, st);
+  if (rc != DFP2S_OK) return rc;
+  const int Wq = (W + TM - 1) / TM * TM + 64;
+  k_pad_shifted<<<dim3((Wq + 255) / 256, H + 32, C), 256, 0, st>>>(img, C, H, W, Wq, 0.5f, p->pad);
+  p->prep_C = C;
+  p->prep_H = H;
+  p->prep_W = W;
+  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+}
+
+// The same for the tilt-warped image (k_warp_pad_shifted), without writing the warped image.
+int dfp2s_launch_blur_tc_prepare_warp(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const float* a2,
+                                      const float* a3, cudaStream_t st) {
+  const int rc = blur_tc_scratch(p, C, H, W, st);
+  if (rc != DFP2S_OK) return rc;
+  const int Wq = (W + TM - 1) / TM * TM + 64;
+  k_warp_pad_shifted<<<dim3((Wq / 8 + 127) / 128, H + 32), 128, 0, st>>>(img, C, H, W, a2, a3, Wq, 0.5f, p->pad);
   p->prep_C = C;
   p->prep_H = H;
   p->prep_W = W;

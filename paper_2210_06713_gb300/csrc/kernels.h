@@ -95,6 +95,8 @@ int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const do
 
 // blur_tc.cu -- BF16 tcgen05 blur (weights in BF16)
 int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, cudaStream_t st);
+int dfp2s_launch_blur_tc_prepare_warp(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const float* a2,
+                                      const float* a3, cudaStream_t st);
 int dfp2s_launch_blur_tc_run(dfp2s_p2s_dev* p, int C, int H, int W, const void* w, int w_dtype, float* out,
                              cudaStream_t st);
 int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,

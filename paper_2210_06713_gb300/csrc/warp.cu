@@ -11,23 +11,9 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tilt.cuh"
 
 namespace {
-
-constexpr float kTiltPix = 1.27323954473516268615f;  // 4 / pi
-
-DFP2S_DEV float bilinear_clamp(const float* __restrict__ I, int H, int W, float sx, float sy) {
-  const float fx = floorf(sx), fy = floorf(sy);
-  const float tx = sx - fx, ty = sy - fy;
-  const int x0 = (int)fx, y0 = (int)fy;
-  const int xa = min(max(x0, 0), W - 1), xb = min(max(x0 + 1, 0), W - 1);
-  const int ya = min(max(y0, 0), H - 1), yb = min(max(y0 + 1, 0), H - 1);
-  const float v00 = __ldg(I + (size_t)ya * W + xa), v01 = __ldg(I + (size_t)ya * W + xb);
-  const float v10 = __ldg(I + (size_t)yb * W + xa), v11 = __ldg(I + (size_t)yb * W + xb);
-  const float top = fmaf(tx, v01 - v00, v00);
-  const float bot = fmaf(tx, v11 - v10, v10);
-  return fmaf(ty, bot - top, top);
-}
 
 __global__ void __launch_bounds__(256) k_tilt_warp(const float* __restrict__ img, int C, int H, int W,
                                                    const float* __restrict__ a2, const float* __restrict__ a3,
@@ -56,7 +42,7 @@ __global__ void __launch_bounds__(256) k_tilt_warp(const float* __restrict__ img
     float r[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      r[i] = bilinear_clamp(I, H, W, fmaf(kTiltPix, dx[i], (float)(x4 + i)), fmaf(kTiltPix, dy[i], (float)y));
+      r[i] = tilt_sample(I, H, W, x4 + i, y, dx[i], dy[i]);
     float* o = out + c * plane + row + x4;
     if (vec) {
       *reinterpret_cast<float4*>(o) = make_float4(r[0], r[1], r[2], r[3]);

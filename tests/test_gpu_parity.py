@@ -209,6 +209,26 @@ def test_blur_bf16_tensor_cores_match_oracle_on_bf16_operands(lib, C, H, W, K):
     assert np.array_equal(g2, g32)
 
 
+@pytest.mark.parametrize("C,H,W,K", [(3, 70, 200, 100), (2, 33, 17, 16)])
+def test_fused_warp_prepare_is_bit_exact(lib, C, H, W, K):
+    # the fused warp + operand preparation gives the same blur, bit for bit, as the warp followed by preparation
+    img = synthetic.blobs(H, W, C, n=6, seed=K)
+    fld = synthetic.random_fields(2, H, W, scale=2.0, seed=W)
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=C).reshape(K, 33, 33)
+    P = lib.P2S(36, cu(basis))
+    w = torch.as_tensor(np.random.default_rng(H).standard_normal((H, W, K)), dtype=torch.float32, device="cuda")
+    warped = lib.tilt_warp(cu(img), cu(fld[0]), cu(fld[1]))
+    lib.basis_blur_tc_prepare(P, warped)
+    ref = lib.basis_blur_tc_run(P, (C, H, W), w).cpu().numpy()
+    lib.tilt_warp_blur_tc_prepare(P, cu(img), cu(fld[0]), cu(fld[1]))
+    got = lib.basis_blur_tc_run(P, (C, H, W), w).cpu().numpy()
+    P.check()
+    assert np.array_equal(got, ref)
+    # and the frame against the oracle's warp + blur on the kernel's bfloat16 operands
+    o = image.basis_blur(_bf16(image.tilt_warp(img, fld[0], fld[1]) - 0.5) + 0.5, w.cpu().numpy(), _bf16(basis))
+    assert rel_l2(got, o) < 1e-4
+
+
 def test_blur_tc_run_needs_a_prepared_image(lib):
     basis = synthetic.random_orthonormal_rows(16, 33 * 33, seed=3).reshape(16, 33, 33)
     P = lib.P2S(36, cu(basis))
