@@ -103,6 +103,17 @@ DFP2S_DEV bool bar_epi_any(bool v) {
   return r != 0;
 }
 
+// 1-D bulk copy shared -> global (both 16-byte aligned, size a multiple of 16) in a bulk group; wait until
+// its source may be overwritten, or until every issued copy has completed.
+DFP2S_DEV void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(umma::smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+DFP2S_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+DFP2S_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 template <typename WT>
 DFP2S_DEV void wstore(WT* p, float v);
 template <>
@@ -371,10 +382,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       umma::fence_before_sync();
+      if (vec_out == 2) umma::fence_proxy_async_smem();  // staging rows -> the bulk copy below
       if (bar_epi_any(s.abort != 0)) break;
       const int nlive = min(TM, npix - p0);
       WT* dst = wout + (size_t)p0 * K;
-      if (vec_out) {  // FP32 with K % 4 == 0 and 16-byte aligned rows
+      if (vec_out == 2) {
+        // staging rows are contiguous (KS == K): one bulk copy of the tile's outputs, shared -> global;
+        // its reads of the staging area finish before the barrier below releases it
+        if (tid == 0) {
+          bulk_s2g(dst, stage, (uint32_t)(nlive * K * 4));
+          bulk_wait_read();
+        }
+      } else if (vec_out) {  // FP32 with K % 4 == 0 and 16-byte aligned rows
         const int n4 = nlive * K / 4;
         for (int i = tid; i < n4; i += EPI_THREADS) {
           const int e = 4 * i;
@@ -391,6 +410,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (bar_epi_any(s.abort != 0)) break;
     }
     if (s.abort && tid == 0) atomicExch(err, 2);
+    if (vec_out == 2 && tid == 0) bulk_wait_all();  // the last tile's outputs have reached global memory
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -459,7 +479,9 @@ int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, v
   // staging row stride: a multiple of 4 floats with an odd number of 16-byte units (no bank conflicts)
   int KS = (K + 3) / 4 * 4;
   if ((KS / 4) % 2 == 0) KS += 4;
-  const int vec_out = (w_dtype == DFP2S_W_F32) && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
+  // 2: contiguous staging rows (KS == K), one bulk copy per tile; 1: vector copy loop; 0: scalar loop
+  int vec_out = (w_dtype == DFP2S_W_F32) && (K % 4) == 0 && ((uintptr_t)w & 15) == 0;
+  if (vec_out && KS == K) vec_out = 2;
   const size_t sm = sizeof(Smem) + 1024;
   static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory layout");
   cudaFuncSetAttribute(k_mlp_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
