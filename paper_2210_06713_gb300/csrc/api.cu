@@ -202,7 +202,7 @@ static void p2s_free(dfp2s_p2s* p) {
   void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt,    p->d.mask, p->d.dft,       p->d.W1,        p->d.b1,
                   p->d.W2,    p->d.b2,   p->d.W3,    p->d.b3,   p->d.in_scale, p->d.out_scale, p->d.out_shift,
                   p->d.bt,    p->d.pad,  p->d.err,   p->d.bsum,     p->d.tc_w1,     p->d.tc_w2,     p->d.tc_w3,
-                  p->d.tc_c3};
+                  p->d.tc_c3, p->d.tc_bias};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ++b_issued;
           // this tile's weights, once the epilogue of the previous tile has released the buffer
           if (w_vec && w_issued == t && iy >= 2) {
-            if (t == 0 || umma::mbar_test(&s.w_empty, (t - 1) & 1)) {
+            if (t == 0 || umma::mbar_ready(&s.w_empty, (t - 1) & 1)) {
               issue_w(t);
             } else if (iy == KS - 1) {
               if (!umma::mbar_wait(&s.w_empty, (t - 1) & 1, kWaitNs)) {

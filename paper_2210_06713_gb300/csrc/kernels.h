@@ -61,6 +61,7 @@ struct dfp2s_p2s_dev {
   // tensor-core surrogate: packed BF16 weights and the folded output offset
   __nv_bfloat16 *tc_w1, *tc_w2, *tc_w3;
   float* tc_c3;
+  __nv_bfloat16* tc_bias;  // hidden biases as the B operand of the bias MMAs
 };
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
 // w_dtype for dfp2s_launch_p2s_exact that writes the normalised 33 x 33 PSFs (npix x 1089 FP32) instead of weights

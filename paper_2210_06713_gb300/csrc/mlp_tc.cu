@@ -3,25 +3,33 @@
 // logistic fit accurate far beyond the BF16 rounding of the activations.
 //
 // A tile is 128 consecutive pixels (MMA M = 128):
-//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T -> TMEM A = columns [0, 256)
+//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T + b1 -> TMEM A = columns [0, 256)
 //            (W1' = W1 diag(in_scale), resident in shared memory)
-//   GELU(z + b1) -> H [128 x 256] BF16 in shared memory (K-major core matrices)
-//   layer 2: H x W2^T -> TMEM B = [256, 512), W2 streamed in four 64-wide K chunks
-//   GELU(z + b2) -> H
-//   layer 3: H x W3^T -> TMEM [384, 384 + NP3), W3 streamed in four K chunks
+//   2 GELU(z) -> H [128 x 256] BF16 in shared memory (K-major core matrices)
+//   layer 2: H x (W2 / 2)^T + b2 -> TMEM B = [256, 512), W2 streamed in four 64-wide K chunks
+//   2 GELU(z) -> H
+//   layer 3: H x (W3 / 2)^T -> TMEM [384, 384 + NP3), W3 streamed in four K chunks
 //   w = y * out_scale + (b3 * out_scale + out_shift) -> global (FP32 or BF16)
 //
+// The hidden biases enter the accumulators through one extra K = 16 MMA per
+// layer (a tile of ones against the bias split into high and low bfloat16
+// parts, exact to about 2^-17 relative), and the activations are stored doubled
+// against halved weights of the next layer (both scalings by a power of two are
+// exact), so that an activation costs the epilogue five instructions.
+//
 // Warp roles: warps 0-15 run the epilogues (warp w reads TMEM lanes 32 (w % 4)
-// .. and a quarter of the columns), warp 16 issues the weight copies and the
-// MMAs, warp 17 converts the next tile's fields into X.  The epilogues hand H
-// over in 64-column chunks (one mbarrier per chunk), so the MMAs of the next
-// layer start on a chunk while the epilogue works on the following one; the
-// second epilogue walks its chunks from the top so that layer 3's columns
-// [384, 512) are free first.  Layer 1 of the next tile runs on the tensor
-// cores while the epilogues finish the current tile.  Weight chunks arrive by
-// 1-D bulk copies into a three-deep ring; their MMAs release a slot through
-// tcgen05.commit.  All waits are bounded; a wait that runs out sets the
-// kernel's error word.
+// .. and a quarter of the columns), warp 16 issues the MMAs, warp 17 converts
+// the next tile's fields into X, warp 18 issues the weight copies.  The
+// epilogues hand H over in 64-column chunks (one mbarrier per chunk), so the
+// MMAs of the next layer start on a chunk while the epilogue works on the
+// following one; the second epilogue walks its chunks from the top so that
+// layer 3's columns [384, 512) are free first.  Layer 1 of the next tile runs
+// on the tensor cores while the epilogues finish the current tile.  Weight
+// chunks arrive by 1-D bulk copies into a three-deep ring; their MMAs release a
+// slot through tcgen05.commit.  The copies have a warp of their own because a
+// bulk copy can hold its issuing thread until the copy engine takes it, which
+// would stall the MMA issue.  All waits are bounded; a wait that runs out sets
+// the kernel's error word.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,12 +48,15 @@ constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int PRODUCER_WARP = EPI_WARPS;
 constexpr int LOADER_WARP = EPI_WARPS + 1;
-constexpr int THREADS = EPI_THREADS + 64;  // + producer and loader warps
+constexpr int COPY_WARP = EPI_WARPS + 2;
+constexpr int THREADS = EPI_THREADS + 96;  // + MMA, loader and copy warps
 constexpr int L3_COL = 384;                // layer-3 accumulator columns [384, 384 + NP3)
 constexpr int NRING = 3;
 constexpr int CHUNK_BYTES = HID * 64 * 2;  // one 64-wide K chunk of W2 (the largest)
 constexpr int STAGE_BYTES = TM * 132 * 4;  // FP32 output rows of up to 128 (+4) weights
 constexpr int HS_BYTES = STAGE_BYTES > TM * HID * 2 ? STAGE_BYTES : TM * HID * 2;
+constexpr int ONES_BYTES = TM * 16 * 2;    // a 128 x 16 A operand, ones in two K columns
+constexpr int BIAS_BYTES = HID * 16 * 2;   // the 256 x 16 B operand of the hidden biases
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct Smem {
@@ -53,7 +64,8 @@ struct Smem {
   uint8_t H[HS_BYTES];               // hidden activations, then the output staging rows
   uint8_t W1[HID * KX * 2];          // 24 KB
   uint8_t X[TM * KX * 2];            // 12 KB
-  float b1[HID], b2[HID];
+  uint8_t ONES[2][ONES_BYTES];       // 8 KB: ones in K columns 0, 1 (layer 1) and 2, 3 (layer 2)
+  uint8_t BIAS[BIAS_BYTES];          // 8 KB: K columns 0, 1 = b1 (high and low bfloat16 parts), 2, 3 = b2
   float c3[128], s3[128];            // output bias and scale
   uint64_t full[NRING], empty[NRING];
   uint64_t w1_full, x_ready, l1_done, l2_done, l3_done;
@@ -62,25 +74,22 @@ struct Smem {
   int abort;
 };
 
-// GELU(z) = z Phi(z) with the logistic fit of Phi in gelu_fit.h (max error
-// 1.9e-5 in Phi); 2^x and the reciprocal use the hardware approximations
-// (ex2.approx, rcp.approx).  For z -> -inf the exponent overflows to +inf and the
-// reciprocal gives 0; the activations are rounded to bfloat16 afterwards.
-DFP2S_DEV float ex2_approx(float x) {
+// 2 GELU(z) = 2 z Phi(z) with the logistic fit of Phi in gelu_fit.h (max error
+// 1.9e-5 in Phi), written as z (1 + tanh(z q ln2 / 2)) and evaluated with the
+// hardware tanh.approx (one special-function instruction per activation; its
+// absolute error, measured on sm_103a at 7.8e-6, leaves the 5.5e-5 GELU error of
+// the fit unchanged).  tanh saturates to -1 for z -> -inf, so GELU -> 0 there.
+DFP2S_DEV float tanh_approx(float x) {
   float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-DFP2S_DEV float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-DFP2S_DEV float gelu(float z) {
+DFP2S_DEV float gelu2x(float z) {
+  constexpr float h = DFP2S_GELU_TANH_SCALE;
+  constexpr float c0 = DFP2S_GELU_C0 * h, c1 = DFP2S_GELU_C1 * h, c2 = DFP2S_GELU_C2 * h;
   const float s = fminf(z * z, DFP2S_GELU_Z2MAX);
-  const float q = fmaf(fmaf(DFP2S_GELU_C2, s, DFP2S_GELU_C1), s, DFP2S_GELU_C0);
-  const float e = ex2_approx(-(z * q));
-  return z * rcp_approx(1.0f + e);
+  const float q = fmaf(fmaf(c2, s, c1), s, c0);
+  return fmaf(z, tanh_approx(z * q), z);
 }
 
 // byte offset of element (row, k) in a K-major no-swizzle tile with `kgroups` 8-element K groups per row group
@@ -123,9 +132,9 @@ DFP2S_DEV void wstore<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2b
 
 // Hidden-layer epilogue of one epilogue warp: for each 64-column chunk c
 // (ascending, or descending if `reverse`), this warp's 16 columns
-// [64 c + 16 sl, +16) of TMEM region `col0` -> GELU(z + b) -> H (K-major,
-// K = column - col0), then the chunk is handed to the MMA warp.
-DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col0, const float* bias, bool reverse) {
+// [64 c + 16 sl, +16) of TMEM region `col0` (biases included) -> 2 GELU -> H
+// (K-major, K = column - col0), then the chunk is handed to the MMA warp.
+DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col0, bool reverse) {
   const int q4 = warp & 3, sl = warp >> 2;
   const int p = q4 * 32 + lane;
   for (int i = 0; i < 4; ++i) {
@@ -136,8 +145,8 @@ DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col
     uint32_t packed[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const float g0 = gelu(d[2 * e] + bias[k0 + 2 * e]);
-      const float g1 = gelu(d[2 * e + 1] + bias[k0 + 2 * e + 1]);
+      const float g0 = gelu2x(d[2 * e]);
+      const float g1 = gelu2x(d[2 * e + 1]);
       __nv_bfloat162 h2 = __floats2bfloat162_rn(g0, g1);
       packed[e] = *reinterpret_cast<uint32_t*>(&h2);
     }
@@ -154,8 +163,8 @@ DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col
 template <typename WT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_mlp_tc(const float* __restrict__ fields, int J, int npix, int K, int NP3, const __nv_bfloat16* __restrict__ w1t,
-             const __nv_bfloat16* __restrict__ w2c, const __nv_bfloat16* __restrict__ w3c, const float* __restrict__ b1,
-             const float* __restrict__ b2, const float* __restrict__ c3, const float* __restrict__ s3,
+             const __nv_bfloat16* __restrict__ w2c, const __nv_bfloat16* __restrict__ w3c,
+             const __nv_bfloat16* __restrict__ bias, const float* __restrict__ c3, const float* __restrict__ s3,
              WT* __restrict__ wout, int KS, int vec_out, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
@@ -177,16 +186,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     s.abort = 0;
     umma::fence_mbar_init();
   }
-  for (int i = tid; i < HID; i += THREADS) {
-    s.b1[i] = b1[i];
-    s.b2[i] = b2[i];
-  }
   for (int i = tid; i < 128; i += THREADS) {
     s.c3[i] = i < K ? c3[i] : 0.f;
     s.s3[i] = i < K ? s3[i] : 0.f;
   }
-  // zero X once (the padded K columns stay zero)
+  // zero X once (the padded K columns stay zero); the ones tiles of the bias MMAs
   for (int i = tid; i < TM * KX * 2 / 16; i += THREADS) reinterpret_cast<uint4*>(s.X)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < 2 * TM * 16; i += THREADS) {
+    const int g = i / (TM * 16), r = (i / 16) % TM, k = i % 16;
+    const __nv_bfloat16 v = __float2bfloat16_rn((k >> 1) == g ? 1.f : 0.f);
+    *reinterpret_cast<__nv_bfloat16*>(s.ONES[g] + kmajor_off(r, k, 2)) = v;
+  }
+  umma::fence_proxy_async_smem();  // X and the ones tiles -> the tensor cores' reads
   if (warp == 0) {
     umma::tmem_alloc(&s.tmem_base, 512);
     umma::tmem_relinquish();
@@ -197,57 +208,25 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = s.tmem_base;
 
   if (warp == PRODUCER_WARP) {
-    // ------------------------------------------------------------ producer: copies and MMAs
+    // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t w2_bytes = (uint32_t)CHUNK_BYTES;
-      const uint32_t w3_bytes = (uint32_t)(NP3 * 64 * 2);
       // K-major no-swizzle descriptors: X and W1 with 6 K groups per 8-row group, H with 32,
-      // weight chunks with 8; per-MMA descriptors add (byte offset >> 4)
+      // weight chunks with 8, the ones and bias tiles with 2; per-MMA descriptors add (byte offset >> 4)
       const uint64_t x_desc = umma::sdesc(umma::smem_u32(s.X), 128, 768);
       const uint64_t w1_desc = umma::sdesc(umma::smem_u32(s.W1), 128, 768);
       const uint64_t h_desc = umma::sdesc(umma::smem_u32(s.H), 128, 4096);
       const uint64_t ring_desc = umma::sdesc(umma::smem_u32(s.ring[0]), 128, 1024);
+      const uint64_t ones1_desc = umma::sdesc(umma::smem_u32(s.ONES[0]), 128, 256);
+      const uint64_t ones2_desc = umma::sdesc(umma::smem_u32(s.ONES[1]), 128, 256);
+      const uint64_t bias_desc = umma::sdesc(umma::smem_u32(s.BIAS), 128, 256);
       const uint32_t idesc1 = umma::idesc_bf16(TM, HID);
       const uint32_t idesc3 = umma::idesc_bf16(TM, NP3);
-      const uint32_t total_chunks = (uint32_t)my_tiles * 8;  // 4 of W2 then 4 of W3 per tile
-      uint32_t u_issue = 0, u_use = 0;
+      uint32_t u_use = 0;
       bool ok = true;
-      // weight chunk u: W2 chunk u % 8 for u % 8 < 4, else W3 chunk in the order layer 3 uses them
-      auto issue_copy = [&](uint32_t u) {
-        const int b = u % NRING;
-        const int c = u % 8;
-        if (c < 4) {
-          umma::mbar_arrive_expect_tx(&s.full[b], w2_bytes);
-          umma::bulk_g2s(s.ring[b], w2c + (size_t)c * (HID * 64), w2_bytes, &s.full[b]);
-        } else {
-          const int c3 = 7 - c;  // layer 3 takes its K chunks 3, 2, 1, 0
-          umma::mbar_arrive_expect_tx(&s.full[b], w3_bytes);
-          umma::bulk_g2s(s.ring[b], w3c + (size_t)c3 * (NP3 * 64), w3_bytes, &s.full[b]);
-        }
-      };
-      // issue every copy whose ring slot is already free (no waiting)
-      auto top_up = [&]() {
-        while (u_issue < total_chunks && u_issue < u_use + NRING) {
-          if (u_issue >= NRING && !umma::mbar_test(&s.empty[u_issue % NRING], ((u_issue / NRING) - 1) & 1)) break;
-          issue_copy(u_issue++);
-        }
-      };
-      // make sure chunk u has been issued (waiting for its slot if needed)
-      auto ensure = [&](uint32_t u) {
-        while (ok && u_issue <= u) {
-          if (u_issue >= NRING &&
-              !umma::mbar_wait(&s.empty[u_issue % NRING], ((u_issue / NRING) - 1) & 1, kWaitNs)) {
-            ok = false;
-            break;
-          }
-          issue_copy(u_issue++);
-        }
-      };
       // MMAs of one 64-wide K chunk (weight chunk u in the ring, H chunk c)
       auto chunk_mmas = [&](uint32_t u, int c, uint32_t d, uint32_t id, bool first) {
-        ensure(u);
         const int b = u % NRING;
-        if (!ok || !umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
+        if (!umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
           ok = false;
           return;
         }
@@ -257,11 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, !(first && ks == 0));
         umma::mma_commit(&s.empty[b]);
-        top_up();
       };
-      umma::mbar_arrive_expect_tx(&s.w1_full, HID * KX * 2);
-      umma::bulk_g2s(s.W1, w1t, HID * KX * 2, &s.w1_full);
-      top_up();
       if (my_tiles > 0 && !umma::mbar_wait(&s.w1_full, 0, kWaitNs)) ok = false;
       for (int t = 0; t < my_tiles && ok; ++t) {
         // layer 1: X of this tile written by the loader; TMEM A free since the previous
@@ -273,14 +248,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         umma::fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < KX / 16; ++ks) umma::mma_bf16(tmem, x_desc + 16 * ks, w1_desc + 16 * ks, idesc1, ks != 0);
+        umma::mma_bf16(tmem, ones1_desc, bias_desc, idesc1, 1);  // + b1
         umma::mma_commit(&s.l1_done);
-        // layer 2 on the first epilogue's chunks (h_ready completion 2t)
+        // layer 2 on the first epilogue's chunks (h_ready completion 2t); TMEM B is free once
+        // chunk 0 has arrived (the epilogues finished the previous tile before this one)
         for (int c = 0; c < 4 && ok; ++c) {
           if (!umma::mbar_wait(&s.h_ready[c], 0, kWaitNs)) {
             ok = false;
             break;
           }
-          chunk_mmas(u_use++, c, tmem + 256, idesc1, c == 0);
+          if (c == 0) {
+            umma::fence_after_sync();
+            umma::mma_bf16(tmem + 256, ones2_desc, bias_desc, idesc1, 0);  // accumulator = b2
+          }
+          chunk_mmas(u_use++, c, tmem + 256, idesc1, false);
         }
         if (!ok) break;
         umma::mma_commit(&s.l2_done);
@@ -305,9 +286,50 @@ __global__ void __launch_bounds__(THREADS, 1)
         s.abort = 1;
         atomicExch(err, 2);
       }
-      // outstanding copies and MMAs finish before the CTA exits (bounded)
-      for (uint32_t u = u_use; u < u_issue; ++u) umma::mbar_wait(&s.full[u % NRING], (u / NRING) & 1, kWaitNs);
+      // the MMAs finish before the CTA exits (bounded)
       if (u_use > 0) umma::mbar_wait(&s.empty[(u_use - 1) % NRING], ((u_use - 1) / NRING) & 1, kWaitNs);
+    }
+  } else if (warp == COPY_WARP) {
+    // ------------------------------------------------------------ weight copies
+    if (lane == 0 && my_tiles > 0) {
+      const uint32_t w3_bytes = (uint32_t)(NP3 * 64 * 2);
+      const uint32_t total = (uint32_t)my_tiles * 8;  // 4 chunks of W2 then 4 of W3 per tile
+      umma::mbar_arrive_expect_tx(&s.w1_full, HID * KX * 2 + BIAS_BYTES);
+      umma::bulk_g2s(s.W1, w1t, HID * KX * 2, &s.w1_full);
+      umma::bulk_g2s(s.BIAS, bias, BIAS_BYTES, &s.w1_full);
+      uint32_t u = 0;
+      for (; u < total; ++u) {
+        const int b = u % NRING;
+        if (u >= NRING) {
+          // the slot is free once the MMAs of chunk u - NRING have completed; stop early if the
+          // MMA warp has given up
+          const uint64_t t0 = umma::global_ns();
+          bool got = false;
+          while (!(got = umma::mbar_ready(&s.empty[b], ((u / NRING) - 1) & 1))) {
+            if (*reinterpret_cast<volatile int*>(&s.abort)) break;
+            if (umma::global_ns() - t0 > kWaitNs) {
+              s.abort = 1;
+              atomicExch(err, 2);
+              break;
+            }
+          }
+          if (!got) break;
+        }
+        // chunk u: W2 chunk u % 8 for u % 8 < 4, else W3 chunk 7 - u % 8 (layer 3 takes its K chunks 3, 2, 1, 0)
+        const int c = u % 8;
+        if (c < 4) {
+          umma::mbar_arrive_expect_tx(&s.full[b], CHUNK_BYTES);
+          umma::bulk_g2s(s.ring[b], w2c + (size_t)c * (HID * 64), CHUNK_BYTES, &s.full[b]);
+        } else {
+          umma::mbar_arrive_expect_tx(&s.full[b], w3_bytes);
+          umma::bulk_g2s(s.ring[b], w3c + (size_t)(7 - c) * (NP3 * 64), w3_bytes, &s.full[b]);
+        }
+      }
+      // every issued copy lands before the CTA exits (bounded): copies before u - NRING were
+      // consumed by the MMA warp before their slots were reissued
+      for (uint32_t v = u > NRING ? u - NRING : 0; v < u; ++v)
+        umma::mbar_wait(&s.full[v % NRING], (v / NRING) & 1, kWaitNs);
+      umma::mbar_wait(&s.w1_full, 0, kWaitNs);
     }
   } else if (warp == LOADER_WARP) {
     // ------------------------------------------------------------ loader: fields -> X (bf16, K-major)
@@ -354,10 +376,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int p0 = tile * TM;
       if (!umma::mbar_wait_backoff(&s.l1_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
-      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, s.b1, false);
+      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, false);
       if (!umma::mbar_wait_backoff(&s.l2_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
-      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, s.b2, true);
+      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, true);
       if (!umma::mbar_wait_backoff(&s.l3_done, t & 1, kWaitNs)) s.abort = 1;
       umma::fence_after_sync();
       // outputs: TMEM [384, 384 + NP3) -> FP32 rows of stride KS in the staging area (H is free now)
@@ -429,8 +451,8 @@ __global__ void k_pack_w1(const float* __restrict__ W1t, const float* __restrict
   out[kmajor_off(n, j, KX / 8) / 2] = __float2bfloat16_rn(v);
 }
 
-// W[n][k] (given transposed: Wt[k * ncols + n]) -> chunks [kc][n/8][k%64/8][8][8] for n < nrows_pad
-__global__ void k_pack_chunks(const float* __restrict__ Wt, int nrows, int nrows_pad, int ncols_t,
+// scale W[n][k] (given transposed: Wt[k * ncols + n]) -> chunks [kc][n/8][k%64/8][8][8] for n < nrows_pad
+__global__ void k_pack_chunks(const float* __restrict__ Wt, int nrows, int nrows_pad, int ncols_t, float scale,
                               __nv_bfloat16* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 4 chunks x nrows_pad x 64
   if (i >= 4 * nrows_pad * 64) return;
@@ -438,8 +460,24 @@ __global__ void k_pack_chunks(const float* __restrict__ Wt, int nrows, int nrows
   const int rem = i - kc * nrows_pad * 64;
   const int n = rem / 64, kk = rem - n * 64;
   const int k = kc * 64 + kk;
-  const float v = n < nrows ? Wt[(size_t)k * ncols_t + n] : 0.f;
+  const float v = n < nrows ? Wt[(size_t)k * ncols_t + n] * scale : 0.f;
   out[(size_t)kc * nrows_pad * 64 + kmajor_off(n, kk, 8) / 2] = __float2bfloat16_rn(v);
+}
+
+// hidden biases -> the 256 x 16 K-major B operand of the bias MMAs: K columns 0, 1 hold
+// b1 = hi + lo (hi = bf16(b1), lo = bf16(b1 - hi)), columns 2, 3 the same split of b2
+__global__ void k_pack_bias(const float* __restrict__ b1, const float* __restrict__ b2,
+                            __nv_bfloat16* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 256 x 16
+  if (i >= HID * 16) return;
+  const int n = i / 16, k = i % 16;
+  float v = 0.f;
+  if (k < 4) {
+    const float b = k < 2 ? b1[n] : b2[n];
+    const float hi = __bfloat162float(__float2bfloat16_rn(b));
+    v = (k & 1) ? b - hi : hi;
+  }
+  out[kmajor_off(n, k, 2) / 2] = __float2bfloat16_rn(v);
 }
 
 __global__ void k_out_affine(const float* __restrict__ b3, const float* __restrict__ sc,
@@ -457,12 +495,15 @@ int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st) {
   if (!p->tc_w1 && (cudaMalloc((void**)&p->tc_w1, HID * KX * sizeof(__nv_bfloat16)) != cudaSuccess ||
                     cudaMalloc((void**)&p->tc_w2, 4 * HID * 64 * sizeof(__nv_bfloat16)) != cudaSuccess ||
                     cudaMalloc((void**)&p->tc_w3, 4 * 128 * 64 * sizeof(__nv_bfloat16)) != cudaSuccess ||
-                    cudaMalloc((void**)&p->tc_c3, 128 * sizeof(float)) != cudaSuccess))
+                    cudaMalloc((void**)&p->tc_c3, 128 * sizeof(float)) != cudaSuccess ||
+                    cudaMalloc((void**)&p->tc_bias, HID * 16 * sizeof(__nv_bfloat16)) != cudaSuccess))
     return DFP2S_ENOMEM;
   // the SIMT layout keeps W1, W2, W3 transposed: W1t (J x 256), W2t (256 x 256), W3t (256 x K)
   k_pack_w1<<<(HID * KX + 255) / 256, 256, 0, st>>>(p->W1, p->in_scale, p->J, p->tc_w1);
-  k_pack_chunks<<<(4 * HID * 64 + 255) / 256, 256, 0, st>>>(p->W2, HID, HID, HID, p->tc_w2);
-  k_pack_chunks<<<(4 * NP3 * 64 + 255) / 256, 256, 0, st>>>(p->W3, K, NP3, K, p->tc_w3);
+  // the hidden layers store 2 GELU: the weights that read them are halved (exact in bfloat16)
+  k_pack_chunks<<<(4 * HID * 64 + 255) / 256, 256, 0, st>>>(p->W2, HID, HID, HID, 0.5f, p->tc_w2);
+  k_pack_chunks<<<(4 * NP3 * 64 + 255) / 256, 256, 0, st>>>(p->W3, K, NP3, K, 0.5f, p->tc_w3);
+  k_pack_bias<<<HID * 16 / 256, 256, 0, st>>>(p->b1, p->b2, p->tc_bias);
   k_out_affine<<<1, 128, 0, st>>>(p->b3, p->out_scale, p->out_shift, K, p->tc_c3);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
@@ -487,10 +528,11 @@ int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, v
   cudaFuncSetAttribute(k_mlp_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_mlp_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (w_dtype == DFP2S_W_BF16)
-    k_mlp_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3, p->b1,
-                                                      p->b2, p->tc_c3, p->out_scale, (__nv_bfloat16*)w, KS, 0, p->err);
+    k_mlp_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3,
+                                                      p->tc_bias, p->tc_c3, p->out_scale, (__nv_bfloat16*)w, KS, 0,
+                                                      p->err);
   else
-    k_mlp_tc<float><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3, p->b1, p->b2,
+    k_mlp_tc<float><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3, p->tc_bias,
                                               p->tc_c3, p->out_scale, (float*)w, KS, vec_out, p->err);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
