@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_rowfft_noise(float2* __r
 #pragma unroll
     for (int c = 0; c < V / 4; ++c) {
       const int i = t + T * c;
-      *reinterpret_cast<float4*>(bf + 4 * i) = dfp2s_gauss4(seed, sub, qa + i);
-      *reinterpret_cast<float4*>(bf + N + 4 * i) = dfp2s_gauss4(seed, sub, qb + i);
+      *reinterpret_cast<float4*>(bf + 4 * i) = dfp2s_gauss4_fast(seed, sub, qa + i);
+      *reinterpret_cast<float4*>(bf + N + 4 * i) = dfp2s_gauss4_fast(seed, sub, qb + i);
     }
   }
   fftr::group_sync<T>();
