@@ -320,12 +320,13 @@ def run_ours(args, rank, world, device):
         byt = 4.0 * npix * (2 + 2 * C)  # tilt fields a2, a3 and the image in, the warped image out
         roof = {"kernel": "k_tilt_warp", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
-    # the field sampler's four launches as one HBM-bound stage: spectrum written and read (16 J N (N/2+1)),
-    # multiplier (4 J N (N/2+1)), cropped columns written and read (16 J H (N/2+1)), fields and mixing (12 J H W)
+    # the field sampler's three launches as one HBM-bound stage: multiplier read (4 J N (N/2+1)), cropped
+    # columns written and read (16 J H (N/2+1)), fields written, then read and written by the mixing (12 J H W);
+    # the noise is made in registers
     N = S["N"]
     half = N // 2 + 1
-    fbytes = 16.0 * J * N * half + 16.0 * J * H * half + 4.0 * J * npix + 4.0 * J * N * half + 8.0 * J * npix
-    fields_roof = {"kernels": "k_rowfft_noise + k_colfilter + k_rowifft + k_mix", "bound": "hbm",
+    fbytes = 4.0 * J * N * half + 16.0 * J * H * half + 12.0 * J * npix
+    fields_roof = {"kernels": "k_colgen + k_rowifft + k_mix", "bound": "hbm",
                    "achieved": fbytes / (mean_stage[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     fields_roof["frac"] = fields_roof["achieved"] / fields_roof["peak"]
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -344,7 +345,7 @@ def run_ours(args, rank, world, device):
         "fields_roofline": fields_roof,
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
-        "gpu_launches": args.steps * 7,  # 4 field launches, warp (+operand), P2S, blur
+        "gpu_launches": args.steps * 6,  # 3 field launches, warp (+operand), P2S, blur
         "other_p2s": other_line,
         "cufft_fields_comparison": cufft,
         "setup": S["info"],
@@ -377,8 +378,8 @@ def run_reference_sample(args):
 
     def one():
         t0 = time.perf_counter()
-        e = np.stack([onoise.gaussian_block(0, 0, 0, j, N, N) for j in range(m_modes)])
-        u = osampler.unit_fields(e, lam[:m_modes])[:, :H, :W]
+        E = onoise.field_spectral_noise(0, 0, m_modes, N)
+        u = osampler.unit_fields_spectral(E, lam[:m_modes])[:, :H, :W]
         t_fields = (time.perf_counter() - t0) * J / m_modes
         t1 = time.perf_counter()
         a = np.zeros((J, tile, tile))

@@ -20,6 +20,17 @@ R8  word w -> u = (2 (w >> 9) + 1) 2^-24, an odd multiple of 2^-24 in (0, 1)
     quadrant taken exactly from the integer (w >> 9) plus Taylor series of
     sin and cos of (pi/2) r on r in [-1/2, 1/2].  Every step is one IEEE FP32
     operation (no fused multiply-add) in a fixed order.
+R27 The field sampler takes its white noise in the Fourier domain.  For real
+    e ~ N(0, I) on the N x N torus, E = FFT2(e) is Hermitian (E(-k) = conj E(k))
+    with independent components: Re and Im of each conjugate pair N(0, N^2 / 2),
+    and the four self-conjugate bins (kx, ky in {0, N/2}) real N(0, N^2).  The
+    sampler draws such an E directly, which has exactly the distribution of
+    FFT2(e), so y = F^-1(S^1/2 E) is the method of Sec. III-A without the forward
+    transform.  Mode j's Gaussians form rows kx = 0 .. N/2 of 2N values,
+    (Re, Im) of E(kx, ky) at columns 2 ky, 2 ky + 1 (counter q = (kx N + ky) / 2
+    for ky even; the R7 layout with y = kx and row length 2N).  In columns
+    kx = 0 and N/2, E(kx, ky) for ky > N/2 is the conjugate of E(kx, N - ky), and
+    at ky = 0, N/2 only the real Gaussian is used, scaled to variance N^2.
 """
 from __future__ import annotations
 
@@ -179,3 +190,27 @@ def gaussian_block(seed: int, tag: int, frame: int, mode: int, rows: int, cols: 
 def field_noise(seed: int, frame: int, J: int, N: int) -> np.ndarray:
     """White noise for the J fields on the N x N grid, shape (J, N, N) FP32 (tag 0)."""
     return np.stack([gaussian_block(seed, TAG_FIELDS, frame, j, N, N) for j in range(J)])
+
+
+def hermitian_spectrum(g: np.ndarray, N: int) -> np.ndarray:
+    """Full N x N Fourier-domain white noise E[ky, kx] (FP64 complex) from the Gaussian rows of one mode,
+    g[kx, 2 ky + c], kx = 0..N/2, c = 0 (Re) / 1 (Im) (R27)."""
+    g = np.asarray(g, dtype=np.float64).reshape(N // 2 + 1, N, 2)
+    half = (g[..., 0] + 1j * g[..., 1]) * (N / math.sqrt(2.0))  # half[kx, ky]
+    for kx in (0, N // 2):
+        for ky in range(N // 2 + 1, N):
+            half[kx, ky] = np.conj(half[kx, N - ky])
+        for ky in (0, N // 2):
+            half[kx, ky] = N * g[kx, ky, 0]
+    E = np.empty((N, N), dtype=np.complex128)
+    E[:, : N // 2 + 1] = half.T
+    kx = np.arange(N // 2 + 1, N)
+    ky = np.arange(N)
+    E[:, N // 2 + 1:] = np.conj(half[(N - kx)[None, :], ((N - ky) % N)[:, None]])  # E(-k) = conj E(k)
+    return E
+
+
+def field_spectral_noise(seed: int, frame: int, J: int, N: int) -> np.ndarray:
+    """Fourier-domain white noise of the J fields, shape (J, N, N) complex, indexed [j, ky, kx] (tag 0, R27)."""
+    return np.stack([hermitian_spectrum(gaussian_block(seed, TAG_FIELDS, frame, j, N // 2 + 1, 2 * N), N)
+                     for j in range(J)])

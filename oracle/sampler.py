@@ -3,6 +3,8 @@
 Test infrastructure only (see the package docstring).
 
 Sec. III-A: for a homogeneous (circulant) covariance, y = F^{-1}(S^{1/2} F(e)).
+The sampler draws F(e) directly as Hermitian Fourier-domain white noise
+(reading R27 in noise.py), which has the same distribution.
 Sec. III-C: step 1 draws N unit-variance fields, each from its own
 autocovariance A_{i,i} with that Fourier method; step 2 mixes them pixel by
 pixel with the Noll matrix through L L^T = A_0 (Cholesky, Fig. rand_gen), so
@@ -30,6 +32,11 @@ def unit_fields(e: np.ndarray, lam: np.ndarray) -> np.ndarray:
     return np.real(np.fft.ifft2(np.sqrt(lam) * np.fft.fft2(e, axes=(-2, -1)), axes=(-2, -1)))
 
 
+def unit_fields_spectral(E: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """Step 1 of Sec. III-C from Fourier-domain noise: a~_j = Re IFFT2(sqrt(lambda_j) E_j), FP64, full torus."""
+    return np.real(np.fft.ifft2(np.sqrt(lam) * E, axes=(-2, -1)))
+
+
 def mix(L: np.ndarray, fields: np.ndarray) -> np.ndarray:
     """Step 2 of Sec. III-C: a(x) = L a~(x) at every pixel."""
     return np.einsum("ij,jyx->iyx", L, fields)
@@ -40,9 +47,9 @@ def sample_fields(seed: int, frame: int, J: int, H: int, W: int, D_over_r0: floa
     """The J x H x W Zernike fields of one frame (factored form, the paper's method)."""
     if N is None:
         N = grid_size(H, W, pix_per_D)
-    e = noise.field_noise(seed, frame, J, N)
+    E = noise.field_spectral_noise(seed, frame, J, N)
     lam = spectrum.lambdas(J, N, pix_per_D)
-    a_unit = unit_fields(e, lam)[:, :H, :W]
+    a_unit = unit_fields_spectral(E, lam)[:, :H, :W]
     return mix(zernike.noll_cholesky(J, D_over_r0), a_unit)
 
 
@@ -52,7 +59,8 @@ def sample_fields_ar1(seed: int, frames: int, alpha: float, J: int, H: int, W: i
 
     The paper enforces temporal correlation by an auto-regressive process; here the white noise of every
     mode and torus position follows e_0 = n_0, e_t = alpha e_{t-1} + sqrt(1 - alpha^2) n_t, n_t the noise
-    of frame t, and each frame's fields are the FFT sampler applied to e_t.  Returns frames 0..frames-1.
+    of frame t, and each frame's fields are the FFT sampler applied to e_t.  The recursion is taken on the
+    Fourier-domain noise (R27), which is the same linear recursion on F(e).  Returns frames 0..frames-1.
     """
     if N is None:
         N = grid_size(H, W, pix_per_D)
@@ -61,9 +69,9 @@ def sample_fields_ar1(seed: int, frames: int, alpha: float, J: int, H: int, W: i
     beta = np.sqrt(1.0 - alpha * alpha)
     out, e = [], None
     for t in range(frames):
-        n = noise.field_noise(seed, t, J, N).astype(np.float64)
+        n = noise.field_spectral_noise(seed, t, J, N)
         e = n if e is None else alpha * e + beta * n
-        out.append(mix(L, unit_fields(e, lam)[:, :H, :W]))
+        out.append(mix(L, unit_fields_spectral(e, lam)[:, :H, :W]))
     return out
 
 
@@ -83,16 +91,15 @@ def dense_root(lam: np.ndarray, L: np.ndarray) -> np.ndarray:
 
 def sample_fields_dense(seed: int, frame: int, J: int, H: int, W: int, D_over_r0: float,
                         pix_per_D: float = 8.0, N: int | None = None) -> np.ndarray:
-    """Fields from the per-frequency J x J symmetric root: a = Re IFFT2(F(f) FFT2(e)), cropped.
+    """Fields from the per-frequency J x J symmetric root: a = Re IFFT2(F(f) E), E the Fourier-domain noise, cropped.
 
     Same covariance as sample_fields, different samples (reading R6).
     """
     if N is None:
         N = grid_size(H, W, pix_per_D)
-    e = noise.field_noise(seed, frame, J, N).astype(np.float64)
+    E = noise.field_spectral_noise(seed, frame, J, N)
     lam = spectrum.lambdas(J, N, pix_per_D)
     Fr = dense_root(lam, zernike.noll_cholesky(J, D_over_r0))
-    E = np.fft.fft2(e, axes=(1, 2))
     Y = np.einsum("yxij,jyx->iyx", Fr, E)
     return np.real(np.fft.ifft2(Y, axes=(1, 2)))[:, :H, :W]
 

@@ -117,40 +117,6 @@ DFP2S_DEV float4 dfp2s_gauss4(uint64_t seed, uint64_t sub, uint64_t q) {
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// The same two samples with the hardware approximations (lg2.approx, sqrt.approx,
-// sin.approx, cos.approx) in place of the correctly rounded sequence above: a
-// fraction of the instructions, each sample within a few 1e-7 of dfp2s_box_muller
-// (the angle error of sin/cos.approx, about 2^-21 absolute, times r <= 5.8).  Both
-// uniforms come from the mantissa bits without an integer conversion:
-// (1 + k 2^-23) - (1 - 2^-24) = (2k + 1) 2^-24 exactly (Sterbenz), and the angle
-// 2 pi (u - 1/2) = 2 pi ((1 + k 2^-23) - 3/2) + pi 2^-23 lies in (-pi, pi), so cos
-// and sin change sign.
-DFP2S_DEV float approx_lg2(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-DFP2S_DEV float approx_sqrt(float x) {
-  float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-DFP2S_DEV float2 dfp2s_box_muller_fast(uint32_t wa, uint32_t wb) {
-  const float ua = __uint_as_float(0x3F800000u | (wa >> 9)) - 0x1.fffffep-1f;
-  const float vb = __uint_as_float(0x3F800000u | (wb >> 9)) - 1.5f;
-  const float r = approx_sqrt(approx_lg2(ua) * -0x1.62e43p+0f);  // -2 ln u = -2 ln2 log2 u
-  float s, c;
-  __sincosf(fmaf(vb, 0x1.921fb6p+2f, 0x1.921fb6p-22f), &s, &c);  // 2 pi vb + pi 2^-23
-  return make_float2(-r * c, -r * s);
-}
-
-DFP2S_DEV float4 dfp2s_gauss4_fast(uint64_t seed, uint64_t sub, uint64_t q) {
-  const uint4 w = philox_at(seed, sub, q);
-  const float2 a = dfp2s_box_muller_fast(w.x, w.y);
-  const float2 b = dfp2s_box_muller_fast(w.z, w.w);
-  return make_float4(a.x, a.y, b.x, b.y);
-}
-
 DFP2S_DEV uint64_t dfp2s_subsequence(uint32_t tag, uint32_t frame, uint32_t mode) {
   return ((uint64_t)tag << 40) | ((uint64_t)frame << 8) | (uint64_t)mode;
 }

@@ -2,19 +2,19 @@
 // 2-D FFT per mode -> multiply by the per-mode spectral factor -> inverse FFT
 // -> crop -> pixel-wise mixing by L.
 //
-// Three passes over a per-factor scratch spectrum S[j][kx][y] (complex FP32,
-// kx in [0, N/2], y in [0, N); a frequency column is contiguous), each FFT
-// done in registers by a group of threads (fft_reg.cuh):
-//   k_rowfft_noise  Philox noise for two real rows, packed as one complex row
-//                   z = a + i b, forward FFT, split into the two half spectra;
-//                   a block of G groups covers 2G consecutive rows and writes
-//                   them through a shared-memory tile, 16 G bytes per column;
-//   k_colfilter     one column per group: forward FFT, multiply by
-//                   sqrt(lambda_j)/N^2, inverse FFT straight from the forward
-//                   FFT's register layout, keep rows y < H (in place);
-//   k_rowifft       2G rows per block read through a tile; per row pair the
-//                   Hermitian completion of Ga + i Gb, inverse FFT, rows to the
-//                   fields, cropped to W;
+// The white noise is drawn in the Fourier domain: E = FFT2(e) of real white
+// noise e is Hermitian white noise (variance N^2 per bin, N^2/2 per real and
+// imaginary part off the four self-conjugate bins), so the sampler draws E from
+// Philox directly (same distribution, no forward transform).  Two passes over a
+// per-factor scratch spectrum S[j][kx][y] (complex FP32, kx in [0, N/2], rows
+// y < H; a frequency column is contiguous), each FFT done in registers by a
+// group of threads (fft_reg.cuh):
+//   k_colgen   one column kx per group: Philox noise E(kx, .), Hermitian in ky
+//              for kx = 0 and N/2, times sqrt(lambda_j)/N^2, inverse FFT over ky,
+//              rows y < H;
+//   k_rowifft  2G rows per block read through a tile; per row pair the
+//              Hermitian completion of Ga + i Gb over kx, inverse FFT, rows to
+//              the fields, cropped to W;
 // and k_mix applies a(x) = L a~(x) in place.
 #include <cuda_runtime.h>
 
@@ -41,80 +41,15 @@ struct Groups {
 };
 
 // -------------------------------------------------------------- pass 1
+// One frequency column kx of mode j per group.  The column's Fourier-domain white noise E(kx, ky)
+// (Re, Im = Gaussians 2 (kx N + ky) + {0, 1}; one Philox block covers ky = 2i, 2i + 1) is staged in
+// shared memory in natural order; columns kx = 0 and N/2 are made Hermitian in ky (E(kx, N - ky) =
+// conj E(kx, ky), real at ky = 0 and N/2 with variance N^2).  Then E (N / sqrt 2) sqrt(lambda_j) / N^2,
+// the inverse FFT over ky, and the rows y < H to S[j][kx][y].
 template <int N>
-__global__ void __launch_bounds__(Groups<N>::THREADS) k_rowfft_noise(float2* __restrict__ S,
-                                                                     const float2* __restrict__ tw, uint64_t seed,
-                                                                     uint32_t frame) {
-  using P = Plan<N>;
-  using GR = Groups<N>;
-  constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
-  extern __shared__ __align__(16) float2 smem[];
-  const int g = threadIdx.x / T;
-  const int t = threadIdx.x - g * T;
-  const int j = blockIdx.y;
-  const int y0 = blockIdx.x * 2 * G;
-  const int ya = y0 + 2 * g, yb = ya + 1;
-  float2* buf = smem + g * GR::BUFE;
-  const uint64_t sub = dfp2s_subsequence(0u, frame, (uint32_t)j);
-  {
-    // noise: chunk i of a row is positions 4i..4i+3 (one Philox block); staged as two float rows
-    float* bf = reinterpret_cast<float*>(buf);
-    const uint64_t qa = ((uint64_t)ya * N) >> 2, qb = ((uint64_t)yb * N) >> 2;
-#pragma unroll
-    for (int c = 0; c < V / 4; ++c) {
-      const int i = t + T * c;
-      *reinterpret_cast<float4*>(bf + 4 * i) = dfp2s_gauss4_fast(seed, sub, qa + i);
-      *reinterpret_cast<float4*>(bf + N + 4 * i) = dfp2s_gauss4_fast(seed, sub, qb + i);
-    }
-  }
-  fftr::group_sync<T>();
-  float2 v[V];
-  {
-    const float* bf = reinterpret_cast<const float*>(buf);
-#pragma unroll
-    for (int m = 0; m < V; ++m) v[m] = make_float2(bf[t + T * m], bf[N + t + T * m]);
-  }
-  fftr::group_sync<T>();
-  fftr::fft<N, false>(v, buf, t, tw);
-  // Z in natural order, then split Z = X_a + i X_b:
-  //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
-  fftr::group_sync<T>();
-#pragma unroll
-  for (int m = 0; m < V; ++m) buf[pad32(t + T * m)] = v[OutIndex<N>::reg(m)];
-  fftr::group_sync<T>();
-  constexpr int NK = V / 2 + 1;  // k = t + T m for m < V / 2, and k = N / 2 on thread 0
-  float2 xa[NK], xb[NK];
-#pragma unroll
-  for (int m = 0; m < NK; ++m) {
-    const int k = t + T * m;
-    if (m < V / 2 || t == 0) {
-      const float2 zk = buf[pad32(k)];
-      const float2 zn = buf[pad32((N - k) & (N - 1))];
-      xa[m] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-      xb[m] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
-    }
-  }
-  __syncthreads();  // the tile overlays every group's buffer
-#pragma unroll
-  for (int m = 0; m < NK; ++m) {
-    const int k = t + T * m;
-    if (m < V / 2 || t == 0) {
-      smem[k * GR::TS + 2 * g] = xa[m];
-      smem[k * GR::TS + 2 * g + 1] = xb[m];
-    }
-  }
-  __syncthreads();
-  float2* Sj = S + (size_t)j * HALF * N;
-  for (int i = threadIdx.x; i < HALF * 2 * G; i += GR::THREADS) {
-    const int k = i / (2 * G), r = i - k * (2 * G);
-    Sj[(size_t)k * N + y0 + r] = smem[k * GR::TS + r];
-  }
-}
-
-// -------------------------------------------------------------- pass 2
-template <int N>
-__global__ void __launch_bounds__(Groups<N>::THREADS) k_colfilter(float2* __restrict__ S, const float* __restrict__ mult,
-                                                                  const float2* __restrict__ tw, int H) {
+__global__ void __launch_bounds__(Groups<N>::THREADS) k_colgen(float2* __restrict__ S, const float* __restrict__ mult,
+                                                               const float2* __restrict__ tw, int H, uint64_t seed,
+                                                               uint32_t frame, float cN) {
   using P = Plan<N>;
   using GR = Groups<N>;
   constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
@@ -125,30 +60,50 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_colfilter(float2* __rest
   const int kx = blockIdx.x * G + g;
   const bool live = kx < HALF;  // dead groups still join the block-wide exchanges when T > 32
   float2* buf = smem + g * GR::BUFE;
-  float2* col = S + ((size_t)j * HALF + (live ? kx : 0)) * N;
+  {
+    const uint64_t sub = dfp2s_subsequence(0u, frame, (uint32_t)j);
+    const uint64_t q0 = (uint64_t)(live ? kx : 0) * (N / 2);
+#pragma unroll
+    for (int c = 0; c < V / 2; ++c) {
+      const int i = t + T * c;
+      const float4 z = dfp2s_gauss4(seed, sub, q0 + i);
+      buf[pad32(2 * i)] = make_float2(z.x, z.y);
+      buf[pad32(2 * i + 1)] = make_float2(z.z, z.w);
+    }
+  }
+  fftr::group_sync<T>();
+  if (live && (kx == 0 || kx == N / 2)) {
+    // the upper half is written from the lower half only, and bins 0 and N/2 by thread 0 alone
+    for (int ky = N / 2 + 1 + t; ky < N; ky += T) {
+      const float2 e = buf[pad32(N - ky)];
+      buf[pad32(ky)] = make_float2(e.x, -e.y);
+    }
+    if (t == 0) {
+      buf[pad32(0)] = make_float2(buf[pad32(0)].x * 1.41421356237309505f, 0.f);
+      buf[pad32(N / 2)] = make_float2(buf[pad32(N / 2)].x * 1.41421356237309505f, 0.f);
+    }
+  }
+  fftr::group_sync<T>();
   const float* mc = mult + ((size_t)j * HALF + (live ? kx : 0)) * N;
   float2 v[V];
 #pragma unroll
-  for (int m = 0; m < V; ++m) v[m] = live ? col[t + T * m] : make_float2(0.f, 0.f);
-  fftr::fft<N, false>(v, buf, t, tw);
-  float2 u[V];
-#pragma unroll
   for (int m = 0; m < V; ++m) {
-    const float s = live ? __ldg(mc + t + T * m) : 0.f;
-    u[m] = cscale(v[OutIndex<N>::reg(m)], s);
+    const float s = live ? __ldg(mc + t + T * m) * cN : 0.f;
+    v[m] = cscale(buf[pad32(t + T * m)], s);
   }
-  fftr::group_sync<T>();
-  fftr::fft<N, true>(u, buf, t, tw);
+  fftr::group_sync<T>();  // the FFT reuses the buffer
+  fftr::fft<N, true>(v, buf, t, tw);
   if (live) {
+    float2* col = S + ((size_t)j * HALF + kx) * N;
 #pragma unroll
     for (int m = 0; m < V; ++m) {
       const int y = t + T * m;
-      if (y < H) col[y] = u[OutIndex<N>::reg(m)];
+      if (y < H) col[y] = v[OutIndex<N>::reg(m)];
     }
   }
 }
 
-// -------------------------------------------------------------- pass 3
+// -------------------------------------------------------------- pass 2
 template <int N>
 __global__ void __launch_bounds__(Groups<N>::THREADS) k_rowifft(const float2* __restrict__ S, float* __restrict__ out,
                                                                 const float2* __restrict__ tw, int H, int W) {
@@ -337,12 +292,11 @@ void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H,
   constexpr int G = GR::G, HALF = N / 2 + 1;
   const size_t sm = GR::smem;
   if (sm > 48 * 1024) {
-    cudaFuncSetAttribute(k_rowfft_noise<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_colfilter<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_colgen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
     cudaFuncSetAttribute(k_rowifft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   }
-  k_rowfft_noise<N><<<dim3(N / (2 * G), J), GR::THREADS, sm, st>>>(S, tw, seed, frame);
-  k_colfilter<N><<<dim3((HALF + G - 1) / G, J), GR::THREADS, sm, st>>>(S, mult, tw, H);
+  const float cN = (float)(N * 0.70710678118654752440);  // the noise scale N / sqrt 2
+  k_colgen<N><<<dim3((HALF + G - 1) / G, J), GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
   k_rowifft<N><<<dim3((H + 2 * G - 1) / (2 * G), J), GR::THREADS, sm, st>>>(S, fields, tw, H, W);
 }
 

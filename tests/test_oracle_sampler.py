@@ -47,6 +47,27 @@ def test_dense_root_operator_identity(small):
     assert np.allclose(M @ M.T, At, atol=1e-12 * np.abs(At).max())
 
 
+@pytest.mark.parametrize("N", [8, 16])
+def test_fourier_domain_noise_is_the_transform_of_white_noise(N):
+    # reading R27: the Gaussian rows g -> E (Hermitian) -> e = F^-1(E) is a linear map whose output is real
+    # and has identity covariance (M M^T = I), i.e. E has exactly the distribution of FFT2 of white noise
+    nz = 2 * (N // 2 + 1) * N
+    M = np.empty((N * N, nz))
+    for c in range(nz):
+        g = np.zeros(nz)
+        g[c] = 1.0
+        e = np.fft.ifft2(noise.hermitian_spectrum(g, N))
+        assert np.abs(e.imag).max() < 1e-15
+        M[:, c] = e.real.ravel()
+    assert np.allclose(M @ M.T, np.eye(N * N), atol=1e-13)
+    # the columns a conjugate or a self-conjugate bin ignores: (kx in {0, N/2}, ky > N/2) and the imaginary
+    # parts at (kx, ky) in {0, N/2}^2
+    unused = [2 * (kx * N + ky) + c for kx in (0, N // 2) for ky in range(N // 2 + 1, N) for c in (0, 1)]
+    unused += [2 * (kx * N + ky) + 1 for kx in (0, N // 2) for ky in (0, N // 2)]
+    assert np.all(M[:, unused] == 0.0)
+    assert np.count_nonzero(np.abs(M).sum(axis=0)) == N * N
+
+
 def test_zero_displacement_is_noll(small):
     lam, L, At = small
     n = N8 * N8
@@ -68,8 +89,8 @@ def test_statistics_of_philox_draws(small):
     seed = 11
     samples = np.empty((nf, J6 * N8 * N8))
     for f in range(nf):
-        e = noise.field_noise(seed, f, J6, N8)
-        samples[f] = sampler.mix(L, sampler.unit_fields(e, lam)).ravel()
+        E = noise.field_spectral_noise(seed, f, J6, N8)
+        samples[f] = sampler.mix(L, sampler.unit_fields_spectral(E, lam)).ravel()
     n = N8 * N8
     idx = np.array([j * n + p for j in range(J6) for p in (0, 1, 8, 27)])
     emp = samples[:, idx].T @ samples[:, idx] / nf
