@@ -47,9 +47,8 @@ struct Groups {
 // conj E(kx, ky), real at ky = 0 and N/2 with variance N^2).  Then E (N / sqrt 2) sqrt(lambda_j) / N^2,
 // the inverse FFT over ky, and the rows y < H to S[j][kx][y].
 template <int N>
-__global__ void __launch_bounds__(Groups<N>::THREADS) k_colgen(float2* __restrict__ S, const float* __restrict__ mult,
-                                                               const float2* __restrict__ tw, int H, uint64_t seed,
-                                                               uint32_t frame, float cN) {
+DFP2S_DEV void colgen_body(float2* __restrict__ S, const float* __restrict__ mult, const float2* __restrict__ tw, int H,
+                           uint64_t seed, uint32_t frame, float cN) {
   using P = Plan<N>;
   using GR = Groups<N>;
   constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
@@ -101,6 +100,21 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_colgen(float2* __restric
       if (y < H) col[y] = v[OutIndex<N>::reg(m)];
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Groups<N>::THREADS) k_colgen(float2* __restrict__ S, const float* __restrict__ mult,
+                                                               const float2* __restrict__ tw, int H, uint64_t seed,
+                                                               uint32_t frame, float cN) {
+  colgen_body<N>(S, mult, tw, H, seed, frame, cN);
+}
+// The same with three blocks per SM (80 registers): the noise phase is issue-bound, and the extra warps hide the
+// latencies of its dependent chains
+template <int N>
+__global__ void __launch_bounds__(Groups<N>::THREADS, 3) k_colgen3(float2* __restrict__ S, const float* __restrict__ mult,
+                                                                   const float2* __restrict__ tw, int H, uint64_t seed,
+                                                                   uint32_t frame, float cN) {
+  colgen_body<N>(S, mult, tw, H, seed, frame, cN);
 }
 
 // -------------------------------------------------------------- pass 2
@@ -292,11 +306,16 @@ void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H,
   constexpr int G = GR::G, HALF = N / 2 + 1;
   const size_t sm = GR::smem;
   if (sm > 48 * 1024) {
-    cudaFuncSetAttribute(k_colgen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
+    if constexpr (N == 1024)
+      cudaFuncSetAttribute(k_colgen3<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
+    else
+      cudaFuncSetAttribute(k_colgen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
     cudaFuncSetAttribute(k_rowifft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   }
   const float cN = (float)(N * 0.70710678118654752440);  // the noise scale N / sqrt 2
-  k_colgen<N><<<dim3((HALF + G - 1) / G, J), GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
+  const dim3 grid((HALF + G - 1) / G, J);
+  if constexpr (N == 1024) k_colgen3<N><<<grid, GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
+  else k_colgen<N><<<grid, GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
   k_rowifft<N><<<dim3((H + 2 * G - 1) / (2 * G), J), GR::THREADS, sm, st>>>(S, fields, tw, H, W);
 }
 
