@@ -152,42 +152,20 @@ def run_ours(args, rank, world, device):
     mode = d.P2S_LEARNED if args.mode == "learned" else d.P2S_EXACT
     wdt = d.W_F32
     stream = torch.cuda.current_stream()
-    fields = torch.empty(J, H, W, device=device)
-    warped = torch.empty(C, H, W, device=device)
-    w = torch.empty(H, W, K, device=device, dtype=torch.float32)
     out = torch.empty(C, H, W, device=device)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
-    nstage = 4
     seed_base = 1000 * rank
 
-    def step(i, ev=None):
+    def step(i):
+        # one frame through the library's frame call (the C ABI's dfp2s_simulate_frame); with stage timing on,
+        # it records CUDA events between the field, warp, P2S and blur stages on this stream
         dr = S["dlist"][i % len(S["dlist"])]
-        if ev is not None:
-            ev[0].record(stream)
-        d.sample_zernike_fields(S["factor"], dr, seed_base, i, H, W, out=fields)
-        if ev is not None:
-            ev[1].record(stream)
-        if mode == d.P2S_LEARNED:
-            # the warp fused with the tensor-core blur's operand; the contraction kernel is timed alone
-            d.tilt_warp_blur_tc_prepare(S["P"], S["img"], fields[0], fields[1])
-        else:
-            d.tilt_warp(S["img"], fields[0], fields[1], out=warped)
-        if ev is not None:
-            ev[2].record(stream)
-        d.p2s_weights(S["P"], mode, fields, w_dtype=wdt, out=w)
-        if ev is not None:
-            ev[3].record(stream)
-        if mode == d.P2S_LEARNED:
-            d.basis_blur_tc_run(S["P"], (C, H, W), w, out=out)
-        else:
-            d.basis_blur(S["P"], warped, w, out=out)
-        if ev is not None:
-            ev[4].record(stream)
+        S["sim"].simulate_frame(S["img"], dr, seed_base, i, mode, out=out, stream=stream)
 
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(nstage + 1)] for _ in range(args.steps)]
+    S["sim"].stage_timing(args.steps)
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -197,14 +175,14 @@ def run_ours(args, rank, world, device):
     t0 = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()  # evict L2 between timed frames (outside the events)
-        step(args.warmup + i, events[i])
+        step(args.warmup + i)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop() if clocks else None
-    stage_ms = np.array([[events[i][s].elapsed_time(events[i][s + 1]) for s in range(nstage)]
-                         for i in range(args.steps)])
+    stage_ms = S["sim"].stage_times(args.steps).astype(np.float64)
+    S["sim"].stage_timing(0)
     frame_ms = stage_ms.sum(axis=1)
     total_ms = float(frame_ms.sum())
     if world > 1:
@@ -277,7 +255,7 @@ def run_ours(args, rank, world, device):
     mean_stage = stage_ms.mean(axis=0)
     peaks, peak_kind = _peaks()
     # dominant kernel roofline: among the stages that are one kernel launch each (warp, P2S weights, blur
-    # contraction); the field stage is four launches, each shorter than the blur contraction (ncu launch list)
+    # contraction); the field stage is two or three launches, each shorter than the blur contraction (ncu list)
     single = [1, 2, 3]
     dom = single[int(np.argmax(mean_stage[single]))]
     npix = H * W
@@ -320,13 +298,14 @@ def run_ours(args, rank, world, device):
         byt = 4.0 * npix * (2 + 2 * C)  # tilt fields a2, a3 and the image in, the warped image out
         roof = {"kernel": "k_tilt_warp", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
-    # the field sampler's three launches as one HBM-bound stage: multiplier read (4 J N (N/2+1)), cropped
-    # columns written and read (16 J H (N/2+1)), fields written, then read and written by the mixing (12 J H W);
-    # the noise is made in registers
+    # the field sampler as one HBM-bound stage: multiplier read (4 J N (N/2+1)), cropped columns written and read
+    # (16 J H (N/2+1)), unit fields written (4 J H W) and, in exact frames, read and written by the mixing
+    # pass (8 J H W; learned frames fold the mixing into the warp and the network); the noise is made in registers
     N = S["N"]
     half = N // 2 + 1
-    fbytes = 4.0 * J * N * half + 16.0 * J * H * half + 12.0 * J * npix
-    fields_roof = {"kernels": "k_colgen + k_rowifft + k_mix", "bound": "hbm",
+    learned = args.mode == "learned"
+    fbytes = 4.0 * J * N * half + 16.0 * J * H * half + (4.0 if learned else 12.0) * J * npix
+    fields_roof = {"kernels": "k_colgen + k_rowifft" + ("" if learned else " + k_mix"), "bound": "hbm",
                    "achieved": fbytes / (mean_stage[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     fields_roof["frac"] = fields_roof["achieved"] / fields_roof["peak"]
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -345,7 +324,8 @@ def run_ours(args, rank, world, device):
         "fields_roofline": fields_roof,
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
-        "gpu_launches": args.steps * 6,  # 3 field launches, warp (+operand), P2S, blur
+        # field launches (noise + column IFFT, row IFFT, and the mixing in exact frames), warp, P2S, blur
+        "gpu_launches": args.steps * (5 if args.mode == "learned" else 6),
         "other_p2s": other_line,
         "cufft_fields_comparison": cufft,
         "setup": S["info"],

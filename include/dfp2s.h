@@ -315,14 +315,29 @@ int dfp2s_ctx_destroy(dfp2s_ctx* c);
  * (FP32) -> blur (p2s_mode EXACT: FP32 CUDA-core blur; LEARNED: the network's
  * weights and the BF16 tensor-core blur, with the warp fused into the blur's
  * operand, dfp2s_tilt_warp_blur_tc_prepare + dfp2s_basis_blur_tc_run) -> out
- * (C x H x W, device).
+ * (C x H x W, device).  LEARNED frames skip the pixel-wise mixing pass: the
+ * mixing a = (D/r0)^(5/6) L u is linear, so the warp forms the two tilt rows of
+ * a from the unit fields u0, u1 (bit for bit as the mixing pass would) and the
+ * network's first layer takes W1 diag(in_scale) L (packed once per installed
+ * network) on the scaled unit fields.
  * Errors: EINVAL, ECUDA. */
 int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img_dev, int C, int H, int W, double D_over_r0,
                          uint64_t seed, uint32_t frame, int p2s_mode, float* out_dev, void* stream);
 /* Device pointers of the context's last fields / warped image / weights
  * (valid until the next call on the context; LEARNED frames do not write the
- * FP32 warped image). */
+ * FP32 warped image, and leave the unit fields u before the mixing by
+ * (D/r0)^(5/6) L in fields_dev). */
 int dfp2s_ctx_buffers(const dfp2s_ctx* c, float** fields_dev, float** warped_dev, void** w_dev);
+/* Stage timing of dfp2s_simulate_frame.  n > 0: from now on every frame
+ * records five CUDA events on its stream (start, after the fields, after the
+ * warp, after the P2S weights, after the blur) into a ring of n frames; n = 0
+ * turns it off.  The context owns the events.  Errors: EINVAL, ECUDA. */
+int dfp2s_ctx_stage_timing(dfp2s_ctx* c, int n);
+/* Stage durations in ms of the last `count` recorded frames, oldest first:
+ * out_host[4 i + s] for stage s (fields, warp, P2S weights, blur) of frame i.
+ * Waits for those frames.  count <= n and <= the frames recorded since
+ * dfp2s_ctx_stage_timing.  Errors: EINVAL, ECUDA. */
+int dfp2s_ctx_stage_times(dfp2s_ctx* c, int count, float* out_host);
 
 #ifdef __cplusplus
 }

@@ -74,6 +74,8 @@ SIGNATURES = {
     "dfp2s_ctx_destroy": (_i, [_vp]),
     "dfp2s_simulate_frame": (_i, [_vp, _vp, _i, _i, _i, _d, _u64, _u32, _i, _vp, _vp]),
     "dfp2s_ctx_buffers": (_i, [_vp, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
+    "dfp2s_ctx_stage_timing": (_i, [_vp, _i]),
+    "dfp2s_ctx_stage_times": (_i, [_vp, _i, _vp]),
 }
 
 _LIB = None
@@ -413,6 +415,17 @@ class Simulator:
         f, wp, w = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         _check(load().dfp2s_ctx_buffers(self._h, ctypes.byref(f), ctypes.byref(wp), ctypes.byref(w)))
         return f.value, wp.value, w.value
+
+    def stage_timing(self, n: int) -> None:
+        """Record per-stage CUDA events for the next frames, in a ring of n (0: off)."""
+        _check(load().dfp2s_ctx_stage_timing(self._h, n))
+
+    def stage_times(self, count: int):
+        """(count, 4) ms of the last `count` frames: fields, warp, P2S weights, blur (waits for them)."""
+        import numpy as np
+        out = np.zeros((count, 4), dtype=np.float32)
+        _check(load().dfp2s_ctx_stage_times(self._h, count, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -301,6 +301,7 @@ int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* d, const float* W1, const float* b1, co
   if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core weight packing");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return dfp2s_fail_cuda(e, "tensor-core weight packing");
   d->has_mlp = 1;
+  ++d->mlp_version;
   return DFP2S_OK;
 }
 
@@ -448,7 +449,24 @@ struct dfp2s_ctx {
   float* fields;
   float* warped;
   void* w;
+  // learned frames: the first layer for unmixed fields, W1 diag(in_scale) L, and the network version it was
+  // packed for; the top-left 2 x 2 block of L (host copy) for the tilt rows
+  __nv_bfloat16* w1_mixed;
+  unsigned w1_mixed_version;
+  float l00, l10, l11;
+  // stage timing: a ring of nev frames x 5 events, frames recorded so far
+  cudaEvent_t* ev;
+  int nev;
+  unsigned long long frames;
 };
+
+static void ctx_free_events(dfp2s_ctx* c) {
+  for (int i = 0; i < 5 * c->nev; ++i) cudaEventDestroy(c->ev[i]);
+  delete[] c->ev;
+  c->ev = nullptr;
+  c->nev = 0;
+  c->frames = 0;
+}
 
 extern "C" int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int maxC, int maxH, int maxW,
                                 dfp2s_ctx** out) {
@@ -466,17 +484,31 @@ extern "C" int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int m
   c->fields = nullptr;
   c->warped = nullptr;
   c->w = nullptr;
+  c->w1_mixed = nullptr;
+  c->w1_mixed_version = 0;
+  c->ev = nullptr;
+  c->nev = 0;
+  c->frames = 0;
   const size_t npix = (size_t)maxH * maxW;
+  const int J = f->d.J;
+  float lt[4] = {1.f, 0.f, 0.f, 1.f};
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&c->fields, (size_t)f->d.J * npix * sizeof(float))) != cudaSuccess ||
+  if ((e = cudaMalloc((void**)&c->fields, (size_t)J * npix * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->warped, (size_t)maxC * npix * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&c->w, (size_t)p->d.K * npix * sizeof(float))) != cudaSuccess) {
+      (e = cudaMalloc(&c->w, (size_t)p->d.K * npix * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->w1_mixed, dfp2s_mlp_tc_w1_elems() * sizeof(__nv_bfloat16))) != cudaSuccess ||
+      (J >= 2 && ((e = cudaMemcpy(lt, f->d.L32, 2 * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+                  (e = cudaMemcpy(lt + 2, f->d.L32 + J, 2 * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess))) {
     cudaFree(c->fields);
     cudaFree(c->warped);
     cudaFree(c->w);
+    cudaFree(c->w1_mixed);
     delete c;
     return dfp2s_fail_cuda(e, "context allocation");
   }
+  c->l00 = lt[0];
+  c->l10 = lt[2];
+  c->l11 = lt[3];
   *out = c;
   return DFP2S_OK;
 }
@@ -486,7 +518,45 @@ extern "C" int dfp2s_ctx_destroy(dfp2s_ctx* c) {
   cudaFree(c->fields);
   cudaFree(c->warped);
   cudaFree(c->w);
+  cudaFree(c->w1_mixed);
+  ctx_free_events(c);
   delete c;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_ctx_stage_timing(dfp2s_ctx* c, int n) {
+  CHECK_ARG(c && n >= 0 && n <= 100000, "bad stage-timing request");
+  ctx_free_events(c);
+  if (n == 0) return DFP2S_OK;
+  c->ev = new cudaEvent_t[5 * (size_t)n]();
+  for (int i = 0; i < 5 * n; ++i) {
+    const cudaError_t e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(c->ev[k]);
+      delete[] c->ev;
+      c->ev = nullptr;
+      return dfp2s_fail_cuda(e, "stage-timing events");
+    }
+  }
+  c->nev = n;
+  c->frames = 0;
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_ctx_stage_times(dfp2s_ctx* c, int count, float* out) {
+  CHECK_ARG(c && out, "null argument");
+  CHECK_ARG(c->nev > 0 && count >= 1 && count <= c->nev && (unsigned long long)count <= c->frames,
+            "%d frames requested, %llu recorded in a ring of %d", count, c->frames, c->nev);
+  for (int i = 0; i < count; ++i) {
+    const unsigned long long fr = c->frames - (unsigned long long)count + (unsigned long long)i;
+    cudaEvent_t* e = c->ev + 5 * (size_t)(fr % (unsigned long long)c->nev);
+    cudaError_t r = cudaEventSynchronize(e[4]);
+    if (r != cudaSuccess) return dfp2s_fail_cuda(r, "stage-timing wait");
+    for (int s = 0; s < 4; ++s) {
+      r = cudaEventElapsedTime(out + 4 * (size_t)i + s, e[s], e[s + 1]);
+      if (r != cudaSuccess) return dfp2s_fail_cuda(r, "stage-timing read");
+    }
+  }
   return DFP2S_OK;
 }
 
@@ -506,21 +576,56 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
             "frame %dx%dx%d exceeds the context's %dx%dx%d", C, H, W, c->maxC, c->maxH, c->maxW);
   CHECK_ARG(p2s_mode == DFP2S_P2S_EXACT || p2s_mode == DFP2S_P2S_LEARNED || p2s_mode == DFP2S_P2S_LEARNED_FP32,
             "unknown P2S mode");
-  int rc = dfp2s_sample_zernike_fields(c->f, D_over_r0, seed, frame, H, W, c->fields, stream);
-  if (rc) return rc;
   const size_t npix = (size_t)H * W;
+  int rc;
+  // stage events (when enabled): start, fields, warp, P2S weights, blur
+  cudaEvent_t* ev = c->nev > 0 ? c->ev + 5 * (size_t)(c->frames % (unsigned long long)c->nev) : nullptr;
+  auto mark = [&](int s) {
+    if (ev) cudaEventRecord(ev[s], as_stream(stream));
+  };
+  mark(0);
   if (p2s_mode == DFP2S_P2S_LEARNED) {
-    // warp fused with the tensor-core blur's operand (the FP32 warped image is not needed)
-    rc = dfp2s_tilt_warp_blur_tc_prepare(c->p, img, C, H, W, c->fields, c->fields + npix, stream);
+    // The mixing a = scale L u of Sec. III-C is linear, so it moves into its two consumers: the warp forms the
+    // tilt rows of a from u0, u1 (in the mixing kernel's operation order, bit for bit), and the network's first
+    // layer takes W1 diag(in_scale) L with the fields scaled on loading.  The unit fields u stay in c->fields.
+    const dfp2s_p2s_dev* pd = &c->p->d;
+    CHECK_ARG(pd->has_mlp, "no surrogate network installed");
+    CHECK_ARG(pd->J <= 48 && pd->J >= 2, "the tensor-core surrogate takes 2 <= J <= 48 fields (J = %d)", pd->J);
+    CHECK_ARG(H <= c->f->d.N && W <= c->f->d.N && D_over_r0 >= 0 && D_over_r0 <= 1e4, "bad frame arguments");
+    cudaStream_t st = as_stream(stream);
+    const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+    CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
+                                            seed, frame, c->f->d.L32, scale, c->fields, st, nullptr, 0.f, false));
+    if (c->w1_mixed_version != pd->mlp_version) {
+      CHECK_LAUNCH(dfp2s_mlp_tc_pack_w1_mixed(pd, c->f->d.L32, c->w1_mixed, st));
+      c->w1_mixed_version = pd->mlp_version;
+    }
+    mark(1);
+    const float m[3] = {c->l00 * scale, c->l10 * scale, c->l11 * scale};
+    rc = dfp2s_launch_blur_tc_prepare_warp(const_cast<dfp2s_p2s_dev*>(pd), img, C, H, W, c->fields,
+                                           c->fields + npix, st, m);
+    if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
+    if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
+    if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "warp + tensor-core blur preparation");
+    mark(2);
+    CHECK_LAUNCH(dfp2s_launch_mlp_tc(pd, c->fields, H * W, c->w, DFP2S_W_F32, st, c->w1_mixed, scale));
+    mark(3);
+    rc = dfp2s_basis_blur_tc_run(c->p, C, H, W, c->w, DFP2S_W_F32, out, stream);
+  } else {
+    rc = dfp2s_sample_zernike_fields(c->f, D_over_r0, seed, frame, H, W, c->fields, stream);
     if (rc) return rc;
+    mark(1);
+    rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
+    if (rc) return rc;
+    mark(2);
     rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, DFP2S_W_F32, stream);
     if (rc) return rc;
-    return dfp2s_basis_blur_tc_run(c->p, C, H, W, c->w, DFP2S_W_F32, out, stream);
+    mark(3);
+    if (p2s_mode == DFP2S_P2S_EXACT) rc = dfp2s_basis_blur(c->p, c->warped, C, H, W, c->w, DFP2S_W_F32, out, stream);
+    else rc = dfp2s_basis_blur_tc(c->p, c->warped, C, H, W, c->w, DFP2S_W_F32, out, stream);
   }
-  rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
   if (rc) return rc;
-  rc = dfp2s_p2s_weights(c->p, p2s_mode, c->fields, H, W, c->w, DFP2S_W_F32, stream);
-  if (rc) return rc;
-  if (p2s_mode == DFP2S_P2S_EXACT) return dfp2s_basis_blur(c->p, c->warped, C, H, W, c->w, DFP2S_W_F32, out, stream);
-  return dfp2s_basis_blur_tc(c->p, c->warped, C, H, W, c->w, DFP2S_W_F32, out, stream);
+  mark(4);
+  if (ev) ++c->frames;
+  return DFP2S_OK;
 }

@@ -147,7 +147,8 @@ __global__ void k_pad_shifted(const float* __restrict__ img, int C, int H, int W
 // columns 8u - 16 .. 8u - 2 and writes one 16-byte run per shift.
 __global__ void __launch_bounds__(128, 6)
     k_warp_pad_shifted(const float* __restrict__ img, int C, int H, int W, const float* __restrict__ a2,
-                       const float* __restrict__ a3, int Wq, float centre, __nv_bfloat16* __restrict__ P) {
+                       const float* __restrict__ a3, int Wq, float centre, __nv_bfloat16* __restrict__ P, int mixed,
+                       float m00, float m10, float m11) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (8 * u >= Wq) return;
@@ -162,7 +163,12 @@ __global__ void __launch_bounds__(128, 6)
 #pragma unroll
     for (int i = 0; i < 15; ++i) {
       const int x = min(max(8 * u - 16 + i, 0), W - 1);
-      const float v = tilt_sample(I, H, W, x, yp, __ldg(t2 + x), __ldg(t3 + x));
+      float s2 = __ldg(t2 + x), s3 = __ldg(t3 + x);
+      if (mixed) {  // the tilt rows of a = scale L u, in the mixing kernel's operation order
+        s3 = fmaf(m11, s3, fmaf(m10, s2, 0.f));
+        s2 = fmaf(m00, s2, 0.f);
+      }
+      const float v = tilt_sample(I, H, W, x, yp, s2, s3);
       h[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - centre));
     }
     __nv_bfloat16* dst = P + ((size_t)c * NSHIFT) * plane + (size_t)r * Wq + 8 * u;
@@ -615,11 +621,13 @@ int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int 
 
 // The same for the tilt-warped image (k_warp_pad_shifted), without writing the warped image.
 int dfp2s_launch_blur_tc_prepare_warp(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const float* a2,
-                                      const float* a3, cudaStream_t st) {
+                                      const float* a3, cudaStream_t st, const float* m) {
   const int rc = blur_tc_scratch(p, C, H, W, st);
   if (rc != DFP2S_OK) return rc;
   const int Wq = (W + TM - 1) / TM * TM + 64;
-  k_warp_pad_shifted<<<dim3((Wq / 8 + 127) / 128, H + 32), 128, 0, st>>>(img, C, H, W, a2, a3, Wq, 0.5f, p->pad);
+  k_warp_pad_shifted<<<dim3((Wq / 8 + 127) / 128, H + 32), 128, 0, st>>>(img, C, H, W, a2, a3, Wq, 0.5f, p->pad,
+                                                                          m != nullptr, m ? m[0] : 1.f, m ? m[1] : 0.f,
+                                                                          m ? m[2] : 1.f);
   p->prep_C = C;
   p->prep_H = H;
   p->prep_W = W;

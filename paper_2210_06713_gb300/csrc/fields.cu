@@ -321,7 +321,7 @@ void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H,
 
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st, const float* prev, float alpha) {
+                               cudaStream_t st, const float* prev, float alpha, bool mix) {
   switch (N) {
     case 16: launch_passes<16>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
     case 32: launch_passes<32>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
@@ -335,6 +335,7 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
     default: return DFP2S_EINVAL;
   }
   const size_t npix = (size_t)H * W;
+  if (!mix) return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
   if (prev) launch_mix_any<true>(fields, L, scale * sqrtf(1.f - alpha * alpha), J, npix, prev, alpha, st);
   else launch_mix_any<false>(fields, L, scale, J, npix, nullptr, 0.f, st);
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;

@@ -10,10 +10,11 @@
 #include "../../include/dfp2s.h"
 
 // fields.cu -- Sec. III-C sampler passes
-// prev != nullptr: fields = alpha prev + sqrt(1 - alpha^2) (this frame's fields), the auto-regressive form
+// prev != nullptr: fields = alpha prev + sqrt(1 - alpha^2) (this frame's fields), the auto-regressive form;
+// mix = false: the unit fields before the mixing by scale L (prev must be null)
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st, const float* prev = nullptr, float alpha = 0.f);
+                               cudaStream_t st, const float* prev = nullptr, float alpha = 0.f, bool mix = true);
 int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st);
 int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cudaStream_t st);
 
@@ -61,7 +62,8 @@ struct dfp2s_p2s_dev {
   // tensor-core surrogate: packed BF16 weights and the folded output offset
   __nv_bfloat16 *tc_w1, *tc_w2, *tc_w3;
   float* tc_c3;
-  __nv_bfloat16* tc_bias;  // hidden biases as the B operand of the bias MMAs
+  __nv_bfloat16* tc_bias;
+  unsigned mlp_version;  // incremented by every network install  // hidden biases as the B operand of the bias MMAs
 };
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
 // w_dtype for dfp2s_launch_p2s_exact that writes the normalised 33 x 33 PSFs (npix x 1089 FP32) instead of weights
@@ -88,7 +90,12 @@ int dfp2s_launch_draw_vectors(int n, int J, const float* L, const float* drs, in
 
 // mlp_tc.cu -- tensor-core surrogate inference
 int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st);
-int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st);
+// first-layer weights for unmixed input: W1 diag(in_scale) L, packed like tc_w1 (HID x 48 bfloat16)
+int dfp2s_mlp_tc_pack_w1_mixed(const dfp2s_p2s_dev* p, const float* L, __nv_bfloat16* out, cudaStream_t st);
+size_t dfp2s_mlp_tc_w1_elems();
+// w1 != nullptr: first-layer weights to use instead of tc_w1; the fields are multiplied by xscale on loading
+int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st,
+                        const __nv_bfloat16* w1 = nullptr, float xscale = 1.f);
 
 // basis.cu -- FP64 SVD basis of exact PSFs
 int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const double* dr_host, int n_dr, uint64_t seed,
@@ -96,8 +103,10 @@ int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const do
 
 // blur_tc.cu -- BF16 tcgen05 blur (weights in BF16)
 int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, cudaStream_t st);
+// m != nullptr: a2/a3 are the unit fields u0, u1 before the mixing, and the tilts are formed as the mixing
+// does, t2 = m[0] u0, t3 = m[2] u1 + m[1] u0 (m = scale (L00, L10, L11))
 int dfp2s_launch_blur_tc_prepare_warp(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const float* a2,
-                                      const float* a3, cudaStream_t st);
+                                      const float* a3, cudaStream_t st, const float* m = nullptr);
 int dfp2s_launch_blur_tc_run(dfp2s_p2s_dev* p, int C, int H, int W, const void* w, int w_dtype, float* out,
                              cudaStream_t st);
 int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,

@@ -160,12 +160,12 @@ DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col
   }
 }
 
-template <typename WT>
+template <typename WT, bool SCALED>
 __global__ void __launch_bounds__(THREADS, 1)
     k_mlp_tc(const float* __restrict__ fields, int J, int npix, int K, int NP3, const __nv_bfloat16* __restrict__ w1t,
              const __nv_bfloat16* __restrict__ w2c, const __nv_bfloat16* __restrict__ w3c,
              const __nv_bfloat16* __restrict__ bias, const float* __restrict__ c3, const float* __restrict__ s3,
-             WT* __restrict__ wout, int KS, int vec_out, int* __restrict__ err) {
+             WT* __restrict__ wout, int KS, int vec_out, int* __restrict__ err, float xscale) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint32_t wd[4];
 #pragma unroll
           for (int e2 = 0; e2 < 4; ++e2) {
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[r][2 * e2], v[r][2 * e2 + 1]);
+            const float x0 = SCALED ? v[r][2 * e2] * xscale : v[r][2 * e2];
+            const float x1 = SCALED ? v[r][2 * e2 + 1] * xscale : v[r][2 * e2 + 1];
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
             wd[e2] = *reinterpret_cast<uint32_t*>(&h2);
           }
           *reinterpret_cast<uint4*>(s.X + kmajor_off(r * 32 + lane, jg * 8, KX / 8)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
@@ -480,6 +482,18 @@ __global__ void k_pack_bias(const float* __restrict__ b1, const float* __restric
   out[kmajor_off(n, k, 2) / 2] = __float2bfloat16_rn(v);
 }
 
+// W1 diag(in_scale) L (L lower triangular, J x J row-major), packed as k_pack_w1: the first layer of the same
+// network for the fields before their mixing by L
+__global__ void k_pack_w1_mixed(const float* __restrict__ W1t, const float* __restrict__ in_scale,
+                                const float* __restrict__ L, int J, __nv_bfloat16* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 256 x 48
+  if (i >= HID * KX) return;
+  const int n = i / KX, j = i - n * KX;
+  float v = 0.f;
+  for (int r = j; r < J; ++r) v = fmaf(W1t[(size_t)r * HID + n] * in_scale[r], L[r * J + j], v);
+  out[kmajor_off(n, j, KX / 8) / 2] = __float2bfloat16_rn(v);
+}
+
 __global__ void k_out_affine(const float* __restrict__ b3, const float* __restrict__ sc,
                              const float* __restrict__ sh, int K, float* __restrict__ c3) {
   const int k = threadIdx.x;
@@ -508,7 +522,25 @@ int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
 
-int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st) {
+size_t dfp2s_mlp_tc_w1_elems() { return (size_t)HID * KX; }
+
+template <typename WT, bool SCALED>
+static void launch_mlp(const float* fields, const dfp2s_p2s_dev* p, int npix, int K, int NP3, const __nv_bfloat16* w1,
+                       WT* out, int KS, int vec_out, float xscale, int grid, size_t sm, cudaStream_t st) {
+  cudaFuncSetAttribute(k_mlp_tc<WT, SCALED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_mlp_tc<WT, SCALED><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, w1, p->tc_w2, p->tc_w3, p->tc_bias,
+                                                  p->tc_c3, p->out_scale, out, KS, vec_out, p->err, xscale);
+}
+
+int dfp2s_mlp_tc_pack_w1_mixed(const dfp2s_p2s_dev* p, const float* L, __nv_bfloat16* out, cudaStream_t st) {
+  if (p->J > KX) return DFP2S_EUNSUPPORTED;
+  k_pack_w1_mixed<<<(HID * KX + 255) / 256, 256, 0, st>>>(p->W1, p->in_scale, L, p->J, out);
+  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+}
+
+int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st,
+                        const __nv_bfloat16* w1, float xscale) {
+  if (!w1) w1 = p->tc_w1;
   const int K = p->K;
   if (p->J > KX) return DFP2S_EUNSUPPORTED;  // the input tile holds at most 48 fields
   const int NP3 = (K + 15) / 16 * 16;
@@ -525,14 +557,15 @@ int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, v
   if (vec_out && KS == K) vec_out = 2;
   const size_t sm = sizeof(Smem) + 1024;
   static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory layout");
-  cudaFuncSetAttribute(k_mlp_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_mlp_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (w_dtype == DFP2S_W_BF16)
-    k_mlp_tc<__nv_bfloat16><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3,
-                                                      p->tc_bias, p->tc_c3, p->out_scale, (__nv_bfloat16*)w, KS, 0,
-                                                      p->err);
-  else
-    k_mlp_tc<float><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, p->tc_w1, p->tc_w2, p->tc_w3, p->tc_bias,
-                                              p->tc_c3, p->out_scale, (float*)w, KS, vec_out, p->err);
+  const bool scaled = xscale != 1.f;
+  if (w_dtype == DFP2S_W_BF16) {
+    __nv_bfloat16* o = (__nv_bfloat16*)w;
+    if (scaled) launch_mlp<__nv_bfloat16, true>(fields, p, npix, K, NP3, w1, o, KS, 0, xscale, grid, sm, st);
+    else launch_mlp<__nv_bfloat16, false>(fields, p, npix, K, NP3, w1, o, KS, 0, xscale, grid, sm, st);
+  } else {
+    float* o = (float*)w;
+    if (scaled) launch_mlp<float, true>(fields, p, npix, K, NP3, w1, o, KS, vec_out, xscale, grid, sm, st);
+    else launch_mlp<float, false>(fields, p, npix, K, NP3, w1, o, KS, vec_out, xscale, grid, sm, st);
+  }
   return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }

@@ -285,6 +285,78 @@ def test_mlp_forward_matches_oracle(lib, K, H, W):
 
 
 # ------------------------------------------------------------------- frame
+def _device_view(ptr, shape):
+    class _A:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (ptr, False), "version": 3}
+    return torch.as_tensor(_A(), device="cuda")
+
+
+@pytest.mark.parametrize("d", [1.0, 3.0])
+def test_learned_frame_folds_the_mixing_into_warp_and_first_layer(lib, d):
+    # the LEARNED frame skips the mixing pass: the warp forms its tilts from the unit fields u0, u1 and the first
+    # layer takes W1 diag(in_scale) L on s u (s = (D/r0)^(5/6)).  Its weights against the oracle network evaluated
+    # with the kernel's BF16 roundings of that input; the frame against the step-by-step calls on the mixed
+    # fields (which round the network's input differently); a new install re-packs the first layer
+    J, K, H, W, N = 36, 100, 96, 80, 256
+    rng = np.random.default_rng(7)
+    params = {"W1": rng.standard_normal((256, J)) / 6, "b1": rng.standard_normal(256) * 0.1,
+              "W2": rng.standard_normal((256, 256)) / 16, "b2": rng.standard_normal(256) * 0.1,
+              "W3": rng.standard_normal((K, 256)) / 16, "b3": rng.standard_normal(K) * 0.1}
+    params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
+    in_scale = rng.uniform(0.5, 2.0, J).astype(np.float32).astype(np.float64)
+    in_scale[:2] = 0
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    f = lib.SpectralFactor(J, N, 8.0)
+    P = lib.P2S(J, cu(basis))
+    img = cu(synthetic.shapes(H, W, 3, seed=2))
+    sim = lib.Simulator(f, P, 3, H, W)
+    L = zernike.noll_cholesky(J, 1.0).astype(np.float32).astype(np.float64)
+    s = float(np.float32(d ** (5.0 / 6.0)))
+    for it in range(2):
+        prm = {k: (v * (1 + it)).astype(np.float32).astype(np.float64) for k, v in params.items()}
+        sc = rng.uniform(0.01, 0.05, K).astype(np.float32).astype(np.float64)
+        P.set_mlp(*[cu(prm[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")], cu(in_scale), cu(sc), cu(np.zeros(K)))
+        g = sim.simulate_frame(img, d, 5, it, lib.P2S_LEARNED)
+        P.check()
+        fp, _, wp = sim.buffers(J, 3, H, W, K)
+        u = _device_view(fp, (J, H * W)).cpu().numpy().astype(np.float64)
+        wg = _device_view(wp, (H * W, K)).cpu().numpy()
+        x = _bf((u.T.astype(np.float32) * np.float32(s)))
+        z1 = x @ _bf((prm["W1"] * in_scale[None, :]) @ L).T + prm["b1"]
+        h1 = _bf(mlp.gelu(z1))
+        h2 = _bf(mlp.gelu(h1 @ _bf(prm["W2"]).T + prm["b2"]))
+        ob = (h2 @ _bf(prm["W3"]).T) * sc + prm["b3"] * sc
+        assert rel_l2(wg, ob) < 1e-3
+        a = lib.sample_zernike_fields(f, d, 5, it, H, W)
+        lib.tilt_warp_blur_tc_prepare(P, img, a[0].contiguous(), a[1].contiguous())
+        w = lib.p2s_weights(P, lib.P2S_LEARNED, a)
+        o = lib.basis_blur_tc_run(P, (3, H, W), w)
+        e = rel_l2(g.cpu().numpy(), o.cpu().numpy())
+        assert e < 3e-3, e
+
+
+def test_frame_stage_timing(lib):
+    J, K, H, W, N = 36, 16, 64, 48, 128
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    f = lib.SpectralFactor(J, N, 8.0)
+    P = lib.P2S(J, cu(basis))
+    sim = lib.Simulator(f, P, 3, H, W)
+    img = cu(synthetic.shapes(H, W, 3, seed=2))
+    sim.stage_timing(3)
+    with pytest.raises(lib.DFP2SError):
+        sim.stage_times(1)  # nothing recorded yet
+    for i in range(5):
+        sim.simulate_frame(img, 2.0, 1, i, lib.P2S_EXACT)
+    t = sim.stage_times(3)
+    assert t.shape == (3, 4) and np.all(t > 0) and np.all(t < 1e3)
+    with pytest.raises(lib.DFP2SError):
+        sim.stage_times(4)  # beyond the ring
+    sim.stage_timing(0)
+    sim.simulate_frame(img, 2.0, 1, 9, lib.P2S_EXACT)
+    with pytest.raises(lib.DFP2SError):
+        sim.stage_times(1)
+
+
 def test_simulate_frame_exact_small_workload(lib):
     J, K, H, W, N, d = 36, 16, 64, 64, 128, 2.0
     img = synthetic.smooth_noise(H, W, seed=0)
