@@ -2,34 +2,41 @@
 // kernel per frame, BF16 operands, FP32 accumulation in tensor memory, GELU by a
 // logistic fit accurate far beyond the BF16 rounding of the activations.
 //
-// A tile is 128 consecutive pixels (MMA M = 128):
-//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T + b1 -> TMEM A = columns [0, 256)
+// A tile is 128 consecutive pixels (MMA M = 128).  Tensor memory (512 columns)
+// holds two 256-column regions; tile t computes in P = region t % 2 and
+// Q = the other:
+//   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T + b1 -> P
 //            (W1' = W1 diag(in_scale), resident in shared memory)
-//   2 GELU(z) -> H [128 x 256] BF16 in shared memory (K-major core matrices)
-//   layer 2: H x (W2 / 2)^T + b2 -> TMEM B = [256, 512), W2 streamed in four 64-wide K chunks
-//   2 GELU(z) -> H
-//   layer 3: H x (W3 / 2)^T -> TMEM [384, 384 + NP3), W3 streamed in four K chunks
-//   w = y * out_scale + (b3 * out_scale + out_shift) -> global (FP32 or BF16)
+//   2 GELU(z) -> H1 (BF16), written back into P: chunk c of 64 columns keeps its
+//            activations in its first 32 columns (two per column)
+//   layer 2: H1 (A operand from tensor memory) x (W2 / 2)^T + b2 -> Q, W2 streamed
+//            in four 64-wide K chunks
+//   2 GELU(z) -> H2 in Q, the same way
+//   layer 3: H2 (from tensor memory) x (W3 / 2)^T -> P columns [0, NP3)
+//   w = y * out_scale + (b3 * out_scale + out_shift) -> staging rows in shared
+//            memory -> global memory by one bulk copy (FP32 or BF16)
 //
 // The hidden biases enter the accumulators through one extra K = 16 MMA per
 // layer (a tile of ones against the bias split into high and low bfloat16
 // parts, exact to about 2^-17 relative), and the activations are stored doubled
 // against halved weights of the next layer (both scalings by a power of two are
-// exact), so that an activation costs the epilogue five instructions.
+// exact).  The activations never touch shared memory, so the MMAs read only
+// their weights there.
 //
 // Warp roles: warps 0-15 run the epilogues (warp w reads TMEM lanes 32 (w % 4)
-// .. and a quarter of the columns), warp 16 issues the MMAs, warp 17 converts
-// the next tile's fields into X, warp 18 issues the weight copies.  The
-// epilogues hand H over in 64-column chunks (one mbarrier per chunk), so the
-// MMAs of the next layer start on a chunk while the epilogue works on the
-// following one; the second epilogue walks its chunks from the top so that
-// layer 3's columns [384, 512) are free first.  Layer 1 of the next tile runs
-// on the tensor cores while the epilogues finish the current tile.  Weight
-// chunks arrive by 1-D bulk copies into a three-deep ring; their MMAs release a
-// slot through tcgen05.commit.  The copies have a warp of their own because a
-// bulk copy can hold its issuing thread until the copy engine takes it, which
-// would stall the MMA issue.  All waits are bounded; a wait that runs out sets
-// the kernel's error word.
+// .. and a quarter of each chunk's columns), warp 16 issues the MMAs, warp 17
+// converts the next tile's fields into X, warp 18 issues the weight copies.
+// The epilogues hand each layer over in 64-column chunks (one mbarrier per
+// chunk), so the next layer's MMAs start on a chunk while the epilogue works on
+// the following one; within a chunk the four warps of a lane quarter meet at a
+// named barrier between reading the accumulators and writing the activations
+// over them.  Layer 1 of the next tile runs on the tensor cores while the
+// epilogues write out the current tile.  Weight chunks arrive by 1-D bulk
+// copies into a three-deep ring; their MMAs release a slot through
+// tcgen05.commit.  The copies have a warp of their own because a bulk copy can
+// hold its issuing thread until the copy engine takes it, which would stall the
+// MMA issue.  All waits are bounded; a wait that runs out sets the kernel's
+// error word.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -50,18 +57,16 @@ constexpr int PRODUCER_WARP = EPI_WARPS;
 constexpr int LOADER_WARP = EPI_WARPS + 1;
 constexpr int COPY_WARP = EPI_WARPS + 2;
 constexpr int THREADS = EPI_THREADS + 96;  // + MMA, loader and copy warps
-constexpr int L3_COL = 384;                // layer-3 accumulator columns [384, 384 + NP3)
 constexpr int NRING = 3;
 constexpr int CHUNK_BYTES = HID * 64 * 2;  // one 64-wide K chunk of W2 (the largest)
 constexpr int STAGE_BYTES = TM * 132 * 4;  // FP32 output rows of up to 128 (+4) weights
-constexpr int HS_BYTES = STAGE_BYTES > TM * HID * 2 ? STAGE_BYTES : TM * HID * 2;
 constexpr int ONES_BYTES = TM * 16 * 2;    // a 128 x 16 A operand, ones in two K columns
 constexpr int BIAS_BYTES = HID * 16 * 2;   // the 256 x 16 B operand of the hidden biases
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct Smem {
   uint8_t ring[NRING][CHUNK_BYTES];  // 96 KB
-  uint8_t H[HS_BYTES];               // hidden activations, then the output staging rows
+  uint8_t stage[STAGE_BYTES];        // 66 KB: the tile's output rows
   uint8_t W1[HID * KX * 2];          // 24 KB
   uint8_t X[TM * KX * 2];            // 12 KB
   uint8_t ONES[2][ONES_BYTES];       // 8 KB: ones in K columns 0, 1 (layer 1) and 2, 3 (layer 2)
@@ -112,6 +117,21 @@ DFP2S_DEV bool bar_epi_any(bool v) {
   return r != 0;
 }
 
+// Barrier of the four epilogue warps that share TMEM lane quarter q4 (named
+// barrier 2 + q4, 128 threads), ORing a flag over them like bar_epi_any.
+DFP2S_DEV bool bar_quarter_any(int q4, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(2 + q4)
+      : "memory");
+  return r != 0;
+}
+
 // 1-D bulk copy shared -> global (both 16-byte aligned, size a multiple of 16) in a bulk group; wait until
 // its source may be overwritten, or until every issued copy has completed.
 DFP2S_DEV void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
@@ -130,34 +150,63 @@ DFP2S_DEV void wstore<float>(float* p, float v) { *p = v; }
 template <>
 DFP2S_DEV void wstore<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-// Hidden-layer epilogue of one epilogue warp: for each 64-column chunk c
-// (ascending, or descending if `reverse`), this warp's 16 columns
-// [64 c + 16 sl, +16) of TMEM region `col0` (biases included) -> 2 GELU -> H
-// (K-major, K = column - col0), then the chunk is handed to the MMA warp.
-DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t tmem, int warp, int lane, int col0, bool reverse) {
+// Warp-wide load of 16 TMEM columns without waiting; tmem_wait16 waits for every
+// outstanding load and ties the destination registers to the wait, so that no
+// use of them is scheduled before it.
+DFP2S_DEV void tmem_ld16_async(uint32_t taddr, float (&v)[16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+DFP2S_DEV void tmem_wait16(float (&v)[16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
+// Hidden-layer epilogue of one epilogue warp (lane quarter q4, slice sl): for
+// each 64-column chunk c of the 256-column region R, this warp's 16 columns
+// [64 c + 16 sl, +16) (biases included) -> 2 GELU -> BF16 pairs written over
+// columns [64 c + 8 sl, +8) of the same lanes (chunk c's activations in its first
+// 32 columns, K = 16 sl .. 16 sl + 15 of the chunk), then the chunk is handed to
+// the MMA warp.  The four warps of the quarter have all read the chunk before any
+// of them writes (quarter barrier, which also makes `skip` uniform over them);
+// the next chunk's load is in flight meanwhile.  Every warp of the quarter calls
+// this the same number of times.  Returns the skip decision.
+DFP2S_DEV bool epilogue_gelu(Smem& s, uint32_t R, int warp, int lane, bool skip) {
   const int q4 = warp & 3, sl = warp >> 2;
-  const int p = q4 * 32 + lane;
-  for (int i = 0; i < 4; ++i) {
-    const int c = reverse ? 3 - i : i;
-    const int k0 = 64 * c + 16 * sl;
-    float d[16];
-    umma::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + col0 + k0, d);
-    uint32_t packed[8];
+  const uint32_t base = R + ((uint32_t)(q4 * 32) << 16);
+  float d[2][16];
+  tmem_ld16_async(base + 16 * sl, d[0]);
+  tmem_wait16(d[0]);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const float g0 = gelu2x(d[2 * e]);
-      const float g1 = gelu2x(d[2 * e + 1]);
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(g0, g1);
-      packed[e] = *reinterpret_cast<uint32_t*>(&h2);
+  for (int c = 0; c < 4; ++c) {
+    float(&cur)[16] = d[c & 1];
+    skip = bar_quarter_any(q4, skip);  // every warp of the quarter has read chunk c
+    if (c < 3) tmem_ld16_async(base + 64 * (c + 1) + 16 * sl, d[(c + 1) & 1]);
+    if (!skip) {
+      uint32_t packed[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu2x(cur[2 * e]), gelu2x(cur[2 * e + 1]));
+        packed[e] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+      umma::tmem_st8(base + 64 * c + 8 * sl, packed);
+      umma::tmem_wait_st();
     }
-    *reinterpret_cast<uint4*>(s.H + kmajor_off(p, k0, HID / 8)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    *reinterpret_cast<uint4*>(s.H + kmajor_off(p, k0 + 8, HID / 8)) =
-        make_uint4(packed[4], packed[5], packed[6], packed[7]);
-    umma::fence_proxy_async_smem();  // H stores -> visible to the tensor cores
-    umma::fence_before_sync();       // TMEM reads ordered before the hand-over
+    umma::fence_before_sync();  // TMEM reads and writes ordered before the hand-over
     __syncwarp();
     if (lane == 0) umma::mbar_arrive(&s.h_ready[c]);
+    if (c < 3) tmem_wait16(d[(c + 1) & 1]);
   }
+  return skip;
 }
 
 template <typename WT, bool SCALED>
@@ -210,11 +259,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == PRODUCER_WARP) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      // K-major no-swizzle descriptors: X and W1 with 6 K groups per 8-row group, H with 32,
-      // weight chunks with 8, the ones and bias tiles with 2; per-MMA descriptors add (byte offset >> 4)
+      // K-major no-swizzle descriptors: X and W1 with 6 K groups per 8-row group, weight chunks with 8, the ones
+      // and bias tiles with 2; per-MMA descriptors add (byte offset >> 4)
       const uint64_t x_desc = umma::sdesc(umma::smem_u32(s.X), 128, 768);
       const uint64_t w1_desc = umma::sdesc(umma::smem_u32(s.W1), 128, 768);
-      const uint64_t h_desc = umma::sdesc(umma::smem_u32(s.H), 128, 4096);
       const uint64_t ring_desc = umma::sdesc(umma::smem_u32(s.ring[0]), 128, 1024);
       const uint64_t ones1_desc = umma::sdesc(umma::smem_u32(s.ONES[0]), 128, 256);
       const uint64_t ones2_desc = umma::sdesc(umma::smem_u32(s.ONES[1]), 128, 256);
@@ -223,61 +271,59 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t idesc3 = umma::idesc_bf16(TM, NP3);
       uint32_t u_use = 0;
       bool ok = true;
-      // MMAs of one 64-wide K chunk (weight chunk u in the ring, H chunk c)
-      auto chunk_mmas = [&](uint32_t u, int c, uint32_t d, uint32_t id, bool first) {
+      // MMAs of one 64-wide K chunk: weight chunk u in the ring against the activations of chunk c, which
+      // sit in the first 32 columns of the chunk at tensor-memory address a (8 columns per K = 16 step)
+      auto chunk_mmas = [&](uint32_t u, uint32_t a, uint32_t d, uint32_t id, bool first) {
         const int b = u % NRING;
         if (!umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
           ok = false;
           return;
         }
         umma::fence_after_sync();
-        const uint64_t a_c = h_desc + (uint64_t)(c * 8 * 8);
         const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) umma::mma_bf16(d, a_c + 16 * ks, b_c + 16 * ks, id, !(first && ks == 0));
+        for (int ks = 0; ks < 4; ++ks) umma::mma_bf16_ta(d, a + 8 * ks, b_c + 16 * ks, id, !(first && ks == 0));
         umma::mma_commit(&s.empty[b]);
       };
       if (my_tiles > 0 && !umma::mbar_wait(&s.w1_full, 0, kWaitNs)) ok = false;
       for (int t = 0; t < my_tiles && ok; ++t) {
-        // layer 1: X of this tile written by the loader; TMEM A free since the previous
-        // tile's first epilogue handed over all four chunks (waited on below for that tile)
+        const uint32_t P = tmem + ((t & 1) ? 256u : 0u), Q = tmem + ((t & 1) ? 0u : 256u);
+        // layer 1 writes P, where the previous tile's second activations were read by its layer-3 MMAs
+        if (t >= 1 && !umma::mbar_wait(&s.l3_done, (t - 1) & 1, kWaitNs)) {
+          ok = false;
+          break;
+        }
         if (!umma::mbar_wait(&s.x_ready, t & 1, kWaitNs)) {
           ok = false;
           break;
         }
         umma::fence_after_sync();
 #pragma unroll
-        for (int ks = 0; ks < KX / 16; ++ks) umma::mma_bf16(tmem, x_desc + 16 * ks, w1_desc + 16 * ks, idesc1, ks != 0);
-        umma::mma_bf16(tmem, ones1_desc, bias_desc, idesc1, 1);  // + b1
+        for (int ks = 0; ks < KX / 16; ++ks) umma::mma_bf16(P, x_desc + 16 * ks, w1_desc + 16 * ks, idesc1, ks != 0);
+        umma::mma_bf16(P, ones1_desc, bias_desc, idesc1, 1);  // + b1
         umma::mma_commit(&s.l1_done);
-        // layer 2 on the first epilogue's chunks (h_ready completion 2t); TMEM B is free once
-        // chunk 0 has arrived (the epilogues finished the previous tile before this one)
+        // layer 2 into Q on the first epilogue's chunks (h_ready completion 2t); Q is free once chunk 0 has
+        // arrived (the epilogues finished the previous tile's outputs, which sat in Q, before this tile)
         for (int c = 0; c < 4 && ok; ++c) {
           if (!umma::mbar_wait(&s.h_ready[c], 0, kWaitNs)) {
             ok = false;
             break;
           }
-          if (c == 0) {
-            umma::fence_after_sync();
-            umma::mma_bf16(tmem + 256, ones2_desc, bias_desc, idesc1, 0);  // accumulator = b2
-          }
-          chunk_mmas(u_use++, c, tmem + 256, idesc1, false);
+          umma::fence_after_sync();
+          if (c == 0) umma::mma_bf16(Q, ones2_desc, bias_desc, idesc1, 0);  // accumulator = b2
+          chunk_mmas(u_use++, P + 64 * c, Q, idesc1, false);
         }
         if (!ok) break;
         umma::mma_commit(&s.l2_done);
-        // layer 3 on the second epilogue's chunks (completion 2t + 1, chunks 3, 2, 1, 0); its
-        // accumulator [384, 384 + NP3) is free once chunks 3 and 2 of layer 2 have been read
-        if (!umma::mbar_wait(&s.h_ready[3], 1, kWaitNs) || !umma::mbar_wait(&s.h_ready[2], 1, kWaitNs)) {
-          ok = false;
-          break;
-        }
-        for (int i = 0; i < 4 && ok; ++i) {
-          const int c = 3 - i;
+        // layer 3 into P columns [0, NP3) on the second epilogue's chunks (completion 2t + 1); the first
+        // activations there were read by the layer-2 MMAs, complete before the second epilogue began
+        for (int c = 0; c < 4 && ok; ++c) {
           if (!umma::mbar_wait(&s.h_ready[c], 1, kWaitNs)) {
             ok = false;
             break;
           }
-          chunk_mmas(u_use++, c, tmem + L3_COL, idesc3, i == 0);
+          umma::fence_after_sync();
+          chunk_mmas(u_use++, Q + 64 * c, P, idesc3, c == 0);
         }
         if (!ok) break;
         umma::mma_commit(&s.l3_done);
@@ -315,14 +361,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           if (!got) break;
         }
-        // chunk u: W2 chunk u % 8 for u % 8 < 4, else W3 chunk 7 - u % 8 (layer 3 takes its K chunks 3, 2, 1, 0)
+        // chunk u: W2 chunk u % 8 for u % 8 < 4, else W3 chunk u % 8 - 4
         const int c = u % 8;
         if (c < 4) {
           umma::mbar_arrive_expect_tx(&s.full[b], CHUNK_BYTES);
           umma::bulk_g2s(s.ring[b], w2c + (size_t)c * (HID * 64), CHUNK_BYTES, &s.full[b]);
         } else {
           umma::mbar_arrive_expect_tx(&s.full[b], w3_bytes);
-          umma::bulk_g2s(s.ring[b], w3c + (size_t)(7 - c) * (NP3 * 64), w3_bytes, &s.full[b]);
+          umma::bulk_g2s(s.ring[b], w3c + (size_t)(c - 4) * (NP3 * 64), w3_bytes, &s.full[b]);
         }
       }
       // every issued copy lands before the CTA exits (bounded): copies before u - NRING were
@@ -373,50 +419,54 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q4 = warp & 3, sl = warp >> 2;
     const int p = q4 * 32 + lane;
     const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    float* stage = reinterpret_cast<float*>(s.stage);
+    volatile int* abort_flag = &s.abort;
     for (int t = 0; t < my_tiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
       const int p0 = tile * TM;
-      if (!umma::mbar_wait_backoff(&s.l1_done, t & 1, kWaitNs)) s.abort = 1;
+      const uint32_t P = tmem + ((t & 1) ? 256u : 0u), Q = tmem + ((t & 1) ? 0u : 256u);
+      // every warp runs both epilogues (their quarter barriers); a failed wait turns the work off
+      bool skip = *abort_flag != 0;
+      if (!skip && !umma::mbar_wait_backoff(&s.l1_done, t & 1, kWaitNs)) skip = true;
       umma::fence_after_sync();
-      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 0, false);
-      if (!umma::mbar_wait_backoff(&s.l2_done, t & 1, kWaitNs)) s.abort = 1;
+      skip = epilogue_gelu(s, P, warp, lane, skip);
+      if (!skip && !umma::mbar_wait_backoff(&s.l2_done, t & 1, kWaitNs)) skip = true;
       umma::fence_after_sync();
-      if (!s.abort) epilogue_gelu(s, tmem, warp, lane, 256, true);
-      if (!umma::mbar_wait_backoff(&s.l3_done, t & 1, kWaitNs)) s.abort = 1;
+      skip = epilogue_gelu(s, Q, warp, lane, skip);
+      if (!skip && !umma::mbar_wait_backoff(&s.l3_done, t & 1, kWaitNs)) skip = true;
       umma::fence_after_sync();
-      // outputs: TMEM [384, 384 + NP3) -> FP32 rows of stride KS in the staging area (H is free now)
-      float* stage = reinterpret_cast<float*>(s.H);
-      if (!s.abort) {
-        const int ngrp = NP3 / 16;
-        for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
-          float d[16];
-          umma::tmem_ld16(tmem + lane_base + L3_COL + q * 16, d);
+      if (skip) *abort_flag = 1;
+      // the previous tile's bulk copy has finished reading the staging rows (its issuing thread waits, the
+      // barrier passes that on)
+      if (vec_out == 2 && tid == 0) bulk_wait_read();
+      if (bar_epi_any(skip)) break;
+      // outputs: TMEM P [0, NP3) -> FP32 rows of stride KS in the staging area
+      const int ngrp = NP3 / 16;
+      for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
+        float d[16];
+        umma::tmem_ld16(P + lane_base + q * 16, d);
 #pragma unroll
-          for (int i4 = 0; i4 < 4; ++i4) {
-            const int k = q * 16 + 4 * i4;
-            if (k < K) {
-              float4 o;
-              o.x = fmaf(d[4 * i4 + 0], s.s3[k + 0], s.c3[k + 0]);
-              o.y = fmaf(d[4 * i4 + 1], s.s3[k + 1], s.c3[k + 1]);
-              o.z = fmaf(d[4 * i4 + 2], s.s3[k + 2], s.c3[k + 2]);
-              o.w = fmaf(d[4 * i4 + 3], s.s3[k + 3], s.c3[k + 3]);
-              *reinterpret_cast<float4*>(stage + p * KS + k) = o;
-            }
+        for (int i4 = 0; i4 < 4; ++i4) {
+          const int k = q * 16 + 4 * i4;
+          if (k < K) {
+            float4 o;
+            o.x = fmaf(d[4 * i4 + 0], s.s3[k + 0], s.c3[k + 0]);
+            o.y = fmaf(d[4 * i4 + 1], s.s3[k + 1], s.c3[k + 1]);
+            o.z = fmaf(d[4 * i4 + 2], s.s3[k + 2], s.c3[k + 2]);
+            o.w = fmaf(d[4 * i4 + 3], s.s3[k + 3], s.c3[k + 3]);
+            *reinterpret_cast<float4*>(stage + p * KS + k) = o;
           }
         }
       }
       umma::fence_before_sync();
       if (vec_out == 2) umma::fence_proxy_async_smem();  // staging rows -> the bulk copy below
-      if (bar_epi_any(s.abort != 0)) break;
+      bar_epi_any(false);
       const int nlive = min(TM, npix - p0);
       WT* dst = wout + (size_t)p0 * K;
       if (vec_out == 2) {
-        // staging rows are contiguous (KS == K): one bulk copy of the tile's outputs, shared -> global;
-        // its reads of the staging area finish before the barrier below releases it
-        if (tid == 0) {
-          bulk_s2g(dst, stage, (uint32_t)(nlive * K * 4));
-          bulk_wait_read();
-        }
+        // staging rows are contiguous (KS == K): one bulk copy of the tile's outputs, shared -> global; the
+        // next tile waits for its reads before writing the staging rows again
+        if (tid == 0) bulk_s2g(dst, stage, (uint32_t)(nlive * K * 4));
       } else if (vec_out) {  // FP32 with K % 4 == 0 and 16-byte aligned rows
         const int n4 = nlive * K / 4;
         for (int i = tid; i < n4; i += EPI_THREADS) {
@@ -430,10 +480,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           wstore<WT>(dst + i, stage[pp * KS + k]);
         }
       }
-      // the next tile's first epilogue overwrites the staging area
-      if (bar_epi_any(s.abort != 0)) break;
     }
-    if (s.abort && tid == 0) atomicExch(err, 2);
+    if (*abort_flag && tid == 0) atomicExch(err, 2);
     if (vec_out == 2 && tid == 0) bulk_wait_all();  // the last tile's outputs have reached global memory
   }
   umma::fence_before_sync();
