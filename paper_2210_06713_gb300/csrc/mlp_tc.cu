@@ -24,8 +24,8 @@
 // their weights there.
 //
 // Warp roles: warps 0-15 run the epilogues (warp w reads TMEM lanes 32 (w % 4)
-// .. and a quarter of each chunk's columns), warp 16 issues the MMAs, warp 17
-// converts the next tile's fields into X, warp 18 issues the weight copies.
+// .. and a quarter of each chunk's columns), warp 16 issues the MMAs, warps 17
+// and 19 convert the next tile's fields into X, warp 18 issues the weight copies.
 // The epilogues hand each layer over in 64-column chunks (one mbarrier per
 // chunk), so the next layer's MMAs start on a chunk while the epilogue works on
 // the following one; within a chunk the four warps of a lane quarter meet at a
@@ -56,7 +56,8 @@ constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int PRODUCER_WARP = EPI_WARPS;
 constexpr int LOADER_WARP = EPI_WARPS + 1;
 constexpr int COPY_WARP = EPI_WARPS + 2;
-constexpr int THREADS = EPI_THREADS + 96;  // + MMA, loader and copy warps
+constexpr int LOADER_WARP2 = EPI_WARPS + 3;
+constexpr int THREADS = EPI_THREADS + 128;  // + MMA, copy and two loader warps
 constexpr int NRING = 3;
 constexpr int CHUNK_BYTES = HID * 64 * 2;  // one 64-wide K chunk of W2 (the largest)
 constexpr int STAGE_BYTES = TM * 132 * 4;  // FP32 output rows of up to 128 (+4) weights
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       umma::mbar_init(&s.empty[i], 1);
     }
     umma::mbar_init(&s.w1_full, 1);
-    umma::mbar_init(&s.x_ready, 1);
+    umma::mbar_init(&s.x_ready, 2);
     umma::mbar_init(&s.l1_done, 1);
     umma::mbar_init(&s.l2_done, 1);
     umma::mbar_init(&s.l3_done, 1);
@@ -377,8 +378,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         umma::mbar_wait(&s.full[v % NRING], (v / NRING) & 1, kWaitNs);
       umma::mbar_wait(&s.w1_full, 0, kWaitNs);
     }
-  } else if (warp == LOADER_WARP) {
-    // ------------------------------------------------------------ loader: fields -> X (bf16, K-major)
+  } else if (warp == LOADER_WARP || warp == LOADER_WARP2) {
+    // ------------------------------------------------------------ loaders: fields -> X (bf16, K-major); the
+    // two warps take alternate groups of eight fields
+    const int l = warp == LOADER_WARP ? 0 : 1;
     for (int t = 0; t < my_tiles; ++t) {
       // X is free once layer 1 of the previous tile has completed
       if (t >= 1 && !umma::mbar_wait(&s.l1_done, (t - 1) & 1, kWaitNs)) s.abort = 1;
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int p0 = (blockIdx.x + t * gridDim.x) * TM;
       // eight fields at a time for this lane's four pixels (32 loads in flight), packed into the
       // 16-byte rows of the K-major core matrices (fields j..j+7 of one pixel)
-      for (int jg = 0; jg < (J + 7) / 8 && jg < KX / 8; ++jg) {
+      for (int jg = l; jg < (J + 7) / 8 && jg < KX / 8; jg += 2) {
         float v[4][8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
