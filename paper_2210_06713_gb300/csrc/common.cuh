@@ -40,6 +40,11 @@ DFP2S_DEV uint4 philox_at(uint64_t seed, uint64_t sub, uint64_t q) {
                        (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// (float) v for |v| < 2^22 without an integer-to-float conversion instruction
+// (those share the special-function pipe): 1.5 2^23 + v is exact in FP32 and
+// has v in its low mantissa bits, and the subtraction is exact.
+DFP2S_DEV float dfp2s_small_int_to_float(int v) { return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f); }
+
 // ln(u) for a positive normal FP32 u: u = 2^e m with m in [sqrt(1/2), sqrt(2)),
 // ln m = 2 atanh(s) = 2s + s^3 (2/3 + s^2 (2/5 + s^2 (2/7 + s^2 (2/9 + s^2 2/11)))),
 // s = (m-1)/(m+1); e ln 2 with ln 2 split into a 12-bit head and an FP32 tail.
@@ -61,7 +66,7 @@ DFP2S_DEV float dfp2s_log(float u) {
   float t = __fmul_rn(s, s2);
   t = __fmul_rn(t, p);
   const float logm = __fadd_rn(__fadd_rn(s, s), t);
-  const float ef = (float)e;
+  const float ef = dfp2s_small_int_to_float(e);  // |e| <= 149
   float lo = __fmul_rn(ef, 0x1.0bfbe8p-15f);  // ln2 - head
   lo = __fadd_rn(lo, logm);
   const float hi = __fmul_rn(ef, 0x1.62ep-1f);  // head of ln 2 (12 significant bits)
@@ -76,7 +81,7 @@ DFP2S_DEV void dfp2s_sincos_2pi(uint32_t k, float* cs, float* sn) {
   const int32_t num = 2 * (int32_t)k + 1;
   const int32_t q = (num + (1 << 21)) >> 22;
   const int32_t rnum = num - (q << 22);
-  const float r = __fmul_rn((float)rnum, 0x1.0p-22f);
+  const float r = __fmul_rn(dfp2s_small_int_to_float(rnum), 0x1.0p-22f);  // |rnum| <= 2^21
   const float r2 = __fmul_rn(r, r);
   float sp = 0x1.507834p-13f;
   sp = __fadd_rn(__fmul_rn(sp, r2), -0x1.32d2ccp-8f);
@@ -100,8 +105,9 @@ DFP2S_DEV void dfp2s_sincos_2pi(uint32_t k, float* cs, float* sn) {
 
 // Two N(0,1) samples from two Philox words: r = sqrt(-2 ln u_a), angle 2 pi u_b.
 DFP2S_DEV float2 dfp2s_box_muller(uint32_t wa, uint32_t wb) {
+  // u = (2 ka + 1) 2^-24 = (1 + ka 2^-23) - (1 - 2^-24), exact (Sterbenz)
   const uint32_t ka = wa >> 9;
-  const float ua = __fmul_rn((float)(2u * ka + 1u), 0x1.0p-24f);
+  const float ua = __fsub_rn(__uint_as_float(0x3F800000u | ka), 0x1.fffffep-1f);
   const float t = __fmul_rn(dfp2s_log(ua), -2.0f);
   const float r = __fsqrt_rn(t);
   float c, s;
