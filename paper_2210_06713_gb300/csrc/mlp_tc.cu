@@ -7,8 +7,8 @@
 // Q = the other:
 //   layer 1: X [128 x 48] (the J fields, zero-padded) x W1'^T + b1 -> P
 //            (W1' = W1 diag(in_scale), resident in shared memory)
-//   2 GELU(z) -> H1 (BF16), written back into P: chunk c of 64 columns keeps its
-//            activations in its first 32 columns (two per column)
+//   2 GELU(z) -> H1 (BF16), written back into P: each 16-column quarter of a
+//            64-column chunk keeps its 16 activations in its first 8 columns
 //   layer 2: H1 (A operand from tensor memory) x (W2 / 2)^T + b2 -> Q, W2 streamed
 //            in four 64-wide K chunks
 //   2 GELU(z) -> H2 in Q, the same way
@@ -28,11 +28,10 @@
 // and 19 convert the next tile's fields into X, warp 18 issues the weight copies.
 // The epilogues hand each layer over in 64-column chunks (one mbarrier per
 // chunk), so the next layer's MMAs start on a chunk while the epilogue works on
-// the following one; within a chunk the four warps of a lane quarter meet at a
-// named barrier between reading the accumulators and writing the activations
-// over them.  Layer 1 of the next tile runs on the tensor cores while the
-// epilogues write out the current tile.  Weight chunks arrive by 1-D bulk
-// copies into a three-deep ring; their MMAs release a slot through
+// the following one; every warp writes its activations only over accumulator
+// columns it has read itself.  Layer 1 of the next tile runs on the tensor
+// cores while the epilogues write out the current tile.  Weight chunks arrive
+// by 1-D bulk copies into a three-deep ring; their MMAs release a slot through
 // tcgen05.commit.  The copies have a warp of their own because a bulk copy can
 // hold its issuing thread until the copy engine takes it, which would stall the
 // MMA issue.  All waits are bounded; a wait that runs out sets the kernel's
@@ -118,21 +117,6 @@ DFP2S_DEV bool bar_epi_any(bool v) {
   return r != 0;
 }
 
-// Barrier of the four epilogue warps that share TMEM lane quarter q4 (named
-// barrier 2 + q4, 128 threads), ORing a flag over them like bar_epi_any.
-DFP2S_DEV bool bar_quarter_any(int q4, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, %2, 128, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(2 + q4)
-      : "memory");
-  return r != 0;
-}
-
 // 1-D bulk copy shared -> global (both 16-byte aligned, size a multiple of 16) in a bulk group; wait until
 // its source may be overwritten, or until every issued copy has completed.
 DFP2S_DEV void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
@@ -174,24 +158,21 @@ DFP2S_DEV void tmem_wait16(float (&v)[16]) {
 
 // Hidden-layer epilogue of one epilogue warp (lane quarter q4, slice sl): for
 // each 64-column chunk c of the 256-column region R, this warp's 16 columns
-// [64 c + 16 sl, +16) (biases included) -> 2 GELU -> BF16 pairs written over
-// columns [64 c + 8 sl, +8) of the same lanes (chunk c's activations in its first
-// 32 columns, K = 16 sl .. 16 sl + 15 of the chunk), then the chunk is handed to
-// the MMA warp.  The four warps of the quarter have all read the chunk before any
-// of them writes (quarter barrier, which also makes `skip` uniform over them);
-// the next chunk's load is in flight meanwhile.  Every warp of the quarter calls
-// this the same number of times.  Returns the skip decision.
-DFP2S_DEV bool epilogue_gelu(Smem& s, uint32_t R, int warp, int lane, bool skip) {
+// [64 c + 16 sl, +16) (biases included) -> 2 GELU -> 8 columns of BF16 pairs
+// written over the first 8 of those same columns (so no other warp reads what
+// it writes), then the chunk is handed to the MMA warp.  Chunk c's K = 16 step
+// ks therefore sits in columns [64 c + 16 ks, +8).  The next chunk's load is in
+// flight meanwhile.
+DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t R, int warp, int lane, bool skip) {
   const int q4 = warp & 3, sl = warp >> 2;
-  const uint32_t base = R + ((uint32_t)(q4 * 32) << 16);
+  const uint32_t base = R + ((uint32_t)(q4 * 32) << 16) + 16 * sl;
   float d[2][16];
-  tmem_ld16_async(base + 16 * sl, d[0]);
+  tmem_ld16_async(base, d[0]);
   tmem_wait16(d[0]);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     float(&cur)[16] = d[c & 1];
-    skip = bar_quarter_any(q4, skip);  // every warp of the quarter has read chunk c
-    if (c < 3) tmem_ld16_async(base + 64 * (c + 1) + 16 * sl, d[(c + 1) & 1]);
+    if (c < 3) tmem_ld16_async(base + 64 * (c + 1), d[(c + 1) & 1]);
     if (!skip) {
       uint32_t packed[8];
 #pragma unroll
@@ -199,7 +180,7 @@ DFP2S_DEV bool epilogue_gelu(Smem& s, uint32_t R, int warp, int lane, bool skip)
         __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu2x(cur[2 * e]), gelu2x(cur[2 * e + 1]));
         packed[e] = *reinterpret_cast<uint32_t*>(&h2);
       }
-      umma::tmem_st8(base + 64 * c + 8 * sl, packed);
+      umma::tmem_st8(base + 64 * c, packed);
       umma::tmem_wait_st();
     }
     umma::fence_before_sync();  // TMEM reads and writes ordered before the hand-over
@@ -207,7 +188,6 @@ DFP2S_DEV bool epilogue_gelu(Smem& s, uint32_t R, int warp, int lane, bool skip)
     if (lane == 0) umma::mbar_arrive(&s.h_ready[c]);
     if (c < 3) tmem_wait16(d[(c + 1) & 1]);
   }
-  return skip;
 }
 
 template <typename WT, bool SCALED>
@@ -272,8 +252,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t idesc3 = umma::idesc_bf16(TM, NP3);
       uint32_t u_use = 0;
       bool ok = true;
-      // MMAs of one 64-wide K chunk: weight chunk u in the ring against the activations of chunk c, which
-      // sit in the first 32 columns of the chunk at tensor-memory address a (8 columns per K = 16 step)
+      // MMAs of one 64-wide K chunk: weight chunk u in the ring against the activations of the chunk that
+      // starts at tensor-memory address a (K = 16 step ks in columns [a + 16 ks, +8))
       auto chunk_mmas = [&](uint32_t u, uint32_t a, uint32_t d, uint32_t id, bool first) {
         const int b = u % NRING;
         if (!umma::mbar_wait(&s.full[b], (u / NRING) & 1, kWaitNs)) {
@@ -283,7 +263,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         umma::fence_after_sync();
         const uint64_t b_c = ring_desc + (uint64_t)(b * (CHUNK_BYTES >> 4));
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) umma::mma_bf16_ta(d, a + 8 * ks, b_c + 16 * ks, id, !(first && ks == 0));
+        for (int ks = 0; ks < 4; ++ks) umma::mma_bf16_ta(d, a + 16 * ks, b_c + 16 * ks, id, !(first && ks == 0));
         umma::mma_commit(&s.empty[b]);
       };
       if (my_tiles > 0 && !umma::mbar_wait(&s.w1_full, 0, kWaitNs)) ok = false;
@@ -428,14 +408,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int tile = blockIdx.x + t * gridDim.x;
       const int p0 = tile * TM;
       const uint32_t P = tmem + ((t & 1) ? 256u : 0u), Q = tmem + ((t & 1) ? 0u : 256u);
-      // every warp runs both epilogues (their quarter barriers); a failed wait turns the work off
+      // a failed wait turns the work off (the hand-overs still happen)
       bool skip = *abort_flag != 0;
       if (!skip && !umma::mbar_wait_backoff(&s.l1_done, t & 1, kWaitNs)) skip = true;
       umma::fence_after_sync();
-      skip = epilogue_gelu(s, P, warp, lane, skip);
+      epilogue_gelu(s, P, warp, lane, skip);
       if (!skip && !umma::mbar_wait_backoff(&s.l2_done, t & 1, kWaitNs)) skip = true;
       umma::fence_after_sync();
-      skip = epilogue_gelu(s, Q, warp, lane, skip);
+      epilogue_gelu(s, Q, warp, lane, skip);
       if (!skip && !umma::mbar_wait_backoff(&s.l3_done, t & 1, kWaitNs)) skip = true;
       umma::fence_after_sync();
       if (skip) *abort_flag = 1;
