@@ -265,7 +265,7 @@ def run_ours(args, rank, world, device):
         flops = 2.0 * 1089 * K * C * npix
         # DRAM bytes per launch from the committed ncu capture of this kernel on this workload
         # (profiles/kernels_512x512x3_learned.md); none for other workloads
-        traffic = 124.6e6 if args.workload == "512" else None
+        traffic = 124.2e6 if args.workload == "512" else None
         roof = {"kernel": "k_blur_tc", "bound": "tensor", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
                 "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": traffic,
                 "peak_source": peak_kind + " (burst bf16 GEMM)"}
