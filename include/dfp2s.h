@@ -226,6 +226,16 @@ typedef struct {
 } dfp2s_mlp_train_params;
 int dfp2s_mlp_train(dfp2s_p2s* p, const dfp2s_factor* f, const dfp2s_mlp_train_params* tp, float* report_host,
                     float* params_out_host, void* stream);
+/* Network files: the installed network, as dfp2s_p2s_set_mlp takes it, to a
+ * host file and back.  Format: the 8 bytes "DFP2SMLP", uint32 version 1,
+ * int32 J, int32 K, then W1 (256 x J), b1 (256), W2 (256 x 256), b2 (256),
+ * W3 (K x 256), b3 (K), in_scale (J), out_scale (K), out_shift (K) as
+ * little-endian float32, nothing after.  _save: EINVAL without an installed
+ * network or when the file cannot be written; _load: EINVAL when the file
+ * cannot be read or is not a network for this handle's J and K, then as
+ * dfp2s_p2s_set_mlp.  Synchronous.  Errors: EINVAL, ECUDA. */
+int dfp2s_mlp_save(const dfp2s_p2s* p, const char* path);
+int dfp2s_mlp_load(dfp2s_p2s* p, const char* path);
 /* Number of FP32 parameters of the J -> 256 -> 256 -> K network. */
 int dfp2s_mlp_param_count(int J, int K);
 /* One forward/backward pass on a given batch (for gradient checks): X (B x J)

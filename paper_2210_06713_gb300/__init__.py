@@ -59,6 +59,8 @@ SIGNATURES = {
     "dfp2s_p2s_destroy": (_i, [_vp]),
     "dfp2s_p2s_check": (_i, [_vp]),
     "dfp2s_p2s_set_mlp": (_i, [_vp] + [_vp] * 9),
+    "dfp2s_mlp_save": (_i, [_vp, _c.c_char_p]),
+    "dfp2s_mlp_load": (_i, [_vp, _c.c_char_p]),
     "dfp2s_mlp_train": (_i, [_vp, _vp, _c.POINTER(TrainParams), _vp, _vp, _vp]),
     "dfp2s_mlp_param_count": (_i, [_i, _i]),
     "dfp2s_mlp_loss_grad": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -261,6 +263,15 @@ class P2S:
         ts = [torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
               for t in (W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift)]
         _check(load().dfp2s_p2s_set_mlp(self._h, *[_ptr(t) for t in ts]))
+        self.has_mlp = True
+
+    def save_mlp(self, path: str) -> None:
+        """Write the installed network to a file (include/dfp2s.h: dfp2s_mlp_save)."""
+        _check(load().dfp2s_mlp_save(self._h, os.fsencode(path)))
+
+    def load_mlp(self, path: str) -> None:
+        """Install the network stored in a file by save_mlp."""
+        _check(load().dfp2s_mlp_load(self._h, os.fsencode(path)))
         self.has_mlp = True
 
     def check(self):

@@ -312,6 +312,69 @@ extern "C" int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1,
   return dfp2s_p2s_install_mlp(&p->d, W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift);
 }
 
+// ---- network files
+static const char kMlpMagic[8] = {'D', 'F', 'P', '2', 'S', 'M', 'L', 'P'};
+
+extern "C" int dfp2s_mlp_save(const dfp2s_p2s* p, const char* path) {
+  CHECK_ARG(p && path, "null argument");
+  const dfp2s_p2s_dev& d = p->d;
+  CHECK_ARG(d.has_mlp, "no surrogate network installed");
+  const int J = d.J, K = d.K;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return dfp2s_fail_cuda(e, "network save");
+  // the handle keeps W1, W2, W3 transposed; the file holds them as dfp2s_p2s_set_mlp takes them
+  auto fetch = [&](const float* src, size_t n, std::vector<float>& h) {
+    h.resize(n);
+    return cudaMemcpy(h.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost);
+  };
+  auto untranspose = [](const std::vector<float>& t, int rows, int cols) {  // t is cols x rows
+    std::vector<float> h((size_t)rows * cols);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) h[(size_t)r * cols + c] = t[(size_t)c * rows + r];
+    return h;
+  };
+  std::vector<float> w1t, b1, w2t, b2, w3t, b3, isc, osc, osh;
+  if ((e = fetch(d.W1, (size_t)256 * J, w1t)) != cudaSuccess || (e = fetch(d.b1, 256, b1)) != cudaSuccess ||
+      (e = fetch(d.W2, (size_t)256 * 256, w2t)) != cudaSuccess || (e = fetch(d.b2, 256, b2)) != cudaSuccess ||
+      (e = fetch(d.W3, (size_t)K * 256, w3t)) != cudaSuccess || (e = fetch(d.b3, K, b3)) != cudaSuccess ||
+      (e = fetch(d.in_scale, J, isc)) != cudaSuccess || (e = fetch(d.out_scale, K, osc)) != cudaSuccess ||
+      (e = fetch(d.out_shift, K, osh)) != cudaSuccess)
+    return dfp2s_fail_cuda(e, "network save");
+  const std::vector<float> W1 = untranspose(w1t, 256, J), W2 = untranspose(w2t, 256, 256),
+                           W3 = untranspose(w3t, K, 256);
+  FILE* fp = fopen(path, "wb");
+  CHECK_ARG(fp, "cannot write %s", path);
+  const uint32_t version = 1;
+  const int32_t jk[2] = {J, K};
+  bool ok = fwrite(kMlpMagic, 1, 8, fp) == 8 && fwrite(&version, 4, 1, fp) == 1 && fwrite(jk, 4, 2, fp) == 2;
+  const std::vector<float>* parts[] = {&W1, &b1, &W2, &b2, &W3, &b3, &isc, &osc, &osh};
+  for (const std::vector<float>* v : parts) ok = ok && fwrite(v->data(), sizeof(float), v->size(), fp) == v->size();
+  ok = (fclose(fp) == 0) && ok;
+  CHECK_ARG(ok, "short write to %s", path);
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_mlp_load(dfp2s_p2s* p, const char* path) {
+  CHECK_ARG(p && path, "null argument");
+  const int J = p->d.J, K = p->d.K;
+  FILE* fp = fopen(path, "rb");
+  CHECK_ARG(fp, "cannot read %s", path);
+  char magic[8];
+  uint32_t version = 0;
+  int32_t jk[2] = {0, 0};
+  bool ok = fread(magic, 1, 8, fp) == 8 && fread(&version, 4, 1, fp) == 1 && fread(jk, 4, 2, fp) == 2 &&
+            memcmp(magic, kMlpMagic, 8) == 0 && version == 1 && jk[0] == J && jk[1] == K;
+  std::vector<float> W1((size_t)256 * J), b1(256), W2((size_t)256 * 256), b2(256), W3((size_t)K * 256), b3(K),
+      isc(J), osc(K), osh(K);
+  std::vector<float>* parts[] = {&W1, &b1, &W2, &b2, &W3, &b3, &isc, &osc, &osh};
+  for (std::vector<float>* v : parts) ok = ok && fread(v->data(), sizeof(float), v->size(), fp) == v->size();
+  ok = ok && fgetc(fp) == EOF;
+  fclose(fp);
+  CHECK_ARG(ok, "%s is not a J = %d, K = %d network file", path, J, K);
+  return dfp2s_p2s_install_mlp(&p->d, W1.data(), b1.data(), W2.data(), b2.data(), W3.data(), b3.data(), isc.data(),
+                               osc.data(), osh.data());
+}
+
 extern "C" int dfp2s_mlp_param_count(int J, int K) {
   CHECK_ARG(J >= 3 && J <= DFP2S_MAX_J && K >= 1 && K <= DFP2S_MAX_K, "J/K out of range");
   return (int)dfp2s_mlp_nparams(J, K);

@@ -335,6 +335,35 @@ def test_learned_frame_folds_the_mixing_into_warp_and_first_layer(lib, d):
         assert e < 3e-3, e
 
 
+def test_network_file_round_trip(lib, tmp_path):
+    J, K = 36, 100
+    rng = np.random.default_rng(2)
+    prm = [rng.standard_normal((256, J)) / 6, rng.standard_normal(256) * 0.1, rng.standard_normal((256, 256)) / 16,
+           rng.standard_normal(256) * 0.1, rng.standard_normal((K, 256)) / 16, rng.standard_normal(K) * 0.1,
+           rng.uniform(0.5, 2.0, J), rng.uniform(0.01, 0.05, K), rng.standard_normal(K) * 0.01]
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
+    P = lib.P2S(J, cu(basis))
+    path = str(tmp_path / "net.bin")
+    with pytest.raises(lib.DFP2SError):
+        P.save_mlp(path)  # nothing installed
+    P.set_mlp(*[cu(x) for x in prm])
+    P.save_mlp(path)
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"DFP2SMLP" and len(raw) == 20 + 4 * (256 * J + 256 + 256 * 256 + 256 + 256 * K + K + J + 2 * K)
+    body = np.frombuffer(raw[20:], dtype="<f4")
+    assert np.array_equal(body[:256 * J], prm[0].astype(np.float32).ravel())  # W1 as given
+    Q = lib.P2S(J, cu(basis))
+    Q.load_mlp(path)
+    a = cu(synthetic.random_fields(J, 40, 24, scale=0.5, seed=3))
+    for mode in (lib.P2S_LEARNED, lib.P2S_LEARNED_FP32):
+        assert torch.equal(lib.p2s_weights(P, mode, a), lib.p2s_weights(Q, mode, a))
+    with pytest.raises(lib.DFP2SError):
+        lib.P2S(J - 1, cu(basis)).load_mlp(path)  # another J
+    open(str(tmp_path / "short.bin"), "wb").write(raw[:-4])
+    with pytest.raises(lib.DFP2SError):
+        Q.load_mlp(str(tmp_path / "short.bin"))
+
+
 def test_frame_stage_timing(lib):
     J, K, H, W, N = 36, 16, 64, 48, 128
     basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
