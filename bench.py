@@ -227,6 +227,29 @@ def run_ours(args, rank, world, device):
         oms = o0.elapsed_time(o1) / n_other
         other_line = {"p2s": "exact" if other == d.P2S_EXACT else "learned", "frames_per_s": 1e3 / oms,
                       "ms_per_frame": oms, "frames": n_other}
+    # field statistics (Sec. III-D): lagged covariances of one frame's fields at four lags, FP32 FMA-bound
+    stat = None
+    try:
+        fl = d.sample_zernike_fields(S["factor"], S["dlist"][0], seed_base + 3, 0, H, W)
+        lags = [(0, 0), (0, 1), (1, 0), (4, -4)]
+        d.field_covariance(fl, lags)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(5):
+            d.field_covariance(fl, lags)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = s0.elapsed_time(s1) / 5
+        fmas = float(J * J) * sum((H - abs(a)) * (W - abs(b)) for a, b in lags)
+        clk = _peaks()[0].get("sm_max_mhz", 2070.0)
+        alu = 152 * 128 * 2 * clk * 1e6 / 1e12
+        stat = {"what": "dfp2s_field_covariance, J x J at 4 lags of one frame's fields", "ms": sms,
+                "achieved_tflops": 2 * fmas / (sms * 1e-3) / 1e12, "alu_peak_tflops": alu,
+                "frac": 2 * fmas / (sms * 1e-3) / 1e12 / alu}
+        del fl
+    except RuntimeError as exc:
+        stat = {"unavailable": str(exc).splitlines()[0][:120]}
     # cuFFT (through torch.fft) on the field sampler's transforms, as a comparison: J real N x N noise planes ->
     # R2C 2-D FFT -> spectral multiply -> C2R 2-D inverse FFT, cropped to H x W (no noise, no mixing)
     cufft = None
@@ -328,6 +351,7 @@ def run_ours(args, rank, world, device):
         "gpu_launches": args.steps * (5 if args.mode == "learned" else 6),
         "other_p2s": other_line,
         "cufft_fields_comparison": cufft,
+        "field_statistics": stat,
         "setup": S["info"],
         "clocks": clk,
         "wall_s": wall,

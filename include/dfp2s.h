@@ -313,6 +313,20 @@ int dfp2s_tilt_warp_blur_tc_prepare(const dfp2s_p2s* p, const float* img_dev, in
 int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void* w_dev, int w_dtype, float* out_dev,
                             void* stream);
 
+/* ------------------------------------------------------------ statistics
+ * Lagged covariances of J x H x W fields (Sec. III-D: the sampled fields'
+ * covariance at separation s is A~(s) of Eq. (A tilde), A_0 at s = 0):
+ *   out[l][i][j] = (1/n_l) sum over x with x + d_l inside the frame of
+ *                  a_i(x) a_j(x + d_l),   d_l = (lags[2l], lags[2l+1]) = (dy, dx),
+ *   n_l = (H - |dy|)(W - |dx|).
+ * fields_dev: J x H x W float32 (device); lags_host: 2 n_lags ints (host);
+ * out_dev: n_lags x J x J doubles (device, row-major).  Products and runs of
+ * 32 pixels in FP32, everything else in FP64, in a fixed order (the result does
+ * not depend on the launch).  1 <= J <= 64, 1 <= n_lags <= 64, |dy| < H,
+ * |dx| < W.  Errors: EINVAL, ENOMEM, ECUDA. */
+int dfp2s_field_covariance(const float* fields_dev, int J, int H, int W, const int* lags_host, int n_lags,
+                           double* out_dev, void* stream);
+
 /* ---------------------------------------------------------------- frames
  * A context binds a factor and a P2S handle and owns the per-frame scratch
  * (fields, warped image, weights) for frames up to max_C x max_H x max_W. */

@@ -23,4 +23,5 @@ Modules
   image     tilt warp and basis blur (Eq. 1, Eq. varying blur)
   mlp       the P2S surrogate network, forward/backward/Adam in FP64
   frame     the whole frame, step by step
+  stats     lagged covariances of fields and their expectation A~(s) (Sec. III-D)
 """

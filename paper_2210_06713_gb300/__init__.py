@@ -60,6 +60,7 @@ SIGNATURES = {
     "dfp2s_p2s_check": (_i, [_vp]),
     "dfp2s_p2s_set_mlp": (_i, [_vp] + [_vp] * 9),
     "dfp2s_mlp_save": (_i, [_vp, _c.c_char_p]),
+    "dfp2s_field_covariance": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dfp2s_mlp_load": (_i, [_vp, _c.c_char_p]),
     "dfp2s_mlp_train": (_i, [_vp, _vp, _c.POINTER(TrainParams), _vp, _vp, _vp]),
     "dfp2s_mlp_param_count": (_i, [_i, _i]),
@@ -346,6 +347,16 @@ def p2s_weights(p: P2S, mode: int, fields: torch.Tensor, w_dtype: int = W_F32, o
     if out is None:
         out = torch.empty(H, W, p.K, dtype=torch.float32 if w_dtype == W_F32 else torch.bfloat16, device="cuda")
     _check(load().dfp2s_p2s_weights(p.handle, mode, _ptr(fields), H, W, _ptr(out), w_dtype, _stream(stream)))
+    return out
+
+
+def field_covariance(fields: torch.Tensor, lags, stream=None) -> torch.Tensor:
+    """Lagged covariances (n_lags x J x J, float64, device) of J x H x W fields; lags = [(dy, dx), ...]."""
+    J, H, W = fields.shape
+    flat = (ctypes.c_int * (2 * len(lags)))(*[int(v) for lag in lags for v in lag])
+    out = torch.empty(len(lags), J, J, device=fields.device, dtype=torch.float64)
+    _check(load().dfp2s_field_covariance(_ptr(fields), J, H, W, ctypes.cast(flat, ctypes.c_void_p), len(lags),
+                                         _ptr(out), _stream(stream)))
     return out
 
 

@@ -312,6 +312,22 @@ extern "C" int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1,
   return dfp2s_p2s_install_mlp(&p->d, W1, b1, W2, b2, W3, b3, in_scale, out_scale, out_shift);
 }
 
+// ---- statistics
+extern "C" int dfp2s_field_covariance(const float* fields, int J, int H, int W, const int* lags, int n_lags,
+                                      double* out, void* stream) {
+  CHECK_ARG(fields && lags && out, "null argument");
+  CHECK_ARG(J >= 1 && J <= DFP2S_MAX_J && H >= 1 && W >= 1 && (long long)H * W <= (1LL << 31),
+            "field shape %d x %d x %d out of range", J, H, W);
+  CHECK_ARG(n_lags >= 1 && n_lags <= 64, "%d lags out of range", n_lags);
+  for (int l = 0; l < n_lags; ++l)
+    CHECK_ARG(abs(lags[2 * l]) < H && abs(lags[2 * l + 1]) < W, "lag (%d, %d) does not fit %d x %d", lags[2 * l],
+              lags[2 * l + 1], H, W);
+  const int rc = dfp2s_launch_field_covariance(fields, J, H, W, lags, n_lags, out, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "covariance scratch allocation");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "field covariance");
+  return DFP2S_OK;
+}
+
 // ---- network files
 static const char kMlpMagic[8] = {'D', 'F', 'P', '2', 'S', 'M', 'L', 'P'};
 

@@ -97,6 +97,10 @@ size_t dfp2s_mlp_tc_w1_elems();
 int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st,
                         const __nv_bfloat16* w1 = nullptr, float xscale = 1.f);
 
+// stats.cu -- lagged covariances of fields (lags_host: n_lags (dy, dx) pairs; out: n_lags x J x J FP64, device)
+int dfp2s_launch_field_covariance(const float* a, int J, int H, int W, const int* lags_host, int n_lags, double* out,
+                                  cudaStream_t st);
+
 // basis.cu -- FP64 SVD basis of exact PSFs
 int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const double* dr_host, int n_dr, uint64_t seed,
                              float* basis_out, double* sigma_host, int* sweeps_out, cudaStream_t st);
