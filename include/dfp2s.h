@@ -320,9 +320,10 @@ int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void*
  *                  a_i(x) a_j(x + d_l),   d_l = (lags[2l], lags[2l+1]) = (dy, dx),
  *   n_l = (H - |dy|)(W - |dx|).
  * fields_dev: J x H x W float32 (device); lags_host: 2 n_lags ints (host);
- * out_dev: n_lags x J x J doubles (device, row-major).  Products and runs of
- * 32 pixels in FP32, everything else in FP64, in a fixed order (the result does
- * not depend on the launch).  1 <= J <= 64, 1 <= n_lags <= 64, |dy| < H,
+ * out_dev: n_lags x J x J doubles (device, row-major).  Products, runs of 32
+ * pixels and each block's compensated (Kahan) sum of its runs in FP32, the
+ * blocks' partials in FP64, all in a fixed order (the result does not depend on
+ * the launch).  1 <= J <= 64, 1 <= n_lags <= 64, |dy| < H,
  * |dx| < W.  Errors: EINVAL, ENOMEM, ECUDA. */
 int dfp2s_field_covariance(const float* fields_dev, int J, int H, int W, const int* lags_host, int n_lags,
                            double* out_dev, void* stream);

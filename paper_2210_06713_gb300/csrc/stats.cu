@@ -6,8 +6,11 @@
 //
 // One block row per lag: each block takes runs of 32 valid pixels (a grid-stride
 // walk over them), stages a(x) and a(x + d) for the run in shared memory, and
-// each thread accumulates its (i, j) pairs: products and the run's sum in FP32,
-// the runs in FP64.  A second kernel sums the blocks' partials in a fixed order.
+// each thread accumulates a 4 x 4 register tile of (i, j) pairs (i = ti + 16 m,
+// j = tj + 16 n for thread (ti, tj) of a 16 x 16 arrangement): products and the
+// run's sum in FP32, the runs in FP32 with Kahan compensation (FP64 arithmetic
+// is a small fraction of the FP32 rate on this part).  A second kernel sums the
+// blocks' partials in FP64 in a fixed order.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -17,10 +20,9 @@ namespace {
 
 constexpr int RUN = 32;
 constexpr int THREADS = 256;
-constexpr int MAXPAIRS = DFP2S_MAX_J * DFP2S_MAX_J;
-constexpr int PPT = MAXPAIRS / THREADS;  // pairs per thread at most (16)
+constexpr int T4 = DFP2S_MAX_J / 16;  // register tile side (4)
 
-__global__ void __launch_bounds__(THREADS) k_cov_partial(const float* __restrict__ a, int J, int H, int W,
+__global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restrict__ a, int J, int H, int W,
                                                          const int2* __restrict__ lags, int nb,
                                                          double* __restrict__ part) {
   // [pixel][field], rows padded to an odd stride: the staging writes walk the pixels, the sums walk the fields
@@ -33,41 +35,77 @@ __global__ void __launch_bounds__(THREADS) k_cov_partial(const float* __restrict
   const long long runs = (n + RUN - 1) / RUN;
   const size_t plane = (size_t)H * W;
   const int npairs = J * J;
-  double acc[PPT];
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  float acc[T4][T4], cmp[T4][T4];  // compensated sums over the runs
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) acc[k] = 0.0;
+  for (int m = 0; m < T4; ++m)
+#pragma unroll
+    for (int k = 0; k < T4; ++k) acc[m][k] = cmp[m][k] = 0.f;
+  // staging role of this thread: pixel q of a run for fields jg, jg + 8, ... (up to 8 of them); the next run's
+  // values are loaded into registers while the current one is summed
+  const int q = threadIdx.x & (RUN - 1), jg = threadIdx.x / RUN;
+  constexpr int NJ = DFP2S_MAX_J / (THREADS / RUN);
+  float nx_[NJ], ny_[NJ];
+  auto load_run = [&](long long r) {
+    const long long p = r * RUN + q;
+    const bool in = r < runs && p < n;
+    const int pi = in ? (int)p : 0;  // n < 2^31
+    const int yy = pi / nx, xx = pi - yy * nx;
+    const size_t o1 = (size_t)(y0 + yy) * W + (x0 + xx);
+    const size_t o2 = (size_t)(y0 + yy + d.x) * W + (x0 + xx + d.y);
+#pragma unroll
+    for (int e = 0; e < NJ; ++e) {
+      const int j = jg + e * (THREADS / RUN);
+      nx_[e] = (in && j < J) ? a[j * plane + o1] : 0.f;
+      ny_[e] = (in && j < J) ? a[j * plane + o2] : 0.f;
+    }
+  };
+  load_run(blockIdx.x);
   for (long long r = blockIdx.x; r < runs; r += nb) {
     __syncthreads();  // the previous run's reads are done
-    for (int e = threadIdx.x; e < J * RUN; e += THREADS) {
-      const int j = e / RUN, q = e - j * RUN;
-      const long long p = r * RUN + q;
-      float u = 0.f, v = 0.f;
-      if (p < n) {
-        const int y = y0 + (int)(p / nx), x = x0 + (int)(p % nx);
-        u = a[j * plane + (size_t)y * W + x];
-        v = a[j * plane + (size_t)(y + d.x) * W + (x + d.y)];
-      }
-      xs[q][j] = u;
-      ys[q][j] = v;
+#pragma unroll
+    for (int e = 0; e < NJ; ++e) {
+      xs[q][jg + e * (THREADS / RUN)] = nx_[e];
+      ys[q][jg + e * (THREADS / RUN)] = ny_[e];
     }
     __syncthreads();
+    load_run(r + nb);
+    float sm[T4][T4];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int pr = threadIdx.x + k * THREADS;
-      if (pr < npairs) {
-        const int i = pr / J, j = pr - i * J;
-        float s = 0.f;
-#pragma unroll 8
-        for (int q = 0; q < RUN; ++q) s = fmaf(xs[q][i], ys[q][j], s);
-        acc[k] += (double)s;
-      }
+    for (int m = 0; m < T4; ++m)
+#pragma unroll
+      for (int k = 0; k < T4; ++k) sm[m][k] = 0.f;
+    const int nm = (J - ti + 15) / 16, nk = (J - tj + 15) / 16;  // tile rows / columns inside J
+#pragma unroll 4
+    for (int qq = 0; qq < RUN; ++qq) {
+      float xv[T4], yv[T4];
+#pragma unroll
+      for (int m = 0; m < T4; ++m) xv[m] = m < nm ? xs[qq][ti + 16 * m] : 0.f;
+#pragma unroll
+      for (int k = 0; k < T4; ++k) yv[k] = k < nk ? ys[qq][tj + 16 * k] : 0.f;
+#pragma unroll
+      for (int m = 0; m < T4; ++m)
+#pragma unroll
+        for (int k = 0; k < T4; ++k) sm[m][k] = fmaf(xv[m], yv[k], sm[m][k]);
     }
+#pragma unroll
+    for (int m = 0; m < T4; ++m)
+#pragma unroll
+      for (int k = 0; k < T4; ++k) {
+        const float y = __fsub_rn(sm[m][k], cmp[m][k]);
+        const float t = __fadd_rn(acc[m][k], y);
+        cmp[m][k] = __fsub_rn(__fsub_rn(t, acc[m][k]), y);
+        acc[m][k] = t;
+      }
   }
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int pr = threadIdx.x + k * THREADS;
-    if (pr < npairs) part[((size_t)l * nb + blockIdx.x) * npairs + pr] = acc[k];
-  }
+  for (int m = 0; m < T4; ++m)
+#pragma unroll
+    for (int k = 0; k < T4; ++k) {
+      const int i = ti + 16 * m, j = tj + 16 * k;
+      if (i < J && j < J)
+        part[((size_t)l * nb + blockIdx.x) * npairs + i * J + j] = (double)acc[m][k] - (double)cmp[m][k];
+    }
 }
 
 __global__ void k_cov_reduce(const double* __restrict__ part, int nb, int npairs, const int2* __restrict__ lags,
