@@ -398,6 +398,34 @@ def test_simulate_frame_exact_small_workload(lib):
     assert rel_l2(g, o["out"]) < TOL
 
 
+def test_exact_frame_full_size_sampled(lib):
+    # the 512 x 512 x 3 workload (J = 36, N = 1024, K = 100) in the frame call the bench times (exact P2S and the
+    # FP32 blur), against the oracle at sampled pixels: corners, edges and interior, each from the oracle's fields,
+    # warp, per-pixel pupil-FFT weights and the blur sum written out over the 33 x 33 window
+    from oracle import image as oimage
+    J, K, H, W, N, d, seed, frame = 36, 100, 512, 512, 1024, 2.0, 17, 3
+    img = synthetic.shapes(H, W, 3, seed=5)
+    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=2).reshape(K, 33, 33)
+    f = lib.SpectralFactor(J, N, 8.0)
+    P = lib.P2S(J, cu(basis))
+    sim = lib.Simulator(f, P, 3, H, W)
+    g = sim.simulate_frame(cu(img), d, seed, frame, lib.P2S_EXACT).cpu().numpy()
+    a = sampler.sample_fields(seed, frame, J, H, W, d, 8.0, N)
+    warped = oimage.tilt_warp(img, a[0], a[1])
+    rng = np.random.default_rng(0)
+    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (5, 300), (300, 7), (H - 3, 200), (128, W - 2)]
+    pts += [tuple(p) for p in rng.integers(0, [H, W], size=(24, 2))]
+    u = np.arange(-16, 17)
+    got, ref = [], []
+    for y, x in pts:
+        w = p2s.weights(a[:, y, x], J, basis)  # K
+        win = warped[:, np.clip(y - u, 0, H - 1)][:, :, np.clip(x - u, 0, W - 1)]  # C x 33 x 33: I(y - uy, x - ux)
+        h = np.tensordot(w, basis, axes=1)  # the pixel's PSF, 33 x 33 over (uy, ux)
+        ref.append((win * h[None]).sum(axis=(1, 2)))
+        got.append(g[:, y, x])
+    assert rel_l2(np.array(got), np.array(ref)) < TOL
+
+
 def test_bad_arguments_return_einval(lib):
     f = lib.SpectralFactor(6, 16, 2.0)
     with pytest.raises(lib.DFP2SError) as e:
