@@ -242,8 +242,8 @@ def run_ours(args, rank, world, device):
         torch.cuda.synchronize()
         sms = s0.elapsed_time(s1) / 5
         fmas = float(J * J) * sum((H - abs(a)) * (W - abs(b)) for a, b in lags)
-        clk = _peaks()[0].get("sm_max_mhz", 2070.0)
-        alu = 152 * 128 * 2 * clk * 1e6 / 1e12
+        mhz = _peaks()[0].get("sm_max_mhz", 2070.0)
+        alu = 152 * 128 * 2 * mhz * 1e6 / 1e12
         stat = {"what": "dfp2s_field_covariance, J x J at 4 lags of one frame's fields", "ms": sms,
                 "achieved_tflops": 2 * fmas / (sms * 1e-3) / 1e12, "alu_peak_tflops": alu,
                 "frac": 2 * fmas / (sms * 1e-3) / 1e12 / alu}
