@@ -145,6 +145,54 @@ def accuracy_vs_exact(d, S, seed):
     return out
 
 
+def stage_roofline(name, ms, args, peaks, peak_kind, H, W, C, K):
+    """Roofline of one single-launch stage of the frame (its CUDA events bracket one kernel launch)."""
+    npix = H * W
+    learned = args.mode == "learned"
+    if name == "blur" and learned:
+        # Eq. (varying blur) as a dense contraction on the tensor cores: 2 x 33^2 x K MACs per pixel and
+        # channel; the events bracket the one k_blur_tc launch of the frame (C <= 3)
+        flops = 2.0 * 1089 * K * C * npix
+        # DRAM bytes per launch from the committed ncu capture of this kernel on this workload
+        # (profiles/kernels_512x512x3_learned.md); none for other workloads
+        traffic = 124.2e6 if args.workload == "512" else None
+        roof = {"kernel": "k_blur_tc", "bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": traffic,
+                "peak_source": peak_kind + " (burst bf16 GEMM)"}
+    elif name == "blur":
+        flops = 2.0 * 1089 * (K + C) * npix  # per-pixel PSF form on FP32 CUDA cores
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "k_blur_psf", "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    elif name.startswith("p2s") and learned:
+        # the surrogate MLP on the tensor cores: 2 (256 J + 256^2 + 256 K) FLOP per pixel, one k_mlp_tc launch
+        flops = npix * 2.0 * (J * 256 + 256 * 256 + 256 * K)
+        roof = {"kernel": "k_mlp_tc", "bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
+                "peak_source": peak_kind + " (burst bf16 GEMM)"}
+    elif name.startswith("p2s"):
+        flops = npix * (2.0 * 1089 * (J - 2) + 2 * 8.0 * 33 ** 3 + 2.0 * 1089 * K)
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "k_p2s_exact", "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    elif learned:
+        wq = (W + 127) // 128 * 128 + 64
+        byt = 4.0 * npix * (2 + C) + 16.0 * C * (H + 32) * wq  # tilts and image in, eight BF16 planes out
+        roof = {"kernel": "k_warp_pad_shifted", "bound": "hbm", "achieved": byt / (ms * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
+    else:
+        byt = 4.0 * npix * (2 + 2 * C)  # tilt fields a2, a3 and the image in, the warped image out
+        roof = {"kernel": "k_tilt_warp", "bound": "hbm", "achieved": byt / (ms * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
+
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return roof
+
+
 def run_ours(args, rank, world, device):
     import torch
     d, S = setup_ours(args.workload, args.mode, device, args.train_steps)
@@ -282,45 +330,8 @@ def run_ours(args, rank, world, device):
     single = [1, 2, 3]
     dom = single[int(np.argmax(mean_stage[single]))]
     npix = H * W
-    if names[dom] == "blur" and args.mode == "learned":
-        # Eq. (varying blur) as a dense contraction on the tensor cores: 2 x 33^2 x K MACs per pixel and
-        # channel; the events bracket the one k_blur_tc launch of the frame (C <= 3)
-        flops = 2.0 * 1089 * K * C * npix
-        # DRAM bytes per launch from the committed ncu capture of this kernel on this workload
-        # (profiles/kernels_512x512x3_learned.md); none for other workloads
-        traffic = 124.2e6 if args.workload == "512" else None
-        roof = {"kernel": "k_blur_tc", "bound": "tensor", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": traffic,
-                "peak_source": peak_kind + " (burst bf16 GEMM)"}
-    elif names[dom] == "blur":
-        flops = 2.0 * 1089 * (K + C) * npix  # per-pixel PSF form on FP32 CUDA cores
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "k_blur_psf", "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-    elif names[dom].startswith("p2s") and args.mode == "learned":
-        # the surrogate MLP on the tensor cores: 2 (256 J + 256^2 + 256 K) FLOP per pixel, one k_mlp_tc launch
-        flops = npix * 2.0 * (J * 256 + 256 * 256 + 256 * K)
-        roof = {"kernel": "k_mlp_tc", "bound": "tensor", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
-                "peak_source": peak_kind + " (burst bf16 GEMM)"}
-    elif names[dom].startswith("p2s"):
-        flops = npix * (2.0 * 1089 * (J - 2) + 2 * 8.0 * 33 ** 3 + 2.0 * 1089 * K)
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "k_p2s_exact", "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-    elif args.mode == "learned":
-        wq = (W + 127) // 128 * 128 + 64
-        byt = 4.0 * npix * (2 + C) + 16.0 * C * (H + 32) * wq  # tilts and image in, eight BF16 planes out
-        roof = {"kernel": "k_warp_pad_shifted", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
-    else:
-        byt = 4.0 * npix * (2 + 2 * C)  # tilt fields a2, a3 and the image in, the warped image out
-        roof = {"kernel": "k_tilt_warp", "bound": "hbm", "achieved": byt / (mean_stage[dom] * 1e-3) / 1e9,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "peak_source": peak_kind}
+    roofs = {i: stage_roofline(names[i], mean_stage[i], args, peaks, peak_kind, H, W, C, K) for i in single}
+    roof = roofs[dom]
     # the field sampler as one HBM-bound stage: multiplier read (4 J N (N/2+1)), cropped columns written and read
     # (16 J H (N/2+1)), unit fields written (4 J H W) and, in exact frames, read and written by the mixing
     # pass (8 J H W; learned frames fold the mixing into the warp and the network); the noise is made in registers
@@ -331,7 +342,6 @@ def run_ours(args, rank, world, device):
     fields_roof = {"kernels": "k_colgen + k_rowifft" + ("" if learned else " + k_mix"), "bound": "hbm",
                    "achieved": fbytes / (mean_stage[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     fields_roof["frac"] = fields_roof["achieved"] / fields_roof["peak"]
-    roof["frac"] = roof["achieved"] / roof["peak"]
     value = world * args.steps / (total_ms * 1e-3)
     line = {
         "metric": "dense-field frames/s at 512^2 and 4K: learned vs exact P2S, same GB300, at tol",
@@ -345,6 +355,8 @@ def run_ours(args, rank, world, device):
         "rel_l2_learned_vs_exact": acc,
         "roofline": roof,
         "fields_roofline": fields_roof,
+        "stage_rooflines": {roofs[i]["kernel"]: {k: roofs[i][k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+                            for i in single},
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
         # field launches (noise + column IFFT, row IFFT, and the mixing in exact frames), warp, P2S, blur
