@@ -145,6 +145,25 @@ def accuracy_vs_exact(d, S, seed):
     return out
 
 
+# ---- the multi-rank host logic: frames are independent, each rank draws its own Philox streams (a seed base of
+# its own), times its frames, and rank 0 reports the whole job from the slowest rank's time (no data collective)
+def rank_seed_base(rank: int) -> int:
+    return 1000 * rank
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    if world == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_frames_per_s(world: int, steps: int, max_total_ms: float) -> float:
+    return world * steps / (max_total_ms * 1e-3)
+
+
 def stage_roofline(name, ms, args, peaks, peak_kind, H, W, C, K):
     """Roofline of one single-launch stage of the frame (its CUDA events bracket one kernel launch)."""
     npix = H * W
@@ -202,7 +221,7 @@ def run_ours(args, rank, world, device):
     stream = torch.cuda.current_stream()
     out = torch.empty(C, H, W, device=device)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
-    seed_base = 1000 * rank
+    seed_base = rank_seed_base(rank)
 
     def step(i):
         # one frame through the library's frame call (the C ABI's dfp2s_simulate_frame); with stage timing on,
@@ -232,11 +251,7 @@ def run_ours(args, rank, world, device):
     stage_ms = S["sim"].stage_times(args.steps).astype(np.float64)
     S["sim"].stage_timing(0)
     frame_ms = stage_ms.sum(axis=1)
-    total_ms = float(frame_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(frame_ms.sum()), world, device)
 
     # end to end through simulate_frame with host buffers
     img_h = S["img"].cpu().pin_memory()
@@ -342,7 +357,7 @@ def run_ours(args, rank, world, device):
     fields_roof = {"kernels": "k_colgen + k_rowifft" + ("" if learned else " + k_mix"), "bound": "hbm",
                    "achieved": fbytes / (mean_stage[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     fields_roof["frac"] = fields_roof["achieved"] / fields_roof["peak"]
-    value = world * args.steps / (total_ms * 1e-3)
+    value = whole_job_frames_per_s(world, args.steps, total_ms)
     line = {
         "metric": "dense-field frames/s at 512^2 and 4K: learned vs exact P2S, same GB300, at tol",
         "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
