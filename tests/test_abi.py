@@ -63,3 +63,23 @@ def test_null_handles_are_rejected_without_a_gpu():
     buf = ctypes.create_string_buffer(256)
     assert lib.dfp2s_last_error(buf, 256) == -1
     assert b"null" in buf.value
+
+
+def test_new_entry_points_validate_arguments_without_a_gpu():
+    lib = dfp2s.load()
+    import ctypes
+    lags = (ctypes.c_int * 2)(0, 0)
+    # field statistics: null pointers, J out of range, a lag that does not fit
+    assert lib.dfp2s_field_covariance(None, 4, 8, 8, lags, 1, None, None) == -1
+    dummy = ctypes.c_void_p(16)
+    assert lib.dfp2s_field_covariance(dummy, 0, 8, 8, lags, 1, dummy, None) == -1
+    assert lib.dfp2s_field_covariance(dummy, 65, 8, 8, lags, 1, dummy, None) == -1
+    assert lib.dfp2s_field_covariance(dummy, 4, 8, 8, lags, 0, dummy, None) == -1
+    far = (ctypes.c_int * 2)(8, 0)
+    assert lib.dfp2s_field_covariance(dummy, 4, 8, 8, far, 1, dummy, None) == -1
+    # network files and frame stage timing: null handles
+    assert lib.dfp2s_mlp_save(None, b"/nonexistent/x") == -1
+    assert lib.dfp2s_mlp_load(None, b"/nonexistent/x") == -1
+    assert lib.dfp2s_ctx_stage_timing(None, 4) == -1
+    out = (ctypes.c_float * 4)()
+    assert lib.dfp2s_ctx_stage_times(None, 1, out) == -1
