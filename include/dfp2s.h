@@ -113,10 +113,14 @@ int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_byt
 
 /* Sec. III-C: draws the J x H x W fields a of frame `frame` of stream `seed`
  * at strength D/r0 into fields_dev (device, J*H*W floats, caller-owned).
- * White noise: Philox-4x32-10, key = seed, counter = ((y N + x)/4,
- * (0 << 40) | (frame << 8) | j); FP32 Box-Muller.  Requires H, W <= factor N
- * (crop of the periodic N x N field) and uses the factor's scratch.
- * Errors: EINVAL, ECUDA. */
+ * The white noise is drawn in the Fourier domain (its distribution is that of
+ * FFT2 of real white noise, Sec. III-A): for mode j, Philox-4x32-10 with
+ * key = seed, subsequence (0 << 40) | (frame << 8) | j, FP32 Box-Muller, gives
+ * rows kx = 0 .. N/2 of 2N Gaussians, (Re, Im) of E(kx, ky) at 2 ky, 2 ky + 1
+ * (counter (kx N + ky)/2 for ky even), scaled by N / sqrt 2; columns kx = 0 and
+ * N/2 are completed to Hermitian symmetry in ky (their bins ky = 0 and N/2 real,
+ * scaled by N).  Requires H, W <= factor N (crop of the periodic N x N field)
+ * and uses the factor's scratch.  Errors: EINVAL, ECUDA. */
 int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
                                 int H, int W, float* fields_dev, void* stream);
 
@@ -156,8 +160,8 @@ int dfp2s_sample_zernike_fields_noalloc(const dfp2s_factor* f, double D_over_r0,
                                         int H, int W, float* fields_dev, void* stream);
 
 /* Debug/verification: the FP32 Gaussians of one (seed, tag, frame, mode) stream
- * as rows x cols (cols % 4 == 0), into out_dev.  The same values the field
- * sampler generates in registers (tag 0). */
+ * as rows x cols (cols % 4 == 0), into out_dev.  With tag 0, rows = N/2 + 1 and
+ * cols = 2N these are the values the field sampler generates in registers. */
 int dfp2s_gaussian_noise(uint64_t seed, uint32_t tag, uint32_t frame, uint32_t mode, int rows, int cols,
                          float* out_dev, void* stream);
 /* Debug/verification: n raw Philox words, 4 per counter q = q0 .. q0+n/4-1 of
