@@ -187,11 +187,6 @@ def gaussian_block(seed: int, tag: int, frame: int, mode: int, rows: int, cols: 
     return np.stack([z0, z1, z2, z3], axis=-1).reshape(rows, cols)
 
 
-def field_noise(seed: int, frame: int, J: int, N: int) -> np.ndarray:
-    """White noise for the J fields on the N x N grid, shape (J, N, N) FP32 (tag 0)."""
-    return np.stack([gaussian_block(seed, TAG_FIELDS, frame, j, N, N) for j in range(J)])
-
-
 def hermitian_spectrum(g: np.ndarray, N: int) -> np.ndarray:
     """Full N x N Fourier-domain white noise E[ky, kx] (FP64 complex) from the Gaussian rows of one mode,
     g[kx, 2 ky + c], kx = 0..N/2, c = 0 (Re) / 1 (Im) (R27)."""
