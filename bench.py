@@ -272,7 +272,7 @@ def run_ours(args, rank, world, device):
         out_h.copy_(out_d, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, device)  # per frame, the slowest rank
 
     # the other P2S form on the same GPU (the metric compares them): whole frames through simulate_frame
     other = d.P2S_EXACT if mode == d.P2S_LEARNED else (d.P2S_LEARNED if S["P"].has_mlp else None)
@@ -372,7 +372,7 @@ def run_ours(args, rank, world, device):
         "fields_roofline": fields_roof,
         "stage_rooflines": {roofs[i]["kernel"]: {k: roofs[i][k] for k in ("bound", "achieved", "peak", "unit", "frac")}
                             for i in single},
-        "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": int(4 * C * H * W),
                 "d2h_bytes_per_step": int(4 * C * H * W)},
         # field launches (noise + column IFFT, row IFFT, and the mixing in exact frames), warp, P2S, blur
         "gpu_launches": args.steps * (5 if args.mode == "learned" else 6),
