@@ -114,10 +114,17 @@ def test_brute_force_full_tensor_8x8x6(small):
     for p in (0, 33):
         assert np.allclose(np.diag(A[p::n, p::n]), np.diag(A0), rtol=1e-12)
         assert np.allclose(At[p::n, p::n], A0, rtol=1e-12, atol=1e-14)
-    # the approximation differs from the full tensor only off the mode diagonal blocks' cross terms;
-    # report its size (informational, not a gate: reading R17)
-    rel = np.linalg.norm(A - At) / np.linalg.norm(A)
-    assert 0.0 < rel < 1.0
+    # the samples tell the full tensor from its approximation: on the sampled index pairs their covariance is
+    # much closer to A than to A tilde, which differ in the cross-mode terms (Sec. III-D)
+    dA = np.linalg.norm(emp - A[np.ix_(idx, idx)])
+    dAt = np.linalg.norm(emp - At[np.ix_(idx, idx)])
+    assert dA < 0.5 * dAt
+    # the zero-lag block of A has Noll's sign pattern (its magnitudes carry the 8 x 8 torus's
+    # low-frequency deficit; the convergence is pinned in test_oracle_spectrum)
+    blk = A[0::n, 0::n]
+    nz = A0 != 0.0
+    assert np.all(np.sign(blk[nz]) == np.sign(A0[nz]))
+    assert np.abs(blk[~nz]).max() < 3e-3 * np.abs(np.diag(A0)).max()
 
 
 def test_ar1_fields_special_cases_and_field_recursion():
