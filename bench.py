@@ -106,7 +106,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def setup_ours(workload: str, mode: str, device, train_steps: int = 20000):
+def setup_ours(workload: str, mode: str, device, train_steps: int = 60000):
     """Untimed setup: spectral factor, SVD basis of 2000 exact PSFs and (learned mode) the trained surrogate,
     all built on the device."""
     import torch
@@ -445,7 +445,7 @@ def main():
     ap.add_argument("--mode", default="learned", choices=["learned", "exact"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--train-steps", type=int, default=60000)
     ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

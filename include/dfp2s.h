@@ -197,7 +197,8 @@ int dfp2s_build_basis(const dfp2s_factor* f, int K, int n_psf, const double* D_o
 /* Installs surrogate-network weights (all device float32, copied):
  * W1 256 x J, b1 256, W2 256 x 256, b2 256, W3 K x 256, b3 K; in_scale J
  * (multiplies the Zernike vector before the first layer; 0 on the tilt
- * fields); out_scale, out_shift K (w = y * out_scale + out_shift). */
+ * fields); out_scale, out_shift K (v = y * out_scale + out_shift; the P2S
+ * weights are v moved onto unit flux, see dfp2s_p2s_weights). */
 int dfp2s_p2s_set_mlp(dfp2s_p2s* p, const float* W1, const float* b1, const float* W2, const float* b2,
                       const float* W3, const float* b3, const float* in_scale, const float* out_scale,
                       const float* out_shift);
@@ -261,13 +262,20 @@ int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params_dev, const floa
 int dfp2s_mlp_image_prior_gram(const dfp2s_p2s* p, const float* sd_dev, float* G_dev, void* stream);
 
 /* Sec. II-C: per-pixel basis weights from the fields (J x H x W, device).
- *   EXACT: PSF of Eq. (2) from modes Noll 4..J+1 on a 64 x 64 pupil grid
+ * Every form returns weights whose PSF keeps the unit sum of the true PSF:
+ * with s_k = sum_u phi_k(u), s^T w = 1 (the least-squares projection of
+ * Eq. p2s PSF under that constraint; without it the projected PSF keeps only
+ * the part of the flux inside the basis span, and a flat image region changes
+ * brightness by 1 - s^T w).
+ *   EXACT: PSF h of Eq. (2) from modes Noll 4..J+1 on a 64 x 64 pupil grid
  *          (aperture 32 samples across, P = 1 inside), |DFT|^2, 33 x 33 centre,
- *          unit sum, then w = Phi^T h;
- *   LEARNED: w = MLP(a * in_scale) * out_scale + out_shift on the tcgen05
+ *          unit sum, then w = Phi^T h + s (1 - s^T Phi^T h) / (s^T s), the
+ *          nearest weights to h's projection with unit flux;
+ *   LEARNED: v = MLP(a * in_scale) * out_scale + out_shift on the tcgen05
  *          tensor cores (BF16 inputs, weights and hidden activations, FP32
- *          accumulation), one fused kernel; J <= 48, K <= 128;
- *   LEARNED_FP32: the same network in FP32 on CUDA cores.
+ *          accumulation), one fused kernel, then in FP32
+ *          w = v + s (1 - s^T v) / (s^T s); J <= 48, K <= 128;
+ *   LEARNED_FP32: the same network and projection in FP32 on CUDA cores.
  * Writes w_dev (H x W x K, dtype w_dtype).  Errors: EINVAL (no MLP for
  * LEARNED, J > 48 for LEARNED, sizes), ECUDA. */
 int dfp2s_p2s_weights(const dfp2s_p2s* p, int mode, const float* fields_dev, int H, int W, void* w_dev,

@@ -9,7 +9,7 @@ shares no code, constants or tables with the CUDA sources.
 Every function cites the part of the paper (Chimitt, Zhang, Mao, Chan,
 "Real-Time Dense Field Phase-to-Space Simulation of Imaging through Atmospheric
 Turbulence", arXiv 2210.06713) that it follows. Where the paper is silent the
-reading taken is named in the docstring (R1..R20, the readings listed in the
+reading taken is named in the docstring (R1..R28, the readings listed in the
 design notes).
 
 Modules

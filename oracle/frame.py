@@ -26,6 +26,7 @@ def simulate_frame(img: np.ndarray, D_over_r0: float, seed: int, frame: int, J: 
         w = p2s.weights_field(a, basis)
     else:
         av = np.moveaxis(a, 0, -1)
-        w = mlp.predict_weights(net["params"], av, net["in_scale"], net["out_scale"], net["out_shift"])
+        w = mlp.predict_weights(net["params"], av, net["in_scale"], net["out_scale"], net["out_shift"],
+                                flux=p2s.flux_vector(basis))
     out = image.basis_blur(warped, w, basis)
     return {"fields": a, "warped": warped, "weights": w, "out": out}

@@ -113,9 +113,18 @@ def adam_step(params: dict, grads: dict, state: dict, lr: float, step: int,
 
 
 def predict_weights(params: dict, a: np.ndarray, in_scale: np.ndarray, out_scale: np.ndarray,
-                    out_shift: np.ndarray) -> np.ndarray:
-    """w = MLP(a * in_scale) * out_scale + out_shift for Zernike vectors a (..., J)."""
+                    out_shift: np.ndarray, flux: np.ndarray | None = None) -> np.ndarray:
+    """w = MLP(a * in_scale) * out_scale + out_shift for Zernike vectors a (..., J).
+
+    flux (the basis sums s_k): the surrogate's P2S weights, the network's output moved to the nearest point
+    with s^T w = 1 (reading R28: the exact weights the network learns keep the PSF's unit sum, and so do
+    its outputs); None: the network's output itself.
+    """
     a = np.asarray(a, dtype=np.float64)
     shp = a.shape[:-1]
     y, _ = forward(params, a.reshape(-1, a.shape[-1]) * in_scale)
-    return (y * out_scale + out_shift).reshape(*shp, -1)
+    w = y * out_scale + out_shift
+    if flux is not None:
+        s = np.asarray(flux, dtype=np.float64)
+        w = w + (1.0 - w @ s)[:, None] * s / (s @ s)
+    return w.reshape(*shp, -1)

@@ -9,8 +9,14 @@ pupil grid with sample coordinates (i - 32)/16 (so the aperture of radius 1 is
 centre shift, a 33 x 33 crop centred at index 32, normalised to unit sum.
 Eq. (p2s PSF): h_x = sum_m beta_{x,m} varphi_m; the basis comes from a
 principal component analysis of a PSF database (Sec. II-C); reading R15 takes
-the uncentred SVD of the stacked PSFs and R13 the orthogonal projection
-w = Phi^T h.
+the uncentred SVD of the stacked PSFs.  Reading R28 takes the least-squares
+projection that keeps the PSF's unit sum: among all w with sum_u (Phi^T w)(u)
+= s^T w = 1 (s_k = sum_u phi_k(u)), the one nearest h,
+w = Phi h + s (1 - s^T Phi h) / (s^T s).  A flat image region of brightness I
+then blurs to exactly I (Eq. varying blur), as with the true PSF, whereas the
+plain projection Phi h keeps only the PSF's part inside the basis span and so
+changes the local brightness by 1 - s^T Phi h (R13, the plain projection, is
+`weights_unconstrained`).
 Tilts (Noll 2, 3) are applied by the warp (Eq. 2's linear phase shifts the
 PSF), so the PSFs here use the modes Noll 4..J+1 (reading R9).
 """
@@ -110,11 +116,30 @@ def build_basis(seed: int, J: int, K: int, n_psf: int, D_over_r0_list) -> np.nda
     return Phi.reshape(K, KS, KS)
 
 
-def weights(a: np.ndarray, J: int, basis: np.ndarray) -> np.ndarray:
-    """w = Phi^T h for Zernike vectors a (..., J): the exact P2S weights (R13), shape (..., K)."""
+def flux_vector(basis: np.ndarray) -> np.ndarray:
+    """s_k = sum_u phi_k(u): the PSF sum (flux) that weight k contributes, shape (K,)."""
+    b = np.asarray(basis, dtype=np.float64)
+    return b.reshape(b.shape[0], -1).sum(axis=1)
+
+
+def flux_projection(w: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """The nearest weights (Euclidean) with s^T w = 1: w + s (1 - s^T w) / (s^T s) (reading R28)."""
+    w = np.asarray(w, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    return w + (1.0 - w @ s)[..., None] * s / (s @ s)
+
+
+def weights_unconstrained(a: np.ndarray, J: int, basis: np.ndarray) -> np.ndarray:
+    """The plain orthogonal projection Phi^T h of the PSFs of Zernike vectors a (..., J) (R13)."""
     K = basis.shape[0]
     h = psf(a, J).reshape(*np.shape(a)[:-1], KS * KS)
     return h @ basis.reshape(K, KS * KS).T
+
+
+def weights(a: np.ndarray, J: int, basis: np.ndarray) -> np.ndarray:
+    """The exact P2S weights (reading R28), shape (..., K): the least-squares projection of the unit-sum PSF
+    on the basis under the constraint that the projected PSF keeps the unit sum."""
+    return flux_projection(weights_unconstrained(a, J, basis), flux_vector(basis))
 
 
 def weights_field(fields: np.ndarray, basis: np.ndarray, chunk: int = 4096) -> np.ndarray:

@@ -32,6 +32,23 @@ int dfp2s_fail(int code, const char* fmt, ...) {
   return code;
 }
 
+namespace {
+thread_local cudaError_t g_launch_err = cudaSuccess;
+}
+
+int dfp2s_launch_status() {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return DFP2S_OK;
+  g_launch_err = e;
+  return DFP2S_ECUDA;
+}
+
+cudaError_t dfp2s_launch_error() {
+  const cudaError_t e = g_launch_err;
+  g_launch_err = cudaSuccess;
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 int dfp2s_fail_cuda(cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation) return dfp2s_fail(DFP2S_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
   return dfp2s_fail(DFP2S_ECUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -44,7 +61,7 @@ int dfp2s_fail_cuda(cudaError_t e, const char* what) {
 
 #define CHECK_LAUNCH(expr)                                                          \
   do {                                                                              \
-    if ((expr) != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), #expr);      \
+    if ((expr) != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), #expr);      \
   } while (0)
 
 extern "C" int dfp2s_last_error(char* buf, size_t n) {
@@ -188,7 +205,7 @@ extern "C" int dfp2s_build_basis(const dfp2s_factor* f, int K, int n_psf, const 
   const int rc = dfp2s_basis_build_device(f->d.J, f->d.L32, K, n_psf, dr, n_dr, seed, basis, sigma_host, sweeps_host,
                                           as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "basis allocation");
-  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "basis build");
+  if (rc) return dfp2s_fail_cuda(dfp2s_launch_error(), "basis build");
   return DFP2S_OK;
 }
 
@@ -199,7 +216,7 @@ struct dfp2s_p2s {
 
 static void p2s_free(dfp2s_p2s* p) {
   if (!p) return;
-  void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt,    p->d.mask, p->d.dft,       p->d.W1,        p->d.b1,
+  void* bufs[] = {p->d.basis, p->d.phiT, p->d.zt,    p->d.mask, p->d.dft,  p->d.flux,     p->d.W1,        p->d.b1,
                   p->d.W2,    p->d.b2,   p->d.W3,    p->d.b3,   p->d.in_scale, p->d.out_scale, p->d.out_shift,
                   p->d.bt,    p->d.pad,  p->d.err,   p->d.bsum,     p->d.tc_w1,     p->d.tc_w2,     p->d.tc_w3,
                   p->d.tc_c3, p->d.tc_bias};
@@ -223,7 +240,8 @@ extern "C" int dfp2s_p2s_create(int J, int K, const float* basis, dfp2s_p2s** ou
       (e = cudaMalloc((void**)&p->d.phiT, K * n2 * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc((void**)&p->d.zt, (J - 2) * n2 * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc((void**)&p->d.mask, n2 * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&p->d.dft, n2 * sizeof(float2))) != cudaSuccess) {
+      (e = cudaMalloc((void**)&p->d.dft, n2 * sizeof(float2))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d.flux, 2 * K * sizeof(float))) != cudaSuccess) {
     p2s_free(p);
     return dfp2s_fail_cuda(e, "p2s allocation");
   }
@@ -233,7 +251,7 @@ extern "C" int dfp2s_p2s_create(int J, int K, const float* basis, dfp2s_p2s** ou
   }
   if (dfp2s_p2s_build_tables(&p->d, 0) != DFP2S_OK || (e = cudaDeviceSynchronize()) != cudaSuccess) {
     p2s_free(p);
-    return dfp2s_fail_cuda(cudaGetLastError(), "p2s tables");
+    return dfp2s_fail_cuda(dfp2s_launch_error(), "p2s tables");
   }
   *out = p;
   return DFP2S_OK;
@@ -298,7 +316,7 @@ int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* d, const float* W1, const float* b1, co
   }
   const int rc = dfp2s_mlp_tc_pack(d, 0);
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "tensor-core weight allocation");
-  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core weight packing");
+  if (rc) return dfp2s_fail_cuda(dfp2s_launch_error(), "tensor-core weight packing");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return dfp2s_fail_cuda(e, "tensor-core weight packing");
   d->has_mlp = 1;
   ++d->mlp_version;
@@ -324,7 +342,7 @@ extern "C" int dfp2s_field_covariance(const float* fields, int J, int H, int W, 
               lags[2 * l + 1], H, W);
   const int rc = dfp2s_launch_field_covariance(fields, J, H, W, lags, n_lags, out, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "covariance scratch allocation");
-  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "field covariance");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "field covariance");
   return DFP2S_OK;
 }
 
@@ -402,7 +420,7 @@ extern "C" int dfp2s_mlp_loss_grad(int J, int K, int B, const float* params, con
   CHECK_ARG(J >= 3 && J <= DFP2S_MAX_J && K >= 1 && K <= DFP2S_MAX_K && B >= 1 && B <= (1 << 20), "bad shape");
   const int rc = dfp2s_mlp_loss_grad_device(J, K, B, params, X, T, lw, G, grads, loss, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "mlp scratch allocation");
-  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "mlp loss/grad");
+  if (rc) return dfp2s_fail_cuda(dfp2s_launch_error(), "mlp loss/grad");
   return DFP2S_OK;
 }
 
@@ -410,7 +428,7 @@ extern "C" int dfp2s_mlp_image_prior_gram(const dfp2s_p2s* p, const float* sd, f
   CHECK_ARG(p && sd && G, "null argument");
   const int rc = dfp2s_prior_gram_device(p->d.basis, p->d.K, sd, G, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "gram scratch allocation");
-  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "image-prior loss form");
+  if (rc) return dfp2s_fail_cuda(dfp2s_launch_error(), "image-prior loss form");
   return DFP2S_OK;
 }
 
@@ -428,7 +446,7 @@ extern "C" int dfp2s_mlp_train(dfp2s_p2s* p, const dfp2s_factor* f, const dfp2s_
   CHECK_ARG(tp->image_prior_loss == 0 || tp->image_prior_loss == 1, "image_prior_loss must be 0 or 1");
   const int rc = dfp2s_mlp_train_device(&p->d, f->d.L32, tp, report, params_out_host, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "training allocation");
-  if (rc) return dfp2s_fail_cuda(cudaGetLastError(), "mlp training");
+  if (rc) return dfp2s_fail_cuda(dfp2s_launch_error(), "mlp training");
   return DFP2S_OK;
 }
 
@@ -482,7 +500,7 @@ extern "C" int dfp2s_basis_blur_tc(const dfp2s_p2s* p, const float* img, int C, 
                                       as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
   if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
-  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur launch");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "tensor-core blur launch");
   return DFP2S_OK;
 }
 
@@ -492,7 +510,7 @@ extern "C" int dfp2s_basis_blur_tc_prepare(const dfp2s_p2s* p, const float* img,
   const int rc = dfp2s_launch_blur_tc_prepare(const_cast<dfp2s_p2s_dev*>(&p->d), img, C, H, W, as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
   if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
-  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur image preparation");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "tensor-core blur image preparation");
   return DFP2S_OK;
 }
 
@@ -504,7 +522,7 @@ extern "C" int dfp2s_tilt_warp_blur_tc_prepare(const dfp2s_p2s* p, const float* 
                                                    as_stream(stream));
   if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
   if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
-  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "warp + tensor-core blur preparation");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "warp + tensor-core blur preparation");
   return DFP2S_OK;
 }
 
@@ -516,7 +534,7 @@ extern "C" int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, 
   const int rc = dfp2s_launch_blur_tc_run(const_cast<dfp2s_p2s_dev*>(&p->d), C, H, W, w, w_dtype, out, as_stream(stream));
   if (rc == DFP2S_EINVAL) return dfp2s_fail(rc, "no prepared image of shape %dx%dx%d on this handle", C, H, W);
   if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128 (and needs TMA)");
-  if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "tensor-core blur launch");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "tensor-core blur launch");
   return DFP2S_OK;
 }
 
@@ -685,7 +703,7 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
                                            c->fields + npix, st, m);
     if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
     if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
-    if (rc != DFP2S_OK) return dfp2s_fail_cuda(cudaGetLastError(), "warp + tensor-core blur preparation");
+    if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "warp + tensor-core blur preparation");
     mark(2);
     CHECK_LAUNCH(dfp2s_launch_mlp_tc(pd, c->fields, H * W, c->w, DFP2S_W_F32, st, c->w1_mixed, scale));
     mark(3);

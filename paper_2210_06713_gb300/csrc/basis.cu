@@ -247,7 +247,7 @@ int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const do
   if ((rc = dfp2s_launch_p2s_exact(&b.t, b.a, 1, m, b.h, DFP2S_W_PSF, st))) return rc;
   k_to_f64_colmajor<<<(unsigned)(((size_t)m * KS2 + 255) / 256), 256, 0, st>>>(b.h, m, b.Hd);
   k_eye<<<(unsigned)(((size_t)KS2 * KS2 + 255) / 256), 256, 0, st>>>(b.V);
-  if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
+  if (dfp2s_launch_status() != DFP2S_OK) return DFP2S_ECUDA;
   // rounding floor for the convergence test: 1e-12 of the squared Frobenius norm
   double floor2 = 0.0;
   {
@@ -295,6 +295,6 @@ int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const do
   k_sort_desc<<<1, 1024, 0, st>>>(b.sig, b.order, b.sorted);
   k_gather_basis<<<K, 256, 0, st>>>(b.V, b.order, K, basis_out);
   if (sigma_host) cudaMemcpyAsync(sigma_host, b.sorted, KS2 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
+  if (dfp2s_launch_status() != DFP2S_OK) return DFP2S_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }

@@ -111,5 +111,5 @@ int dfp2s_launch_blur(const dfp2s_p2s_dev* p, const float* img, int C, int H, in
     cudaFuncSetAttribute(k_blur_psf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_blur_psf<float><<<grid, NTH, sm, st>>>(img, C, H, W, p->basis, K, (const float*)w, out);
   }
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }

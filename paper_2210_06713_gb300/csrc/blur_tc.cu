@@ -616,7 +616,7 @@ int dfp2s_launch_blur_tc_prepare(dfp2s_p2s_dev* p, const float* img, int C, int 
   p->prep_C = C;
   p->prep_H = H;
   p->prep_W = W;
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 // The same for the tilt-warped image (k_warp_pad_shifted), without writing the warped image.
@@ -631,7 +631,7 @@ int dfp2s_launch_blur_tc_prepare_warp(dfp2s_p2s_dev* p, const float* img, int C,
   p->prep_C = C;
   p->prep_H = H;
   p->prep_W = W;
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 // The tensor-core contraction on the prepared planes.
@@ -692,7 +692,7 @@ int dfp2s_launch_blur_tc_run(dfp2s_p2s_dev* p, int C, int H, int W, const void* 
     }
 #undef DFP2S_BLUR_LAUNCH
   }
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,

@@ -194,3 +194,10 @@ DFP2S_DEV void dft8(float2* v) {
 
 int dfp2s_fail(int code, const char* fmt, ...);
 int dfp2s_fail_cuda(cudaError_t e, const char* what);
+// Status of the launches a launcher has just enqueued: reads (and so clears) the
+// runtime's last error and, when it is one, keeps it for dfp2s_launch_error(),
+// so that the entry point reporting the failure names the actual cause.
+int dfp2s_launch_status();
+// The error the last failing dfp2s_launch_status() of this thread saw (then
+// forgotten); cudaGetLastError() when there is none.
+cudaError_t dfp2s_launch_error();

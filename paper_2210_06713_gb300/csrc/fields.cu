@@ -335,18 +335,18 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
     default: return DFP2S_EINVAL;
   }
   const size_t npix = (size_t)H * W;
-  if (!mix) return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  if (!mix) return dfp2s_launch_status();
   if (prev) launch_mix_any<true>(fields, L, scale * sqrtf(1.f - alpha * alpha), J, npix, prev, alpha, st);
   else launch_mix_any<false>(fields, L, scale, J, npix, nullptr, 0.f, st);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st) {
   k_philox_words<<<(nq + 255) / 256, 256, 0, st>>>(seed, sub, q0, nq, out);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cudaStream_t st) {
   k_gaussian<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(seed, sub, nq, out);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }

@@ -25,7 +25,7 @@
 
 namespace {
 
-// 48 MiB of complex FP32: J (N/2+1) N <= 6,291,456, e.g. N = 512 with J <= 45,
+// 48 MiB of complex FP32: J (N/2+1) N <= 6,291,456, e.g. N = 512 with J <= 47,
 // N = 256 with J <= 64, N = 1024 with J <= 11.
 constexpr size_t kNoallocScratchElems = DFP2S_NOALLOC_SCRATCH_BYTES / sizeof(float2);
 
@@ -78,6 +78,6 @@ extern "C" int dfp2s_sample_zernike_fields_noalloc(const dfp2s_factor* f, double
   const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
   if (dfp2s_launch_sample_fields(scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame, f->d.L32, scale,
                                  fields_dev, reinterpret_cast<cudaStream_t>(stream)) != DFP2S_OK)
-    return dfp2s_fail_cuda(cudaGetLastError(), "sample fields (static scratch)");
+    return dfp2s_fail_cuda(dfp2s_launch_error(), "sample fields (static scratch)");
   return DFP2S_OK;
 }

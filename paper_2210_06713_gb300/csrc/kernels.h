@@ -49,6 +49,7 @@ struct dfp2s_p2s_dev {
   float* zt;      // (J-2) x 1089 Zernike values of Noll 4..J+1 on the 33 x 33 pupil window
   float* mask;    // 1089 aperture mask
   float2* dft;    // 33 x 33, exp(-2 pi i (k-16)(i-16) / 64)
+  float* flux;    // 2 K: s_k = sum_u phi_k(u), then s_k / (s^T s) (the unit-flux projection of the weights)
   // surrogate network (optional)
   int has_mlp;
   float *W1, *b1, *W2, *b2, *W3, *b3, *in_scale, *out_scale, *out_shift;

@@ -14,7 +14,10 @@
 //   2 GELU(z) -> H2 in Q, the same way
 //   layer 3: H2 (from tensor memory) x (W3 / 2)^T -> P columns [0, NP3)
 //   w = y * out_scale + (b3 * out_scale + out_shift) -> staging rows in shared
-//            memory -> global memory by one bulk copy (FP32 or BF16)
+//            memory; each pixel's flux s^T w (s_k = sum_u phi_k(u), four
+//            partial sums per pixel) -> w += (1 - s^T w) s / (s^T s) in the
+//            staging rows (reading R28: the P2S weights keep the PSF's unit
+//            sum) -> global memory by one bulk copy (FP32 or BF16)
 //
 // The hidden biases enter the accumulators through one extra K = 16 MMA per
 // layer (a tile of ones against the bias split into high and low bfloat16
@@ -72,6 +75,8 @@ struct Smem {
   uint8_t ONES[2][ONES_BYTES];       // 8 KB: ones in K columns 0, 1 (layer 1) and 2, 3 (layer 2)
   uint8_t BIAS[BIAS_BYTES];          // 8 KB: K columns 0, 1 = b1 (high and low bfloat16 parts), 2, 3 = b2
   float c3[128], s3[128];            // output bias and scale
+  float fs[128], fg[128];            // s_k and s_k / (s^T s) of the unit-flux projection
+  float mpart[4][TM];                // partial flux sums of the tile's pixels, one per epilogue slice
   uint64_t full[NRING], empty[NRING];
   uint64_t w1_full, x_ready, l1_done, l2_done, l3_done;
   uint64_t h_ready[4];
@@ -195,7 +200,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_mlp_tc(const float* __restrict__ fields, int J, int npix, int K, int NP3, const __nv_bfloat16* __restrict__ w1t,
              const __nv_bfloat16* __restrict__ w2c, const __nv_bfloat16* __restrict__ w3c,
              const __nv_bfloat16* __restrict__ bias, const float* __restrict__ c3, const float* __restrict__ s3,
-             WT* __restrict__ wout, int KS, int vec_out, int* __restrict__ err, float xscale) {
+             const float* __restrict__ flux, WT* __restrict__ wout, int KS, int vec_out, int* __restrict__ err,
+             float xscale) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -219,6 +225,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   for (int i = tid; i < 128; i += THREADS) {
     s.c3[i] = i < K ? c3[i] : 0.f;
     s.s3[i] = i < K ? s3[i] : 0.f;
+    s.fs[i] = i < K ? flux[i] : 0.f;
+    s.fg[i] = i < K ? flux[K + i] : 0.f;
   }
   // zero X once (the padded K columns stay zero); the ones tiles of the bias MMAs
   for (int i = tid; i < TM * KX * 2 / 16; i += THREADS) reinterpret_cast<uint4*>(s.X)[i] = make_uint4(0, 0, 0, 0);
@@ -423,8 +431,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       // barrier passes that on)
       if (vec_out == 2 && tid == 0) bulk_wait_read();
       if (bar_epi_any(skip)) break;
-      // outputs: TMEM P [0, NP3) -> FP32 rows of stride KS in the staging area
+      // outputs: TMEM P [0, NP3) -> FP32 rows of stride KS in the staging area, with this slice's part of
+      // the pixel's flux s^T w (columns past K hold s_k = 0)
       const int ngrp = NP3 / 16;
+      float mp = 0.f;
       for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
         float d[16];
         umma::tmem_ld16(P + lane_base + q * 16, d);
@@ -437,11 +447,36 @@ __global__ void __launch_bounds__(THREADS, 1)
             o.y = fmaf(d[4 * i4 + 1], s.s3[k + 1], s.c3[k + 1]);
             o.z = fmaf(d[4 * i4 + 2], s.s3[k + 2], s.c3[k + 2]);
             o.w = fmaf(d[4 * i4 + 3], s.s3[k + 3], s.c3[k + 3]);
+            mp = fmaf(o.x, s.fs[k + 0], mp);
+            mp = fmaf(o.y, s.fs[k + 1], mp);
+            mp = fmaf(o.z, s.fs[k + 2], mp);
+            mp = fmaf(o.w, s.fs[k + 3], mp);
             *reinterpret_cast<float4*>(stage + p * KS + k) = o;
           }
         }
       }
+      s.mpart[sl][p] = mp;
       umma::fence_before_sync();
+      bar_epi_any(false);
+      // unit-flux projection of the pixel's weights, on the staging rows this thread wrote
+      {
+        const float cfl = 1.f - ((s.mpart[0][p] + s.mpart[1][p]) + (s.mpart[2][p] + s.mpart[3][p]));
+        for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
+#pragma unroll
+          for (int i4 = 0; i4 < 4; ++i4) {
+            const int k = q * 16 + 4 * i4;
+            if (k < K) {
+              float4* r = reinterpret_cast<float4*>(stage + p * KS + k);
+              float4 o = *r;
+              o.x = fmaf(cfl, s.fg[k + 0], o.x);
+              o.y = fmaf(cfl, s.fg[k + 1], o.y);
+              o.z = fmaf(cfl, s.fg[k + 2], o.z);
+              o.w = fmaf(cfl, s.fg[k + 3], o.w);
+              *r = o;
+            }
+          }
+        }
+      }
       if (vec_out == 2) umma::fence_proxy_async_smem();  // staging rows -> the bulk copy below
       bar_epi_any(false);
       const int nlive = min(TM, npix - p0);
@@ -550,7 +585,7 @@ int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st) {
   k_pack_chunks<<<(4 * NP3 * 64 + 255) / 256, 256, 0, st>>>(p->W3, K, NP3, K, 0.5f, p->tc_w3);
   k_pack_bias<<<HID * 16 / 256, 256, 0, st>>>(p->b1, p->b2, p->tc_bias);
   k_out_affine<<<1, 128, 0, st>>>(p->b3, p->out_scale, p->out_shift, K, p->tc_c3);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 size_t dfp2s_mlp_tc_w1_elems() { return (size_t)HID * KX; }
@@ -560,13 +595,13 @@ static void launch_mlp(const float* fields, const dfp2s_p2s_dev* p, int npix, in
                        WT* out, int KS, int vec_out, float xscale, int grid, size_t sm, cudaStream_t st) {
   cudaFuncSetAttribute(k_mlp_tc<WT, SCALED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_mlp_tc<WT, SCALED><<<grid, THREADS, sm, st>>>(fields, p->J, npix, K, NP3, w1, p->tc_w2, p->tc_w3, p->tc_bias,
-                                                  p->tc_c3, p->out_scale, out, KS, vec_out, p->err, xscale);
+                                                  p->tc_c3, p->out_scale, p->flux, out, KS, vec_out, p->err, xscale);
 }
 
 int dfp2s_mlp_tc_pack_w1_mixed(const dfp2s_p2s_dev* p, const float* L, __nv_bfloat16* out, cudaStream_t st) {
   if (p->J > KX) return DFP2S_EUNSUPPORTED;
   k_pack_w1_mixed<<<(HID * KX + 255) / 256, 256, 0, st>>>(p->W1, p->in_scale, L, p->J, out);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, void* w, int w_dtype, cudaStream_t st,
@@ -598,5 +633,5 @@ int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, v
     if (scaled) launch_mlp<float, true>(fields, p, npix, K, NP3, w1, o, KS, vec_out, xscale, grid, sm, st);
     else launch_mlp<float, false>(fields, p, npix, K, NP3, w1, o, KS, vec_out, xscale, grid, sm, st);
   }
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }

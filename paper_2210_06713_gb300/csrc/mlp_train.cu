@@ -470,7 +470,7 @@ int dfp2s_prior_gram_device(const float* basis, int K, const float* sd, float* G
   k_prior_dft_cols<<<K, 256, 0, st>>>(Tm, Phi);
   k_prior_gram<<<dim3(K, K), 256, 0, st>>>(Phi, K, G);
   k_prior_scale<<<1, 256, 0, st>>>(G, sd, K, Gh);
-  if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
+  if (dfp2s_launch_status() != DFP2S_OK) return DFP2S_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;  // before the pool frees
 }
 
@@ -483,7 +483,7 @@ int dfp2s_mlp_loss_grad_device(int J, int K, int B, const float* params, const f
   const Net g = carve(grads, J, K);
   if (loss) cudaMemsetAsync(loss, 0, sizeof(float), st);
   fwd_bwd(st, p, g, a, X, T, lw, G, B, loss);
-  if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
+  if (dfp2s_launch_status() != DFP2S_OK) return DFP2S_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
 }
 
@@ -515,7 +515,7 @@ __global__ void k_draw_vectors(int n, int J, const float* __restrict__ L, const 
 int dfp2s_launch_draw_vectors(int n, int J, const float* L, const float* drs, int nd, uint64_t seed, uint32_t tag,
                               float* out, cudaStream_t st) {
   k_draw_vectors<<<(n + 127) / 128, 128, 0, st>>>(n, J, L, drs, nd, seed, tag, out);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }
 
 int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_train_params* tp, float* report,
@@ -576,7 +576,7 @@ int dfp2s_mlp_train_device(dfp2s_p2s_dev* p, const float* L32, const dfp2s_mlp_t
   cudaMemsetAsync(m1, 0, np * sizeof(float), st);
   cudaMemsetAsync(m2, 0, np * sizeof(float), st);
   cudaMemsetAsync(state, 0, sizeof(TrainState), st);
-  if (cudaGetLastError() != cudaSuccess) return DFP2S_ECUDA;
+  if (dfp2s_launch_status() != DFP2S_OK) return DFP2S_ECUDA;
   // one training step, captured once and replayed
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DFP2S_ECUDA;

@@ -5,10 +5,14 @@
 // on a 64 x 64 pupil grid whose aperture (radius 16 samples) fills the central
 // 33 x 33 window, so the DFT is pruned to that window on input and to the 33 x 33
 // PSF window on output: X = F U F^T with F[k][i] = exp(-2 pi i (k-16)(i-16)/64).
-// h is normalised to unit sum and projected on the orthonormal basis,
-// w = Phi^T h.  FP32 throughout (tables built in FP64).
+// h is normalised to unit sum and projected on the orthonormal basis under the
+// constraint that the projected PSF keeps that unit sum (reading R28 of the
+// least-squares projection of Eq. p2s PSF): with s_k = sum_u phi_k(u),
+// w = Phi^T h + s (1 - s^T Phi^T h) / (s^T s).  FP32 throughout (tables built
+// in FP64).
 //
-// Learned form: the surrogate network J -> 256 -> 256 -> K with GELU (erf).
+// Learned form: the surrogate network J -> 256 -> 256 -> K with GELU (erf), its
+// output moved onto s^T w = 1 the same way.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -66,6 +70,33 @@ __global__ void k_p2s_tables(int J, int K, const float* __restrict__ basis, floa
   for (int kk = 0; kk < K; ++kk) phiT[(size_t)q * K + kk] = basis[(size_t)kk * KS2 + q];
 }
 
+// s_k = sum_u phi_k(u) and s_k / (s^T s), FP64 sums (one block)
+__global__ void k_flux_tables(const float* __restrict__ basis, int K, float* __restrict__ flux) {
+  __shared__ double sk[DFP2S_MAX_K];
+  __shared__ double ss;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < KS2; ++q) t += (double)basis[(size_t)k * KS2 + q];
+    sk[k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < K; ++k) t += sk[k] * sk[k];
+    ss = t;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    flux[k] = (float)sk[k];
+    flux[K + k] = (float)(sk[k] / ss);
+  }
+}
+
+DFP2S_DEV float warp_sum(float v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 template <typename WT>
 DFP2S_DEV void store_w(WT* w, size_t idx, float v);
 template <>
@@ -77,7 +108,7 @@ template <typename WT, bool PSF_OUT>
 __global__ void __launch_bounds__(NT) k_p2s_exact(const float* __restrict__ fields, int J, int npix, int K,
                                                   const float* __restrict__ zt, const float* __restrict__ mask,
                                                   const float2* __restrict__ dft, const float* __restrict__ phiT,
-                                                  WT* __restrict__ w) {
+                                                  const float* __restrict__ flux, WT* __restrict__ w) {
   extern __shared__ float4 smem_f4[];
   float2* F = reinterpret_cast<float2*>(smem_f4);
   float2* U = F + KS2;
@@ -86,6 +117,7 @@ __global__ void __launch_bounds__(NT) k_p2s_exact(const float* __restrict__ fiel
   float (*a_s)[DFP2S_MAX_J] = reinterpret_cast<float (*)[DFP2S_MAX_J]>(&ph[PB][0]);
   float* hsum = &a_s[PB][0];
   float* red = hsum + PB;
+  float* fred = red + NT / 32;  // per-warp parts of each pixel's flux s^T w (PB x 4 per pixel group)
   const int tid = threadIdx.x;
   for (int q = tid; q < KS2; q += NT) F[q] = dft[q];
   const int nbatch = (npix + PB - 1) / PB;
@@ -166,21 +198,35 @@ __global__ void __launch_bounds__(NT) k_p2s_exact(const float* __restrict__ fiel
       }
       continue;
     }
-    // w[p][k] = sum_q Phi[k][q] h[p][q] / sum h[p]
+    // w[p][k] = sum_q Phi[k][q] h[p][q] / sum h[p], then w += (1 - s^T w) s / (s^T s)
     {
       const int kk = tid % 128;
       const int pg = tid / 128;  // pixels pg*4 .. pg*4+3
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
       if (kk < K) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < KS2; ++q) {
           const float ph_ = __ldg(phiT + (size_t)q * K + kk);
 #pragma unroll
           for (int i = 0; i < 4; ++i) acc[i] = fmaf(ph_, ph[pg * 4 + i][q], acc[i]);
         }
 #pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = acc[i] / hsum[pg * 4 + i];
+      }
+      const float sk = kk < K ? __ldg(flux + kk) : 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float m = warp_sum(sk * acc[i]);
+        if ((tid & 31) == 0) fred[(pg * 4 + i) * 4 + ((tid >> 5) & 3)] = m;
+      }
+      __syncthreads();
+      if (kk < K) {
+        const float gk = __ldg(flux + K + kk);
+#pragma unroll
         for (int i = 0; i < 4; ++i) {
+          const float* fr = fred + (pg * 4 + i) * 4;
+          const float m = (fr[0] + fr[1]) + (fr[2] + fr[3]);
           const int p = p0 + pg * 4 + i;
-          if (p < npix) store_w<WT>(w, (size_t)p * K + kk, acc[i] / hsum[pg * 4 + i]);
+          if (p < npix) store_w<WT>(w, (size_t)p * K + kk, fmaf(1.f - m, gk, acc[i]));
         }
       }
     }
@@ -200,7 +246,8 @@ __global__ void __launch_bounds__(HID) k_p2s_mlp(const float* __restrict__ field
                                                  const float* __restrict__ W2t, const float* __restrict__ b2,
                                                  const float* __restrict__ W3t, const float* __restrict__ b3,
                                                  const float* __restrict__ in_scale, const float* __restrict__ out_scale,
-                                                 const float* __restrict__ out_shift, WT* __restrict__ w) {
+                                                 const float* __restrict__ out_shift, const float* __restrict__ flux,
+                                                 WT* __restrict__ w) {
   extern __shared__ float4 smem_f4[];
   float (*h1)[HID] = reinterpret_cast<float (*)[HID]>(smem_f4);
   float (*h2)[HID] = h1 + MP;
@@ -252,8 +299,25 @@ __global__ void __launch_bounds__(HID) k_p2s_mlp(const float* __restrict__ field
     }
     const float sc = out_scale[tid], sh = out_shift[tid];
 #pragma unroll
+    for (int p = 0; p < MP; ++p) h1[p][tid] = fmaf(acc[p], sc, sh);  // h1 is free after layer 2
+  }
+  __syncthreads();
+  // the flux s^T w of each pixel's weights (warp w: pixels w, w + 8, ...), then w += (1 - s^T w) s / (s^T s)
+  float* mass = &xin[0][0];
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int p = warp; p < MP; p += HID / 32) {
+      float m = 0.f;
+      for (int k = lane; k < K; k += 32) m = fmaf(h1[p][k], __ldg(flux + k), m);
+      m = warp_sum(m);
+      if (lane == 0) mass[p] = m;
+    }
+  }
+  __syncthreads();
+  if (tid < K) {
+    const float gk = __ldg(flux + K + tid);
     for (int p = 0; p < MP; ++p)
-      if (p0 + p < npix) store_w<WT>(w, (size_t)(p0 + p) * K + tid, fmaf(acc[p], sc, sh));
+      if (p0 + p < npix) store_w<WT>(w, (size_t)(p0 + p) * K + tid, fmaf(1.f - mass[p], gk, h1[p][tid]));
   }
 }
 
@@ -261,7 +325,8 @@ __global__ void __launch_bounds__(HID) k_p2s_mlp(const float* __restrict__ field
 
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st) {
   k_p2s_tables<<<(KS2 + 127) / 128, 128, 0, st>>>(p->J, p->K, p->basis, p->zt, p->mask, p->dft, p->phiT);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  if (p->flux) k_flux_tables<<<1, 128, 0, st>>>(p->basis, p->K, p->flux);  // absent in PSF-only tables
+  return dfp2s_launch_status();
 }
 
 int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
@@ -272,20 +337,20 @@ int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, i
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = nbatch < sms * 3 ? nbatch : sms * 3;
-  const size_t sm = 3 * KS2 * sizeof(float2) + (PB * KS2 + PB * DFP2S_MAX_J + PB + NT / 32) * sizeof(float);
+  const size_t sm = 3 * KS2 * sizeof(float2) + (PB * KS2 + PB * DFP2S_MAX_J + PB + NT / 32 + 4 * PB) * sizeof(float);
   cudaFuncSetAttribute(k_p2s_exact<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_p2s_exact<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_p2s_exact<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (w_dtype == DFP2S_W_PSF)
     k_p2s_exact<float, true><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft, p->phiT,
-                                                   (float*)w);
+                                                   p->flux, (float*)w);
   else if (w_dtype == DFP2S_W_BF16)
     k_p2s_exact<__nv_bfloat16, false><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft,
-                                                          p->phiT, (__nv_bfloat16*)w);
+                                                          p->phiT, p->flux, (__nv_bfloat16*)w);
   else
     k_p2s_exact<float, false><<<grid, NT, sm, st>>>(fields, p->J, npix, p->K, p->zt, p->mask, p->dft, p->phiT,
-                                                    (float*)w);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+                                                    p->flux, (float*)w);
+  return dfp2s_launch_status();
 }
 
 int dfp2s_launch_p2s_mlp(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
@@ -297,9 +362,9 @@ int dfp2s_launch_p2s_mlp(const dfp2s_p2s_dev* p, const float* fields, int H, int
   cudaFuncSetAttribute(k_p2s_mlp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (w_dtype == DFP2S_W_BF16)
     k_p2s_mlp<__nv_bfloat16><<<grid, HID, sm, st>>>(fields, p->J, npix, p->K, p->W1, p->b1, p->W2, p->b2, p->W3,
-                                                  p->b3, p->in_scale, p->out_scale, p->out_shift, (__nv_bfloat16*)w);
+                                                  p->b3, p->in_scale, p->out_scale, p->out_shift, p->flux, (__nv_bfloat16*)w);
   else
     k_p2s_mlp<float><<<grid, HID, sm, st>>>(fields, p->J, npix, p->K, p->W1, p->b1, p->W2, p->b2, p->W3, p->b3,
-                                          p->in_scale, p->out_scale, p->out_shift, (float*)w);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+                                          p->in_scale, p->out_scale, p->out_shift, p->flux, (float*)w);
+  return dfp2s_launch_status();
 }

@@ -146,7 +146,7 @@ int dfp2s_launch_field_covariance(const float* a, int J, int H, int W, const int
   }
   k_cov_partial<<<dim3(nb, n_lags), THREADS, 0, st>>>(a, J, H, W, dl, nb, part);
   k_cov_reduce<<<dim3((npairs + 255) / 256, n_lags), 256, 0, st>>>(part, nb, npairs, dl, H, W, out);
-  const bool ok = cudaGetLastError() == cudaSuccess;
+  const bool ok = dfp2s_launch_status() == DFP2S_OK;
   cudaFreeAsync(dl, st);
   cudaFreeAsync(part, st);
   return ok ? DFP2S_OK : DFP2S_ECUDA;

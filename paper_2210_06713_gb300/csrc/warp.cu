@@ -60,5 +60,5 @@ int dfp2s_launch_tilt_warp(const float* img, int C, int H, int W, const float* a
   dim3 grid((per_row + 255) / 256, H);
   const int aligned = ((W & 3) == 0) && (((uintptr_t)a2 | (uintptr_t)a3 | (uintptr_t)out) & 15) == 0;
   k_tilt_warp<<<grid, 256, 0, st>>>(img, C, H, W, a2, a3, out, aligned);
-  return cudaGetLastError() == cudaSuccess ? DFP2S_OK : DFP2S_ECUDA;
+  return dfp2s_launch_status();
 }

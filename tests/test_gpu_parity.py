@@ -265,7 +265,8 @@ def test_mlp_forward_matches_oracle(lib, K, H, W):
               cu(out_shift))
     a = synthetic.random_fields(J, H, W, scale=0.5, seed=3)
     av = np.moveaxis(a, 0, -1).reshape(-1, J).astype(np.float64)
-    o = mlp.predict_weights(params, av, in_scale, out_scale, out_shift).reshape(H, W, K)
+    fl = p2s.flux_vector(basis)
+    o = mlp.predict_weights(params, av, in_scale, out_scale, out_shift, flux=fl).reshape(H, W, K)
     # FP32 CUDA-core form against the FP64 oracle
     g32 = lib.p2s_weights(P, lib.P2S_LEARNED_FP32, cu(a)).cpu().numpy()
     assert rel_l2(g32, o) < TOL
@@ -277,7 +278,7 @@ def test_mlp_forward_matches_oracle(lib, K, H, W):
     z2 = h1 @ _bf(params["W2"]).T + params["b2"]
     h2 = _bf(mlp.gelu(z2))
     y = h2 @ _bf(params["W3"]).T
-    ob = (y * out_scale + (params["b3"] * out_scale + out_shift)).reshape(H, W, K)
+    ob = p2s.flux_projection(y * out_scale + (params["b3"] * out_scale + out_shift), fl).reshape(H, W, K)
     assert rel_l2(g, ob) < 1e-3
     assert rel_l2(g, o) < 2e-2
     gb = lib.p2s_weights(P, lib.P2S_LEARNED, cu(a), w_dtype=lib.W_BF16).float().cpu().numpy()
@@ -325,7 +326,7 @@ def test_learned_frame_folds_the_mixing_into_warp_and_first_layer(lib, d):
         z1 = x @ _bf((prm["W1"] * in_scale[None, :]) @ L).T + prm["b1"]
         h1 = _bf(mlp.gelu(z1))
         h2 = _bf(mlp.gelu(h1 @ _bf(prm["W2"]).T + prm["b2"]))
-        ob = (h2 @ _bf(prm["W3"]).T) * sc + prm["b3"] * sc
+        ob = p2s.flux_projection((h2 @ _bf(prm["W3"]).T) * sc + prm["b3"] * sc, p2s.flux_vector(basis))
         assert rel_l2(wg, ob) < 1e-3
         a = lib.sample_zernike_fields(f, d, 5, it, H, W)
         lib.tilt_warp_blur_tc_prepare(P, img, a[0].contiguous(), a[1].contiguous())

@@ -72,12 +72,60 @@ def test_basis_draws_have_noll_covariance():
 
 
 def test_weights_recover_in_span_coefficients():
+    # a basis whose span holds the PSFs themselves (orthonormalised PSFs): the weights are their exact
+    # coefficients, and since each PSF has unit sum the flux constraint of R28 changes nothing
     J, K = 12, 8
-    Phi = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
-    a = np.random.default_rng(2).standard_normal((3, J)) * 0.2
-    h = p2s.psf(a, J).reshape(3, -1)
-    w = p2s.weights(a, J, Phi)
-    assert np.allclose(w, h @ Phi.reshape(K, -1).T, rtol=1e-12)
+    a = np.random.default_rng(2).standard_normal((K, J)) * 0.2
+    h = p2s.psf(a, J).reshape(K, -1)
+    Q, _ = np.linalg.qr(h.T)  # 1089 x K, orthonormal columns spanning the PSFs
+    Phi = Q.T.reshape(K, 33, 33)
+    w = p2s.weights(a[:3], J, Phi)
+    assert np.allclose(w, h[:3] @ Q, rtol=1e-12, atol=1e-14)
+    assert np.allclose((w @ Q.T), h[:3], atol=1e-13)
+
+
+def test_flux_preserving_projection_is_the_constrained_least_squares_solution():
+    # reading R28: w = argmin ||h - Phi^T w||^2 subject to s^T w = 1, s_k = sum_u phi_k(u).  Checked against
+    # the KKT system of that problem solved directly (no closed form, no orthonormality used), the constraint,
+    # and the cost identity ||h - Phi^T w||^2 = ||h - Phi^T w_ls||^2 + (1 - s^T w_ls)^2 / s^T s
+    J, K = 20, 24
+    basis = p2s.build_basis(3, J, K, 300, [4.0])
+    B = basis.reshape(K, -1)
+    a = p2s.basis_draws(9, J, 6, [4.0])
+    h = p2s.psf(a, J).reshape(6, -1)
+    w = p2s.weights(a, J, basis)
+    w_ls = p2s.weights_unconstrained(a, J, basis)
+    s = B.sum(axis=1)
+    kkt = np.zeros((K + 1, K + 1))
+    kkt[:K, :K] = B @ B.T
+    kkt[:K, K] = s
+    kkt[K, :K] = s
+    for i in range(6):
+        sol = np.linalg.solve(kkt, np.concatenate([B @ h[i], [1.0]]))
+        assert np.allclose(w[i], sol[:K], rtol=1e-10, atol=1e-13)
+        assert w[i] @ s == pytest.approx(1.0, abs=1e-13)
+        c = np.sum((h[i] - w[i] @ B) ** 2)
+        c_ls = np.sum((h[i] - w_ls[i] @ B) ** 2)
+        assert c == pytest.approx(c_ls + (1.0 - w_ls[i] @ s) ** 2 / (s @ s), rel=1e-9)
+    # the plain projection loses flux at this strength (the reason for R28)
+    assert np.abs(w_ls @ s - 1.0).max() > 1e-3
+
+
+def test_surrogate_output_keeps_unit_flux():
+    J, K = 10, 12
+    rng = np.random.default_rng(4)
+    params = {"W1": rng.standard_normal((256, J)) / 4, "b1": rng.standard_normal(256) * 0.1,
+              "W2": rng.standard_normal((256, 256)) / 16, "b2": rng.standard_normal(256) * 0.1,
+              "W3": rng.standard_normal((K, 256)) / 16, "b3": rng.standard_normal(K) * 0.1}
+    s = rng.standard_normal(K)
+    a = rng.standard_normal((5, 7, J))
+    isc, osc, osh = np.ones(J), rng.uniform(0.5, 2, K), rng.standard_normal(K)
+    raw = mlp.predict_weights(params, a, isc, osc, osh)
+    w = mlp.predict_weights(params, a, isc, osc, osh, flux=s)
+    assert np.allclose(w @ s, 1.0, atol=1e-12)
+    # the smallest change that meets the constraint: along s only
+    d = (w - raw).reshape(-1, K)
+    assert np.allclose(d - np.outer(d @ s / (s @ s), s), 0.0, atol=1e-12)
 
 
 # ------------------------------------------------------------------ image

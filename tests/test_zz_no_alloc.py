@@ -59,3 +59,36 @@ def test_noalloc_rejects_factors_beyond_the_static_scratch(d):
     buf = ctypes.create_string_buffer(512)
     lib.dfp2s_last_error(buf, 512)
     assert b"static scratch" in buf.value
+
+
+def test_noalloc_call_takes_no_device_memory(d):
+    # the property the entry point exists for: once the first call on the device has looked up the static
+    # array (and the kernels are loaded), further calls leave the device's free memory unchanged
+    lib = d.load()
+    J, N, H, W = 36, 256, 256, 256
+    f = d.SpectralFactor(J, N, 8.0)
+    out = torch.empty((J, H, W), device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.dfp2s_sample_zernike_fields_noalloc(f.handle, 3.0, 5, 0, H, W, ctypes.c_void_p(out.data_ptr()),
+                                                   stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for frame in range(1, 4):
+        assert lib.dfp2s_sample_zernike_fields_noalloc(f.handle, 3.0, 5, frame, H, W,
+                                                       ctypes.c_void_p(out.data_ptr()), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs a second GPU to make another device current")
+def test_noalloc_rejects_a_factor_of_another_device(d):
+    lib = d.load()
+    with torch.cuda.device(0):
+        f = d.SpectralFactor(6, 64, 8.0)
+    with torch.cuda.device(1):
+        out = torch.empty(6, 32, 32, device="cuda")
+        rc = lib.dfp2s_sample_zernike_fields_noalloc(f.handle, 1.0, 0, 0, 32, 32, ctypes.c_void_p(out.data_ptr()),
+                                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1
