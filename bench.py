@@ -131,7 +131,8 @@ def setup_ours(workload: str, mode: str, device, train_steps: int = 60000):
         info.update({"train_s": time.perf_counter() - t0, "train_steps": rep["steps"],
                      "val_weight_rel_l2": rep["val_weight_rel_l2"]})
     sim = d.Simulator(factor, P, C, H, W)
-    return d, dict(H=H, W=W, C=C, K=K, N=N, dlist=dlist, img=img, factor=factor, P=P, sim=sim, info=info)
+    return d, dict(H=H, W=W, C=C, K=K, N=N, dlist=dlist, img=img, factor=factor, P=P, P_basis=basis, sim=sim,
+                   info=info)
 
 
 def accuracy_vs_exact(d, S, seed):
@@ -172,11 +173,9 @@ def stage_roofline(name, ms, args, peaks, peak_kind, H, W, C, K):
         # Eq. (varying blur) as a dense contraction on the tensor cores: 2 x 33^2 x K MACs per pixel and
         # channel; the events bracket the one k_blur_tc launch of the frame (C <= 3)
         flops = 2.0 * 1089 * K * C * npix
-        # DRAM bytes per launch from the committed ncu capture of this kernel on this workload
-        # (profiles/kernels_512x512x3_learned.md); none for other workloads
-        traffic = 124.2e6 if args.workload == "512" else None
+        # DRAM traffic is not measured in this process (ncu captures only, reported beside the bench)
         roof = {"kernel": "k_blur_tc", "bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": traffic,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
                 "peak_source": peak_kind + " (burst bf16 GEMM)"}
     elif name == "blur":
         flops = 2.0 * 1089 * (K + C) * npix  # per-pixel PSF form on FP32 CUDA cores
@@ -210,6 +209,44 @@ def stage_roofline(name, ms, args, peaks, peak_kind, H, W, C, K):
 
     roof["frac"] = roof["achieved"] / roof["peak"]
     return roof
+
+
+def large_frame(d, S, device, stream, flush):
+    """The other half of the metric: a 3840 x 2160 x 3 frame (1/f^2 texture, J = 36, N = 4096, K = 100,
+    D/r0 = 4) with this run's basis and trained network, learned and exact P2S on the same GPU, frames/s of
+    each (CUDA events on this stream, L2 flushed between frames) and the learned frame's rel-L2 against the
+    exact frame."""
+    import torch
+    from inputs import synthetic
+    H, W, C, kind, K, dlist, desc = WORKLOADS["4k"]
+    N = d.grid_size(H, W, PIX_PER_D)
+    img = torch.as_tensor(synthetic.image_for(kind, H, W, C, seed=0), device=device).contiguous()
+    factor = d.SpectralFactor(J, N, PIX_PER_D)
+    sim = d.Simulator(factor, S["P"], C, H, W)
+    out = torch.empty(C, H, W, device=device)
+    dr = dlist[0]
+    res = {"workload": desc}
+    for name, mode, nw, nt in (("learned", d.P2S_LEARNED, 3, 10), ("exact", d.P2S_EXACT, 1, 3)):
+        for i in range(nw):
+            sim.simulate_frame(img, dr, 500, i, mode, out=out, stream=stream)
+        torch.cuda.synchronize()
+        sim.stage_timing(nt)
+        for i in range(nt):
+            flush.zero_()
+            sim.simulate_frame(img, dr, 500, nw + i, mode, out=out, stream=stream)
+        st = sim.stage_times(nt).astype(np.float64)
+        sim.stage_timing(0)
+        ms = float(st.sum(axis=1).mean())
+        res[name] = {"frames_per_s": 1e3 / ms, "ms_per_frame": ms, "frames": nt,
+                     "stage_ms": dict(zip(["fields", "warp", "p2s", "blur"], st.mean(axis=0).tolist()))}
+    ex = sim.simulate_frame(img, dr, 77, 0, d.P2S_EXACT).double()
+    le = sim.simulate_frame(img, dr, 77, 0, d.P2S_LEARNED).double()
+    S["P"].check()
+    res["rel_l2_learned_vs_exact"] = float((le - ex).norm() / ex.norm())
+    res["learned_over_exact"] = res["learned"]["frames_per_s"] / res["exact"]["frames_per_s"]
+    del sim, factor, ex, le
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args, rank, world, device):
@@ -363,9 +400,7 @@ def run_ours(args, rank, world, device):
         "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if args.mode == "learned" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][6], "p2s": args.mode, "H": H, "W": W, "C": C, "J": J,
-                   "K": K, "N": S["N"], "l2": "flushed between timed frames (256 MB write)",
-                   "parallelism": f"replicas{world}"},
+        "config": config_for(args.workload, args.mode, world),
         "stage_ms": {n: float(v) for n, v in zip(names, mean_stage)},
         "rel_l2_learned_vs_exact": acc,
         "roofline": roof,
@@ -383,57 +418,115 @@ def run_ours(args, rank, world, device):
         "clocks": clk,
         "wall_s": wall,
     }
-    return line
+    if args.workload == "512" and args.mode == "learned" and not args.no_4k:
+        try:
+            line["workloads"] = {"3840x2160x3": large_frame(d, S, device, stream, flush)}
+        except RuntimeError as exc:
+            line["workloads"] = {"3840x2160x3": {"unavailable": str(exc).splitlines()[0][:160]}}
+    return line, S
 
 
-def run_reference_sample(args):
-    """The FP64 oracle on a bounded sample of the same workload, scaled to frames/s."""
-    from oracle import image as oimage, mlp as omlp, noise as onoise, sampler as osampler, spectrum as ospec
-    from oracle import zernike as ozern
+# ---- the FP64 oracle on the host cores: whole frames (oracle.frame.simulate_frame as it stands: fields,
+# warp, network with the unit-flux projection, blur), independent frames on separate processes (spawn, one per
+# core, as the GPU runs independent replicas), timed from the first submitted frame to the last finished one
+_ORACLE = {}
+
+
+def _oracle_worker_init(img, basis, net, J_, N, ppd):
+    from oracle import spectrum
+    _ORACLE.update(img=img, basis=basis, net=net, J=J_, N=N, ppd=ppd)
+    spectrum.lambdas(J_, N, ppd)  # the radial spectrum table (cached per process): setup, not frame work
+
+
+def _oracle_frame(dr, seed, frame):
+    from oracle import frame as oframe
+    o = _ORACLE
+    t0 = time.perf_counter()
+    out = oframe.simulate_frame(o["img"], dr, seed, frame, o["J"], o["basis"], o["ppd"], o["N"], net=o["net"])
+    return time.perf_counter() - t0, float(np.abs(out["out"]).sum())
+
+
+def _oracle_ping(sec):
+    time.sleep(sec)
+    return os.getpid()
+
+
+def oracle_frames(img, basis, net, dlist, N, n_timed, n_warm, workers):
+    """Whole oracle frames on `workers` host processes; returns (wall seconds of the n_timed frames, mean
+    seconds of one frame on one core)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"  # one core per worker process (inherited at spawn)
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx, initializer=_oracle_worker_init,
+                                initargs=(img, basis, net, J, N, PIX_PER_D)) as ex:
+        # start and initialise every worker before anything is timed
+        list(ex.map(_oracle_ping, [1.0] * workers))
+        list(ex.map(_oracle_frame, [dlist[i % len(dlist)] for i in range(n_warm)], [7] * n_warm, range(n_warm)))
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_frame, [dlist[i % len(dlist)] for i in range(n_timed)], [7] * n_timed,
+                          range(n_warm, n_warm + n_timed)))
+        wall = time.perf_counter() - t0
+    return wall, float(np.mean([r[0] for r in res]))
+
+
+def oracle_inputs(workload, basis=None, net=None):
+    """Image, basis and network for the oracle frames.  Without a device basis / trained network (the reference
+    arm runs on the host alone) the oracle's own SVD basis of the same 2000 PSFs and a network of the trained
+    shape with seeded weights (the frame's cost does not depend on their values)."""
+    from oracle import p2s as op2s, sampler as osampler
     from inputs import synthetic
-
-    H, W, C, kind, K, dlist, desc = WORKLOADS[args.workload]
+    H, W, C, kind, K, dlist, _ = WORKLOADS[workload]
     N = osampler.grid_size(H, W, PIX_PER_D)
     img = synthetic.image_for(kind, H, W, C, seed=0)
-    lam = ospec.lambdas(J, N, PIX_PER_D)  # setup, not timed (like the device factor)
-    basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=1).reshape(K, 33, 33)
-    rng = np.random.default_rng(0)
-    params = {"W1": rng.standard_normal((256, J)) / 6, "b1": np.zeros(256), "W2": rng.standard_normal((256, 256)) / 16,
-              "b2": np.zeros(256), "W3": rng.standard_normal((K, 256)) / 16, "b3": np.zeros(K)}
-    in_scale = np.ones(J)
-    in_scale[:2] = 0
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    m_modes = max(1, min(J, int(budget / 0.25)))
-    tile = 64 if args.workload != "64" else 32
-    L = ozern.noll_cholesky(J, dlist[0])
+    if basis is None:
+        basis = op2s.build_basis(0, J, K, 2000, dlist)
+    if net is None:
+        rng = np.random.default_rng(0)
+        params = {"W1": rng.standard_normal((256, J)) / 6, "b1": np.zeros(256),
+                  "W2": rng.standard_normal((256, 256)) / 16, "b2": np.zeros(256),
+                  "W3": rng.standard_normal((K, 256)) / 16, "b3": np.zeros(K)}
+        in_scale = np.ones(J)
+        in_scale[:2] = 0
+        net = {"params": params, "in_scale": in_scale, "out_scale": np.full(K, 0.01),
+               "out_shift": op2s.weights(np.zeros(J), J, basis)}
+    return img, basis, net, dlist, N
 
-    def one():
-        t0 = time.perf_counter()
-        E = onoise.field_spectral_noise(0, 0, m_modes, N)
-        u = osampler.unit_fields_spectral(E, lam[:m_modes])[:, :H, :W]
-        t_fields = (time.perf_counter() - t0) * J / m_modes
-        t1 = time.perf_counter()
-        a = np.zeros((J, tile, tile))
-        a[:m_modes] = u[:, :tile, :tile]
-        a = osampler.mix(L, a)
-        wp = oimage.tilt_warp(img[:, :tile, :tile], a[0], a[1])
-        wgt = omlp.predict_weights(params, np.moveaxis(a, 0, -1), in_scale, np.full(K, 0.01), np.zeros(K))
-        oimage.basis_blur(wp, wgt, basis)
-        t_tile = (time.perf_counter() - t1) * (H * W) / (tile * tile)
-        return t_fields + t_tile
 
-    for _ in range(args.warmup):
-        one()
-    ts = [one() for _ in range(args.steps)]
-    per_frame = float(np.mean(ts))
+def read_network_file(path, J_, K):
+    """The network file of dfp2s_mlp_save (magic, version, J, K, then float32 arrays) as oracle parameters."""
+    raw = open(path, "rb").read()
+    if raw[:8] != b"DFP2SMLP" or tuple(np.frombuffer(raw[8:20], dtype="<i4")) != (1, J_, K):
+        raise ValueError(f"{path} is not a J = {J_}, K = {K} network file")
+    v = np.frombuffer(raw[20:], dtype="<f4").astype(np.float64)
+    out, o = {}, 0
+    for name, shp in (("W1", (256, J_)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (K, 256)),
+                      ("b3", (K,)), ("in_scale", (J_,)), ("out_scale", (K,)), ("out_shift", (K,))):
+        n = int(np.prod(shp))
+        out[name] = v[o:o + n].reshape(shp)
+        o += n
+    return {"params": {k: out[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}, "in_scale": out["in_scale"],
+            "out_scale": out["out_scale"], "out_shift": out["out_shift"]}
+
+
+def host_cores():
     try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+        return len(os.sched_getaffinity(0))
     except Exception:
-        cores = os.cpu_count()
-    sample = (f"per step: fields for {m_modes}/{J} modes on the {N}x{N} grid (scaled by {J}/{m_modes}) + "
-              f"mix, warp, learned P2S and blur on a {tile}x{tile} tile (scaled by pixel count)")
-    return 1.0 / per_frame, cores, sample, desc
+        return os.cpu_count() or 1
+
+
+def config_for(workload, mode, world, extra=None):
+    """The workload description both arms print."""
+    H, W, C, kind, K, dlist, desc = WORKLOADS[workload]
+    from oracle import sampler as osampler  # grid-size rule only
+    cfg = {"workload": desc, "p2s": mode, "H": H, "W": W, "C": C, "J": J, "K": K,
+           "N": osampler.grid_size(H, W, PIX_PER_D), "D_over_r0": dlist,
+           "l2": "flushed between timed frames (256 MB write)", "parallelism": f"replicas{world}"}
+    if extra:
+        cfg.update(extra)
+    return cfg
 
 
 def main():
@@ -447,6 +540,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=60000)
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160x3 half of the metric")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -457,12 +551,22 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        v, cores, sample, desc = run_reference_sample(args)
+        # the FP64 oracle on the host cores: every step one whole frame of the workload; the frames run
+        # concurrently, one per core, so the K timed frames take about K / cores frame times
+        img, basis, net, dlist, N = oracle_inputs(args.workload)
+        if args.mode == "exact":
+            net = None
+        cores = min(host_cores(), max(1, args.steps))
+        wall, per = oracle_frames(img, basis, net, dlist, N, args.steps, args.warmup, cores)
+        v = args.steps / wall
+        sample = (f"whole {args.workload} frames (oracle.frame.simulate_frame: fields on the {N}x{N} grid, warp, "
+                  f"{args.mode} P2S with the oracle's SVD basis of 2000 PSFs{' and a seeded network of the trained shape' if net else ''}, blur), "
+                  f"{args.steps} timed frames on {cores} processes, {per:.2f} s per frame on one core")
         line = {"impl": "reference", "metric": "dense-field frames/s at 512^2 and 4K: learned vs exact P2S, same "
                 "GB300, at tol", "value": v, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": desc, "p2s": args.mode},
+                "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_for(args.workload, args.mode, args.gpus),
                 "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -473,14 +577,29 @@ def main():
         torch.distributed.init_process_group("nccl")
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    line = run_ours(args, rank, world, device)
+    line, S = run_ours(args, rank, world, device)
     if rank == 0:
         if not args.no_cpu_baseline:
-            a2 = argparse.Namespace(**vars(args))
-            a2.steps, a2.warmup = 1, 0
-            v, cores, sample, _ = run_reference_sample(a2)
-            line["cpu_baseline"] = {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                    "sample": sample}
+            # the oracle on this host's cores, on the same workload with this run's device basis and trained
+            # network (read back through the network file): one round of whole frames, one per core
+            import tempfile
+            basis = S["P_basis"].cpu().numpy().astype(np.float64)
+            net = None
+            if args.mode == "learned":
+                fd, path = tempfile.mkstemp(suffix=".bin")
+                os.close(fd)
+                S["P"].save_mlp(path)
+                net = read_network_file(path, J, S["K"])
+                os.unlink(path)
+            img, _, _, dlist, N = oracle_inputs(args.workload, basis=basis, net=net or {})
+            cores = host_cores()
+            nfr = cores if args.mode == "learned" else max(1, cores // 4)
+            wall, per = oracle_frames(img, basis, net, dlist, N, nfr, 0, cores)
+            line["cpu_baseline"] = {
+                "value": nfr / wall, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                "sample": f"{nfr} whole {args.workload} frames ({args.mode} P2S with this run's SVD basis"
+                          f"{' and trained network' if net else ''}) on {cores} processes in {wall:.1f} s, "
+                          f"{per:.2f} s per frame on one core"}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -182,10 +182,13 @@ def _bf16(a):
 
 
 @pytest.mark.parametrize("C,H,W,K", [(3, 64, 130, 100), (1, 33, 200, 16), (5, 20, 128, 112), (2, 17, 19, 128),
-                                     (3, 40, 256, 100)])
+                                     (3, 40, 256, 100), (3, 256, 512, 100), (3, 512, 512, 100)])
 def test_blur_bf16_tensor_cores_match_oracle_on_bf16_operands(lib, C, H, W, K):
     # the tcgen05 blur rounds image and basis to bfloat16 and accumulates in FP32; against the oracle
-    # evaluated on the same bfloat16 operands it must agree to FP32 accumulation error
+    # evaluated on the same bfloat16 operands it must agree to FP32 accumulation error.  The last two shapes
+    # give every CTA of the persistent grid several tiles (1024 and 2048 tiles over at most 152 CTAs; the
+    # second is the 512 x 512 x 3 frame of the benchmark), so the operand rings and the accumulator slots
+    # wrap around many times
     img = synthetic.blobs(H, W, C, n=6, seed=K)
     basis = synthetic.random_orthonormal_rows(K, 33 * 33, seed=C).reshape(K, 33, 33)
     w = torch.as_tensor(np.random.default_rng(H).standard_normal((H, W, K)), dtype=torch.bfloat16, device="cuda")
