@@ -22,8 +22,10 @@
 // the 16-byte run at x0 - 16 + 8b + s, which is 16-byte aligned in the image
 // copy shifted left by s columns; with eight shifted copies of the padded image
 // in global memory one TMA tile load (box 8 x 8 shifts x 20 blocks) writes the
-// blocks of one row and channel straight into shared memory.  L is gathered
-// from those blocks (E_b[s][0], 8b + s = p + 32) row by row as they arrive.
+// blocks of one row and channel straight into shared memory.  L is built by two
+// warps of its own from the unshifted copy in global memory (each image row's
+// 128 values are one contiguous 256-byte run, resident in L2), transposed in
+// registers into its core matrices.
 // The row tiles of B for each iy are laid out once per basis in global memory
 // and streamed with 1-D bulk copies; C stays in shared memory, and so do the
 // tile's weights (one bulk copy per tile).  The epilogue reads D from TMEM (one
@@ -31,9 +33,11 @@
 // pixel's weights: out = sum_k w_k (D[p][k] + c s_k).
 //
 // Precision: the image enters as bfloat16(I - c) with c = 0.5 (centring halves
-// the magnitudes of [0, 1] images and so the rounding error), and the exact
-// term c s_k, s_k = sum_u bf16(phi_k(u)), is added back in FP32; the weights
-// are read in FP32 or BF16 as stored.
+// the magnitudes of [0, 1] images and so the rounding error), and the term
+// c s_k, s_k = sum_u bf16(phi_k(u)), is added back inside the column
+// contraction: its K columns 33, 34, 35 (padding of the 33 taps) hold ones in
+// L and a three-part bfloat16 split of c s_k in C (exact to about 2^-25
+// relative); the weights are read in FP32 or BF16 as stored.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -50,8 +54,8 @@ constexpr int KS = 33;
 constexpr int TM = 128;              // pixels per tile (MMA M)
 constexpr int KM = 32;               // row taps ix = 1..32 (two K = 16 steps)
 constexpr int KL = 48;               // column taps iy = 0..32 padded to three K = 16 steps
-constexpr int NBLK = 20;             // blocks E_0..E_19 per image row (the MMAs use E_0..E_18)
-constexpr int ROWB = NBLK * 128;     // 2560 bytes per row and channel
+constexpr int NBLK = 19;             // blocks E_0..E_18 per image row (the two K = 16 steps reach E_18)
+constexpr int ROWB = NBLK * 128;     // 2432 bytes per row and channel
 constexpr int NSHIFT = 8;            // shifted image copies
 constexpr int CMAX = 3;              // channels per pass
 constexpr int NSLOT = 4;             // TMEM accumulator slots of NP <= 128 columns (512 in all)
@@ -61,24 +65,24 @@ constexpr int L_WARP0 = 2;
 constexpr int NL_WARPS = 2;
 constexpr int EPI_WARP0 = 4;
 constexpr int THREADS = (EPI_WARP0 + 4 * CMAX) * 32;
-constexpr int NB = 6;                // row-block ring (one slot per basis row iy)
-constexpr int NBB = 6;               // basis-tile ring
+constexpr int NB = 7;                // operand ring: one slot per basis row iy (its image row blocks and basis tile)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
 constexpr int B_SLOT = 128 * KM * 2;         // bytes of one basis-tile slot (NP <= 128)
 constexpr int L_BYTES = TM * KL * 2;         // column operand of one channel
 constexpr int C_BYTES = 128 * KL * 2;        // column taps of the basis
 
+struct Slot {
+  uint8_t A[CMAX][ROWB];           // Hankel blocks of one image row per channel (TMA)
+  uint8_t B[B_SLOT];               // the basis row tile
+};
 struct Smem {
-  uint8_t A[NB][CMAX][ROWB];       // Hankel blocks of one image row per channel (TMA)
-  uint8_t B[NBB][B_SLOT];          // basis tiles of one row each
+  Slot ring[NB];                   // operand ring, one basis row per slot
   uint8_t L[CMAX][L_BYTES];        // column operand of the tile
   uint8_t Cb[C_BYTES];             // column taps (resident)
   float Wt[TM * 128];              // the tile's weights (FP32, K per pixel)
-  float csum[128];
-  uint64_t a_full[NB], a_free[NB];
-  uint64_t b_full[NBB], b_free[NBB];
+  uint64_t full[NB], empty[NB];
   uint64_t l_full, l_free;
-  uint64_t c_full, w_full, w_empty;
+  uint64_t c_full, w_full, w_empty, drain;
   uint64_t acc_full[NSLOT], acc_empty[NSLOT];
   uint32_t tmem_base;
   int abort;
@@ -181,8 +185,11 @@ __global__ void __launch_bounds__(128, 6)
 }
 
 // Row tiles: Bt[iy][j][g][n8][k8] = phi_{8j+n8}(iy, 32 - (8g+k8)), g < 4 (taps ix = 1..32),
-// then the column taps Ct[j][g][n8][k8] = phi_{8j+n8}(8g+k8, 0), g < 6; zero outside.
-__global__ void k_build_bt(const float* __restrict__ basis, int K, int NP, __nv_bfloat16* __restrict__ Bt) {
+// then the column taps Ct[j][g][n8][k8] = phi_{8j+n8}(8g+k8, 0), g < 6, with the rows 8g+k8 = 33, 34, 35
+// holding the bfloat16 parts hi, mid, lo of the centring term cs_k (cs_k = hi + mid + lo to about 2^-25);
+// zero outside.
+__global__ void k_build_bt(const float* __restrict__ basis, int K, int NP, const float* __restrict__ cs,
+                           __nv_bfloat16* __restrict__ Bt) {
   const int per_iy = NP * KM;
   const int nrow = KS * per_iy;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,6 +214,12 @@ __global__ void k_build_bt(const float* __restrict__ basis, int K, int NP, __nv_
     const int n8 = rem / 8, k8 = rem - n8 * 8;
     const int k = 8 * j + n8, iy = 8 * g + k8;
     if (k < K && iy < KS) v = basis[((size_t)k * KS + iy) * KS];
+    if (k < K && iy >= KS && iy < KS + 3) {
+      const float c = cs[k];
+      const float hi = __bfloat162float(__float2bfloat16_rn(c));
+      const float mid = __bfloat162float(__float2bfloat16_rn(c - hi));
+      v = iy == KS ? hi : (iy == KS + 1 ? mid : c - hi - mid);
+    }
   }
   Bt[i] = __float2bfloat16_rn(v);
 }
@@ -243,8 +256,8 @@ __global__ void k_scale(float* __restrict__ v, int n, float a) {
 template <typename WT, int C>
 __global__ void __launch_bounds__(THREADS, 1)
     k_blur_tc(const __grid_constant__ CUtensorMap tmap, int H, int W, const __nv_bfloat16* __restrict__ Bt, int K,
-              int NP, const float* __restrict__ csum, const WT* __restrict__ w, int w_vec, float* __restrict__ out,
-              int* __restrict__ err) {
+              int NP, const __nv_bfloat16* __restrict__ planes, int Wq, size_t chan_stride,
+              const WT* __restrict__ w, int w_vec, float* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned base in the shared window (the launch adds 1024 bytes of slack)
   uint8_t* sbase = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -261,18 +274,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (tid == 0) {
     for (int i = 0; i < NB; ++i) {
-      umma::mbar_init(&s.a_full[i], 1);
-      umma::mbar_init(&s.a_free[i], 1 + NL_WARPS);  // the MMAs' commit and the column-operand warps
-    }
-    for (int i = 0; i < NBB; ++i) {
-      umma::mbar_init(&s.b_full[i], 1);
-      umma::mbar_init(&s.b_free[i], 1);
+      umma::mbar_init(&s.full[i], 1);   // the producer's expect_tx: image row blocks and basis tile
+      umma::mbar_init(&s.empty[i], 1);  // the MMAs' commit
     }
     umma::mbar_init(&s.l_full, NL_WARPS);
     umma::mbar_init(&s.l_free, 1);
     umma::mbar_init(&s.c_full, 1);
     umma::mbar_init(&s.w_full, 1);
     umma::mbar_init(&s.w_empty, 4 * C);
+    umma::mbar_init(&s.drain, 1);
     for (int i = 0; i < NSLOT; ++i) {
       umma::mbar_init(&s.acc_full[i], 1);
       umma::mbar_init(&s.acc_empty[i], 4);
@@ -280,8 +290,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     s.abort = 0;
     umma::fence_mbar_init();
   }
-  for (int i = tid; i < 128; i += THREADS) s.csum[i] = i < NP ? csum[i] : 0.f;
-  // the column operand's padding K columns (iy = 33..47) stay zero
+  // the column operand's padding K columns (iy = 36..47) stay zero
   for (int i = tid; i < CMAX * L_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(&s.L[0][0])[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
     umma::tmem_alloc(&s.tmem_base, 512);
@@ -300,11 +309,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     // ---------------------------------------------------------- copies (one lane)
+    // The ring position (slot, round) is kept in counters: this thread and the MMA thread run a tight loop
+    // each, and the MMA thread's instruction latency bounds the tensor cores' rate.
     if (lane == 0) {
       bool ok = true;
-      uint32_t it = 0;                    // rows handled
-      uint32_t a_issued = 0, b_issued = 0;  // row-block and basis-tile copies issued
-      int w_issued = 0;                   // weight tiles issued
+      uint32_t slot = 0, round = 0, issued = 0;  // ring position; operand rows issued
+      int w_issued = 0;                          // weight tiles issued
+      const uint32_t row_tx = (uint32_t)(C * ROWB) + bt_bytes;
       umma::mbar_arrive_expect_tx(&s.c_full, ct_bytes);
       umma::bulk_g2s(s.Cb, Ct, ct_bytes, &s.c_full);
       auto issue_w = [&](int t) {
@@ -319,23 +330,23 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = 0; t < my_tiles && ok; ++t) {
         int y, x0;
         tile_xy(t, y, x0);
-        for (int iy = 0; iy < KS; ++iy, ++it) {
-          const int sb = it % NB, bb = it % NBB;
-          if (it >= NB && !umma::mbar_wait(&s.a_free[sb], ((it / NB) - 1) & 1, kWaitNs)) {
+        const int xb = x0 >> 3;
+        const __nv_bfloat16* bsrc = Bt;
+        for (int iy = 0; iy < KS; ++iy, bsrc += NP * KM) {
+          if (issued >= NB && !umma::mbar_wait(&s.empty[slot], (round - 1) & 1, kWaitNs)) {
             ok = false;
             break;
           }
-          umma::mbar_arrive_expect_tx(&s.a_full[sb], (uint32_t)(C * ROWB));
+          Slot& sl = s.ring[slot];
+          umma::mbar_arrive_expect_tx(&s.full[slot], row_tx);
 #pragma unroll
-          for (int c = 0; c < C; ++c) tma_load_5d(s.A[sb][c], &tmap, 0, 0, x0 >> 3, y + (KS - 1 - iy), c, &s.a_full[sb]);
-          ++a_issued;
-          if (it >= NBB && !umma::mbar_wait(&s.b_free[bb], ((it / NBB) - 1) & 1, kWaitNs)) {
-            ok = false;
-            break;
+          for (int c = 0; c < C; ++c) tma_load_5d(sl.A[c], &tmap, 0, 0, xb, y + (KS - 1 - iy), c, &s.full[slot]);
+          umma::bulk_g2s(sl.B, bsrc, bt_bytes, &s.full[slot]);
+          ++issued;
+          if (++slot == NB) {
+            slot = 0;
+            ++round;
           }
-          umma::mbar_arrive_expect_tx(&s.b_full[bb], bt_bytes);
-          umma::bulk_g2s(s.B[bb], Bt + (size_t)iy * (NP * KM), bt_bytes, &s.b_full[bb]);
-          ++b_issued;
           // this tile's weights, once the epilogue of the previous tile has released the buffer
           if (w_vec && w_issued == t && iy >= 2) {
             if (t == 0 || umma::mbar_ready(&s.w_empty, (t - 1) & 1)) {
@@ -356,10 +367,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       // every issued copy must land before the CTA exits (bounded)
       umma::mbar_wait(&s.c_full, 0, kWaitNs);
-      for (uint32_t u = (a_issued >= NB ? a_issued - NB : 0); u < a_issued; ++u)
-        umma::mbar_wait(&s.a_full[u % NB], (u / NB) & 1, kWaitNs);
-      for (uint32_t u = (b_issued >= NBB ? b_issued - NBB : 0); u < b_issued; ++u)
-        umma::mbar_wait(&s.b_full[u % NBB], (u / NBB) & 1, kWaitNs);
+      for (uint32_t u = (issued >= NB ? issued - NB : 0); u < issued; ++u)
+        umma::mbar_wait(&s.full[u % NB], (u / NB) & 1, kWaitNs);
       if (w_issued > 0) umma::mbar_wait(&s.w_full, (w_issued - 1) & 1, kWaitNs);
     }
   } else if (warp == 1) {
@@ -367,118 +376,133 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       // row blocks: core matrices 128 B apart along M and K (Hankel); row tiles [j][g][8][8]: K-adjacent
       // core matrices 128 B apart, 8-filter groups 512 B apart; column operand [p/8][g][8][8] and
-      // column taps [j][g][8][8]: 128 B along K, 768 B along M/N
-      const uint64_t a_base = umma::sdesc(umma::smem_u32(s.A[0][0]), 128, 128);
-      const uint64_t b_base = umma::sdesc(umma::smem_u32(s.B[0]), 128, KM / 8 * 128);
+      // column taps [j][g][8][8]: 128 B along K, 768 B along M/N.  Descriptors = base + (byte offset >> 4).
+      const uint64_t a_base = umma::sdesc(umma::smem_u32(s.ring[0].A[0]), 128, 128);
+      const uint64_t b_base = umma::sdesc(umma::smem_u32(s.ring[0].B), 128, KM / 8 * 128);
       const uint64_t l_base = umma::sdesc(umma::smem_u32(s.L[0]), 128, KL / 8 * 128);
       const uint64_t c_desc = umma::sdesc(umma::smem_u32(s.Cb), 128, KL / 8 * 128);
+      constexpr uint32_t SLOT16 = sizeof(Slot) >> 4, ROW16 = ROWB >> 4, L16 = L_BYTES >> 4;
       bool ok = my_tiles == 0 || umma::mbar_wait(&s.c_full, 0, kWaitNs);
-      uint32_t it = 0;
+      uint32_t slot = 0, round = 0;
+      uint64_t a_s = a_base, b_s = b_base;  // descriptors of the current slot
       for (int t = 0; t < my_tiles && ok; ++t) {
-        for (int iy = 0; iy < KS; ++iy, ++it) {
-          const int sb = it % NB, bb = it % NBB;
-          if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs) ||
-              !umma::mbar_wait(&s.b_full[bb], (it / NBB) & 1, kWaitNs)) {
+        uint32_t dch[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) dch[c] = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
+        for (int iy = 0; iy < KS; ++iy) {
+          if (!umma::mbar_wait(&s.full[slot], round & 1, kWaitNs)) {
             ok = false;
             break;
           }
           umma::fence_after_sync();
-          // descriptors = base descriptor + (byte offset >> 4)
-          const uint64_t a_it = a_base + (uint64_t)(((uint32_t)sb * (CMAX * ROWB)) >> 4);
-          const uint64_t b_it = b_base + (uint64_t)(((uint32_t)bb * B_SLOT) >> 4);
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const uint32_t g = (uint32_t)(t * C + c);
-            if (iy == 0 && g >= NSLOT) {
-              // a fresh accumulator: wait until the epilogue has emptied the slot (the previous
-              // channels' MMAs are already running meanwhile)
-              if (!umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) {
-                ok = false;
-                break;
-              }
-              umma::fence_after_sync();
-            }
-            const uint32_t d = tmem + (g % NSLOT) * NP;
-            const uint64_t a_c = a_it + (uint64_t)((c * ROWB) >> 4);
-            umma::mma_bf16(d, a_c, b_it, idesc, iy != 0);
-            umma::mma_bf16(d, a_c + 16, b_it + 16, idesc, 1);
-          }
-          if (!ok) break;
-          umma::mma_commit(&s.a_free[sb]);
-          umma::mma_commit(&s.b_free[bb]);
-          if (iy == KS - 1) {
-            // the column taps, once the tile's column operand is complete
-            if (!umma::mbar_wait(&s.l_full, t & 1, kWaitNs)) {
-              ok = false;
-              break;
-            }
-            umma::fence_after_sync();
+          if (iy == 0) {
+            // fresh accumulators: each waits until the epilogue has emptied its slot (the previous channels'
+            // MMAs are already running meanwhile)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              const uint32_t d = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
-              const uint64_t l_c = l_base + (uint64_t)((c * L_BYTES) >> 4);
-              umma::mma_bf16(d, l_c, c_desc, idesc, 1);
-              umma::mma_bf16(d, l_c + 16, c_desc + 16, idesc, 1);
-              umma::mma_bf16(d, l_c + 32, c_desc + 32, idesc, 1);
+              const uint32_t g = (uint32_t)(t * C + c);
+              if (g >= NSLOT) {
+                if (!umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) {
+                  ok = false;
+                  break;
+                }
+                umma::fence_after_sync();
+              }
+              umma::mma_bf16(dch[c], a_s + c * ROW16, b_s, idesc, 0);
+              umma::mma_bf16(dch[c], a_s + c * ROW16 + 16, b_s + 16, idesc, 1);
             }
-            umma::mma_commit(&s.l_free);
+            if (!ok) break;
+          } else {
 #pragma unroll
-            for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
+            for (int c = 0; c < C; ++c) {
+              umma::mma_bf16(dch[c], a_s + c * ROW16, b_s, idesc, 1);
+              umma::mma_bf16(dch[c], a_s + c * ROW16 + 16, b_s + 16, idesc, 1);
+            }
+          }
+          umma::mma_commit(&s.empty[slot]);
+          if (++slot == NB) {
+            slot = 0;
+            ++round;
+            a_s = a_base;
+            b_s = b_base;
+          } else {
+            a_s += SLOT16;
+            b_s += SLOT16;
           }
         }
+        if (!ok) break;
+        // the column taps, once the tile's column operand is complete
+        if (!umma::mbar_wait(&s.l_full, t & 1, kWaitNs)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const uint64_t l_c = l_base + c * L16;
+          umma::mma_bf16(dch[c], l_c, c_desc, idesc, 1);
+          umma::mma_bf16(dch[c], l_c + 16, c_desc + 16, idesc, 1);
+          umma::mma_bf16(dch[c], l_c + 32, c_desc + 32, idesc, 1);
+        }
+        umma::mma_commit(&s.l_free);
+#pragma unroll
+        for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
       }
       if (!ok) {
         s.abort = 1;
         atomicExch(err, 1);
+        // the MMAs issued so far complete before the tensor memory is released (bounded)
+        umma::mma_commit(&s.drain);
+        umma::mbar_wait(&s.drain, 0, kWaitNs);
       } else if (my_tiles > 0) {
         const int t = my_tiles - 1;  // the last MMAs have completed before the CTA exits
         umma::mbar_wait(&s.l_free, t & 1, kWaitNs);
       }
     }
   } else if (warp < EPI_WARP0) {
-    // ---------------------------------------------------------- column operand L from the row blocks
-    // Thread (c, m) keeps, for eight consecutive basis rows iy = 8 g + e, the pixels p = 8 m .. 8 m + 7
-    // of row 0 of block E_{m+4} (8 b + t = p + 32, one 16-byte load per row), then transposes the
-    // 8 x 8 tile in registers and writes the core matrix L[8 m .. 8 m + 7][8 g .. 8 g + 7].
+    // ---------------------------------------------------------- column operand L
+    // L[p][iy] = P[c][0][y + 32 - iy][x0 + 32 + p] (the unshifted padded plane).  Thread (c, m) loads, for
+    // eight basis rows iy = 8 g + e, the pixels p = 8 m .. 8 m + 7 (one 16-byte load per row, 16 threads
+    // read a row's 256 contiguous bytes), transposes the 8 x 8 tile in registers and writes the core matrix
+    // L[8 m .. 8 m + 7][8 g .. 8 g + 7], its eight 16-byte rows in an order rotated by m so that the 16
+    // threads of a channel hit distinct banks.  Columns 33, 34, 35 hold ones (the centring term's factor).
     const int lt = tid - L_WARP0 * 32;
     const int lc = lt >> 4, m = lt & 15;
     const bool active = lc < C;
-    uint32_t it = 0;
+    const __nv_bfloat16* plane = planes + (size_t)(active ? lc : 0) * chan_stride;
     for (int t = 0; t < my_tiles && !s.abort; ++t) {
+      int y, x0;
+      tile_xy(t, y, x0);
+      const __nv_bfloat16* src = plane + (size_t)(y + 32) * Wq + x0 + 32 + 8 * m;
       // the column operand was last read by the column MMAs of tile t - 1
       if (t >= 1 && !umma::mbar_wait(&s.l_free, (t - 1) & 1, kWaitNs)) s.abort = 1;
-      for (int g = 0; g < (KS + 7) / 8 && !s.abort; ++g) {
+      if (s.abort) break;
+      for (int g = 0; g < (KS + 3 + 7) / 8; ++g) {
         uint4 win[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          win[e] = make_uint4(0, 0, 0, 0);
-          if (8 * g + e < KS) {
-            const int sb = it % NB;
-            if (!umma::mbar_wait(&s.a_full[sb], (it / NB) & 1, kWaitNs)) {
-              s.abort = 1;
-              break;
-            }
-            if (active) win[e] = *reinterpret_cast<const uint4*>(s.A[sb][lc] + (m + 4) * 128);
-            __syncwarp();
-            if (lane == 0) umma::mbar_arrive(&s.a_free[sb]);
-            ++it;
-          }
+          const int iy = 8 * g + e;
+          if (iy < KS) win[e] = active ? __ldg(reinterpret_cast<const uint4*>(src - (size_t)iy * Wq)) : make_uint4(0, 0, 0, 0);
+          else if (iy < KS + 3) win[e] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+          else win[e] = make_uint4(0, 0, 0, 0);
         }
         if (active) {
-          // out[j] = column j of the 8 x 8 bf16 tile: rows 2k and 2k + 1 in word k
+          // row j of the transposed tile: element e is bf16 j of win[e] (word j / 2, half j % 2)
           uint8_t* dst = s.L[lc] + (m * (KL / 8) + g) * 128;
+          auto comp = [](const uint4& v, int q) { return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w)); };
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int jp = 0; jp < 8; ++jp) {
+            const int j = (jp + m) & 7;
             const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;
             const int wj = j >> 1;
-            auto word = [&](const uint4& v) { return wj == 0 ? v.x : (wj == 1 ? v.y : (wj == 2 ? v.z : v.w)); };
-            const uint4 o = make_uint4(__byte_perm(word(win[0]), word(win[1]), sel), __byte_perm(word(win[2]), word(win[3]), sel),
-                                       __byte_perm(word(win[4]), word(win[5]), sel), __byte_perm(word(win[6]), word(win[7]), sel));
+            const uint4 o = make_uint4(__byte_perm(comp(win[0], wj), comp(win[1], wj), sel),
+                                       __byte_perm(comp(win[2], wj), comp(win[3], wj), sel),
+                                       __byte_perm(comp(win[4], wj), comp(win[5], wj), sel),
+                                       __byte_perm(comp(win[6], wj), comp(win[7], wj), sel));
             *reinterpret_cast<uint4*>(dst + j * 16) = o;
           }
         }
       }
-      if (s.abort) break;
       umma::fence_proxy_async_smem();  // L stores -> visible to the tensor cores
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&s.l_full);
@@ -496,7 +520,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool live = x < W;
         const uint32_t g = (uint32_t)(t * C + c);
         const uint32_t slot = g % NSLOT;
-        if (!umma::mbar_wait_backoff(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs)) s.abort = 1;
+        if (!umma::mbar_wait_backoff(&s.acc_full[slot], (g / NSLOT) & 1, kWaitNs, 128)) s.abort = 1;
         if (w_vec && !umma::mbar_wait_backoff(&s.w_full, t & 1, kWaitNs)) s.abort = 1;
         if (s.abort) break;
         umma::fence_after_sync();
@@ -514,6 +538,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int qq = 0; qq < 4; ++qq)
               if (4 * h + qq < nq) tmem_ld16_async(taddr + (4 * h + qq) * 16, d[qq]);
             tmem_wait_ld4(d);
+            if (4 * (h + 1) >= nq) {
+              // the accumulator is in registers: hand the slot back to the MMAs before the weighted sums
+              umma::fence_before_sync();
+              __syncwarp();
+              if (lane == 0) umma::mbar_arrive(&s.acc_empty[slot]);
+            }
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
               const int q = 4 * h + qq;
@@ -538,17 +568,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                   }
                 }
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc = fmaf(wk[i], d[qq][i] + s.csum[q * 16 + i], acc);
+                for (int i = 0; i < 16; ++i) acc = fmaf(wk[i], d[qq][i], acc);
               }
             }
           }
         }
-        umma::fence_before_sync();
         __syncwarp();
-        if (lane == 0) {
-          umma::mbar_arrive(&s.acc_empty[slot]);
-          if (w_vec) umma::mbar_arrive(&s.w_empty);
-        }
+        if (lane == 0 && w_vec) umma::mbar_arrive(&s.w_empty);
         if (live) out[((size_t)c * H + y) * W + x] = acc;
       }
     }
@@ -586,9 +612,9 @@ static int blur_tc_scratch(dfp2s_p2s_dev* p, int C, int H, int W, cudaStream_t s
     const int n = KS * NP * KM + NP * KL;  // row tiles, then the column taps
     if (cudaMalloc((void**)&p->bt, (size_t)n * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
     if (cudaMalloc((void**)&p->bsum, (size_t)NP * sizeof(float)) != cudaSuccess) return DFP2S_ENOMEM;
-    k_build_bt<<<(n + 255) / 256, 256, 0, st>>>(p->basis, K, NP, p->bt);
     k_basis_sums<<<NP, 256, 0, st>>>(p->basis, K, NP, p->bsum);
     k_scale<<<1, 128, 0, st>>>(p->bsum, NP, centre);
+    k_build_bt<<<(n + 255) / 256, 256, 0, st>>>(p->basis, K, NP, p->bsum, p->bt);
   }
   if (!p->err) {
     if (cudaMalloc((void**)&p->err, sizeof(int)) != cudaSuccess) return DFP2S_ENOMEM;
@@ -677,8 +703,10 @@ int dfp2s_launch_blur_tc_run(dfp2s_p2s_dev* p, int C, int H, int W, const void* 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return DFP2S_EUNSUPPORTED;
     float* oc = out + (size_t)c0 * H * W;
-#define DFP2S_BLUR_LAUNCH(WT, NC, WPTR, WV) \
-  k_blur_tc<WT, NC><<<grid, THREADS, sm, st>>>(tmap, H, W, p->bt, K, NP, p->bsum, WPTR, WV, oc, p->err)
+    const __nv_bfloat16* planes = p->pad + (size_t)c0 * NSHIFT * plane;  // shift 0 of channel c0
+#define DFP2S_BLUR_LAUNCH(WT, NC, WPTR, WV)                                                                    \
+  k_blur_tc<WT, NC><<<grid, THREADS, sm, st>>>(tmap, H, W, p->bt, K, NP, planes, Wq, (size_t)NSHIFT * plane, WPTR, \
+                                               WV, oc, p->err)
     if (w_dtype == DFP2S_W_BF16) {
       const __nv_bfloat16* wb = (const __nv_bfloat16*)w;
       if (nc == 1) DFP2S_BLUR_LAUNCH(__nv_bfloat16, 1, wb, 0);

@@ -122,6 +122,10 @@ DFP2S_DEV bool bar_epi_any(bool v) {
   return r != 0;
 }
 
+// Barrier of the four epilogue warps that read TMEM lane quarter q4 (warps q4, q4 + 4, q4 + 8, q4 + 12):
+// named barriers 2..5, 128 threads each.
+DFP2S_DEV void bar_quarter(int q4) { asm volatile("bar.sync %0, 128;" ::"r"(2 + q4) : "memory"); }
+
 // 1-D bulk copy shared -> global (both 16-byte aligned, size a multiple of 16) in a bulk group; wait until
 // its source may be overwritten, or until every issued copy has completed.
 DFP2S_DEV void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
@@ -431,48 +435,44 @@ __global__ void __launch_bounds__(THREADS, 1)
       // barrier passes that on)
       if (vec_out == 2 && tid == 0) bulk_wait_read();
       if (bar_epi_any(skip)) break;
-      // outputs: TMEM P [0, NP3) -> FP32 rows of stride KS in the staging area, with this slice's part of
-      // the pixel's flux s^T w (columns past K hold s_k = 0)
+      // outputs: TMEM P [0, NP3) -> y * s3 + c3 in registers (groups q = sl and sl + 4 of 16 columns; NP3 <= 128)
+      // with this slice's part of the pixel's flux s^T w (columns past K hold s_k = 0); the four slices of a
+      // pixel (the warps sharing its TMEM lane quarter) exchange their parts, then each writes its columns of
+      // the unit-flux weights w + (1 - s^T w) s / (s^T s) into FP32 rows of stride KS in the staging area
       const int ngrp = NP3 / 16;
+      float o[2][16];
       float mp = 0.f;
-      for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
-        float d[16];
-        umma::tmem_ld16(P + lane_base + q * 16, d);
 #pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4) {
-          const int k = q * 16 + 4 * i4;
-          if (k < K) {
-            float4 o;
-            o.x = fmaf(d[4 * i4 + 0], s.s3[k + 0], s.c3[k + 0]);
-            o.y = fmaf(d[4 * i4 + 1], s.s3[k + 1], s.c3[k + 1]);
-            o.z = fmaf(d[4 * i4 + 2], s.s3[k + 2], s.c3[k + 2]);
-            o.w = fmaf(d[4 * i4 + 3], s.s3[k + 3], s.c3[k + 3]);
-            mp = fmaf(o.x, s.fs[k + 0], mp);
-            mp = fmaf(o.y, s.fs[k + 1], mp);
-            mp = fmaf(o.z, s.fs[k + 2], mp);
-            mp = fmaf(o.w, s.fs[k + 3], mp);
-            *reinterpret_cast<float4*>(stage + p * KS + k) = o;
+      for (int iq = 0; iq < 2; ++iq) {
+        const int q = sl + 4 * iq;
+        if (q < ngrp) {
+          umma::tmem_ld16(P + lane_base + q * 16, o[iq]);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int k = q * 16 + i;
+            o[iq][i] = fmaf(o[iq][i], s.s3[k], s.c3[k]);
+            mp = fmaf(o[iq][i], s.fs[k], mp);
           }
         }
       }
       s.mpart[sl][p] = mp;
       umma::fence_before_sync();
-      bar_epi_any(false);
-      // unit-flux projection of the pixel's weights, on the staging rows this thread wrote
-      {
-        const float cfl = 1.f - ((s.mpart[0][p] + s.mpart[1][p]) + (s.mpart[2][p] + s.mpart[3][p]));
-        for (int q = sl; q < ngrp; q += EPI_WARPS / 4) {
+      bar_quarter(q4);
+      const float cfl = 1.f - ((s.mpart[0][p] + s.mpart[1][p]) + (s.mpart[2][p] + s.mpart[3][p]));
+#pragma unroll
+      for (int iq = 0; iq < 2; ++iq) {
+        const int q = sl + 4 * iq;
+        if (q < ngrp) {
 #pragma unroll
           for (int i4 = 0; i4 < 4; ++i4) {
             const int k = q * 16 + 4 * i4;
             if (k < K) {
-              float4* r = reinterpret_cast<float4*>(stage + p * KS + k);
-              float4 o = *r;
-              o.x = fmaf(cfl, s.fg[k + 0], o.x);
-              o.y = fmaf(cfl, s.fg[k + 1], o.y);
-              o.z = fmaf(cfl, s.fg[k + 2], o.z);
-              o.w = fmaf(cfl, s.fg[k + 3], o.w);
-              *r = o;
+              float4 v;
+              v.x = fmaf(cfl, s.fg[k + 0], o[iq][4 * i4 + 0]);
+              v.y = fmaf(cfl, s.fg[k + 1], o[iq][4 * i4 + 1]);
+              v.z = fmaf(cfl, s.fg[k + 2], o[iq][4 * i4 + 2]);
+              v.w = fmaf(cfl, s.fg[k + 3], o[iq][4 * i4 + 3]);
+              *reinterpret_cast<float4*>(stage + p * KS + k) = v;
             }
           }
         }

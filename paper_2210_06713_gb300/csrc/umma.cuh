@@ -76,11 +76,10 @@ DFP2S_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   }
 }
 
-// The same wait with a sleep between polls (32 ns doubling to 512 ns), for
-// warps that wait long and are not latency-critical (epilogues): their polling
-// otherwise competes for shared-memory cycles with the tensor cores' operand
-// reads.
-DFP2S_DEV bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+// The same wait with a sleep between polls (32 ns doubling to max_ns), for
+// warps that wait long (epilogues): their polling otherwise competes for
+// shared-memory cycles with the tensor cores' operand reads.
+DFP2S_DEV bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, uint64_t limit_ns, uint32_t max_ns = 512) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   uint32_t ns = 32;
@@ -88,7 +87,7 @@ DFP2S_DEV bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, uint64_t limit_
     __nanosleep(ns);
     if (mbar_test(bar, parity)) return true;
     if (global_ns() - t0 > limit_ns) return false;
-    if (ns < 512) ns <<= 1;
+    if (ns < max_ns) ns <<= 1;
   }
 }
 
