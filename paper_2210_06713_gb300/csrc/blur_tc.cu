@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int xb = x0 >> 3;
         const __nv_bfloat16* bsrc = Bt;
         for (int iy = 0; iy < KS; ++iy, bsrc += NP * KM) {
-          if (issued >= NB && !umma::mbar_wait(&s.empty[slot], (round - 1) & 1, kWaitNs)) {
+          // (a sleep between polls: a spinning wait slows the MMA thread's barrier operations)
+          if (issued >= NB && !umma::mbar_wait_backoff(&s.empty[slot], (round - 1) & 1, kWaitNs, 64)) {
             ok = false;
             break;
           }
@@ -372,8 +373,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (w_issued > 0) umma::mbar_wait(&s.w_full, (w_issued - 1) & 1, kWaitNs);
     }
   } else if (warp == 1) {
-    // ---------------------------------------------------------- MMA issue (one lane)
-    if (lane == 0) {
+    // ---------------------------------------------------------- MMA issue (whole warp, one elected lane)
+    // The warp runs the loop together (its waits and branches are warp-uniform: every wait's outcome goes
+    // through a vote) and one elected lane issues the MMAs and commits; the issuing thread's instruction
+    // latency, not the tensor cores, bounds a stream of these MMAs, and a loop run by one lane of a warp
+    // whose other lanes have left costs it more per MMA.
+    {
+      const bool leader = umma::elect_one();
       // row blocks: core matrices 128 B apart along M and K (Hankel); row tiles [j][g][8][8]: K-adjacent
       // core matrices 128 B apart, 8-filter groups 512 B apart; column operand [p/8][g][8][8] and
       // column taps [j][g][8][8]: 128 B along K, 768 B along M/N.  Descriptors = base + (byte offset >> 4).
@@ -382,47 +388,43 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint64_t l_base = umma::sdesc(umma::smem_u32(s.L[0]), 128, KL / 8 * 128);
       const uint64_t c_desc = umma::sdesc(umma::smem_u32(s.Cb), 128, KL / 8 * 128);
       constexpr uint32_t SLOT16 = sizeof(Slot) >> 4, ROW16 = ROWB >> 4, L16 = L_BYTES >> 4;
-      bool ok = my_tiles == 0 || umma::mbar_wait(&s.c_full, 0, kWaitNs);
-      uint32_t slot = 0, round = 0;
+      bool ok = __all_sync(0xffffffffu, my_tiles == 0 || umma::mbar_wait(&s.c_full, 0, kWaitNs));
+      uint32_t slot = 0, par = 0;           // ring slot and the parity of its current use
       uint64_t a_s = a_base, b_s = b_base;  // descriptors of the current slot
       for (int t = 0; t < my_tiles && ok; ++t) {
         uint32_t dch[C];
+        bool got = true;
 #pragma unroll
-        for (int c = 0; c < C; ++c) dch[c] = tmem + ((uint32_t)(t * C + c) % NSLOT) * NP;
+        for (int c = 0; c < C; ++c) {
+          const uint32_t g = (uint32_t)(t * C + c);
+          dch[c] = tmem + (g % NSLOT) * NP;
+          // a reused accumulator slot: the epilogue has read it out
+          if (g >= NSLOT) got = got && umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs);
+        }
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        uint32_t acc = 0;  // the first row starts the accumulators
         for (int iy = 0; iy < KS; ++iy) {
-          if (!umma::mbar_wait(&s.full[slot], round & 1, kWaitNs)) {
+          if (!__all_sync(0xffffffffu, umma::mbar_wait(&s.full[slot], par, kWaitNs))) {
             ok = false;
             break;
           }
           umma::fence_after_sync();
-          if (iy == 0) {
-            // fresh accumulators: each waits until the epilogue has emptied its slot (the previous channels'
-            // MMAs are already running meanwhile)
+          if (leader) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              const uint32_t g = (uint32_t)(t * C + c);
-              if (g >= NSLOT) {
-                if (!umma::mbar_wait(&s.acc_empty[g % NSLOT], ((g / NSLOT) - 1) & 1, kWaitNs)) {
-                  ok = false;
-                  break;
-                }
-                umma::fence_after_sync();
-              }
-              umma::mma_bf16(dch[c], a_s + c * ROW16, b_s, idesc, 0);
+              umma::mma_bf16(dch[c], a_s + c * ROW16, b_s, idesc, acc);
               umma::mma_bf16(dch[c], a_s + c * ROW16 + 16, b_s + 16, idesc, 1);
             }
-            if (!ok) break;
-          } else {
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              umma::mma_bf16(dch[c], a_s + c * ROW16, b_s, idesc, 1);
-              umma::mma_bf16(dch[c], a_s + c * ROW16 + 16, b_s + 16, idesc, 1);
-            }
+            umma::mma_commit(&s.empty[slot]);
           }
-          umma::mma_commit(&s.empty[slot]);
+          acc = 1;
           if (++slot == NB) {
             slot = 0;
-            ++round;
+            par ^= 1;
             a_s = a_base;
             b_s = b_base;
           } else {
@@ -432,29 +434,33 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!ok) break;
         // the column taps, once the tile's column operand is complete
-        if (!umma::mbar_wait(&s.l_full, t & 1, kWaitNs)) {
+        if (!__all_sync(0xffffffffu, umma::mbar_wait(&s.l_full, t & 1, kWaitNs))) {
           ok = false;
           break;
         }
         umma::fence_after_sync();
+        if (leader) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const uint64_t l_c = l_base + c * L16;
-          umma::mma_bf16(dch[c], l_c, c_desc, idesc, 1);
-          umma::mma_bf16(dch[c], l_c + 16, c_desc + 16, idesc, 1);
-          umma::mma_bf16(dch[c], l_c + 32, c_desc + 32, idesc, 1);
+          for (int c = 0; c < C; ++c) {
+            const uint64_t l_c = l_base + c * L16;
+            umma::mma_bf16(dch[c], l_c, c_desc, idesc, 1);
+            umma::mma_bf16(dch[c], l_c + 16, c_desc + 16, idesc, 1);
+            umma::mma_bf16(dch[c], l_c + 32, c_desc + 32, idesc, 1);
+          }
+          umma::mma_commit(&s.l_free);
+#pragma unroll
+          for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
         }
-        umma::mma_commit(&s.l_free);
-#pragma unroll
-        for (int c = 0; c < C; ++c) umma::mma_commit(&s.acc_full[(t * C + c) % NSLOT]);
       }
       if (!ok) {
-        s.abort = 1;
-        atomicExch(err, 1);
-        // the MMAs issued so far complete before the tensor memory is released (bounded)
-        umma::mma_commit(&s.drain);
-        umma::mbar_wait(&s.drain, 0, kWaitNs);
-      } else if (my_tiles > 0) {
+        if (leader) {
+          s.abort = 1;
+          atomicExch(err, 1);
+          // the MMAs issued so far complete before the tensor memory is released (bounded)
+          umma::mma_commit(&s.drain);
+          umma::mbar_wait(&s.drain, 0, kWaitNs);
+        }
+      } else if (my_tiles > 0 && leader) {
         const int t = my_tiles - 1;  // the last MMAs have completed before the CTA exits
         umma::mbar_wait(&s.l_free, t & 1, kWaitNs);
       }
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tile_xy(t, y, x0);
       const __nv_bfloat16* src = plane + (size_t)(y + 32) * Wq + x0 + 32 + 8 * m;
       // the column operand was last read by the column MMAs of tile t - 1
-      if (t >= 1 && !umma::mbar_wait(&s.l_free, (t - 1) & 1, kWaitNs)) s.abort = 1;
+      if (t >= 1 && !umma::mbar_wait_backoff(&s.l_free, (t - 1) & 1, kWaitNs, 256)) s.abort = 1;
       if (s.abort) break;
       for (int g = 0; g < (KS + 3 + 7) / 8; ++g) {
         uint4 win[8];

@@ -67,8 +67,12 @@ DFP2S_DEV bool mbar_ready(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits until the phase of parity `parity` has completed; false after `limit_ns`.
+// The first check is the non-blocking test_wait: on sm_103a a try_wait on a
+// phase that has already completed still costs a thread that issues tensor-core
+// instructions about 30 cycles per MMA of a row it guards (measured against a
+// stream of 128 x 112 x 16 MMAs), test_wait almost nothing.
 DFP2S_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_test(bar, parity)) return true;
+  if (mbar_ready(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     if (mbar_test(bar, parity)) return true;
@@ -80,7 +84,7 @@ DFP2S_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
 // warps that wait long (epilogues): their polling otherwise competes for
 // shared-memory cycles with the tensor cores' operand reads.
 DFP2S_DEV bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, uint64_t limit_ns, uint32_t max_ns = 512) {
-  if (mbar_test(bar, parity)) return true;
+  if (mbar_ready(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   uint32_t ns = 32;
   while (true) {
@@ -89,6 +93,20 @@ DFP2S_DEV bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, uint64_t limit_
     if (global_ns() - t0 > limit_ns) return false;
     if (ns < max_ns) ns <<= 1;
   }
+}
+
+// True in one lane of the (fully active) warp, the same lane every call: the
+// lane that issues a warp's tensor-core instructions.  A loop that only one lane
+// runs while the rest of its warp has left costs a thread that issues
+// tcgen05.mma noticeably more per MMA than the same loop run by the whole warp.
+DFP2S_DEV bool elect_one() {
+  uint32_t p;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "elect.sync _|q, 0xffffffff;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(p));
+  return p != 0;
 }
 
 // 1-D bulk copy global -> shared, completion counted in bytes on `bar`.
