@@ -168,6 +168,23 @@ int dfp2s_gaussian_noise(uint64_t seed, uint32_t tag, uint32_t frame, uint32_t m
  * subsequence `sub` (n % 4 == 0), into out_dev. */
 int dfp2s_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int n, uint32_t* out_dev, void* stream);
 
+/* Verification tap for the failure path of the tensor-core kernels (their
+ * waits on mbarriers are bounded: a wait that runs out sets the kernel's error
+ * word, the kernel still lets its own bulk copies land and releases its tensor
+ * memory, and the host reads DFP2S_ETIMEOUT, e.g. from dfp2s_p2s_check).  One
+ * kernel takes those steps on a barrier that nothing completes: allocates tensor
+ * memory, starts a bulk copy, waits until limit_ns runs out, lets the copy land
+ * (bounded by 2 s) and releases the tensor memory.  Returns DFP2S_ETIMEOUT, the
+ * expected outcome; DFP2S_ECUDA if the wait did not run out or the copy did not
+ * land; DFP2S_EINVAL for limit_ns outside [1 us, 1 s].  Synchronous. */
+int dfp2s_check_bounded_wait(uint64_t limit_ns, void* stream);
+
+/* Test hook for the allocation-failure paths: the n-th next device allocation
+ * made by the library (1 = the next one; 0 disarms) reports
+ * cudaErrorMemoryAllocation without allocating, so that the entry point returns
+ * DFP2S_ENOMEM.  Process-wide.  Errors: EINVAL (n < 0). */
+int dfp2s_debug_fail_allocation(int n);
+
 /* -------------------------------------------------------- phase-to-space
  * A P2S handle holds the PSF basis phi_k (K x 33 x 33, Sec. II-C Eq. p2s PSF)
  * and, optionally, the surrogate network. */

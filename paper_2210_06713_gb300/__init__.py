@@ -54,6 +54,8 @@ SIGNATURES = {
     "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
+    "dfp2s_check_bounded_wait": (_i, [_u64, _vp]),
+    "dfp2s_debug_fail_allocation": (_i, [_i]),
     "dfp2s_build_basis": (_i, [_vp, _i, _i, _vp, _i, _u64, _vp, _vp, _vp, _vp]),
     "dfp2s_p2s_create": (_i, [_i, _i, _vp, _c.POINTER(_vp)]),
     "dfp2s_p2s_destroy": (_i, [_vp]),

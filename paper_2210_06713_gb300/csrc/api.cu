@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -34,6 +35,39 @@ int dfp2s_fail(int code, const char* fmt, ...) {
 
 namespace {
 thread_local cudaError_t g_launch_err = cudaSuccess;
+}
+
+// simulated allocation failure: the n-th next device allocation (1 = the next one) fails; 0 = none armed
+static std::atomic<int> g_fail_alloc{0};
+
+static bool take_simulated_failure() {
+  int n = g_fail_alloc.load();
+  while (n > 0) {
+    if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 1;
+  }
+  return false;
+}
+
+cudaError_t dfp2s_device_malloc(void** p, size_t bytes) {
+  if (take_simulated_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t dfp2s_device_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  if (take_simulated_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, st);
+}
+
+extern "C" int dfp2s_debug_fail_allocation(int n) {
+  if (n < 0 || n > (1 << 20)) return dfp2s_fail(DFP2S_EINVAL, "n = %d out of range", n);
+  g_fail_alloc.store(n);
+  return DFP2S_OK;
 }
 
 int dfp2s_launch_status() {
@@ -112,11 +146,11 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
   cudaGetDevice(&f->device);
   const size_t half = (size_t)(p->N / 2 + 1) * p->N;
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&f->d.mult, (size_t)p->J * half * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&f->d.L64, (size_t)p->J * p->J * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&f->d.L32, (size_t)p->J * p->J * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&f->d.tw, (size_t)p->N * sizeof(float2))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&f->d.scratch, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
+  if ((e = dfp2s_device_malloc((void**)&f->d.mult, (size_t)p->J * half * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&f->d.L64, (size_t)p->J * p->J * sizeof(double))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&f->d.L32, (size_t)p->J * p->J * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&f->d.tw, (size_t)p->N * sizeof(float2))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&f->d.scratch, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
     factor_free(f);
     return dfp2s_fail_cuda(e, "factor allocation");
   }
@@ -236,12 +270,12 @@ extern "C" int dfp2s_p2s_create(int J, int K, const float* basis, dfp2s_p2s** ou
   p->d.K = K;
   const size_t n2 = DFP2S_KS * DFP2S_KS;
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&p->d.basis, K * n2 * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&p->d.phiT, K * n2 * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&p->d.zt, (J - 2) * n2 * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&p->d.mask, n2 * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&p->d.dft, n2 * sizeof(float2))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&p->d.flux, 2 * K * sizeof(float))) != cudaSuccess) {
+  if ((e = dfp2s_device_malloc((void**)&p->d.basis, K * n2 * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&p->d.phiT, K * n2 * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&p->d.zt, (J - 2) * n2 * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&p->d.mask, n2 * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&p->d.dft, n2 * sizeof(float2))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&p->d.flux, 2 * K * sizeof(float))) != cudaSuccess) {
     p2s_free(p);
     return dfp2s_fail_cuda(e, "p2s allocation");
   }
@@ -281,12 +315,12 @@ static cudaError_t copy_transposed(float** dst, const float* src, int rows, int 
   if (e != cudaSuccess) return e;
   for (int r = 0; r < rows; ++r)
     for (int c = 0; c < cols; ++c) t[(size_t)c * rows + r] = h[(size_t)r * cols + c];
-  if ((e = cudaMalloc((void**)dst, t.size() * sizeof(float))) != cudaSuccess) return e;
+  if ((e = dfp2s_device_malloc((void**)dst, t.size() * sizeof(float))) != cudaSuccess) return e;
   return cudaMemcpy(*dst, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
 }
 
 static cudaError_t copy_vec(float** dst, const float* src, int n) {
-  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(float));
+  cudaError_t e = dfp2s_device_malloc((void**)dst, n * sizeof(float));
   if (e != cudaSuccess) return e;
   return cudaMemcpy(*dst, src, n * sizeof(float), cudaMemcpyDefault);
 }
@@ -311,7 +345,7 @@ int dfp2s_p2s_install_mlp(dfp2s_p2s_dev* d, const float* W1, const float* b1, co
       (e = copy_vec(&d->out_shift, out_shift, K)) != cudaSuccess)
     return dfp2s_fail_cuda(e, "mlp weights");
   if (!d->err) {
-    if ((e = cudaMalloc((void**)&d->err, sizeof(int))) != cudaSuccess) return dfp2s_fail_cuda(e, "error word");
+    if ((e = dfp2s_device_malloc((void**)&d->err, sizeof(int))) != cudaSuccess) return dfp2s_fail_cuda(e, "error word");
     cudaMemset(d->err, 0, sizeof(int));
   }
   const int rc = dfp2s_mlp_tc_pack(d, 0);
@@ -590,10 +624,10 @@ extern "C" int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int m
   const int J = f->d.J;
   float lt[4] = {1.f, 0.f, 0.f, 1.f};
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&c->fields, (size_t)J * npix * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&c->warped, (size_t)maxC * npix * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&c->w, (size_t)p->d.K * npix * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&c->w1_mixed, dfp2s_mlp_tc_w1_elems() * sizeof(__nv_bfloat16))) != cudaSuccess ||
+  if ((e = dfp2s_device_malloc((void**)&c->fields, (size_t)J * npix * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&c->warped, (size_t)maxC * npix * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc(&c->w, (size_t)p->d.K * npix * sizeof(float))) != cudaSuccess ||
+      (e = dfp2s_device_malloc((void**)&c->w1_mixed, dfp2s_mlp_tc_w1_elems() * sizeof(__nv_bfloat16))) != cudaSuccess ||
       (J >= 2 && ((e = cudaMemcpy(lt, f->d.L32, 2 * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess ||
                   (e = cudaMemcpy(lt + 2, f->d.L32 + J, 2 * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess))) {
     cudaFree(c->fields);

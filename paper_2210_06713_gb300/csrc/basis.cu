@@ -219,20 +219,20 @@ int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const do
     }
   } b;
   const int m = n_psf;
-  if (cudaMalloc((void**)&b.a, (size_t)J * m * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.h, (size_t)m * KS2 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.drs, 8 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.dummy_basis, KS2 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.Hd, (size_t)m * KS2 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&b.V, (size_t)KS2 * KS2 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&b.sig, KS2 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&b.sorted, KS2 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&b.order, KS2 * sizeof(int)) != cudaSuccess ||
-      cudaMalloc((void**)&b.rotated, sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc((void**)&b.t.phiT, KS2 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.t.zt, (size_t)(J - 2) * KS2 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.t.mask, KS2 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc((void**)&b.t.dft, KS2 * sizeof(float2)) != cudaSuccess)
+  if (dfp2s_device_malloc((void**)&b.a, (size_t)J * m * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.h, (size_t)m * KS2 * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.drs, 8 * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.dummy_basis, KS2 * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.Hd, (size_t)m * KS2 * sizeof(double)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.V, (size_t)KS2 * KS2 * sizeof(double)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.sig, KS2 * sizeof(double)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.sorted, KS2 * sizeof(double)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.order, KS2 * sizeof(int)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.rotated, sizeof(unsigned long long)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.t.phiT, KS2 * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.t.zt, (size_t)(J - 2) * KS2 * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.t.mask, KS2 * sizeof(float)) != cudaSuccess ||
+      dfp2s_device_malloc((void**)&b.t.dft, KS2 * sizeof(float2)) != cudaSuccess)
     return DFP2S_ENOMEM;
   float hdr[8];
   for (int i = 0; i < n_dr; ++i) hdr[i] = (float)dr_host[i];

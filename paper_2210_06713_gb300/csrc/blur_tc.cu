@@ -616,14 +616,14 @@ static int blur_tc_scratch(dfp2s_p2s_dev* p, int C, int H, int W, cudaStream_t s
   if (NP > 128) return DFP2S_EUNSUPPORTED;
   if (!p->bt) {
     const int n = KS * NP * KM + NP * KL;  // row tiles, then the column taps
-    if (cudaMalloc((void**)&p->bt, (size_t)n * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
-    if (cudaMalloc((void**)&p->bsum, (size_t)NP * sizeof(float)) != cudaSuccess) return DFP2S_ENOMEM;
+    if (dfp2s_device_malloc((void**)&p->bt, (size_t)n * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
+    if (dfp2s_device_malloc((void**)&p->bsum, (size_t)NP * sizeof(float)) != cudaSuccess) return DFP2S_ENOMEM;
     k_basis_sums<<<NP, 256, 0, st>>>(p->basis, K, NP, p->bsum);
     k_scale<<<1, 128, 0, st>>>(p->bsum, NP, centre);
     k_build_bt<<<(n + 255) / 256, 256, 0, st>>>(p->basis, K, NP, p->bsum, p->bt);
   }
   if (!p->err) {
-    if (cudaMalloc((void**)&p->err, sizeof(int)) != cudaSuccess) return DFP2S_ENOMEM;
+    if (dfp2s_device_malloc((void**)&p->err, sizeof(int)) != cudaSuccess) return DFP2S_ENOMEM;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
   }
   const int nseg = (W + TM - 1) / TM;
@@ -633,7 +633,7 @@ static int blur_tc_scratch(dfp2s_p2s_dev* p, int C, int H, int W, cudaStream_t s
     if (p->pad) cudaFree(p->pad);
     p->pad = nullptr;
     p->pad_cap = 0;
-    if (cudaMalloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
+    if (dfp2s_device_malloc((void**)&p->pad, need * sizeof(__nv_bfloat16)) != cudaSuccess) return DFP2S_ENOMEM;
     p->pad_cap = need;
   }
   return DFP2S_OK;

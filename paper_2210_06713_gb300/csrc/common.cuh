@@ -194,6 +194,11 @@ DFP2S_DEV void dft8(float2* v) {
 
 int dfp2s_fail(int code, const char* fmt, ...);
 int dfp2s_fail_cuda(cudaError_t e, const char* what);
+// Device allocations of the library: cudaMalloc / cudaMallocAsync, unless a test
+// has armed a simulated failure (dfp2s_debug_fail_allocation): the armed
+// allocation then reports cudaErrorMemoryAllocation without allocating.
+cudaError_t dfp2s_device_malloc(void** p, size_t bytes);
+cudaError_t dfp2s_device_malloc_async(void** p, size_t bytes, cudaStream_t st);
 // Status of the launches a launcher has just enqueued: reads (and so clears) the
 // runtime's last error and, when it is one, keeps it for dfp2s_launch_error(),
 // so that the entry point reporting the failure names the actual cause.

@@ -240,7 +240,7 @@ struct DevBuf {
   ~DevBuf() {
     if (p) cudaFree(p);
   }
-  cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, n * sizeof(T)); }
+  cudaError_t alloc(size_t n) { return dfp2s_device_malloc((void**)&p, n * sizeof(T)); }
 };
 
 }  // namespace

@@ -130,28 +130,28 @@ __global__ void __launch_bounds__(Groups<N>::THREADS) k_rowifft(const float2* __
   const int j = blockIdx.y;
   const int y0 = blockIdx.x * 2 * G;
   const float2* Sj = S + (size_t)j * HALF * N;
-  // the tile, eight loads in flight per thread
+  // the tile: every element an asynchronous 8-byte copy straight into its padded place, so that all of a
+  // thread's loads are in flight at once (no register staging); rows past H are zero
   constexpr int TOT = HALF * 2 * G;
   constexpr int PER = (TOT + GR::THREADS - 1) / GR::THREADS;
+  const uint32_t tile = (uint32_t)__cvta_generic_to_shared(smem);
 #pragma unroll
-  for (int b0 = 0; b0 < PER; b0 += 8) {
-    float2 x[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = threadIdx.x + (b0 + q) * GR::THREADS;
+  for (int b = 0; b < PER; ++b) {
+    const int i = threadIdx.x + b * GR::THREADS;
+    if (i < TOT) {
       const int k = i / (2 * G), r = i - k * (2 * G);
-      x[q] = (b0 + q < PER && i < TOT && y0 + r < H) ? Sj[(size_t)k * N + y0 + r] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = threadIdx.x + (b0 + q) * GR::THREADS;
-      const int k = i / (2 * G), r = i - k * (2 * G);
-      if (b0 + q < PER && i < TOT) {
-        if (k == 0 || k == N / 2) x[q].y = 0.f;  // C2R convention: DC and Nyquist bins are real
-        smem[k * GR::TS + r] = x[q];
-      }
+      if (y0 + r < H)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tile + (uint32_t)((k * GR::TS + r) * 8)),
+                     "l"(Sj + (size_t)k * N + y0 + r)
+                     : "memory");
+      else
+        smem[k * GR::TS + r] = make_float2(0.f, 0.f);
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  // C2R convention: the DC and Nyquist bins are real
+  for (int i = threadIdx.x; i < 4 * G; i += GR::THREADS) smem[(i < 2 * G ? 0 : N / 2) * GR::TS + (i % (2 * G))].y = 0.f;
   __syncthreads();
   // Z[n] = Ga[n] + i Gb[n] for n <= N/2, conj Ga[N-n] + i conj Gb[N-n] above
   float2 v[V];

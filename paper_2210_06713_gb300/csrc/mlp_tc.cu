@@ -572,11 +572,11 @@ int dfp2s_mlp_tc_pack(dfp2s_p2s_dev* p, cudaStream_t st) {
   const int K = p->K;
   const int NP3 = (K + 15) / 16 * 16;
   if (NP3 > 128) return DFP2S_EUNSUPPORTED;
-  if (!p->tc_w1 && (cudaMalloc((void**)&p->tc_w1, HID * KX * sizeof(__nv_bfloat16)) != cudaSuccess ||
-                    cudaMalloc((void**)&p->tc_w2, 4 * HID * 64 * sizeof(__nv_bfloat16)) != cudaSuccess ||
-                    cudaMalloc((void**)&p->tc_w3, 4 * 128 * 64 * sizeof(__nv_bfloat16)) != cudaSuccess ||
-                    cudaMalloc((void**)&p->tc_c3, 128 * sizeof(float)) != cudaSuccess ||
-                    cudaMalloc((void**)&p->tc_bias, HID * 16 * sizeof(__nv_bfloat16)) != cudaSuccess))
+  if (!p->tc_w1 && (dfp2s_device_malloc((void**)&p->tc_w1, HID * KX * sizeof(__nv_bfloat16)) != cudaSuccess ||
+                    dfp2s_device_malloc((void**)&p->tc_w2, 4 * HID * 64 * sizeof(__nv_bfloat16)) != cudaSuccess ||
+                    dfp2s_device_malloc((void**)&p->tc_w3, 4 * 128 * 64 * sizeof(__nv_bfloat16)) != cudaSuccess ||
+                    dfp2s_device_malloc((void**)&p->tc_c3, 128 * sizeof(float)) != cudaSuccess ||
+                    dfp2s_device_malloc((void**)&p->tc_bias, HID * 16 * sizeof(__nv_bfloat16)) != cudaSuccess))
     return DFP2S_ENOMEM;
   // the SIMT layout keeps W1, W2, W3 transposed: W1t (J x 256), W2t (256 x 256), W3t (256 x K)
   k_pack_w1<<<(HID * KX + 255) / 256, 256, 0, st>>>(p->W1, p->in_scale, p->J, p->tc_w1);

@@ -434,7 +434,7 @@ struct Pool {
   template <typename T>
   T* get(size_t n) {
     void* p = nullptr;
-    if (cudaMalloc(&p, n * sizeof(T) + 16) != cudaSuccess) return nullptr;
+    if (dfp2s_device_malloc(&p, n * sizeof(T) + 16) != cudaSuccess) return nullptr;
     bufs.push_back(p);
     return static_cast<T*>(p);
   }

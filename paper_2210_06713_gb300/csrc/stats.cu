@@ -133,8 +133,8 @@ int dfp2s_launch_field_covariance(const float* a, int J, int H, int W, const int
   const int npairs = J * J;
   int2* dl = nullptr;
   double* part = nullptr;
-  if (cudaMallocAsync((void**)&dl, n_lags * sizeof(int2), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&part, (size_t)n_lags * nb * npairs * sizeof(double), st) != cudaSuccess) {
+  if (dfp2s_device_malloc_async((void**)&dl, n_lags * sizeof(int2), st) != cudaSuccess ||
+      dfp2s_device_malloc_async((void**)&part, (size_t)n_lags * nb * npairs * sizeof(double), st) != cudaSuccess) {
     if (dl) cudaFreeAsync(dl, st);
     return DFP2S_ENOMEM;
   }
