@@ -393,6 +393,51 @@ int dfp2s_ctx_stage_timing(dfp2s_ctx* c, int n);
  * dfp2s_ctx_stage_timing.  Errors: EINVAL, ECUDA. */
 int dfp2s_ctx_stage_times(dfp2s_ctx* c, int count, float* out_host);
 
+/* ------------------------------------------------------- batched requests
+ * The serving pattern: many requests of mixed image size, J, D/r0 and P2S
+ * form, each with several frames (frame numbers first_frame .. first_frame +
+ * n_frames - 1 of Philox stream `seed`, so every frame is independent), run
+ * by one call.  An engine holds the P2S handles (one per J; not owned) and
+ * builds, the first time a shape class (J, C, H, W) appears, its spectral
+ * factor (shared by the classes of equal J and grid N) and its frame context.
+ *   DFP2S_ENGINE_AUTOTUNE: on a class's first use its field column-pass
+ *     kernels are timed on its own frames (CUDA events) and the faster kept
+ *     (dfp2s_engine_class_info reports the choice and the times);
+ *   DFP2S_ENGINE_GRAPHS: the frames of each class are captured into one CUDA
+ *     graph per run and launched once; a class's graph is updated in place
+ *     when the next run gives it the same number of frames.
+ * Each frame is what dfp2s_simulate_frame gives for the request's arguments
+ * (bit for bit: the same kernels, whichever column-pass kernel is chosen). */
+typedef struct dfp2s_engine dfp2s_engine;
+typedef struct {
+  const float* img_dev;  /* C x H x W float32, device */
+  int C, H, W;           /* 1 <= C <= 64, 1 <= H, W <= 4096 */
+  int J;                 /* fields; the engine holds a P2S handle with this J */
+  double D_over_r0;
+  uint64_t seed;
+  uint32_t first_frame;
+  int n_frames;          /* >= 0 */
+  int p2s_mode;          /* DFP2S_P2S_EXACT, _LEARNED, _LEARNED_FP32 (a network installed for the last two) */
+  float* out_dev;        /* n_frames x C x H x W float32, device */
+} dfp2s_request;
+#define DFP2S_ENGINE_GRAPHS 1
+#define DFP2S_ENGINE_AUTOTUNE 2
+/* p2s: n_p2s handles with distinct J (1..16).  Errors: EINVAL, ECUDA. */
+int dfp2s_engine_create(const dfp2s_p2s* const* p2s, int n_p2s, double pix_per_D, int flags, dfp2s_engine** out);
+/* Enqueues every frame of the n_req requests (stream-ordered after the work
+ * already on `stream`, and `stream` waits for them).  New classes are built
+ * and warmed (and tuned) synchronously first.  Calls on one engine must not
+ * overlap.  Errors: EINVAL (request arguments), ENOMEM, ECUDA. */
+int dfp2s_engine_run(dfp2s_engine* e, const dfp2s_request* req, int n_req, void* stream);
+/* n_classes (optional); counters_host (optional, 4): frames run, graph launches,
+ * graph instantiations, graph updates. */
+int dfp2s_engine_info(const dfp2s_engine* e, int* n_classes, long long* counters_host);
+/* Class i: shape_host (6 ints) = J, C, H, W, N, column-pass kernel in use
+ * (0 or 1; -1 before tuning); tuned_ms_host (2 floats) = ms per frame of each
+ * candidate (-1 if not timed).  Errors: EINVAL. */
+int dfp2s_engine_class_info(const dfp2s_engine* e, int i, int* shape_host, float* tuned_ms_host);
+int dfp2s_engine_destroy(dfp2s_engine* e);
+
 #ifdef __cplusplus
 }
 #endif

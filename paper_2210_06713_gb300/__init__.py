@@ -40,6 +40,13 @@ class TrainParams(ctypes.Structure):
                 ("image_prior_loss", _i)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("img_dev", _vp), ("C", _i), ("H", _i), ("W", _i), ("J", _i), ("D_over_r0", _d), ("seed", _u64),
+                ("first_frame", _u32), ("n_frames", _i), ("p2s_mode", _i), ("out_dev", _vp)]
+
+
+ENGINE_GRAPHS, ENGINE_AUTOTUNE = 1, 2
+
 SIGNATURES = {
     "dfp2s_last_error": (_i, [_c.c_char_p, _sz]),
     "dfp2s_version": (_c.c_char_p, []),
@@ -81,6 +88,11 @@ SIGNATURES = {
     "dfp2s_ctx_buffers": (_i, [_vp, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
     "dfp2s_ctx_stage_timing": (_i, [_vp, _i]),
     "dfp2s_ctx_stage_times": (_i, [_vp, _i, _vp]),
+    "dfp2s_engine_create": (_i, [_c.POINTER(_vp), _i, _d, _i, _c.POINTER(_vp)]),
+    "dfp2s_engine_run": (_i, [_vp, _c.POINTER(Request), _i, _vp]),
+    "dfp2s_engine_info": (_i, [_vp, _c.POINTER(_i), _vp]),
+    "dfp2s_engine_class_info": (_i, [_vp, _i, _vp, _vp]),
+    "dfp2s_engine_destroy": (_i, [_vp]),
 }
 
 _LIB = None
@@ -466,3 +478,56 @@ class Simulator:
 def simulate_frame(sim: Simulator, img: torch.Tensor, D_over_r0: float, seed: int, frame: int,
                    mode: int = P2S_EXACT, out: torch.Tensor | None = None) -> torch.Tensor:
     return sim.simulate_frame(img, D_over_r0, seed, frame, mode, out)
+
+
+# ---------------------------------------------------------------- batches
+class Engine:
+    """Batched frames of uneven requests (include/dfp2s.h: dfp2s_engine_*): one P2S handle per J."""
+
+    def __init__(self, p2s_list, pix_per_D: float = 8.0, graphs: bool = True, autotune: bool = True):
+        self._p2s = list(p2s_list)  # kept alive: the engine does not own them
+        arr = (ctypes.c_void_p * len(self._p2s))(*[p.handle.value for p in self._p2s])
+        h = ctypes.c_void_p()
+        flags = (ENGINE_GRAPHS if graphs else 0) | (ENGINE_AUTOTUNE if autotune else 0)
+        _check(load().dfp2s_engine_create(arr, len(self._p2s), pix_per_D, flags, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, requests, stream=None):
+        """requests: dicts with img (C x H x W CUDA tensor), J, D_over_r0, seed, first_frame, n_frames, mode and
+        out (n_frames x C x H x W CUDA tensor)."""
+        arr = (Request * max(1, len(requests)))()
+        for i, r in enumerate(requests):
+            C, H, W = r["img"].shape
+            out = r["out"]
+            if tuple(out.shape) != (r["n_frames"], C, H, W):
+                raise ValueError("out must be n_frames x C x H x W")
+            arr[i] = Request(_ptr(r["img"]).value, C, H, W, r["J"], r["D_over_r0"], r["seed"],
+                             r.get("first_frame", 0), r["n_frames"], r.get("mode", P2S_EXACT), _ptr(out).value)
+        _check(load().dfp2s_engine_run(self._h, arr, len(requests), _stream(stream)))
+
+    def info(self):
+        import numpy as np
+        n = ctypes.c_int()
+        cnt = np.zeros(4, dtype=np.int64)
+        _check(load().dfp2s_engine_info(self._h, ctypes.byref(n), cnt.ctypes.data_as(ctypes.c_void_p)))
+        classes = []
+        for i in range(n.value):
+            shp = np.zeros(6, dtype=np.int32)
+            ms = np.zeros(2, dtype=np.float32)
+            _check(load().dfp2s_engine_class_info(self._h, i, shp.ctypes.data_as(ctypes.c_void_p),
+                                                  ms.ctypes.data_as(ctypes.c_void_p)))
+            classes.append({"J": int(shp[0]), "C": int(shp[1]), "H": int(shp[2]), "W": int(shp[3]), "N": int(shp[4]),
+                            "column_pass": int(shp[5]), "tuned_ms": [float(ms[0]), float(ms[1])]})
+        return {"frames": int(cnt[0]), "graph_launches": int(cnt[1]), "graph_instantiations": int(cnt[2]),
+                "graph_updates": int(cnt[3]), "classes": classes}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dfp2s_engine_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -244,9 +244,6 @@ extern "C" int dfp2s_build_basis(const dfp2s_factor* f, int K, int n_psf, const 
 }
 
 // ---------------------------------------------------------------------- P2S
-struct dfp2s_p2s {
-  dfp2s_p2s_dev d;
-};
 
 static void p2s_free(dfp2s_p2s* p) {
   if (!p) return;
@@ -589,7 +586,14 @@ struct dfp2s_ctx {
   cudaEvent_t* ev;
   int nev;
   unsigned long long frames;
+  int field_variant;  // column-pass kernel of the field sampler (-1: the default)
 };
+
+int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant) {
+  if (!c || variant < -1 || variant > 1) return dfp2s_fail(DFP2S_EINVAL, "bad field-sampler variant %d", variant);
+  c->field_variant = variant;
+  return DFP2S_OK;
+}
 
 static void ctx_free_events(dfp2s_ctx* c) {
   for (int i = 0; i < 5 * c->nev; ++i) cudaEventDestroy(c->ev[i]);
@@ -620,6 +624,7 @@ extern "C" int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int m
   c->ev = nullptr;
   c->nev = 0;
   c->frames = 0;
+  c->field_variant = -1;
   const size_t npix = (size_t)maxH * maxW;
   const int J = f->d.J;
   float lt[4] = {1.f, 0.f, 0.f, 1.f};
@@ -726,7 +731,8 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
     cudaStream_t st = as_stream(stream);
     const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
     CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
-                                            seed, frame, c->f->d.L32, scale, c->fields, st, nullptr, 0.f, false));
+                                            seed, frame, c->f->d.L32, scale, c->fields, st, nullptr, 0.f, false,
+                                            c->field_variant));
     if (c->w1_mixed_version != pd->mlp_version) {
       CHECK_LAUNCH(dfp2s_mlp_tc_pack_w1_mixed(pd, c->f->d.L32, c->w1_mixed, st));
       c->w1_mixed_version = pd->mlp_version;
@@ -743,8 +749,11 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
     mark(3);
     rc = dfp2s_basis_blur_tc_run(c->p, C, H, W, c->w, DFP2S_W_F32, out, stream);
   } else {
-    rc = dfp2s_sample_zernike_fields(c->f, D_over_r0, seed, frame, H, W, c->fields, stream);
-    if (rc) return rc;
+    CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
+    const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+    CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
+                                            seed, frame, c->f->d.L32, scale, c->fields, as_stream(stream), nullptr,
+                                            0.f, true, c->field_variant));
     mark(1);
     rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
     if (rc) return rc;

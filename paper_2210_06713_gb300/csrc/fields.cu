@@ -299,39 +299,47 @@ __global__ void k_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* __rest
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
+// variant: the column pass's kernel, 0 = k_colgen (the compiler's register budget), 1 = k_colgen3 (three blocks
+// per SM, at most 80 registers; N <= 2048), -1 = the default (k_colgen3 at N = 1024 only).  Same results.
 template <int N>
 void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H, int W, uint64_t seed,
-                   uint32_t frame, float* fields, cudaStream_t st) {
+                   uint32_t frame, float* fields, cudaStream_t st, int variant) {
   using GR = Groups<N>;
   constexpr int G = GR::G, HALF = N / 2 + 1;
   const size_t sm = GR::smem;
+  if (variant < 0) variant = N == 1024 ? 1 : 0;
+  if (N > 2048) variant = 0;
   if (sm > 48 * 1024) {
-    if constexpr (N == 1024)
-      cudaFuncSetAttribute(k_colgen3<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
-    else
-      cudaFuncSetAttribute(k_colgen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
+    if constexpr (N <= 2048) cudaFuncSetAttribute(k_colgen3<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
+    cudaFuncSetAttribute(k_colgen<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
     cudaFuncSetAttribute(k_rowifft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   }
   const float cN = (float)(N * 0.70710678118654752440);  // the noise scale N / sqrt 2
   const dim3 grid((HALF + G - 1) / G, J);
-  if constexpr (N == 1024) k_colgen3<N><<<grid, GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
-  else k_colgen<N><<<grid, GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
+  bool done = false;
+  if constexpr (N <= 2048) {
+    if (variant == 1) {
+      k_colgen3<N><<<grid, GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
+      done = true;
+    }
+  }
+  if (!done) k_colgen<N><<<grid, GR::THREADS, GR::smem_fft, st>>>(S, mult, tw, H, seed, frame, cN);
   k_rowifft<N><<<dim3((H + 2 * G - 1) / (2 * G), J), GR::THREADS, sm, st>>>(S, fields, tw, H, W);
 }
 
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st, const float* prev, float alpha, bool mix) {
+                               cudaStream_t st, const float* prev, float alpha, bool mix, int variant) {
   switch (N) {
-    case 16: launch_passes<16>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 32: launch_passes<32>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 64: launch_passes<64>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 128: launch_passes<128>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 256: launch_passes<256>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 512: launch_passes<512>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 1024: launch_passes<1024>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 2048: launch_passes<2048>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
-    case 4096: launch_passes<4096>(S, mult, tw, J, H, W, seed, frame, fields, st); break;
+    case 16: launch_passes<16>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 32: launch_passes<32>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 64: launch_passes<64>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 128: launch_passes<128>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 256: launch_passes<256>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 512: launch_passes<512>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 1024: launch_passes<1024>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 2048: launch_passes<2048>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
+    case 4096: launch_passes<4096>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
     default: return DFP2S_EINVAL;
   }
   const size_t npix = (size_t)H * W;

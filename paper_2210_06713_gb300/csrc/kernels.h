@@ -14,7 +14,8 @@
 // mix = false: the unit fields before the mixing by scale L (prev must be null)
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st, const float* prev = nullptr, float alpha = 0.f, bool mix = true);
+                               cudaStream_t st, const float* prev = nullptr, float alpha = 0.f, bool mix = true,
+                               int variant = -1);
 int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st);
 int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cudaStream_t st);
 
@@ -67,6 +68,10 @@ struct dfp2s_p2s_dev {
   unsigned mlp_version;  // incremented by every network install  // hidden biases as the B operand of the bias MMAs
 };
 int dfp2s_p2s_build_tables(dfp2s_p2s_dev* p, cudaStream_t st);
+// The opaque handle of include/dfp2s.h.
+struct dfp2s_p2s {
+  dfp2s_p2s_dev d;
+};
 // w_dtype for dfp2s_launch_p2s_exact that writes the normalised 33 x 33 PSFs (npix x 1089 FP32) instead of weights
 #define DFP2S_W_PSF 2
 int dfp2s_launch_p2s_exact(const dfp2s_p2s_dev* p, const float* fields, int H, int W, void* w, int w_dtype,
@@ -120,3 +125,7 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
 // blur.cu
 int dfp2s_launch_blur(const dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
                       float* out, cudaStream_t st);
+
+// api.cu -- frame contexts (the opaque handle of include/dfp2s.h): the column-pass variant of the field sampler
+// its frames use (see dfp2s_launch_sample_fields; -1 = the default)
+int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant);
