@@ -9,7 +9,7 @@ shares no code, constants or tables with the CUDA sources.
 Every function cites the part of the paper (Chimitt, Zhang, Mao, Chan,
 "Real-Time Dense Field Phase-to-Space Simulation of Imaging through Atmospheric
 Turbulence", arXiv 2210.06713) that it follows. Where the paper is silent the
-reading taken is named in the docstring (R1..R28, the readings listed in the
+reading taken is named in the docstring (R1..R29, the readings listed in the
 design notes).
 
 Modules
@@ -19,6 +19,8 @@ Modules
   noise     Philox-4x32-10 words and the Box-Muller Gaussians (R7, R8)
   sampler   FFT field sampler (Sec. III-A/III-C), dense-root variant, brute-force
             full-tensor sampler (Fig. rand_gen)
+  fullsampler  the exact FFT sampler of the full cross-spectral density
+            (Sec. III-B, no approximation; R29)
   p2s       pupil -> PSF (Eq. 2), SVD basis, projection weights (Sec. II-C)
   image     tilt warp and basis blur (Eq. 1, Eq. varying blur)
   mlp       the P2S surrogate network, forward/backward/Adam in FP64
