@@ -250,6 +250,56 @@ def large_frame(d, S, device, stream, flush):
     return res
 
 
+def batched_uneven(d, S, device, stream, seed_base=0, train_steps=20000):
+    """The batched workload: 64 requests, image sides uniform in {256, 512, 768, 1024} (x 3 channels), D/r0 uniform
+    in [1, 5], J in {15, 36}, 8 frames each with independent seeds, learned P2S, through one engine call
+    (per-shape-class frame graphs, autotuned field column pass). The J = 36 handle is this run's; a J = 15 basis
+    and network are built on the device the same way (train_steps, 20 000 by default). Returns frames/s of whole
+    runs."""
+    import torch
+    from inputs import synthetic
+    rng = np.random.default_rng(4)
+    sides = [256, 512, 768, 1024]
+    reqs_spec = [(int(rng.choice(sides)), float(rng.uniform(1.0, 5.0)), int(rng.choice([15, 36]))) for _ in range(64)]
+    f15 = d.SpectralFactor(15, 1024, PIX_PER_D)
+    b15, _, _ = d.build_basis(f15, 100, 2000, (1.0, 2.0, 3.0, 4.0, 5.0), seed=0)
+    P15 = d.P2S(15, b15)
+    d.mlp_train(P15, f15, n_pairs=1 << 20, D_over_r0=(1.0, 2.0, 3.0, 4.0, 5.0), seed=1, batch=2048,
+                steps=train_steps, lr=2e-3)
+    imgs = {sd: torch.as_tensor(synthetic.shapes(sd, sd, 3, seed=sd), device=device) for sd in sides}
+    reqs = [{"img": imgs[sd], "J": J, "D_over_r0": dr, "seed": seed_base + 500 + r, "n_frames": 8,
+             "mode": d.P2S_LEARNED, "out": torch.empty(8, 3, sd, sd, device=device)}
+            for r, (sd, dr, J) in enumerate(reqs_spec)]
+    nframes = 64 * 8
+    pix = sum(8 * sd * sd for sd, _, _ in reqs_spec)
+    res = {"workload": "64 requests, sides {256,512,768,1024}x3, D/r0 U[1,5], J {15,36}, 8 frames each, learned P2S",
+           "frames": nframes, "megapixels": pix / 1e6, "l2": "not flushed (512 frames per run)"}
+    for name, graphs in (("graphs", True), ("no_graphs", False)):
+        eng = d.Engine([P15, S["P"]], PIX_PER_D, graphs=graphs, autotune=True)
+        eng.run(reqs, stream=stream)  # builds the classes, tunes them, instantiates the graphs
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(3):
+            e0.record(stream)
+            eng.run(reqs, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        info = eng.info()
+        res[name] = {"ms_per_run": ms, "frames_per_s": nframes / (ms * 1e-3), "megapixels_per_s": pix / 1e6 / (ms * 1e-3),
+                     "graph_launches": info["graph_launches"], "graph_updates": info["graph_updates"]}
+        if graphs:
+            res["classes"] = [{k: c[k] for k in ("J", "H", "N", "column_pass", "tuned_ms")} for c in info["classes"]]
+        eng.close()
+    S["P"].check()
+    P15.check()
+    del reqs
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args, rank, world, device):
     import torch
     d, S = setup_ours(args.workload, args.mode, device, args.train_steps)
@@ -433,6 +483,13 @@ def run_ours(args, rank, world, device):
             line["workloads"] = {"3840x2160x3": large_frame(d, S, device, stream, flush)}
         except RuntimeError as exc:
             line["workloads"] = {"3840x2160x3": {"unavailable": str(exc).splitlines()[0][:160]}}
+    if args.workload == "512" and args.mode == "learned" and not args.no_batched:
+        line.setdefault("workloads", {})
+        try:
+            line["workloads"]["batched_uneven"] = batched_uneven(d, S, device, stream, seed_base,
+                                                                      min(20000, args.train_steps))
+        except RuntimeError as exc:
+            line["workloads"]["batched_uneven"] = {"unavailable": str(exc).splitlines()[0][:160]}
     return line, S
 
 
@@ -551,6 +608,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=60000)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160x3 half of the metric")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-request workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -61,6 +61,8 @@ extern "C" {
 #define DFP2S_FACTOR_DENSE 1    /* per-frequency J x J symmetric root of L diag(lambda) L^T: not built in
                                    this version (DFP2S_EUNSUPPORTED); FACTORED applies the J x J root
                                    L diag(sqrt(lambda(f))) of the same spectral density */
+#define DFP2S_FACTOR_FULL 2     /* FACTORED, plus the tables of the exact sampler of the full cross-spectral
+                                   density (Sec. III-B, no approximation): dfp2s_sample_zernike_fields_full */
 
 #define DFP2S_KS 33       /* PSF / basis support is 33 x 33 pixels */
 #define DFP2S_MAX_J 64    /* at most 64 Zernike fields (Noll 2..65) */
@@ -95,7 +97,8 @@ typedef struct {
   int J;            /* number of fields, Noll modes 2..J+1; 3 <= J <= DFP2S_MAX_J */
   int N;            /* FFT grid side, power of two, 16 <= N <= 4096 */
   double pix_per_D; /* image pixels per aperture diameter of displacement s */
-  int kind;         /* DFP2S_FACTOR_FACTORED (DFP2S_FACTOR_DENSE returns DFP2S_EUNSUPPORTED) */
+  int kind;         /* DFP2S_FACTOR_FACTORED or DFP2S_FACTOR_FULL (DFP2S_FACTOR_DENSE returns
+                       DFP2S_EUNSUPPORTED) */
 } dfp2s_factor_params;
 
 /* Builds the factor (allocates device memory, synchronises `stream` before
@@ -123,6 +126,26 @@ int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_byt
  * and uses the factor's scratch.  Errors: EINVAL, ECUDA. */
 int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
                                 int H, int W, float* fields_dev, void* stream);
+
+/* The exact sampler (Sec. III-B): fields whose every auto- and cross-covariance
+ * at every displacement is the full homogeneous tensor A (the slices A_{i,j}(s)
+ * of Sec. III-B, not the approximation of Eq. A tilde), at strength D/r0.
+ * Under the path-integrated model the angular part of Q_i(u) conj Q_j(u)
+ * leaves the path integral, so the J x J cross-spectral density is
+ * S(k) = D(k) P Gamma(|f_k|) P^T D(k)^H with D = diag(c_j sqrt(n_j+1) Theta_j(phi_k)),
+ * P the J x R indicator of each mode's radial order (R distinct orders: 5 for
+ * J = 15, 8 for J = 36) and Gamma the R x R matrix of the radial spectra
+ * G_{n n'}(|f|); its root D P chol(Gamma) needs R complex Gaussians per
+ * frequency instead of J.  Noise: Philox-4x32-10, key = seed, subsequence
+ * (5 << 40) | (frame << 8) | r for stream r, the element layout of
+ * dfp2s_sample_zernike_fields (rows kx = 0 .. N/2 of 2N Gaussians, (Re, Im) of
+ * bin ky at 2 ky, 2 ky + 1); streams R .. 2R-1 feed the second half of the root
+ * on the lines kx = N/2 and ky = N/2, where index N/2 is the frequency -N/2 for
+ * k and -k alike.  The fields are complete: no mixing follows.  Needs a factor
+ * built with DFP2S_FACTOR_FULL (else EINVAL); uses the factor's scratch.
+ * Errors: EINVAL, ECUDA. */
+int dfp2s_sample_zernike_fields_full(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                     int H, int W, float* fields_dev, void* stream);
 
 /* Temporally correlated fields (Sec. III, spatio-temporally correlated
  * fields: the paper enforces the temporal correlation with an auto-regressive

@@ -64,15 +64,32 @@ def radial_orders(J: int):
 
 def order_gram(J: int, N: int, pix_per_D: float) -> np.ndarray:
     """Gamma(|f_k|) on the N x N torus, shape (N, N, R, R): G_{n_o n_o'} for every pair of radial orders."""
+    inv, Gu = order_gram_unique(J, N, pix_per_D)
+    return Gu[inv]
+
+
+def order_gram_unique(J: int, N: int, pix_per_D: float):
+    """Gamma per distinct |k|^2 of the torus: (inverse index (N, N), Gamma (U, R, R)); zero at DC."""
     orders, _ = radial_orders(J)
     R = len(orders)
-    Gm = np.zeros((N, N, R, R))
+    pairs = spectrum._all_pairs()
+    inv, vals = spectrum._radial_table(N, pix_per_D, pairs)
+    Gu = np.zeros((vals.shape[1], R, R))
     for a in range(R):
         for b in range(a, R):
-            g = spectrum._radial_on_torus(N, pix_per_D, orders[a], orders[b])
-            Gm[:, :, a, b] = g
-            Gm[:, :, b, a] = g
-    return Gm
+            g = vals[pairs.index((orders[a], orders[b]))]
+            Gu[:, a, b] = g
+            Gu[:, b, a] = g
+    return inv, Gu
+
+
+def order_cholesky_unique(J: int, N: int, pix_per_D: float):
+    """(inverse index, C (U, R, R)): the lower Cholesky factor of Gamma per distinct |k|^2, zero at DC."""
+    inv, Gu = order_gram_unique(J, N, pix_per_D)
+    C = np.zeros_like(Gu)
+    nz = np.abs(Gu).sum(axis=(1, 2)) > 0
+    C[nz] = np.linalg.cholesky(Gu[nz])
+    return inv, C
 
 
 def mode_scales(J: int, N: int, pix_per_D: float, A0: np.ndarray) -> np.ndarray:
@@ -89,11 +106,8 @@ def full_root(J: int, N: int, pix_per_D: float, A0: np.ndarray) -> np.ndarray:
     """R(k) = D(k) P chol(Gamma(|f_k|)) on the N x N torus, shape (N, N, J, R) complex, [ky, kx] order; 0 at DC."""
     _, phi, _, _ = spectrum.torus_frequencies(N, pix_per_D)
     _, order_of = radial_orders(J)
-    Gm = order_gram(J, N, pix_per_D)
-    C = np.zeros_like(Gm)
-    nz = np.ones((N, N), dtype=bool)
-    nz[0, 0] = False
-    C[nz] = np.linalg.cholesky(Gm[nz])
+    inv, Cu = order_cholesky_unique(J, N, pix_per_D)
+    C = Cu[inv]
     scale = mode_scales(J, N, pix_per_D, A0)
     Rt = np.empty((N, N, J, C.shape[-1]), dtype=np.complex128)
     for j in range(J):
@@ -102,40 +116,63 @@ def full_root(J: int, N: int, pix_per_D: float, A0: np.ndarray) -> np.ndarray:
     return Rt
 
 
-def full_spectrum(seed: int, frame: int, J: int, N: int, pix_per_D: float, A0: np.ndarray) -> np.ndarray:
-    """The Fourier-domain fields E (J, N, N) complex, [j, ky, kx], of one frame of the full sampler (R29)."""
-    Rt = full_root(J, N, pix_per_D, A0)
-    R = Rt.shape[-1]
+def _line_gaussians(seed, frame, stream, N):
+    """z' of one stream on the half plane, drawn only where it is used: column kx = N/2 and row ky = N/2."""
     half = N // 2 + 1
+    out = np.zeros((half, N), dtype=np.complex128)
+    sub = noise.subsequence(TAG_FULL_FIELDS, frame, stream)
+    kx = np.concatenate([np.full(N // 2, N // 2), np.arange(N // 2)])
+    i = np.concatenate([np.arange(N // 2), np.full(N // 2, N // 4)])  # bins (kx, 2i), (kx, 2i + 1)
+    w0, w1, w2, w3 = noise.philox_words(seed, sub, (kx * (N // 2) + i).astype(np.uint64))
+    g0, g1 = noise.box_muller(w0, w1)
+    g2, g3 = noise.box_muller(w2, w3)
+    out[kx, 2 * i] = g0.astype(np.float64) + 1j * g1.astype(np.float64)
+    out[kx, 2 * i + 1] = g2.astype(np.float64) + 1j * g3.astype(np.float64)
+    return out
 
-    def z_of(stream):
-        g = np.asarray(noise.gaussian_block(seed, TAG_FULL_FIELDS, frame, stream, half, 2 * N), np.float64)
-        g = g.reshape(half, N, 2)
-        return g[..., 0] + 1j * g[..., 1]  # [kx, ky]
 
-    z = np.stack([z_of(r) for r in range(R)])        # (R, half, N)
-    z2 = np.stack([z_of(R + r) for r in range(R)])
-    Eh = np.zeros((J, half, N), dtype=np.complex128)  # [j, kx, ky]
-    for kx in range(half):
-        for ky in range(N):
-            if kx == 0 and ky == 0:
-                continue
-            Rk = Rt[ky, kx]                           # (J, R)
-            if (kx in (0, N // 2)) and (ky in (0, N // 2)):
-                Eh[:, kx, ky] = N * np.real(np.conj(Rk) @ z[:, kx, ky])
-            elif kx == N // 2 or ky == N // 2:
-                Rm = Rt[(N - ky) % N, (N - kx) % N]   # R(-k)
-                Eh[:, kx, ky] = (N / 2) * (np.conj(Rk) @ z[:, kx, ky] + Rm @ z2[:, kx, ky])
-            else:
-                Eh[:, kx, ky] = (N / math.sqrt(2.0)) * (np.conj(Rk) @ z[:, kx, ky])
-    for kx in (0, N // 2):
-        for ky in range(N // 2 + 1, N):
-            Eh[:, kx, ky] = np.conj(Eh[:, kx, N - ky])
+def full_spectrum(seed: int, frame: int, J: int, N: int, pix_per_D: float, A0: np.ndarray) -> np.ndarray:
+    """The Fourier-domain fields E (J, N, N) complex, [j, ky, kx], of one frame of the full sampler (R29).
+
+    conj(R(k)) z = conj(c_j sqrt(n_j+1) Theta_j(phi_k)) eta_{o_j}(k) with eta_o = sum_r C_or z_r, C real: the
+    per-bin rules of the module docstring, evaluated for all bins of a mode at once.
+    """
+    orders, order_of = radial_orders(J)
+    R = len(orders)
+    half = N // 2 + 1
+    inv, Cu = order_cholesky_unique(J, N, pix_per_D)
+    Ch = Cu[inv.T[:half]]                              # (half, N, R, R) at [kx, ky]
+    z = np.stack([np.asarray(noise.gaussian_block(seed, TAG_FULL_FIELDS, frame, r, half, 2 * N), np.float64)
+                  .reshape(half, N, 2) @ np.array([1.0, 1j]) for r in range(R)], axis=-1)   # (half, N, R)
+    z2 = np.stack([_line_gaussians(seed, frame, R + r, N) for r in range(R)], axis=-1)
+    eta = np.einsum("xyor,xyr->xyo", Ch, z)
+    eta2 = np.einsum("xyor,xyr->xyo", Ch, z2)
+    _, phi, _, _ = spectrum.torus_frequencies(N, pix_per_D)
+    phi_h = phi.T[:half]                               # phi at [kx, ky]
+    phi_m = phi[(N - np.arange(N)[None, :]) % N, (N - np.arange(half)[:, None]) % N]  # phi(-k) at [kx, ky]
+    kx = np.arange(half)[:, None] * np.ones((1, N), dtype=int)
+    ky = np.ones((half, 1), dtype=int) * np.arange(N)[None, :]
+    corner = np.isin(kx, (0, N // 2)) & np.isin(ky, (0, N // 2))
+    line = ((kx == N // 2) | (ky == N // 2)) & ~corner
+    scale = mode_scales(J, N, pix_per_D, A0)
+    Eh = np.zeros((J, half, N), dtype=np.complex128)
+    for j in range(J):
+        th = spectrum.theta_complex(j + 2, phi_h)
+        tm = spectrum.theta_complex(j + 2, phi_m)
+        a = scale[j] * np.conj(th) * eta[:, :, order_of[j]]
+        b = scale[j] * tm * eta2[:, :, order_of[j]]
+        e = (N / math.sqrt(2.0)) * a
+        e[line] = (N / 2) * (a[line] + b[line])
+        e[corner] = N * a[corner].real
+        e[0, 0] = 0.0
+        Eh[j] = e
+    for c in (0, N // 2):
+        Eh[:, c, N // 2 + 1:] = np.conj(Eh[:, c, 1: N // 2][:, ::-1])
     E = np.empty((J, N, N), dtype=np.complex128)
     E[:, :, :half] = np.transpose(Eh, (0, 2, 1))
-    kx = np.arange(half, N)
-    ky = np.arange(N)
-    E[:, :, half:] = np.conj(Eh[:, (N - kx)[None, :], ((N - ky) % N)[:, None]])
+    kxs = np.arange(half, N)
+    kys = np.arange(N)
+    E[:, :, half:] = np.conj(Eh[:, (N - kxs)[None, :], ((N - kys) % N)[:, None]])
     return E
 
 

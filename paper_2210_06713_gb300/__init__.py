@@ -20,7 +20,7 @@ from . import build as _build
 OK = 0
 W_F32, W_BF16 = 0, 1
 P2S_EXACT, P2S_LEARNED, P2S_LEARNED_FP32 = 0, 1, 2
-FACTOR_FACTORED, FACTOR_DENSE = 0, 1
+FACTOR_FACTORED, FACTOR_DENSE, FACTOR_FULL = 0, 1, 2
 KS = 33
 MAX_J = 64
 MAX_K = 128
@@ -58,6 +58,7 @@ SIGNATURES = {
     "dfp2s_factor_info": (_i, [_vp, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_sz)]),
     "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_ar1": (_i, [_vp, _d, _u64, _u32, _d, _i, _i, _vp, _vp, _vp]),
+    "dfp2s_sample_zernike_fields_full": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
@@ -209,6 +210,16 @@ def sample_zernike_fields(factor: SpectralFactor, D_over_r0: float, seed: int, f
         out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
     _check(load().dfp2s_sample_zernike_fields(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
                                               _stream(stream)))
+    return out
+
+
+def sample_zernike_fields_full(factor: SpectralFactor, D_over_r0: float, seed: int, frame: int, H: int, W: int,
+                               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Fields of the full cross-spectral density (no approximation); the factor needs kind=FACTOR_FULL."""
+    if out is None:
+        out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_sample_zernike_fields_full(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
+                                                   _stream(stream)))
     return out
 
 

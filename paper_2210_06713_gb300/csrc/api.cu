@@ -126,6 +126,9 @@ static void factor_free(dfp2s_factor* f) {
   cudaFree(f->d.L32);
   cudaFree(f->d.tw);
   cudaFree(f->d.scratch);
+  cudaFree(f->d.fchol);
+  cudaFree(f->d.fmode);
+  cudaFree(f->d.eta);
   delete f;
 }
 
@@ -135,7 +138,8 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
   CHECK_ARG(p->J >= 3 && p->J <= DFP2S_MAX_J, "J = %d out of range [3, %d]", p->J, DFP2S_MAX_J);
   CHECK_ARG(is_pow2(p->N) && p->N >= 16 && p->N <= 4096, "N = %d must be a power of two in [16, 4096]", p->N);
   CHECK_ARG(p->pix_per_D > 0 && p->pix_per_D <= 64, "pix_per_D out of range");
-  CHECK_ARG(p->kind == DFP2S_FACTOR_FACTORED || p->kind == DFP2S_FACTOR_DENSE, "unknown factor kind");
+  CHECK_ARG(p->kind == DFP2S_FACTOR_FACTORED || p->kind == DFP2S_FACTOR_DENSE || p->kind == DFP2S_FACTOR_FULL,
+            "unknown factor kind");
   if (p->kind == DFP2S_FACTOR_DENSE) return dfp2s_fail(DFP2S_EUNSUPPORTED, "dense factor not built in this version");
   dfp2s_factor* f = new dfp2s_factor();
   memset(&f->d, 0, sizeof(f->d));
@@ -153,6 +157,18 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
       (e = dfp2s_device_malloc((void**)&f->d.scratch, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
     factor_free(f);
     return dfp2s_fail_cuda(e, "factor allocation");
+  }
+  if (p->kind == DFP2S_FACTOR_FULL) {
+    const int R = dfp2s_radial_order_count(p->J);
+    const size_t noct = (size_t)(p->N / 2 + 1) * (p->N / 2 + 2) / 2;
+    f->d.R = R;
+    if ((e = dfp2s_device_malloc((void**)&f->d.fchol, noct * (R * (R + 1) / 2) * sizeof(float))) != cudaSuccess ||
+        (e = dfp2s_device_malloc((void**)&f->d.fmode, (size_t)p->J * sizeof(dfp2s_full_mode))) != cudaSuccess ||
+        (e = dfp2s_device_malloc((void**)&f->d.eta, (size_t)R * (half + p->N + p->N / 2 + 1) * sizeof(float2))) !=
+            cudaSuccess) {
+      factor_free(f);
+      return dfp2s_fail_cuda(e, "full-sampler table allocation");
+    }
   }
   const int rc = dfp2s_factor_build_device(&f->d, as_stream(stream));
   if (rc != DFP2S_OK) {
@@ -197,6 +213,17 @@ extern "C" int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_
   const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
   CHECK_LAUNCH(dfp2s_launch_sample_fields(f->d.scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame,
                                           f->d.L32, scale, fields, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_sample_zernike_fields_full(const dfp2s_factor* f, double D_over_r0, uint64_t seed,
+                                                uint32_t frame, int H, int W, float* fields, void* stream) {
+  CHECK_ARG(f && fields, "null argument");
+  CHECK_ARG(f->kind == DFP2S_FACTOR_FULL, "the factor was not built with DFP2S_FACTOR_FULL");
+  CHECK_ARG(H >= 1 && W >= 1 && H <= f->d.N && W <= f->d.N, "frame %dx%d does not fit the %d grid", H, W, f->d.N);
+  CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
+  const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+  CHECK_LAUNCH(dfp2s_launch_sample_fields_full(&f->d, H, W, seed, frame, scale, fields, as_stream(stream)));
   return DFP2S_OK;
 }
 

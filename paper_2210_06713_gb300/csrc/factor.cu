@@ -90,20 +90,23 @@ __global__ void k_noll_chol(int J, double* __restrict__ L64, float* __restrict__
   }
 }
 
-// g_n(v_q) * w_q for every needed radial order n (layout [q][o]).
-__global__ void k_gtab(const double* __restrict__ v, const double* __restrict__ w, int Q, const int* __restrict__ orders,
-                       int no, double* __restrict__ gtab) {
+// g_nn'(v_q) * w_q for every needed pair of radial orders (n, n') = (orders_a[p], orders_b[p]) (layout [q][p]);
+// the per-mode spectra take the diagonal pairs.
+__global__ void k_gtab(const double* __restrict__ v, const double* __restrict__ w, int Q, const int* __restrict__ orders_a,
+                       const int* __restrict__ orders_b, int no, double* __restrict__ gtab) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Q * no) return;
   const int q = i / no, o = i - q * no;
   const double pi = 3.14159265358979323846;
   const double x = v[q];
-  const double jb = jn(orders[o] + 1, 2.0 * pi * x);
-  gtab[i] = w[q] * pow(x, -11.0 / 3.0) * jb * jb / (pi * pi * x * x);
+  const double ja = jn(orders_a[o] + 1, 2.0 * pi * x);
+  const double jb = orders_b[o] == orders_a[o] ? ja : jn(orders_b[o] + 1, 2.0 * pi * x);
+  gtab[i] = w[q] * pow(x, -11.0 / 3.0) * ja * jb / (pi * pi * x * x);
 }
 
-// G_n(f) on the octant 0 <= b <= a <= N/2 of integer frequency pairs, index a(a+1)/2 + b.
-__global__ void k_radial(const double* __restrict__ v, const double* __restrict__ gtab, int Q, int no, int N,
+// G_n(f) on the octant 0 <= b <= a <= N/2 of integer frequency pairs, index a(a+1)/2 + b, for the no <= kMaxOrders
+// columns of gtab (row stride ld) that start at gtab[0].
+__global__ void k_radial(const double* __restrict__ v, const double* __restrict__ gtab, int Q, int no, int ld, int N,
                          double fscale, double* __restrict__ G, int noct) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= noct) return;
@@ -120,7 +123,7 @@ __global__ void k_radial(const double* __restrict__ v, const double* __restrict_
       const double x = v[q];
       const double d = 2.0 * x + f;
       const double K = exp((5.0 / 3.0) * log(2.0 * x / d)) * 2.0 * x * x / (f * d * d);
-      const double* g = gtab + (size_t)q * no;
+      const double* g = gtab + (size_t)q * ld;
 #pragma unroll
       for (int o = 0; o < kMaxOrders; ++o)
         if (o < no) acc[o] = fma(K, g[o], acc[o]);
@@ -185,6 +188,63 @@ __global__ void k_lambda_write(const ModeInfo* __restrict__ modes, int J, int N,
   }
 }
 
+// ---- the full cross-spectral sampler (Sec. III-B; reading R29)
+// Per octant bin: Gamma_oo' = G_{n_o n_o'}(|f|) (pairs p(a, b) = a no - a(a-1)/2 + (b - a), a <= b), its lower
+// Cholesky factor in FP64, stored in FP32 as C[bin][o(o+1)/2 + r], r <= o.  Gamma is positive definite off DC (a
+// Gram matrix of the J_{n+1}(2 pi v) under a positive weight); a pivot that is not positive (DC, where Gamma = 0)
+// zeroes its column.
+__global__ void k_full_chol(const double* __restrict__ Gp, int no, int noct, float* __restrict__ C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= noct) return;
+  double A[kMaxOrders * kMaxOrders];
+  for (int a = 0; a < no; ++a)
+    for (int b = a; b < no; ++b) {
+      const double g = Gp[(size_t)(a * no - a * (a - 1) / 2 + (b - a)) * noct + i];
+      A[a * no + b] = g;
+      A[b * no + a] = g;
+    }
+  for (int a = 0; a < no; ++a) {
+    for (int b = 0; b <= a; ++b) {
+      double s = A[a * no + b];
+      for (int k = 0; k < b; ++k) s -= A[a * no + k] * A[b * no + k];
+      if (a == b) A[a * no + a] = s > 0.0 ? sqrt(s) : 0.0;
+      else A[a * no + b] = A[b * no + b] > 0.0 ? s / A[b * no + b] : 0.0;
+    }
+  }
+  float* c = C + (size_t)i * (no * (no + 1) / 2);
+  for (int a = 0; a < no; ++a)
+    for (int b = 0; b <= a; ++b) c[a * (a + 1) / 2 + b] = (float)A[a * no + b];
+}
+
+// Per mode: the order slot, m, sin/cos, Noll's angular prefactor (-1)^((n-m)/2) i^m sqrt 2 ((-1)^(n/2) for m = 0)
+// and kappa0_j = sqrt(A0_jj (n_j + 1) / sum_k P_jj(k)) (A0_jj from the rows of L, D/r0 = 1).
+__global__ void k_full_modes(const ModeInfo* __restrict__ modes, int J, const double* __restrict__ L64,
+                             const double* __restrict__ sums, dfp2s_full_mode* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= J) return;
+  const ModeInfo mi = modes[j];
+  double a0 = 0.0;
+  for (int k = 0; k <= j; ++k) a0 += L64[j * J + k] * L64[j * J + k];
+  dfp2s_full_mode o;
+  o.o = mi.o;
+  o.m = mi.m;
+  o.odd = mi.odd;
+  o.pad = 0;
+  if (mi.m == 0) {
+    o.pre_re = ((mi.n / 2) & 1) ? -1.f : 1.f;
+    o.pre_im = 0.f;
+  } else {
+    const float sg = (((mi.n - mi.m) / 2) & 1) ? -1.f : 1.f;
+    const float r2 = 1.41421356237309505f;
+    const int q = mi.m & 3;  // i^m
+    o.pre_re = q == 0 ? sg * r2 : (q == 2 ? -sg * r2 : 0.f);
+    o.pre_im = q == 1 ? sg * r2 : (q == 3 ? -sg * r2 : 0.f);
+  }
+  o.kappa0 = (float)sqrt(a0 * (mi.n + 1) / sums[j]);
+  o.pad2 = 0.f;
+  out[j] = o;
+}
+
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
@@ -245,6 +305,17 @@ struct DevBuf {
 
 }  // namespace
 
+int dfp2s_radial_order_count(int J) {
+  int count = 0, last = -1;
+  for (int j = 2; j <= J + 1; ++j) {
+    int n = 0;
+    while ((n + 1) * (n + 2) / 2 < j) ++n;
+    if (n != last) ++count;  // Noll's index runs through the orders in ascending order
+    last = n;
+  }
+  return count;
+}
+
 int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st) {
   const int J = f->J, N = f->N;
   // ---- twiddles (FP64 -> FP32)
@@ -302,13 +373,41 @@ int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st) {
   DFP2S_CUDA_TRY(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
 
   k_noll_chol<<<1, 256, 0, st>>>(J, f->L64, f->L32, derr.p);
-  k_gtab<<<(Q * no + 255) / 256, 256, 0, st>>>(dv.p, dw.p, Q, dord.p, no, gtab.p);
-  k_radial<<<(noct + 127) / 128, 128, 0, st>>>(dv.p, gtab.p, Q, no, N, f->pix_per_D / N, G.p, noct);
+  k_gtab<<<(Q * no + 255) / 256, 256, 0, st>>>(dv.p, dw.p, Q, dord.p, dord.p, no, gtab.p);
+  k_radial<<<(noct + 127) / 128, 128, 0, st>>>(dv.p, gtab.p, Q, no, no, N, f->pix_per_D / N, G.p, noct);
   const size_t total = (size_t)(N / 2 + 1) * N;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   k_lambda_sums<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p);
   k_lambda_write<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p, f->mult);
   DFP2S_CUDA_TRY(cudaGetLastError());
+  DevBuf<double> gtab2, Gp;
+  DevBuf<int> dpa, dpb;
+  if (f->fchol) {
+    // the full sampler: radial spectra of every pair of orders, their Cholesky factor per octant bin, mode constants
+    if (f->R != no) return dfp2s_fail(DFP2S_EINVAL, "full sampler: %d radial orders, tables sized for %d", no, f->R);
+    std::vector<int> pa, pb;
+    for (int a = 0; a < no; ++a)
+      for (int b = a; b < no; ++b) {
+        pa.push_back(orders[a]);
+        pb.push_back(orders[b]);
+      }
+    const int np = (int)pa.size();
+    DFP2S_CUDA_TRY(gtab2.alloc((size_t)Q * np));
+    DFP2S_CUDA_TRY(Gp.alloc((size_t)np * noct));
+    DFP2S_CUDA_TRY(dpa.alloc(np));
+    DFP2S_CUDA_TRY(dpb.alloc(np));
+    DFP2S_CUDA_TRY(cudaMemcpyAsync(dpa.p, pa.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    DFP2S_CUDA_TRY(cudaMemcpyAsync(dpb.p, pb.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_gtab<<<(Q * np + 255) / 256, 256, 0, st>>>(dv.p, dw.p, Q, dpa.p, dpb.p, np, gtab2.p);
+    for (int c0 = 0; c0 < np; c0 += kMaxOrders) {
+      const int nc = np - c0 < kMaxOrders ? np - c0 : kMaxOrders;
+      k_radial<<<(noct + 127) / 128, 128, 0, st>>>(dv.p, gtab2.p + c0, Q, nc, np, N, f->pix_per_D / N,
+                                                   Gp.p + (size_t)c0 * noct, noct);
+    }
+    k_full_chol<<<(noct + 127) / 128, 128, 0, st>>>(Gp.p, no, noct, f->fchol);
+    k_full_modes<<<1, 64, 0, st>>>(dmodes.p, J, f->L64, sums.p, f->fmode);
+    DFP2S_CUDA_TRY(cudaGetLastError());
+  }
   int herr = 0;
   DFP2S_CUDA_TRY(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   DFP2S_CUDA_TRY(cudaStreamSynchronize(st));

@@ -28,7 +28,23 @@ struct dfp2s_factor_dev {
   float* L32;      // J x J
   float2* tw;      // N twiddles exp(-2 pi i m / N)
   float2* scratch; // J x (N/2+1) x N spectrum
+  // the full cross-spectral sampler (factor kind DFP2S_FACTOR_FULL; null otherwise)
+  int R;                          // distinct radial orders of Noll 2..J+1
+  float* fchol;                   // octant bins x R(R+1)/2: Cholesky factor of Gamma(|k|), [a(a+1)/2 + b][o(o+1)/2 + r]
+  struct dfp2s_full_mode* fmode;  // J mode constants
+  float2* eta;                    // R x (N/2+1) x N order fields, then R x (N + N/2 + 1) for the Nyquist lines
 };
+// Per-mode constants of the full sampler: order slot, azimuthal frequency m, sin (odd Noll index) or cos, Noll's
+// angular prefactor (complex) and kappa0 = sqrt(A0_jj (n+1) / sum_k P_jj(k)).
+struct dfp2s_full_mode {
+  int o, m, odd, pad;
+  float pre_re, pre_im, kappa0, pad2;
+};
+// Number of distinct radial orders among Noll modes 2..J+1.
+int dfp2s_radial_order_count(int J);
+// fields.cu -- the full sampler's per-frame passes (needs a factor built with the full tables)
+int dfp2s_launch_sample_fields_full(const dfp2s_factor_dev* f, int H, int W, uint64_t seed, uint32_t frame,
+                                    float scale, float* fields, cudaStream_t st);
 int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st);
 
 // The opaque handle of include/dfp2s.h.
