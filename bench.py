@@ -250,6 +250,45 @@ def large_frame(d, S, device, stream, flush):
     return res
 
 
+def full_sampler_timing(d, device, stream, flush, peak_gbs):
+    """The exact sampler of the full cross-spectral density (no approximation) against the factored sampler with
+    its mixing pass, J = 36, at the 512 x 512 frame's grid (N = 1024) and at 3840 x 2160 (N = 4096): ms per
+    call (CUDA events on this stream, L2 flushed before each call) and the full sampler's HBM roofline over its
+    algorithmic bytes (order fields written and read once, column spectra written and read, fields written,
+    Cholesky table read once)."""
+    import torch
+    out = {}
+    for name, H, W in (("512x512", 512, 512), ("3840x2160", 2160, 3840)):
+        N = d.grid_size(H, W, PIX_PER_D)
+        t0 = time.perf_counter()
+        f = d.SpectralFactor(J, N, PIX_PER_D, kind=d.FACTOR_FULL)
+        setup_s = time.perf_counter() - t0
+        fields = torch.empty(J, H, W, device=device)
+        res = {"N": N, "setup_s": setup_s}
+        for label, fn in (("full", d.sample_zernike_fields_full), ("factored", d.sample_zernike_fields)):
+            for i in range(3):
+                fn(f, 2.0, 9, i, H, W, out=fields, stream=stream)
+            e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for i, (a, b) in enumerate(e):
+                flush.zero_()
+                a.record(stream)
+                fn(f, 2.0, 9, 10 + i, H, W, out=fields, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            res[label + "_ms"] = float(np.median([a.elapsed_time(b) for a, b in e]))
+        R = 8
+        half = N // 2 + 1
+        noct = half * (half + 1) // 2
+        alg = (2 * R * half * N * 8 + 2 * J * half * H * 8 + J * H * W * 4 + noct * (R * (R + 1) // 2) * 4)
+        res["full_roofline"] = {"bound": "hbm", "bytes": alg, "achieved": alg / (res["full_ms"] * 1e-3) / 1e9,
+                                "peak": peak_gbs, "unit": "GB/s",
+                                "frac": alg / (res["full_ms"] * 1e-3) / 1e9 / peak_gbs}
+        out[name] = res
+        del f, fields
+        torch.cuda.empty_cache()
+    return out
+
+
 def batched_uneven(d, S, device, stream, seed_base=0, train_steps=20000):
     """The batched workload: 64 requests, image sides uniform in {256, 512, 768, 1024} (x 3 channels), D/r0 uniform
     in [1, 5], J in {15, 36}, 8 frames each with independent seeds, learned P2S, through one engine call
@@ -483,6 +522,13 @@ def run_ours(args, rank, world, device):
             line["workloads"] = {"3840x2160x3": large_frame(d, S, device, stream, flush)}
         except RuntimeError as exc:
             line["workloads"] = {"3840x2160x3": {"unavailable": str(exc).splitlines()[0][:160]}}
+    if args.workload == "512" and args.mode == "learned" and not args.no_full_sampler:
+        line.setdefault("workloads", {})
+        try:
+            line["workloads"]["full_cross_spectrum_fields"] = full_sampler_timing(d, device, stream, flush,
+                                                                                  peaks["hbm_gbs"])
+        except RuntimeError as exc:
+            line["workloads"]["full_cross_spectrum_fields"] = {"unavailable": str(exc).splitlines()[0][:160]}
     if args.workload == "512" and args.mode == "learned" and not args.no_batched:
         line.setdefault("workloads", {})
         try:
@@ -609,6 +655,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160x3 half of the metric")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-request workload")
+    ap.add_argument("--no-full-sampler", action="store_true", help="skip the full cross-spectrum sampler timing")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -162,7 +162,8 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
     const int R = dfp2s_radial_order_count(p->J);
     const size_t noct = (size_t)(p->N / 2 + 1) * (p->N / 2 + 2) / 2;
     f->d.R = R;
-    if ((e = dfp2s_device_malloc((void**)&f->d.fchol, noct * (R * (R + 1) / 2) * sizeof(float))) != cudaSuccess ||
+    const size_t trip = (size_t)(R * (R + 1) / 2 + 3) / 4 * 4;  // Cholesky rows padded to whole float4
+    if ((e = dfp2s_device_malloc((void**)&f->d.fchol, noct * trip * sizeof(float))) != cudaSuccess ||
         (e = dfp2s_device_malloc((void**)&f->d.fmode, (size_t)p->J * sizeof(dfp2s_full_mode))) != cudaSuccess ||
         (e = dfp2s_device_malloc((void**)&f->d.eta, (size_t)R * (half + p->N + p->N / 2 + 1) * sizeof(float2))) !=
             cudaSuccess) {

@@ -190,7 +190,7 @@ __global__ void k_lambda_write(const ModeInfo* __restrict__ modes, int J, int N,
 
 // ---- the full cross-spectral sampler (Sec. III-B; reading R29)
 // Per octant bin: Gamma_oo' = G_{n_o n_o'}(|f|) (pairs p(a, b) = a no - a(a-1)/2 + (b - a), a <= b), its lower
-// Cholesky factor in FP64, stored in FP32 as C[bin][o(o+1)/2 + r], r <= o.  Gamma is positive definite off DC (a
+// Cholesky factor in FP64, stored in FP32 as C[bin][o(o+1)/2 + r], r <= o (rows padded to a multiple of 4).  Gamma is positive definite off DC (a
 // Gram matrix of the J_{n+1}(2 pi v) under a positive weight); a pivot that is not positive (DC, where Gamma = 0)
 // zeroes its column.
 __global__ void k_full_chol(const double* __restrict__ Gp, int no, int noct, float* __restrict__ C) {
@@ -211,9 +211,11 @@ __global__ void k_full_chol(const double* __restrict__ Gp, int no, int noct, flo
       else A[a * no + b] = A[b * no + b] > 0.0 ? s / A[b * no + b] : 0.0;
     }
   }
-  float* c = C + (size_t)i * (no * (no + 1) / 2);
+  const int tri = no * (no + 1) / 2, trip = (tri + 3) / 4 * 4;  // rows padded to whole float4
+  float* c = C + (size_t)i * trip;
   for (int a = 0; a < no; ++a)
     for (int b = 0; b <= a; ++b) c[a * (a + 1) / 2 + b] = (float)A[a * no + b];
+  for (int e = tri; e < trip; ++e) c[e] = 0.f;
 }
 
 // Per mode: the order slot, m, sin/cos, Noll's angular prefactor (-1)^((n-m)/2) i^m sqrt 2 ((-1)^(n/2) for m = 0)

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "fft_reg.cuh"
+#include "field_groups.cuh"
 #include "kernels.h"
 
 namespace {
@@ -28,19 +29,6 @@ using fftr::OutIndex;
 using fftr::pad32;
 using fftr::Plan;
 
-constexpr int kMaxR = 10;  // radial orders of Noll 2..65
-
-// FFT groups per block: 8 up to N = 1024, then enough for 256 threads.
-template <int N>
-struct Groups {
-  static constexpr int G = N >= 4096 ? 2 : (N >= 2048 ? 4 : 8);
-  static constexpr int THREADS = G * Plan<N>::T;
-  static constexpr int BUFE = (Plan<N>::BUF + 1) / 2 * 2;  // even: 16-byte aligned group buffers
-  static constexpr int TS = 2 * G + 1;                     // tile row stride (complex), odd against conflicts
-  static constexpr size_t smem_fft = (size_t)G * BUFE * sizeof(float2);
-  static constexpr size_t smem_tile = (size_t)(N / 2 + 1) * TS * sizeof(float2);
-  static constexpr size_t smem = smem_fft > smem_tile ? smem_fft : smem_tile;
-};
 
 // -------------------------------------------------------------- pass 1
 // One frequency column kx of mode j per group.  The column's Fourier-domain white noise E(kx, ky)
@@ -298,152 +286,6 @@ __global__ void k_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* __rest
   reinterpret_cast<float4*>(out)[i] = dfp2s_gauss4(seed, sub, i);
 }
 
-// ------------------------------------------------- the full cross-spectral sampler (Sec. III-B; reading R29)
-// Pass 0, k_fullnoise: per half-plane bin (kx, ky) the R complex Gaussians z_r (Philox tag 5, stream r, the same
-// element layout as the factored sampler's noise) and the order fields eta_o = sum_{r <= o} C_or(|k|) z_r, C the
-// Cholesky factor of the radial-order matrix Gamma(|k|).  On the lines kx = N/2 (0 < ky < N/2) and ky = N/2
-// (0 < kx < N/2) also eta'_o from streams R + r.  One thread per pair of bins ky = 2i, 2i + 1 (one Philox block).
-template <int N>
-__global__ void __launch_bounds__(256) k_fullnoise(const float* __restrict__ C, int R, float2* __restrict__ eta,
-                                                   uint64_t seed, uint32_t frame) {
-  constexpr int HALF = N / 2 + 1;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= HALF * (N / 2)) return;
-  const int kx = idx / (N / 2), i = idx - kx * (N / 2);
-  const int tri = R * (R + 1) / 2;
-  float4 z[kMaxR];
-#pragma unroll
-  for (int r = 0; r < kMaxR; ++r)
-    if (r < R) z[r] = dfp2s_gauss4(seed, dfp2s_subsequence(5u, frame, (uint32_t)r), (uint64_t)kx * (N / 2) + i);
-  float2* nyq = eta + (size_t)R * HALF * N;
-#pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    const int ky = 2 * i + b;
-    const int ay = ky < N / 2 ? ky : N - ky;
-    const int oa = kx > ay ? kx : ay, ob = kx > ay ? ay : kx;
-    const float* c = C + (size_t)(oa * (oa + 1) / 2 + ob) * tri;
-    const bool line = (kx == N / 2 && ky > 0 && ky < N / 2) || (ky == N / 2 && kx > 0 && kx < N / 2);
-    float4 z2[kMaxR];
-    if (line) {
-#pragma unroll
-      for (int r = 0; r < kMaxR; ++r)
-        if (r < R)
-          z2[r] = dfp2s_gauss4(seed, dfp2s_subsequence(5u, frame, (uint32_t)(R + r)), (uint64_t)kx * (N / 2) + i);
-    }
-    for (int o = 0; o < R; ++o) {
-      float2 e = make_float2(0.f, 0.f), e2 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int r = 0; r < kMaxR; ++r) {
-        if (r <= o) {
-          const float cr = __ldg(c + o * (o + 1) / 2 + r);
-          const float zx = b ? z[r].z : z[r].x, zy = b ? z[r].w : z[r].y;
-          e.x = fmaf(cr, zx, e.x);
-          e.y = fmaf(cr, zy, e.y);
-          if (line) {
-            const float wx = b ? z2[r].z : z2[r].x, wy = b ? z2[r].w : z2[r].y;
-            e2.x = fmaf(cr, wx, e2.x);
-            e2.y = fmaf(cr, wy, e2.y);
-          }
-        }
-      }
-      eta[((size_t)o * HALF + kx) * N + ky] = e;
-      if (line) nyq[(size_t)o * (N + HALF) + (kx == N / 2 ? ky : N + kx)] = e2;
-    }
-  }
-}
-
-// cos(m phi), sin(m phi) of the direction of the signed frequency (x, y) != 0, by powers of the unit vector.
-DFP2S_DEV float2 unit_power(float x, float y, int m) {
-  const float inv = rsqrtf(x * x + y * y);
-  const float2 u = make_float2(x * inv, y * inv);
-  float2 p = make_float2(1.f, 0.f);
-  for (int k = 0; k < m; ++k) p = make_float2(p.x * u.x - p.y * u.y, p.x * u.y + p.y * u.x);
-  return p;
-}
-
-// Noll's Theta_j at the signed frequency (x, y): prefactor times cos(m phi) (even j) or sin(m phi) (odd j).
-DFP2S_DEV float2 theta_at(const dfp2s_full_mode& md, float x, float y) {
-  float a = 1.f;
-  if (md.m != 0) {
-    const float2 p = unit_power(x, y, md.m);
-    a = md.odd ? p.y : p.x;
-  }
-  return make_float2(md.pre_re * a, md.pre_im * a);
-}
-
-// Pass 1, k_colfull: one frequency column kx of mode j per group.  E_j(kx, ky) from eta_{o_j}: kappa/sqrt2
-// conj(Theta(k)) eta on generic bins, kappa/2 (conj(Theta(k)) eta + Theta(-k) eta') on the Nyquist lines, kappa
-// Re(conj(Theta) eta) on the three Nyquist corners, 0 at DC (kappa = kappa0_j (D/r0)^{5/6}, the 1/N^2 of the
-// inverse transform included); columns kx = 0 and N/2 completed by E(kx, N - ky) = conj E(kx, ky); then the
-// inverse FFT over ky and the rows y < H to S[j][kx][y], as k_colgen leaves them for k_rowifft.
-template <int N>
-__global__ void __launch_bounds__(Groups<N>::THREADS) k_colfull(float2* __restrict__ S, const float2* __restrict__ eta,
-                                                                const dfp2s_full_mode* __restrict__ modes, int R,
-                                                                const float2* __restrict__ tw, int H, float scale) {
-  using P = Plan<N>;
-  using GR = Groups<N>;
-  constexpr int V = P::V, T = P::T, G = GR::G, HALF = N / 2 + 1;
-  extern __shared__ __align__(16) float2 smem[];
-  const int g = threadIdx.x / T;
-  const int t = threadIdx.x - g * T;
-  const int j = blockIdx.y;
-  const int kx = blockIdx.x * G + g;
-  const bool live = kx < HALF;
-  float2* buf = smem + g * GR::BUFE;
-  const dfp2s_full_mode md = modes[j];
-  const float kappa = md.kappa0 * scale;
-  const float2* col = eta + ((size_t)md.o * HALF + (live ? kx : 0)) * N;
-  const float2* nyq = eta + (size_t)R * HALF * N + (size_t)md.o * (N + HALF);
-  const float xs = kx == N / 2 ? -(float)(N / 2) : (float)kx;  // signed frequency of the column
-#pragma unroll
-  for (int m = 0; m < V; ++m) {
-    const int ky = t + T * m;
-    float2 e = make_float2(0.f, 0.f);
-    // (columns 0 and N/2 take their upper half from the completion below)
-    if (live && !(kx == 0 && ky == 0) && !((kx == 0 || kx == N / 2) && ky > N / 2)) {
-      const float ys = ky < N / 2 ? (float)ky : (float)(ky - N);
-      const float2 th = theta_at(md, xs, ys);
-      const float2 h = __ldg(col + ky);
-      const float re = th.x * h.x + th.y * h.y, im = th.x * h.y - th.y * h.x;  // conj(Theta) eta
-      const bool xn = kx == 0 || kx == N / 2, yn = ky == 0 || ky == N / 2;
-      if (xn && yn) {
-        e = make_float2(kappa * re, 0.f);
-      } else if (kx == N / 2 || ky == N / 2) {
-        // -k: column N/2 keeps x = -N/2 and negates y; row N/2 negates x and keeps y = -N/2
-        const float2 tm = kx == N / 2 ? theta_at(md, xs, -ys) : theta_at(md, -xs, ys);
-        const float2 h2 = __ldg(nyq + (kx == N / 2 ? ky : N + kx));
-        const float re2 = tm.x * h2.x - tm.y * h2.y, im2 = tm.x * h2.y + tm.y * h2.x;  // Theta(-k) eta'
-        e = make_float2(0.5f * kappa * (re + re2), 0.5f * kappa * (im + im2));
-      } else {
-        const float s = kappa * 0.70710678118654752440f;
-        e = make_float2(s * re, s * im);
-      }
-    }
-    buf[pad32(ky)] = e;
-  }
-  fftr::group_sync<T>();
-  if (live && (kx == 0 || kx == N / 2)) {
-    for (int ky = N / 2 + 1 + t; ky < N; ky += T) {
-      const float2 e = buf[pad32(N - ky)];
-      buf[pad32(ky)] = make_float2(e.x, -e.y);
-    }
-  }
-  fftr::group_sync<T>();
-  float2 v[V];
-#pragma unroll
-  for (int m = 0; m < V; ++m) v[m] = buf[pad32(t + T * m)];
-  fftr::group_sync<T>();  // the FFT reuses the buffer
-  fftr::fft<N, true>(v, buf, t, tw);
-  if (live) {
-    float2* out = S + ((size_t)j * HALF + kx) * N;
-#pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const int y = t + T * m;
-      if (y < H) out[y] = v[OutIndex<N>::reg(m)];
-    }
-  }
-}
-
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
@@ -508,35 +350,24 @@ int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cu
 }
 
 template <int N>
-void launch_full(const dfp2s_factor_dev* f, int H, int W, uint64_t seed, uint32_t frame, float scale, float* fields,
-                 cudaStream_t st) {
+static void launch_rowifft(const float2* S, float* out, const float2* tw, int J, int H, int W, cudaStream_t st) {
   using GR = Groups<N>;
-  constexpr int G = GR::G, HALF = N / 2 + 1;
-  const size_t sm = GR::smem;
-  if (sm > 48 * 1024) {
-    cudaFuncSetAttribute(k_colfull<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem_fft);
-    cudaFuncSetAttribute(k_rowifft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  }
-  const int pairs = HALF * (N / 2);
-  k_fullnoise<N><<<(pairs + 255) / 256, 256, 0, st>>>(f->fchol, f->R, f->eta, seed, frame);
-  k_colfull<N><<<dim3((HALF + G - 1) / G, f->J), GR::THREADS, GR::smem_fft, st>>>(f->scratch, f->eta, f->fmode, f->R,
-                                                                                  f->tw, H, scale);
-  k_rowifft<N><<<dim3((H + 2 * G - 1) / (2 * G), f->J), GR::THREADS, sm, st>>>(f->scratch, fields, f->tw, H, W);
+  constexpr int G = GR::G;
+  if (GR::smem > 48 * 1024) cudaFuncSetAttribute(k_rowifft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR::smem);
+  k_rowifft<N><<<dim3((H + 2 * G - 1) / (2 * G), J), GR::THREADS, GR::smem, st>>>(S, out, tw, H, W);
 }
 
-int dfp2s_launch_sample_fields_full(const dfp2s_factor_dev* f, int H, int W, uint64_t seed, uint32_t frame,
-                                    float scale, float* fields, cudaStream_t st) {
-  if (!f->fchol || f->R < 1 || f->R > kMaxR) return DFP2S_EINVAL;
-  switch (f->N) {
-    case 16: launch_full<16>(f, H, W, seed, frame, scale, fields, st); break;
-    case 32: launch_full<32>(f, H, W, seed, frame, scale, fields, st); break;
-    case 64: launch_full<64>(f, H, W, seed, frame, scale, fields, st); break;
-    case 128: launch_full<128>(f, H, W, seed, frame, scale, fields, st); break;
-    case 256: launch_full<256>(f, H, W, seed, frame, scale, fields, st); break;
-    case 512: launch_full<512>(f, H, W, seed, frame, scale, fields, st); break;
-    case 1024: launch_full<1024>(f, H, W, seed, frame, scale, fields, st); break;
-    case 2048: launch_full<2048>(f, H, W, seed, frame, scale, fields, st); break;
-    case 4096: launch_full<4096>(f, H, W, seed, frame, scale, fields, st); break;
+int dfp2s_launch_rowifft(const float2* S, float* out, const float2* tw, int N, int J, int H, int W, cudaStream_t st) {
+  switch (N) {
+    case 16: launch_rowifft<16>(S, out, tw, J, H, W, st); break;
+    case 32: launch_rowifft<32>(S, out, tw, J, H, W, st); break;
+    case 64: launch_rowifft<64>(S, out, tw, J, H, W, st); break;
+    case 128: launch_rowifft<128>(S, out, tw, J, H, W, st); break;
+    case 256: launch_rowifft<256>(S, out, tw, J, H, W, st); break;
+    case 512: launch_rowifft<512>(S, out, tw, J, H, W, st); break;
+    case 1024: launch_rowifft<1024>(S, out, tw, J, H, W, st); break;
+    case 2048: launch_rowifft<2048>(S, out, tw, J, H, W, st); break;
+    case 4096: launch_rowifft<4096>(S, out, tw, J, H, W, st); break;
     default: return DFP2S_EINVAL;
   }
   return dfp2s_launch_status();

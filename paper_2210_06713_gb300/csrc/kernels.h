@@ -16,6 +16,8 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
                                cudaStream_t st, const float* prev = nullptr, float alpha = 0.f, bool mix = true,
                                int variant = -1);
+// the row pass alone (S as the column passes leave it), for the full sampler
+int dfp2s_launch_rowifft(const float2* S, float* out, const float2* tw, int N, int J, int H, int W, cudaStream_t st);
 int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st);
 int dfp2s_launch_gaussian(uint64_t seed, uint64_t sub, size_t nq, float* out, cudaStream_t st);
 
@@ -30,7 +32,8 @@ struct dfp2s_factor_dev {
   float2* scratch; // J x (N/2+1) x N spectrum
   // the full cross-spectral sampler (factor kind DFP2S_FACTOR_FULL; null otherwise)
   int R;                          // distinct radial orders of Noll 2..J+1
-  float* fchol;                   // octant bins x R(R+1)/2: Cholesky factor of Gamma(|k|), [a(a+1)/2 + b][o(o+1)/2 + r]
+  float* fchol;                   // octant bins x R(R+1)/2 (padded to a multiple of 4): Cholesky factor of Gamma(|k|),
+                                  // [a(a+1)/2 + b][o(o+1)/2 + r]
   struct dfp2s_full_mode* fmode;  // J mode constants
   float2* eta;                    // R x (N/2+1) x N order fields, then R x (N + N/2 + 1) for the Nyquist lines
 };
@@ -42,7 +45,7 @@ struct dfp2s_full_mode {
 };
 // Number of distinct radial orders among Noll modes 2..J+1.
 int dfp2s_radial_order_count(int J);
-// fields.cu -- the full sampler's per-frame passes (needs a factor built with the full tables)
+// fields_full.cu -- the full sampler's per-frame passes (needs a factor built with the full tables)
 int dfp2s_launch_sample_fields_full(const dfp2s_factor_dev* f, int H, int W, uint64_t seed, uint32_t frame,
                                     float scale, float* fields, cudaStream_t st);
 int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st);
