@@ -380,6 +380,40 @@ int dfp2s_basis_blur_tc_run(const dfp2s_p2s* p, int C, int H, int W, const void*
 int dfp2s_field_covariance(const float* fields_dev, int J, int H, int W, const int* lags_host, int n_lags,
                            double* out_dev, void* stream);
 
+/* Sec. IV-B, aperture statistics of sampled fields: the structure function
+ * of the pupil phase (to compare with 6.88 (r/r0)^{5/3}, Eq. fried_struct)
+ * and the long- and short-exposure OTFs (Eqs. H_LE, H_SE).  The realisations
+ * are the Zernike vectors (all J fields, Noll 2..J+1) of the pixels on the
+ * sub-grid y = 0, step, 2 step, ..., x likewise; each gives the phase
+ * phi = sum_j a_j Z_j on the 64 x 64 pupil grid of the exact P2S (coordinates
+ * (i - 32)/16, aperture rho <= 1).
+ * out_dev (device, caller-owned), FP64:
+ *   [0, 33)     D_x(d), d = 0..32 samples (r = d/32 aperture diameters): the mean
+ *               over realisations and aperture pairs (i, k), (i, k + d) of
+ *               (phi(i, k) - phi(i, k + d))^2; [33, 66) D_y likewise along rows;
+ *   [66, 66 + 4096)         H_LE[nu_y][nu_x] (FFT order, nu/32 diameters): Re
+ *               of the inverse DFT of the mean |DFT(P e^{-j phi})|^2, divided
+ *               by its value at nu = 0;
+ *   [66 + 4096, 66 + 8192)  H_SE: the same with phi minus its least-squares
+ *               plane c0 + c1 x + c2 y over the aperture samples.
+ * 2 <= J <= DFP2S_MAX_J, step >= 1.  Errors: EINVAL, ENOMEM (scratch), ECUDA. */
+#define DFP2S_SF_LAGS 33
+#define DFP2S_OTF_N 64
+int dfp2s_aperture_statistics(const float* fields_dev, int J, int H, int W, int step, double* out_dev,
+                              void* stream);
+
+/* Sec. IV-B, spatial statistics: the tilt correlation and the differential
+ * tilt variance of the two tilt fields (the first two H x W planes of
+ * fields_dev: Noll 2, then Noll 3) at pixel lags d = 0..max_lag along x
+ * (dir 0) and along y (dir 1).  out_dev (FP64) [dir][d][8] holds the means
+ * over the pixel pairs (p, p + d) inside the frame of
+ *   a2(p) a2(p+d), a3(p) a3(p+d), (a2(p) - a2(p+d))^2, (a3(p) - a3(p+d))^2,
+ *   a2(p)^2, a2(p+d)^2, a3(p)^2, a3(p+d)^2,
+ * so that the paper's identity DTV = 2 (E[alpha^2] - E[alpha(0) alpha(d)])
+ * reads DTV = var(p) + var(p + d) - 2 corr for these window means.
+ * 0 <= max_lag < min(H, W), max_lag <= 1024.  Errors: EINVAL, ENOMEM, ECUDA. */
+int dfp2s_tilt_statistics(const float* fields_dev, int H, int W, int max_lag, double* out_dev, void* stream);
+
 /* ---------------------------------------------------------------- frames
  * A context binds a factor and a P2S handle and owns the per-frame scratch
  * (fields, warped image, weights) for frames up to max_C x max_H x max_W. */

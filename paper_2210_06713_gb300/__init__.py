@@ -59,6 +59,8 @@ SIGNATURES = {
     "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_ar1": (_i, [_vp, _d, _u64, _u32, _d, _i, _i, _vp, _vp, _vp]),
     "dfp2s_sample_zernike_fields_full": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_aperture_statistics": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "dfp2s_tilt_statistics": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_gaussian_noise": (_i, [_u64, _u32, _u32, _u32, _i, _i, _vp, _vp]),
     "dfp2s_philox_words": (_i, [_u64, _u64, _u64, _i, _vp, _vp]),
@@ -382,6 +384,24 @@ def field_covariance(fields: torch.Tensor, lags, stream=None) -> torch.Tensor:
     out = torch.empty(len(lags), J, J, device=fields.device, dtype=torch.float64)
     _check(load().dfp2s_field_covariance(_ptr(fields), J, H, W, ctypes.cast(flat, ctypes.c_void_p), len(lags),
                                          _ptr(out), _stream(stream)))
+    return out
+
+
+def aperture_statistics(fields: torch.Tensor, step: int = 1, stream=None):
+    """Structure function and LE / SE OTFs of the sub-grid pixels' Zernike vectors (include/dfp2s.h): a dict of
+    float64 device tensors D_x, D_y (33), H_LE, H_SE (64 x 64, FFT order)."""
+    J, H, W = fields.shape
+    out = torch.empty(2 * 33 + 2 * 64 * 64, device=fields.device, dtype=torch.float64)
+    _check(load().dfp2s_aperture_statistics(_ptr(fields), J, H, W, step, _ptr(out), _stream(stream)))
+    return {"D_x": out[:33], "D_y": out[33:66], "H_LE": out[66:66 + 4096].view(64, 64),
+            "H_SE": out[66 + 4096:].view(64, 64)}
+
+
+def tilt_statistics(fields: torch.Tensor, max_lag: int, stream=None) -> torch.Tensor:
+    """Tilt correlation and DTV window means (2 x (max_lag+1) x 8, float64, device) of the first two planes."""
+    _, H, W = fields.shape
+    out = torch.empty(2, max_lag + 1, 8, device=fields.device, dtype=torch.float64)
+    _check(load().dfp2s_tilt_statistics(_ptr(fields), H, W, max_lag, _ptr(out), _stream(stream)))
     return out
 
 

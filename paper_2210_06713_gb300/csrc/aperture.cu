@@ -1,0 +1,375 @@
+// Aperture and spatial statistics of sampled Zernike fields (Sec. IV-B), the checks the paper applies to its
+// simulator: the structure function of the pupil phase against 6.88 (r / r0)^{5/3} (Eq. fried_struct), the long-
+// and short-exposure OTFs (Eqs. H_LE, H_SE: the mean autocorrelation of P e^{-j phi}, the second with the plane
+// of best fit removed), and the tilt correlation with the differential tilt variance.
+//
+// Realisations are the Zernike vectors of the pixels on a sub-grid of the frame (every `step`-th row and column).
+// The pupil is the 64 x 64 grid of the exact P2S (coordinates (i - 32)/16, aperture rho <= 1: 797 samples inside
+// the 33 x 33 window at rows and columns 16..48).  One CTA (256 threads) per SM walks the realisations:
+//   phi = sum_j a_j Z_j on the window (FP32, the Zernike table evaluated in FP64 at the call), the plane
+//   c0 + c1 x + c2 y of least squares over the aperture (X^T X is diagonal on the symmetric aperture: three block
+//   sums), the squared phase differences of every aperture pair at x and y offsets 1..32 (shared-memory atomics,
+//   folded per realisation into FP64 sums), and two 64 x 64 FFTs at once (64 thread pairs per grid, the register
+//   FFT of the field sampler): P e^{-j phi} and P e^{-j (phi - plane)}.  |X|^2 accumulates in FP64 in shared
+//   memory, each grid point owned by one thread.  The OTF is the normalised inverse transform of the mean PSF (the
+//   mean autocorrelation, by linearity), taken by a finishing kernel in FP64 after a fixed-order sum over CTAs.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "fft_reg.cuh"
+#include "kernels.h"
+#include "zernike.cuh"
+
+namespace {
+
+constexpr int GN = 64;            // pupil grid
+constexpr int WS = 33;            // aperture window side (rows / columns 16..48 of the grid)
+constexpr int W0 = 16;            // first window row / column on the grid
+constexpr int WQ = WS * WS;       // 1089 window samples
+constexpr int SFL = DFP2S_SF_LAGS;  // 33 offsets 0..32
+constexpr int THREADS = 256;
+constexpr int US = GN + 1;        // padded row stride of the pupil grids (complex)
+constexpr int GBUF = fftr::Plan<GN>::BUF;  // 66 entries per FFT group
+constexpr int NPART = 2 * SFL + 2 * GN * GN;  // per-CTA partial sums
+
+// Z_j on the window for j = Noll 2..J+1 ([j][q], q = row * 33 + column, zero outside the aperture), the window
+// coordinates, and the 64 twiddles exp(-2 pi i m / 64).
+__global__ void k_aperture_tables(int J, float* __restrict__ Z, float2* __restrict__ tw) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < GN) {
+    double s, c;
+    sincospi(-2.0 * q / GN, &s, &c);
+    tw[q] = make_float2((float)c, (float)s);
+  }
+  if (q >= WQ) return;
+  const int i = q / WS, l = q - i * WS;
+  const int iy = i - 16, ix = l - 16;
+  const double x = ix / 16.0, y = iy / 16.0;
+  const bool inside = ix * ix + iy * iy <= 256;
+  const double rho = sqrt(x * x + y * y), th = atan2(y, x);
+  for (int j = 0; j < J; ++j) Z[(size_t)j * WQ + q] = inside ? (float)dfp2s_zernike(j + 2, rho, th) : 0.f;
+}
+
+struct ApSmem {
+  float2 U[2][GN * US];       // the two pupil grids (LE, SE), rows 16..48 filled
+  float2 gbuf[128][GBUF];     // FFT exchange buffers, one per thread pair
+  double psf[2][GN * GN];     // the CTA's PSF sums [set][ky * 64 + kx]
+  float phi[2][WQ + 3];       // phi and phi - plane on the window
+  float a[DFP2S_MAX_J];
+  float sf[2 * SFL];          // this realisation's structure-function sums (x offsets, then y)
+  float red[THREADS / 32][3];
+};
+
+__global__ void __launch_bounds__(THREADS, 1) k_aperture_partial(const float* __restrict__ fields, int J, int H, int W,
+                                                              int step, int nx, long long nreal,
+                                                              const float* __restrict__ Z,
+                                                              const float2* __restrict__ tw,
+                                                              double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ApSmem& s = *reinterpret_cast<ApSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t plane = (size_t)H * W;
+  for (int e = tid; e < 2 * GN * GN; e += THREADS) (&s.psf[0][0])[e] = 0.0;
+  for (int e = tid; e < 2 * SFL; e += THREADS) s.sf[e] = 0.f;
+  double sf_acc = 0.0;  // thread t < 66 owns structure-function entry t
+  // the aperture's constants: sample count and sum x^2 (= sum y^2) over rho <= 1 of the window
+  int na = 0;
+  double sxx = 0.0;
+  for (int iy = -16; iy <= 16; ++iy)
+    for (int ix = -16; ix <= 16; ++ix)
+      if (ix * ix + iy * iy <= 256) {
+        ++na;
+        sxx += (ix / 16.0) * (ix / 16.0);
+      }
+  const float inv_na = (float)(1.0 / na), inv_sxx = (float)(1.0 / sxx);
+  __syncthreads();
+  for (long long r = blockIdx.x; r < nreal; r += gridDim.x) {
+    const int ry = (int)(r / nx), rx = (int)(r - (long long)ry * nx);
+    const size_t pix = (size_t)(ry * step) * W + (size_t)(rx * step);
+    if (tid < J) s.a[tid] = fields[(size_t)tid * plane + pix];
+    __syncthreads();
+    // ---- phase on the window and the plane-fit sums
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f;
+    for (int q = tid; q < WQ; q += THREADS) {
+      float v = 0.f;
+      for (int j = 0; j < J; ++j) v = fmaf(s.a[j], __ldg(Z + (size_t)j * WQ + q), v);
+      const int i = q / WS, l = q - i * WS;
+      const bool inside = (i - 16) * (i - 16) + (l - 16) * (l - 16) <= 256;
+      v = inside ? v : 0.f;
+      s.phi[0][q] = v;
+      p0 += v;
+      p1 = fmaf(v, (l - 16) * 0.0625f, p1);
+      p2 = fmaf(v, (i - 16) * 0.0625f, p2);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      p0 += __shfl_xor_sync(0xffffffffu, p0, off);
+      p1 += __shfl_xor_sync(0xffffffffu, p1, off);
+      p2 += __shfl_xor_sync(0xffffffffu, p2, off);
+    }
+    if (lane == 0) {
+      s.red[warp][0] = p0;
+      s.red[warp][1] = p1;
+      s.red[warp][2] = p2;
+    }
+    __syncthreads();
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    for (int w = 0; w < THREADS / 32; ++w) {
+      c0 += s.red[w][0];
+      c1 += s.red[w][1];
+      c2 += s.red[w][2];
+    }
+    c0 *= inv_na;
+    c1 *= inv_sxx;
+    c2 *= inv_sxx;
+    for (int q = tid; q < WQ; q += THREADS) {
+      const int i = q / WS, l = q - i * WS;
+      const bool inside = (i - 16) * (i - 16) + (l - 16) * (l - 16) <= 256;
+      s.phi[1][q] = inside ? s.phi[0][q] - (c0 + c1 * ((l - 16) * 0.0625f) + c2 * ((i - 16) * 0.0625f)) : 0.f;
+    }
+    // ---- structure function: task (direction, offset d, window line) sums the pairs along the line
+    for (int task = tid; task < 2 * (SFL - 1) * WS; task += THREADS) {
+      const int dir = task / ((SFL - 1) * WS);
+      const int rem = task - dir * (SFL - 1) * WS;
+      const int d = 1 + rem / WS, line = rem - (d - 1) * WS;
+      float acc = 0.f;
+      for (int u = 0; u + d < WS; ++u) {
+        const int ia = dir == 0 ? line : u, la = dir == 0 ? u : line;
+        const int ib = dir == 0 ? line : u + d, lb = dir == 0 ? u + d : line;
+        const bool in = (ia - 16) * (ia - 16) + (la - 16) * (la - 16) <= 256 &&
+                        (ib - 16) * (ib - 16) + (lb - 16) * (lb - 16) <= 256;
+        const float df = s.phi[0][ia * WS + la] - s.phi[0][ib * WS + lb];
+        acc = in ? fmaf(df, df, acc) : acc;
+      }
+      atomicAdd(&s.sf[dir * SFL + d], acc);
+    }
+    __syncthreads();  // phi[1] and the sums complete
+    if (tid < 2 * SFL) {
+      sf_acc += (double)s.sf[tid];
+      s.sf[tid] = 0.f;
+    }
+    // ---- the two pupil grids, rows 16..48: P e^{-j phi}
+    for (int e = tid; e < 2 * WS * GN; e += THREADS) {
+      const int set = e / (WS * GN), rem = e - set * WS * GN;
+      const int i = rem / GN, k = rem - i * GN;  // window row i, grid column k
+      float2 u = make_float2(0.f, 0.f);
+      const int l = k - W0;
+      if (l >= 0 && l < WS && (i - 16) * (i - 16) + (l - 16) * (l - 16) <= 256) {
+        float sn, cs;
+        sincosf(s.phi[set][i * WS + l], &sn, &cs);
+        u = make_float2(cs, -sn);
+      }
+      s.U[set][(W0 + i) * US + k] = u;
+    }
+    __syncthreads();
+    // ---- row transforms (rows 16..48 of each grid; every pair runs the transform, the others on zeros)
+    {
+      const int g = tid >> 1, t = tid & 1, set = g >> 6, rr = g & 63;
+      const bool live = rr < WS;
+      float2* row = s.U[set] + (W0 + (live ? rr : 0)) * US;
+      float2 v[fftr::Plan<GN>::V];
+#pragma unroll
+      for (int m = 0; m < fftr::Plan<GN>::V; ++m) v[m] = live ? row[t + 2 * m] : make_float2(0.f, 0.f);
+      fftr::fft<GN, false>(v, s.gbuf[g], t, tw);
+      __syncthreads();  // every row read before any is written
+      if (live) {
+#pragma unroll
+        for (int m = 0; m < fftr::Plan<GN>::V; ++m) row[t + 2 * m] = v[fftr::OutIndex<GN>::reg(m)];
+      }
+    }
+    __syncthreads();
+    // ---- column transforms (rows outside 16..48 are zero) and |X|^2 into the CTA's PSF sums
+    {
+      const int g = tid >> 1, t = tid & 1, set = g >> 6, col = g & 63;
+      float2 v[fftr::Plan<GN>::V];
+#pragma unroll
+      for (int m = 0; m < fftr::Plan<GN>::V; ++m) {
+        const int row = t + 2 * m;
+        v[m] = (row >= W0 && row < W0 + WS) ? s.U[set][row * US + col] : make_float2(0.f, 0.f);
+      }
+      fftr::fft<GN, false>(v, s.gbuf[g], t, tw);
+#pragma unroll
+      for (int m = 0; m < fftr::Plan<GN>::V; ++m) {
+        const float2 x = v[fftr::OutIndex<GN>::reg(m)];
+        s.psf[set][(t + 2 * m) * GN + col] += (double)x.x * x.x + (double)x.y * x.y;
+      }
+    }
+    __syncthreads();  // the grids and buffers are rewritten by the next realisation
+  }
+  double* out = part + (size_t)blockIdx.x * NPART;
+  if (tid < 2 * SFL) out[tid] = sf_acc;
+  for (int e = tid; e < 2 * GN * GN; e += THREADS) out[2 * SFL + e] = (&s.psf[0][0])[e];
+}
+
+// Fixed-order sum over the CTAs; the structure function divided by its pair counts and realisations.
+__global__ void k_aperture_sum(const double* __restrict__ part, int nb, long long nreal, double* __restrict__ sums,
+                               double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NPART) return;
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) acc += part[(size_t)b * NPART + e];
+  if (e < 2 * SFL) {
+    const int dir = e / SFL, d = e - dir * SFL;
+    (void)dir;  // the aperture is symmetric: the pair counts along x and y are equal
+    long long pairs = 0;
+    for (int i = 0; i < WS; ++i)
+      for (int u = 0; u + d < WS; ++u) {
+        const bool a = (i - 16) * (i - 16) + (u - 16) * (u - 16) <= 256;
+        const bool b = (i - 16) * (i - 16) + (u + d - 16) * (u + d - 16) <= 256;
+        pairs += (d > 0 && a && b) ? 1 : 0;
+      }
+    out[e] = pairs ? acc / ((double)pairs * (double)nreal) : 0.0;
+  } else {
+    sums[e - 2 * SFL] = acc;
+  }
+}
+
+// OTF of grid `set`: H(nu) = Re sum_k psf(k) e^{+2 pi i k.nu / 64} / sum_k psf(k), separable, FP64; one CTA.
+constexpr size_t kOtfSmem = (size_t)GN * GN * sizeof(double2) + 2 * GN * sizeof(double);
+
+__global__ void __launch_bounds__(256) k_aperture_otf(const double* __restrict__ sums, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char otf_raw[];
+  double2* T1 = reinterpret_cast<double2*>(otf_raw);  // [ky][nu_x]
+  double* cs = reinterpret_cast<double*>(otf_raw + (size_t)GN * GN * sizeof(double2));
+  double* sn = cs + GN;
+  const int set = blockIdx.x;
+  const double* p = sums + (size_t)set * GN * GN;
+  for (int m = threadIdx.x; m < GN; m += blockDim.x) sincospi(2.0 * m / GN, &sn[m], &cs[m]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < GN * GN; e += blockDim.x) {
+    const int ky = e / GN, vx = e - ky * GN;
+    double re = 0.0, im = 0.0;
+    for (int kx = 0; kx < GN; ++kx) {
+      const double v = p[ky * GN + kx];
+      const int m = (kx * vx) & (GN - 1);
+      re = fma(v, cs[m], re);
+      im = fma(v, sn[m], im);
+    }
+    T1[e] = make_double2(re, im);
+  }
+  __syncthreads();
+  double total = 0.0;
+  for (int ky = 0; ky < GN; ++ky) total += T1[ky * GN].x;  // nu = 0: the sum of the PSF
+  for (int e = threadIdx.x; e < GN * GN; e += blockDim.x) {
+    const int vy = e / GN, vx = e - vy * GN;
+    double re = 0.0;
+    for (int ky = 0; ky < GN; ++ky) {
+      const double2 t = T1[ky * GN + vx];
+      const int m = (ky * vy) & (GN - 1);
+      re += t.x * cs[m] - t.y * sn[m];
+    }
+    out[(size_t)set * GN * GN + e] = re / total;
+  }
+}
+
+// ---- tilt correlation and DTV: per (direction, lag) CTA row, grid-stride over the pixel pairs, eight sums
+constexpr int TB = 16;  // CTAs per lag
+
+__global__ void __launch_bounds__(256) k_tilt_partial(const float* __restrict__ a, int H, int W, int max_lag,
+                                                   double* __restrict__ part) {
+  const int row = blockIdx.y;  // dir * (max_lag + 1) + d
+  const int dir = row / (max_lag + 1), d = row - dir * (max_lag + 1);
+  const int h = dir == 0 ? H : H - d, w = dir == 0 ? W - d : W;
+  const long long n = (long long)h * w;
+  const size_t plane = (size_t)H * W;
+  const size_t off = dir == 0 ? (size_t)d : (size_t)d * W;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  double dacc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int cnt = 0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(p / w), x = (int)(p - (long long)y * w);
+    const size_t o = (size_t)y * W + x;
+    const float ux = a[o], vx = a[o + off], uy = a[plane + o], vy = a[plane + o + off];
+    const float dx = ux - vx, dy = uy - vy;
+    acc[0] = fmaf(ux, vx, acc[0]);
+    acc[1] = fmaf(uy, vy, acc[1]);
+    acc[2] = fmaf(dx, dx, acc[2]);
+    acc[3] = fmaf(dy, dy, acc[3]);
+    acc[4] = fmaf(ux, ux, acc[4]);
+    acc[5] = fmaf(vx, vx, acc[5]);
+    acc[6] = fmaf(uy, uy, acc[6]);
+    acc[7] = fmaf(vy, vy, acc[7]);
+    if (++cnt == 64) {  // FP32 over at most 64 pairs, then FP64
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        dacc[k] += acc[k];
+        acc[k] = 0.f;
+      }
+      cnt = 0;
+    }
+  }
+  __shared__ double red[8][8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    double v = dacc[k] + acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double v = 0.0;
+    for (int wi = 0; wi < 8; ++wi) v += red[wi][threadIdx.x];
+    part[((size_t)row * TB + blockIdx.x) * 8 + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_tilt_sum(const double* __restrict__ part, int H, int W, int max_lag, double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rows = 2 * (max_lag + 1);
+  if (e >= rows * 8) return;
+  const int row = e / 8, k = e - row * 8;
+  const int dir = row / (max_lag + 1), d = row - dir * (max_lag + 1);
+  const double n = dir == 0 ? (double)H * (W - d) : (double)(H - d) * W;
+  double acc = 0.0;
+  for (int b = 0; b < TB; ++b) acc += part[((size_t)row * TB + b) * 8 + k];
+  out[e] = acc / n;
+}
+
+}  // namespace
+
+int dfp2s_launch_aperture_statistics(const float* fields, int J, int H, int W, int step, double* out, cudaStream_t st) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nx = (W + step - 1) / step, ny = (H + step - 1) / step;
+  const long long nreal = (long long)nx * ny;
+  const int nb = (int)(nreal < sms ? nreal : sms);
+  float* Z = nullptr;
+  float2* tw = nullptr;
+  double *part = nullptr, *sums = nullptr;
+  auto release = [&]() {
+    if (Z) cudaFreeAsync(Z, st);
+    if (tw) cudaFreeAsync(tw, st);
+    if (part) cudaFreeAsync(part, st);
+    if (sums) cudaFreeAsync(sums, st);
+  };
+  if (dfp2s_device_malloc_async((void**)&Z, (size_t)J * WQ * sizeof(float), st) != cudaSuccess ||
+      dfp2s_device_malloc_async((void**)&tw, GN * sizeof(float2), st) != cudaSuccess ||
+      dfp2s_device_malloc_async((void**)&part, (size_t)nb * NPART * sizeof(double), st) != cudaSuccess ||
+      dfp2s_device_malloc_async((void**)&sums, (size_t)2 * GN * GN * sizeof(double), st) != cudaSuccess) {
+    release();
+    return DFP2S_ENOMEM;
+  }
+  const size_t smem = sizeof(ApSmem);
+  cudaFuncSetAttribute(k_aperture_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_aperture_tables<<<(WQ + 255) / 256, 256, 0, st>>>(J, Z, tw);
+  k_aperture_partial<<<nb, THREADS, smem, st>>>(fields, J, H, W, step, nx, nreal, Z, tw, part);
+  k_aperture_sum<<<(NPART + 255) / 256, 256, 0, st>>>(part, nb, nreal, sums, out);
+  cudaFuncSetAttribute(k_aperture_otf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOtfSmem);
+  k_aperture_otf<<<2, 256, kOtfSmem, st>>>(sums, out + 2 * SFL);
+  const bool ok = dfp2s_launch_status() == DFP2S_OK;
+  release();
+  return ok ? DFP2S_OK : DFP2S_ECUDA;
+}
+
+int dfp2s_launch_tilt_statistics(const float* fields, int H, int W, int max_lag, double* out, cudaStream_t st) {
+  const int rows = 2 * (max_lag + 1);
+  double* part = nullptr;
+  if (dfp2s_device_malloc_async((void**)&part, (size_t)rows * TB * 8 * sizeof(double), st) != cudaSuccess)
+    return DFP2S_ENOMEM;
+  k_tilt_partial<<<dim3(TB, rows), 256, 0, st>>>(fields, H, W, max_lag, part);
+  k_tilt_sum<<<(rows * 8 + 255) / 256, 256, 0, st>>>(part, H, W, max_lag, out);
+  const bool ok = dfp2s_launch_status() == DFP2S_OK;
+  cudaFreeAsync(part, st);
+  return ok ? DFP2S_OK : DFP2S_ECUDA;
+}

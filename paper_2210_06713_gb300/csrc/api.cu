@@ -405,6 +405,28 @@ extern "C" int dfp2s_field_covariance(const float* fields, int J, int H, int W, 
   return DFP2S_OK;
 }
 
+extern "C" int dfp2s_aperture_statistics(const float* fields, int J, int H, int W, int step, double* out,
+                                         void* stream) {
+  CHECK_ARG(fields && out, "null argument");
+  CHECK_ARG(J >= 2 && J <= DFP2S_MAX_J && H >= 1 && W >= 1 && (long long)H * W <= (1LL << 31),
+            "field shape %d x %d x %d out of range", J, H, W);
+  CHECK_ARG(step >= 1 && step <= (H > W ? H : W) + 1, "step %d out of range", step);
+  const int rc = dfp2s_launch_aperture_statistics(fields, J, H, W, step, out, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "aperture statistics scratch allocation");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "aperture statistics");
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_tilt_statistics(const float* fields, int H, int W, int max_lag, double* out, void* stream) {
+  CHECK_ARG(fields && out, "null argument");
+  CHECK_ARG(H >= 1 && W >= 1 && (long long)H * W <= (1LL << 31), "field shape %d x %d out of range", H, W);
+  CHECK_ARG(max_lag >= 0 && max_lag < H && max_lag < W && max_lag <= 1024, "max_lag %d out of range", max_lag);
+  const int rc = dfp2s_launch_tilt_statistics(fields, H, W, max_lag, out, as_stream(stream));
+  if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "tilt statistics scratch allocation");
+  if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "tilt statistics");
+  return DFP2S_OK;
+}
+
 // ---- network files
 static const char kMlpMagic[8] = {'D', 'F', 'P', '2', 'S', 'M', 'L', 'P'};
 

@@ -126,6 +126,10 @@ int dfp2s_launch_mlp_tc(const dfp2s_p2s_dev* p, const float* fields, int npix, v
 int dfp2s_launch_field_covariance(const float* a, int J, int H, int W, const int* lags_host, int n_lags, double* out,
                                   cudaStream_t st);
 
+// aperture.cu -- Sec. IV-B statistics (out as include/dfp2s.h documents for the two entry points)
+int dfp2s_launch_aperture_statistics(const float* fields, int J, int H, int W, int step, double* out, cudaStream_t st);
+int dfp2s_launch_tilt_statistics(const float* fields, int H, int W, int max_lag, double* out, cudaStream_t st);
+
 // basis.cu -- FP64 SVD basis of exact PSFs
 int dfp2s_basis_build_device(int J, const float* L32, int K, int n_psf, const double* dr_host, int n_dr, uint64_t seed,
                              float* basis_out, double* sigma_host, int* sweeps_out, cudaStream_t st);

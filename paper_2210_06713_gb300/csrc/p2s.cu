@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "zernike.cuh"
 
 namespace {
 
@@ -26,14 +27,6 @@ constexpr int KS = 33;
 constexpr int KS2 = KS * KS;
 constexpr int PB = 8;       // pixels per batch of the exact kernel
 constexpr int NT = 256;     // threads of the exact kernel
-
-DFP2S_DEV void noll_nm_dev(int j, int* n, int* m) {
-  int nn = 0;
-  while ((nn + 1) * (nn + 2) / 2 < j) ++nn;
-  const int r = j - nn * (nn + 1) / 2 - 1;
-  *n = nn;
-  *m = (nn % 2 == 0) ? 2 * ((r + 1) / 2) : 2 * (r / 2) + 1;
-}
 
 __global__ void k_p2s_tables(int J, int K, const float* __restrict__ basis, float* __restrict__ zt,
                              float* __restrict__ mask, float2* __restrict__ dft, float* __restrict__ phiT) {
@@ -46,19 +39,7 @@ __global__ void k_p2s_tables(int J, int K, const float* __restrict__ basis, floa
   const bool inside = ix * ix + iy * iy <= 256;
   mask[q] = inside ? 1.f : 0.f;
   for (int jj = 0; jj < J - 2; ++jj) {
-    const int j = jj + 4;
-    int n, m;
-    noll_nm_dev(j, &n, &m);
-    double R = 0.0;
-    for (int s = 0; s <= (n - m) / 2; ++s) {
-      double c = tgamma((double)(n - s + 1)) /
-                 (tgamma((double)(s + 1)) * tgamma((double)((n + m) / 2 - s + 1)) * tgamma((double)((n - m) / 2 - s + 1)));
-      if (s & 1) c = -c;
-      R += c * pow(rho, (double)(n - 2 * s));
-    }
-    double z;
-    if (m == 0) z = sqrt((double)(n + 1)) * R;
-    else z = sqrt(2.0 * (n + 1)) * R * ((j & 1) ? sin(m * th) : cos(m * th));
+    const double z = dfp2s_zernike(jj + 4, rho, th);
     zt[(size_t)jj * KS2 + q] = inside ? (float)z : 0.f;
   }
   // DFT matrix entry (k = i, index = l): exp(-2 pi i (k-16)(i-16)/64)
