@@ -9,7 +9,7 @@ shares no code, constants or tables with the CUDA sources.
 Every function cites the part of the paper (Chimitt, Zhang, Mao, Chan,
 "Real-Time Dense Field Phase-to-Space Simulation of Imaging through Atmospheric
 Turbulence", arXiv 2210.06713) that it follows. Where the paper is silent the
-reading taken is named in the docstring (R1..R30, the readings listed in the
+reading taken is named in the docstring (R1..R31, the readings listed in the
 design notes).
 
 Modules
@@ -28,4 +28,5 @@ Modules
   stats     lagged covariances of fields and their expectation A~(s) (Sec. III-D)
   aperture  structure function, LE / SE OTFs, tilt correlation and DTV of
             sampled fields (Sec. IV-B; R30)
+  subharmonics  low-frequency compensation of the FFT sampler (Sec. IV-B; R31)
 """
