@@ -61,16 +61,36 @@ def _v_rule():
     return np.concatenate(nodes), np.concatenate(weights)
 
 
+@functools.lru_cache(maxsize=None)
+def _v_rule_deep():
+    """The v-rule for frequencies far below the torus bins (the subharmonics, R31): 8-point panels of width 0.2
+    in ln v from 1e-14 to 1 (the integrand's mass lies at v >~ f), then the uniform panels of _v_rule."""
+    xs8, ws8 = np.polynomial.legendre.leggauss(8)
+    nodes, weights = [], []
+    y0 = math.log(1e-14)
+    npan = int(math.ceil(-y0 / 0.2))
+    for p in range(npan):
+        a, b = y0 * (1 - p / npan), y0 * (1 - (p + 1) / npan)
+        y = 0.5 * (b - a) * xs8 + 0.5 * (a + b)
+        v = np.exp(y)
+        nodes.append(v)
+        weights.append(0.5 * (b - a) * ws8 * v)
+    v1, w1 = _v_rule()
+    up = v1 >= 1.0
+    return np.concatenate(nodes + [v1[up]]), np.concatenate(weights + [w1[up]])
+
+
 def g_radial(n: int, n2: int, v: np.ndarray) -> np.ndarray:
     """g_nn'(v) = v^{-11/3} J_{n+1}(2 pi v) J_{n'+1}(2 pi v) / (pi v)^2."""
     v = np.asarray(v, dtype=np.float64)
     return v ** (-11.0 / 3.0) * jv(n + 1, 2 * math.pi * v) * jv(n2 + 1, 2 * math.pi * v) / (math.pi * v) ** 2
 
 
-def radial_spectra(pairs, f: np.ndarray) -> np.ndarray:
-    """G_nn'(f) for f > 0 and every (n, n') in pairs (reading R1, v-form); shape (len(pairs), len(f))."""
+def radial_spectra(pairs, f: np.ndarray, deep: bool = False) -> np.ndarray:
+    """G_nn'(f) for f > 0 and every (n, n') in pairs (reading R1, v-form); shape (len(pairs), len(f)).
+    deep: the rule that reaches v = 1e-14, for f far below the torus bins."""
     f = np.atleast_1d(np.asarray(f, dtype=np.float64))
-    v, w = _v_rule()
+    v, w = _v_rule_deep() if deep else _v_rule()
     Gw = np.stack([w * g_radial(n, n2, v) for n, n2 in pairs], axis=1)  # (Q, P)
     out = np.empty((len(pairs), f.size))
     chunk = 1024

@@ -19,7 +19,8 @@ In units of the torus bins (weight df^2) a level-p frequency carries
 P_j(f) / 9^p.  The unit-variance normalisation covers both parts:
   Z_j = sum_{k != 0} P_j(f_k) + sum_{p, d} P_j(f_{p,d}) / 9^p,
   lambda_j(k) = N^2 P_j(f_k) / Z_j,   s_{j,p,d}^2 = P_j(f_{p,d}) / 9^p / Z_j,
-and the unit field is the FFT part plus
+(G at the subharmonic frequencies, down to df / 3^12, from the v-rule that reaches
+v = 1e-14), and the unit field is the FFT part plus
   sum_{p, d} Re[(g_re + i g_im) s_{j,p,d} e^{2 pi i (n_d x + m_d y) / (N 3^p)}]
 at pixel (y, x), (g_re, g_im) unit Gaussians: each term adds s^2 to the
 variance, so the field keeps variance 1 exactly.  The eight directions d are
@@ -56,7 +57,7 @@ def mode_subharmonic_power(j: int, N: int, pix_per_D: float, levels: int) -> np.
     """P_j(f_{p,d}) / 9^p, shape (levels, 8), in the units of mode_spectrum_shape's bins."""
     n, _ = zernike.noll_nm(j)
     fmag, phi = subharmonic_frequencies(N, pix_per_D, levels)
-    G = spectrum.radial_spectra([(n, n)], fmag.ravel())[0].reshape(fmag.shape)
+    G = spectrum.radial_spectra([(n, n)], fmag.ravel(), deep=True)[0].reshape(fmag.shape)
     w = 9.0 ** -np.arange(1, levels + 1)
     return (n + 1) * spectrum.angular_factor(j, phi) * G * w[:, None]
 

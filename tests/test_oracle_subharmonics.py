@@ -87,3 +87,22 @@ def test_philox_layout_of_the_subharmonic_gaussians():
     a, b = noise.box_muller(w0, w1)
     c, d = noise.box_muller(w2, w3)
     assert g[1, 1, 2] == complex(float(a[0]), float(b[0])) and g[1, 1, 3] == complex(float(c[0]), float(d[0]))
+
+
+def test_deep_rule_reaches_the_small_frequency_limits():
+    # the subharmonics need G_n far below the torus bins.  For n >= 2, g_n is integrable at 0 and
+    # f G_n(f) -> (1/2) int g_n dv as f -> 0; for n = 1 the deep rule agrees with the t-form of R1 where that
+    # adaptive quadrature converges; at the torus bins it agrees with the standard rule
+    from scipy.integrate import quad
+    for n in (2, 3):
+        edges = [0, 1e-6, 1e-3, 0.1, 1, 2, 4, 8, 16, 32, 64, 128, 400]
+        half = 0.5 * sum(quad(lambda v: spectrum.g_radial(n, n, v), a, b, limit=500, epsrel=1e-12)[0]
+                         for a, b in zip(edges[:-1], edges[1:]))
+        f = 1e-9
+        assert f * spectrum.radial_spectra([(n, n)], [f], deep=True)[0, 0] == pytest.approx(half, rel=1e-6)
+    for f in (1e-3, 1e-5, 1e-7, 3.7e-9):  # (the t-form's adaptive quadrature does not converge at every f)
+        assert spectrum.radial_spectra([(1, 1)], [f], deep=True)[0, 0] == pytest.approx(
+            spectrum.radial_spectrum_tform(1, 1, f), rel=1e-9)
+    fs = np.array([2e-3, 0.05, 1.0, 4.0])
+    pairs = [(1, 1), (2, 2), (5, 5)]
+    assert np.allclose(spectrum.radial_spectra(pairs, fs, deep=True), spectrum.radial_spectra(pairs, fs), rtol=1e-9)
