@@ -446,6 +446,20 @@ def run_ours(args, rank, world, device):
         stat = {"what": "dfp2s_field_covariance, J x J at 4 lags of one frame's fields", "ms": sms,
                 "achieved_tflops": 2 * fmas / (sms * 1e-3) / 1e12, "alu_peak_tflops": alu,
                 "frac": 2 * fmas / (sms * 1e-3) / 1e12 / alu}
+        # Sec. IV-B validation: structure function + LE/SE OTFs of every fourth pixel's vector (two 64 x 64 FFTs
+        # each), and the tilt correlation / DTV at lags 0..64 along both axes
+        for name, fn in (("aperture_statistics", lambda: d.aperture_statistics(fl, 4)),
+                         ("tilt_statistics", lambda: d.tilt_statistics(fl, 64))):
+            fn()
+            torch.cuda.synchronize()
+            s0.record(stream)
+            for _ in range(3):
+                fn()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            stat[name + "_ms"] = s0.elapsed_time(s1) / 3
+        nreal = ((H + 3) // 4) * ((W + 3) // 4)
+        stat["aperture_statistics_realisations_per_s"] = nreal / (stat["aperture_statistics_ms"] * 1e-3)
         del fl
     except RuntimeError as exc:
         stat = {"unavailable": str(exc).splitlines()[0][:120]}

@@ -99,6 +99,17 @@ typedef struct {
   double pix_per_D; /* image pixels per aperture diameter of displacement s */
   int kind;         /* DFP2S_FACTOR_FACTORED or DFP2S_FACTOR_FULL (DFP2S_FACTOR_DENSE returns
                        DFP2S_EUNSUPPORTED) */
+  int subharmonic_levels; /* 0 (the paper's sampler) .. 12: subharmonic levels of the factored sampler
+                       (Sec. IV-B: the low-frequency deficit of the FFT method).  The DC cell of the
+                       torus is split into 3 x 3 sub-cells of side df/3 (df = pix_per_D / N), the eight
+                       outer ones represented by their centres f = (n, m) df/3 with weight 1/9 of a
+                       bin, the centre split again, for `levels` levels; the per-mode normalisation to
+                       unit variance covers bins and subharmonics together.  Each level adds to every
+                       unit field sum_d Re[(g_re + i g_im) s_{j,p,d} e^{2 pi i (n x + m y) / (N 3^p)}]
+                       (pixel (y, x); Gaussians from Philox tag 6, subsequence mode j, counter
+                       4 (p - 1) + k for directions 2k, 2k + 1 of (n, m) = (-1,-1), (0,-1), (1,-1),
+                       (-1,0), (1,0), (-1,1), (0,1), (1,1)).  Not with DFP2S_FACTOR_FULL
+                       (DFP2S_EUNSUPPORTED). */
 } dfp2s_factor_params;
 
 /* Builds the factor (allocates device memory, synchronises `stream` before

@@ -31,7 +31,7 @@ _vp, _i, _u32, _u64, _d, _sz = _c.c_void_p, _c.c_int, _c.c_uint32, _c.c_uint64, 
 
 
 class FactorParams(ctypes.Structure):
-    _fields_ = [("J", _i), ("N", _i), ("pix_per_D", _d), ("kind", _i)]
+    _fields_ = [("J", _i), ("N", _i), ("pix_per_D", _d), ("kind", _i), ("subharmonic_levels", _i)]
 
 
 class TrainParams(ctypes.Structure):
@@ -161,11 +161,12 @@ def grid_size(H: int, W: int, pix_per_D: float = 8.0) -> int:
 class SpectralFactor:
     """Spectral factor of the homogeneous tensor approximation for (J, N, pix_per_D)."""
 
-    def __init__(self, J: int, N: int, pix_per_D: float = 8.0, kind: int = FACTOR_FACTORED, stream=None):
+    def __init__(self, J: int, N: int, pix_per_D: float = 8.0, kind: int = FACTOR_FACTORED, stream=None,
+                 subharmonics: int = 0):
         lib = load()
-        self.J, self.N, self.pix_per_D, self.kind = J, N, pix_per_D, kind
+        self.J, self.N, self.pix_per_D, self.kind, self.subharmonics = J, N, pix_per_D, kind, subharmonics
         h = ctypes.c_void_p()
-        p = FactorParams(J, N, pix_per_D, kind)
+        p = FactorParams(J, N, pix_per_D, kind, subharmonics)
         _check(lib.dfp2s_build_spectral_factor(ctypes.byref(p), ctypes.byref(h), _stream(stream)))
         self._h = h
 

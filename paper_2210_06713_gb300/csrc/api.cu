@@ -129,6 +129,8 @@ static void factor_free(dfp2s_factor* f) {
   cudaFree(f->d.fchol);
   cudaFree(f->d.fmode);
   cudaFree(f->d.eta);
+  cudaFree(f->d.sh_amp);
+  cudaFree(f->d.sh_coef);
   delete f;
 }
 
@@ -141,12 +143,17 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
   CHECK_ARG(p->kind == DFP2S_FACTOR_FACTORED || p->kind == DFP2S_FACTOR_DENSE || p->kind == DFP2S_FACTOR_FULL,
             "unknown factor kind");
   if (p->kind == DFP2S_FACTOR_DENSE) return dfp2s_fail(DFP2S_EUNSUPPORTED, "dense factor not built in this version");
+  CHECK_ARG(p->subharmonic_levels >= 0 && p->subharmonic_levels <= 12, "subharmonic levels %d out of [0, 12]",
+            p->subharmonic_levels);
+  if (p->kind == DFP2S_FACTOR_FULL && p->subharmonic_levels > 0)
+    return dfp2s_fail(DFP2S_EUNSUPPORTED, "subharmonics are built for the factored sampler only");
   dfp2s_factor* f = new dfp2s_factor();
   memset(&f->d, 0, sizeof(f->d));
   f->d.J = p->J;
   f->d.N = p->N;
   f->d.pix_per_D = p->pix_per_D;
   f->kind = p->kind;
+  f->d.sh_levels = p->subharmonic_levels;
   cudaGetDevice(&f->device);
   const size_t half = (size_t)(p->N / 2 + 1) * p->N;
   cudaError_t e;
@@ -157,6 +164,14 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
       (e = dfp2s_device_malloc((void**)&f->d.scratch, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
     factor_free(f);
     return dfp2s_fail_cuda(e, "factor allocation");
+  }
+  if (p->subharmonic_levels > 0) {
+    const size_t n = (size_t)p->J * p->subharmonic_levels * 8;
+    if ((e = dfp2s_device_malloc((void**)&f->d.sh_amp, n * sizeof(float))) != cudaSuccess ||
+        (e = dfp2s_device_malloc((void**)&f->d.sh_coef, n * sizeof(float2))) != cudaSuccess) {
+      factor_free(f);
+      return dfp2s_fail_cuda(e, "subharmonic table allocation");
+    }
   }
   if (p->kind == DFP2S_FACTOR_FULL) {
     const int R = dfp2s_radial_order_count(p->J);
@@ -213,7 +228,8 @@ extern "C" int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_
   CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
   const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
   CHECK_LAUNCH(dfp2s_launch_sample_fields(f->d.scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame,
-                                          f->d.L32, scale, fields, as_stream(stream)));
+                                          f->d.L32, scale, fields, as_stream(stream), nullptr, 0.f, true, -1,
+                                          &f->d));
   return DFP2S_OK;
 }
 
@@ -238,7 +254,8 @@ extern "C" int dfp2s_sample_zernike_fields_ar1(const dfp2s_factor* f, double D_o
   CHECK_ARG(prev != fields, "prev must not alias fields");
   const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
   CHECK_LAUNCH(dfp2s_launch_sample_fields(f->d.scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame,
-                                          f->d.L32, scale, fields, as_stream(stream), prev, (float)alpha));
+                                          f->d.L32, scale, fields, as_stream(stream), prev, (float)alpha, true, -1,
+                                          &f->d));
   return DFP2S_OK;
 }
 
@@ -782,7 +799,7 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
     const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
     CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
                                             seed, frame, c->f->d.L32, scale, c->fields, st, nullptr, 0.f, false,
-                                            c->field_variant));
+                                            c->field_variant, &c->f->d));
     if (c->w1_mixed_version != pd->mlp_version) {
       CHECK_LAUNCH(dfp2s_mlp_tc_pack_w1_mixed(pd, c->f->d.L32, c->w1_mixed, st));
       c->w1_mixed_version = pd->mlp_version;
@@ -803,7 +820,7 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
     const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
     CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
                                             seed, frame, c->f->d.L32, scale, c->fields, as_stream(stream), nullptr,
-                                            0.f, true, c->field_variant));
+                                            0.f, true, c->field_variant, &c->f->d));
     mark(1);
     rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
     if (rc) return rc;

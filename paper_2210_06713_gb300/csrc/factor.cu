@@ -134,6 +134,29 @@ __global__ void k_radial(const double* __restrict__ v, const double* __restrict_
     if (o < no) G[(size_t)o * noct + i] = acc[o];
 }
 
+// G_n(f) at nf listed frequencies (the subharmonics), the same quadrature as k_radial; G[o * nf + i].
+__global__ void k_radial_list(const double* __restrict__ v, const double* __restrict__ gtab, int Q, int no,
+                              const double* __restrict__ flist, int nf, double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const double f = flist[i];
+  double acc[kMaxOrders];
+#pragma unroll
+  for (int o = 0; o < kMaxOrders; ++o) acc[o] = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const double x = v[q];
+    const double d = 2.0 * x + f;
+    const double K = exp((5.0 / 3.0) * log(2.0 * x / d)) * 2.0 * x * x / (f * d * d);
+    const double* g = gtab + (size_t)q * no;
+#pragma unroll
+    for (int o = 0; o < kMaxOrders; ++o)
+      if (o < no) acc[o] = fma(K, g[o], acc[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < kMaxOrders; ++o)
+    if (o < no) G[(size_t)o * nf + i] = acc[o];
+}
+
 struct ModeInfo {
   int n, m, odd, o;  // radial order, azimuthal frequency, sin (odd Noll index), order slot
 };
@@ -173,6 +196,40 @@ __global__ void k_lambda_sums(const ModeInfo* __restrict__ modes, int J, int N, 
   }
   __syncthreads();
   for (int j = threadIdx.x; j < J; j += blockDim.x) atomicAdd(&sums[j], part[j]);
+}
+
+// The subharmonic levels (Sec. IV-B): level p, direction d = (n, m) in {-1, 0, 1}^2 \ {0} (order (-1,-1),
+// (0,-1), (1,-1), (-1,0), (1,0), (-1,1), (0,1), (1,1)) at f = (n, m) df / 3^p with weight 1/9^p of a bin; their
+// power joins the per-mode sum of the bins (sums[j], so lambda is normalised over both), and the amplitudes are
+// s_{j,p,d} = sqrt(P_j(f_{p,d}) / 9^p / sum_j).  Gl holds G_n at |f| = df/3^p (axis) and sqrt2 df/3^p (diagonal),
+// [o][2 (p-1) + diagonal].  One thread per mode.
+__global__ void k_sh_tables(const ModeInfo* __restrict__ modes, int J, int levels, const double* __restrict__ Gl,
+                            double* __restrict__ sums, float* __restrict__ amp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  const ModeInfo mi = modes[j];
+  const int dn[8] = {-1, 0, 1, -1, 1, -1, 0, 1}, dm[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+  double pw[12 * 8];
+  double extra = 0.0, w = 1.0;
+  for (int p = 0; p < levels; ++p) {
+    w /= 9.0;
+    for (int d = 0; d < 8; ++d) {
+      const bool diag = dn[d] != 0 && dm[d] != 0;
+      const double g = Gl[(size_t)mi.o * (2 * levels) + 2 * p + (diag ? 1 : 0)];
+      double ang = 1.0;
+      if (mi.m != 0) {
+        const double phi = atan2((double)dm[d], (double)dn[d]);
+        double sn, cs;
+        sincos(mi.m * phi, &sn, &cs);
+        ang = mi.odd ? 2.0 * sn * sn : 2.0 * cs * cs;
+      }
+      pw[p * 8 + d] = (mi.n + 1) * ang * g * w;
+      extra += pw[p * 8 + d];
+    }
+  }
+  const double total = sums[j] + extra;
+  sums[j] = total;
+  for (int e = 0; e < levels * 8; ++e) amp[(size_t)j * levels * 8 + e] = (float)sqrt(pw[e] / total);
 }
 
 __global__ void k_lambda_write(const ModeInfo* __restrict__ modes, int J, int N, const double* __restrict__ G, int noct,
@@ -296,6 +353,31 @@ void v_rule(std::vector<double>& v, std::vector<double>& w) {
   }
 }
 
+// The v-rule for frequencies far below the torus bins (the subharmonics): 8-point panels of width <= 0.2 in ln v
+// from 1e-14 to 1 (the integrand's mass lies at v >~ f, down to df / 3^12), then the uniform panels of v_rule.
+void v_rule_deep(std::vector<double>& v, std::vector<double>& w) {
+  std::vector<double> x8, w8, x16, w16;
+  gauss_legendre(8, x8, w8);
+  gauss_legendre(16, x16, w16);
+  const double y0 = log(1e-14);
+  const int nlog = (int)ceil(-y0 / 0.2);
+  for (int p = 0; p < nlog; ++p) {
+    const double a = y0 * (1.0 - (double)p / nlog), b = y0 * (1.0 - (double)(p + 1) / nlog);
+    for (int i = 0; i < 8; ++i) {
+      const double vv = exp(0.5 * (b - a) * x8[i] + 0.5 * (a + b));
+      v.push_back(vv);
+      w.push_back(0.5 * (b - a) * w8[i] * vv);
+    }
+  }
+  for (int p = 0; p < 94; ++p) {
+    const double a = 1.0 + 0.5 * p, b = a + 0.5;
+    for (int i = 0; i < 16; ++i) {
+      v.push_back(0.5 * (b - a) * x16[i] + 0.5 * (a + b));
+      w.push_back(0.5 * (b - a) * w16[i]);
+    }
+  }
+}
+
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
@@ -380,6 +462,32 @@ int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st) {
   const size_t total = (size_t)(N / 2 + 1) * N;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   k_lambda_sums<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p);
+  DevBuf<double> dfl, Gl, dv2, dw2, gtab2d;
+  if (f->sh_levels > 0) {
+    const int L = f->sh_levels, nf = 2 * L;
+    std::vector<double> fl(nf);
+    const double df = f->pix_per_D / N;
+    double scale = 1.0;
+    for (int p = 0; p < L; ++p) {
+      scale /= 3.0;
+      fl[2 * p] = df * scale;                          // axis directions
+      fl[2 * p + 1] = df * scale * 1.41421356237309505;  // diagonals
+    }
+    std::vector<double> hv2, hw2;
+    v_rule_deep(hv2, hw2);
+    const int Q2 = (int)hv2.size();
+    DFP2S_CUDA_TRY(dfl.alloc(nf));
+    DFP2S_CUDA_TRY(Gl.alloc((size_t)no * nf));
+    DFP2S_CUDA_TRY(dv2.alloc(Q2));
+    DFP2S_CUDA_TRY(dw2.alloc(Q2));
+    DFP2S_CUDA_TRY(gtab2d.alloc((size_t)Q2 * no));
+    DFP2S_CUDA_TRY(cudaMemcpyAsync(dfl.p, fl.data(), nf * sizeof(double), cudaMemcpyHostToDevice, st));
+    DFP2S_CUDA_TRY(cudaMemcpyAsync(dv2.p, hv2.data(), Q2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    DFP2S_CUDA_TRY(cudaMemcpyAsync(dw2.p, hw2.data(), Q2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_gtab<<<(Q2 * no + 255) / 256, 256, 0, st>>>(dv2.p, dw2.p, Q2, dord.p, dord.p, no, gtab2d.p);
+    k_radial_list<<<1, 32, 0, st>>>(dv2.p, gtab2d.p, Q2, no, dfl.p, nf, Gl.p);
+    k_sh_tables<<<1, 64, 0, st>>>(dmodes.p, J, L, Gl.p, sums.p, f->sh_amp);
+  }
   k_lambda_write<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p, f->mult);
   DFP2S_CUDA_TRY(cudaGetLastError());
   DevBuf<double> gtab2, Gp;

@@ -273,6 +273,71 @@ void launch_mix_any(float* fields, const float* L, float scale, int J, size_t np
   else launch_mix<64, AR>(fields, L, scale, J, npix, prev, alpha, st);
 }
 
+// ------------------------------------------------------------ subharmonics (Sec. IV-B; reading R31)
+DFP2S_DEV float dfp2s_pow3f(int k) {  // 3^k, exact in FP32 for k <= 15
+  float r = 1.f;
+  for (int i = 0; i < k; ++i) r *= 3.f;
+  return r;
+}
+
+// This frame's complex amplitudes c_{j,p,d} = s_{j,p,d} (g_re + i g_im): Philox tag 6, subsequence mode j,
+// counter 4 p + k for directions 2k, 2k + 1 (levels counted from 0 here).  One thread per (j, p, k).
+__global__ void k_sh_coeffs(const float* __restrict__ amp, int J, int levels, uint64_t seed, uint32_t frame,
+                            float2* __restrict__ coef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= J * levels * 4) return;
+  const int j = i / (levels * 4), r = i - j * levels * 4;  // r = 4 p + k
+  const float4 g = dfp2s_gauss4(seed, dfp2s_subsequence(6u, frame, (uint32_t)j), (uint64_t)r);
+  const size_t e = (size_t)j * levels * 8 + 2 * r;  // direction 2k of level p: 8 p + 2 k = 2 r
+  coef[e] = make_float2(amp[e] * g.x, amp[e] * g.y);
+  coef[e + 1] = make_float2(amp[e + 1] * g.z, amp[e + 1] * g.w);
+}
+
+// Adds sum_{p,d} Re[c_{j,p,d} u^n v^m] to every unit field, u = e^{2 pi i x / (N 3^p)}, v = e^{2 pi i y / (N 3^p)}
+// (pixel (y, x)).  Per row the m-sums C_n = sum_m c_{(n,m)} v^m are formed once, so a pixel takes
+// Re(C_0) + Re(C_1 u) + Re(C_{-1} conj u) = A + B u.x + D u.y per mode and level.  One CTA per row.
+__global__ void __launch_bounds__(256) k_sh_add(float* __restrict__ fields, int J, int H, int W, int N, int levels,
+                                             const float2* __restrict__ coef) {
+  extern __shared__ float shc[];  // [j][p][3]: A, B, D
+  const int y = blockIdx.x;
+  const size_t plane = (size_t)H * W;
+  for (int e = threadIdx.x; e < J * levels; e += blockDim.x) {
+    const int p = e % levels;
+    const float2* c = coef + (size_t)e * 8;  // e = j * levels + p
+    float sv, cv;
+    sincospif(2.f * (float)y / ((float)N * dfp2s_pow3f(p + 1)), &sv, &cv);
+    // directions: 0 (-1,-1), 1 (0,-1), 2 (1,-1), 3 (-1,0), 4 (1,0), 5 (-1,1), 6 (0,1), 7 (1,1)
+    const float2 vp = make_float2(cv, sv), vm = make_float2(cv, -sv);
+    const float2 cm1 = make_float2(c[0].x * vm.x - c[0].y * vm.y + c[3].x + c[5].x * vp.x - c[5].y * vp.y,
+                                   c[0].x * vm.y + c[0].y * vm.x + c[3].y + c[5].x * vp.y + c[5].y * vp.x);
+    const float c0x = c[1].x * vm.x - c[1].y * vm.y + c[6].x * vp.x - c[6].y * vp.y;
+    const float2 c1 = make_float2(c[2].x * vm.x - c[2].y * vm.y + c[4].x + c[7].x * vp.x - c[7].y * vp.y,
+                                  c[2].x * vm.y + c[2].y * vm.x + c[4].y + c[7].x * vp.y + c[7].y * vp.x);
+    shc[3 * e] = c0x;
+    shc[3 * e + 1] = c1.x + cm1.x;  // B: Re(C_1 u) + Re(C_-1 conj u) = (C1.x + Cm1.x) u.x + (Cm1.y - C1.y) u.y
+    shc[3 * e + 2] = cm1.y - c1.y;  // D
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    float2 u[12];
+#pragma unroll
+    for (int p = 0; p < 12; ++p)
+      if (p < levels) sincospif(2.f * (float)x / ((float)N * dfp2s_pow3f(p + 1)), &u[p].y, &u[p].x);
+    float* f = fields + (size_t)y * W + x;
+    for (int j = 0; j < J; ++j) {
+      float add = 0.f;
+#pragma unroll
+      for (int p = 0; p < 12; ++p) {
+        if (p < levels) {
+          const float* t = shc + 3 * (j * levels + p);
+          add += t[0] + t[1] * u[p].x + t[2] * u[p].y;
+        }
+      }
+      f[(size_t)j * plane] += add;
+    }
+  }
+}
+
 __global__ void k_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq) return;
@@ -319,7 +384,8 @@ void launch_passes(float2* S, const float* mult, const float2* tw, int J, int H,
 
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
-                               cudaStream_t st, const float* prev, float alpha, bool mix, int variant) {
+                               cudaStream_t st, const float* prev, float alpha, bool mix, int variant,
+                               const dfp2s_factor_dev* sh) {
   switch (N) {
     case 16: launch_passes<16>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
     case 32: launch_passes<32>(S, mult, tw, J, H, W, seed, frame, fields, st, variant); break;
@@ -333,6 +399,11 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
     default: return DFP2S_EINVAL;
   }
   const size_t npix = (size_t)H * W;
+  if (sh && sh->sh_levels > 0) {
+    const int L = sh->sh_levels;
+    k_sh_coeffs<<<(J * L * 4 + 255) / 256, 256, 0, st>>>(sh->sh_amp, J, L, seed, frame, sh->sh_coef);
+    k_sh_add<<<H, 256, (size_t)J * L * 3 * sizeof(float), st>>>(fields, J, H, W, N, L, sh->sh_coef);
+  }
   if (!mix) return dfp2s_launch_status();
   if (prev) launch_mix_any<true>(fields, L, scale * sqrtf(1.f - alpha * alpha), J, npix, prev, alpha, st);
   else launch_mix_any<false>(fields, L, scale, J, npix, nullptr, 0.f, st);

@@ -77,7 +77,8 @@ extern "C" int dfp2s_sample_zernike_fields_noalloc(const dfp2s_factor* f, double
   // nothing needs clearing between calls
   const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
   if (dfp2s_launch_sample_fields(scratch, f->d.mult, f->d.tw, f->d.N, f->d.J, H, W, seed, frame, f->d.L32, scale,
-                                 fields_dev, reinterpret_cast<cudaStream_t>(stream)) != DFP2S_OK)
+                                 fields_dev, reinterpret_cast<cudaStream_t>(stream), nullptr, 0.f, true, -1,
+                                 &f->d) != DFP2S_OK)
     return dfp2s_fail_cuda(dfp2s_launch_error(), "sample fields (static scratch)");
   return DFP2S_OK;
 }

@@ -12,10 +12,12 @@
 // fields.cu -- Sec. III-C sampler passes
 // prev != nullptr: fields = alpha prev + sqrt(1 - alpha^2) (this frame's fields), the auto-regressive form;
 // mix = false: the unit fields before the mixing by scale L (prev must be null)
+// sh: the factor whose subharmonic levels (if any) are added to the unit fields before the mixing
+struct dfp2s_factor_dev;
 int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, int N, int J, int H, int W,
                                uint64_t seed, uint32_t frame, const float* L, float scale, float* fields,
                                cudaStream_t st, const float* prev = nullptr, float alpha = 0.f, bool mix = true,
-                               int variant = -1);
+                               int variant = -1, const dfp2s_factor_dev* sh = nullptr);
 // the row pass alone (S as the column passes leave it), for the full sampler
 int dfp2s_launch_rowifft(const float2* S, float* out, const float2* tw, int N, int J, int H, int W, cudaStream_t st);
 int dfp2s_launch_philox_words(uint64_t seed, uint64_t sub, uint64_t q0, int nq, uint32_t* out, cudaStream_t st);
@@ -36,6 +38,10 @@ struct dfp2s_factor_dev {
                                   // [a(a+1)/2 + b][o(o+1)/2 + r]
   struct dfp2s_full_mode* fmode;  // J mode constants
   float2* eta;                    // R x (N/2+1) x N order fields, then R x (N + N/2 + 1) for the Nyquist lines
+  // subharmonic levels of the factored sampler (0: none)
+  int sh_levels;
+  float* sh_amp;                  // J x levels x 8: s_{j,p,d}, normalised with lambda to unit variance
+  float2* sh_coef;                // J x levels x 8: this frame's complex amplitudes (per-frame scratch)
 };
 // Per-mode constants of the full sampler: order slot, azimuthal frequency m, sin (odd Noll index) or cos, Noll's
 // angular prefactor (complex) and kappa0 = sqrt(A0_jj (n+1) / sum_k P_jj(k)).
