@@ -286,6 +286,25 @@ def full_sampler_timing(d, device, stream, flush, peak_gbs):
         out[name] = res
         del f, fields
         torch.cuda.empty_cache()
+    # the subharmonic levels of the factored sampler (nine, the tilt's low-frequency compensation) at 512 x 512
+    f0 = d.SpectralFactor(J, 1024, PIX_PER_D)
+    f9 = d.SpectralFactor(J, 1024, PIX_PER_D, subharmonics=9)
+    fields = torch.empty(J, 512, 512, device=device)
+    res = {}
+    for label, f in (("levels_0", f0), ("levels_9", f9)):
+        for i in range(3):
+            d.sample_zernike_fields(f, 2.0, 9, i, 512, 512, out=fields, stream=stream)
+        e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        for i, (a, b) in enumerate(e):
+            flush.zero_()
+            a.record(stream)
+            d.sample_zernike_fields(f, 2.0, 9, 10 + i, 512, 512, out=fields, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        res[label + "_ms"] = float(np.median([a.elapsed_time(b) for a, b in e]))
+    out["subharmonics_512x512"] = res
+    del f0, f9, fields
+    torch.cuda.empty_cache()
     return out
 
 
