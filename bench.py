@@ -303,7 +303,27 @@ def full_sampler_timing(d, device, stream, flush, peak_gbs):
         torch.cuda.synchronize()
         res[label + "_ms"] = float(np.median([a.elapsed_time(b) for a, b in e]))
     out["subharmonics_512x512"] = res
-    del f0, f9, fields
+    # the dense per-frequency root (FP64 Jacobi at setup, the J x J product per frame) at 512 x 512
+    t0 = time.perf_counter()
+    fd = d.SpectralFactor(J, 1024, PIX_PER_D, kind=d.FACTOR_DENSE)
+    torch.cuda.synchronize()
+    dres = {"setup_s": time.perf_counter() - t0}
+    for i in range(3):
+        d.sample_zernike_fields_dense(fd, 2.0, 9, i, 512, 512, out=fields, stream=stream)
+    e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for i, (a, b) in enumerate(e):
+        flush.zero_()
+        a.record(stream)
+        d.sample_zernike_fields_dense(fd, 2.0, 9, 10 + i, 512, 512, out=fields, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    dres["ms"] = float(np.median([a.elapsed_time(b) for a, b in e]))
+    half = 513 * 1024
+    dbytes = J * J * half * 4 + 2 * J * half * 8 + 2 * J * half * 512 * 8 // 1024 + J * 512 * 512 * 4
+    dres["roofline"] = {"bound": "hbm", "bytes": dbytes, "achieved": dbytes / (dres["ms"] * 1e-3) / 1e9,
+                        "peak": peak_gbs, "unit": "GB/s", "frac": dbytes / (dres["ms"] * 1e-3) / 1e9 / peak_gbs}
+    out["dense_root_512x512"] = dres
+    del f0, f9, fd, fields
     torch.cuda.empty_cache()
     return out
 

@@ -58,9 +58,13 @@ extern "C" {
 #define DFP2S_P2S_LEARNED_FP32 2 /* the same network in FP32 on CUDA cores (check mode) */
 
 #define DFP2S_FACTOR_FACTORED 0 /* sqrt(lambda_j(f)) per mode, then mixing by L (Sec. III-C) */
-#define DFP2S_FACTOR_DENSE 1    /* per-frequency J x J symmetric root of L diag(lambda) L^T: not built in
-                                   this version (DFP2S_EUNSUPPORTED); FACTORED applies the J x J root
-                                   L diag(sqrt(lambda(f))) of the same spectral density */
+#define DFP2S_FACTOR_DENSE 1    /* FACTORED, plus the per-frequency J x J symmetric root F(f) of
+                                   S~(f) = L diag(lambda(f)) L^T (Sec. III-A's eigen-root form per frequency:
+                                   FP64 Jacobi eigendecomposition on the device, eigenvalues clamped at 0,
+                                   stored FP32; J <= 48, else DFP2S_EUNSUPPORTED): the sampler
+                                   dfp2s_sample_zernike_fields_dense.  FACTORED applies the other J x J root
+                                   L diag(sqrt(lambda(f))) of the same density (same covariance, other
+                                   samples) */
 #define DFP2S_FACTOR_FULL 2     /* FACTORED, plus the tables of the exact sampler of the full cross-spectral
                                    density (Sec. III-B, no approximation): dfp2s_sample_zernike_fields_full */
 
@@ -97,8 +101,7 @@ typedef struct {
   int J;            /* number of fields, Noll modes 2..J+1; 3 <= J <= DFP2S_MAX_J */
   int N;            /* FFT grid side, power of two, 16 <= N <= 4096 */
   double pix_per_D; /* image pixels per aperture diameter of displacement s */
-  int kind;         /* DFP2S_FACTOR_FACTORED or DFP2S_FACTOR_FULL (DFP2S_FACTOR_DENSE returns
-                       DFP2S_EUNSUPPORTED) */
+  int kind;         /* DFP2S_FACTOR_FACTORED, DFP2S_FACTOR_DENSE or DFP2S_FACTOR_FULL */
   int subharmonic_levels; /* 0 (the paper's sampler) .. 12: subharmonic levels of the factored sampler
                        (Sec. IV-B: the low-frequency deficit of the FFT method).  The DC cell of the
                        torus is split into 3 x 3 sub-cells of side df/3 (df = pix_per_D / N), the eight
@@ -108,8 +111,8 @@ typedef struct {
                        unit field sum_d Re[(g_re + i g_im) s_{j,p,d} e^{2 pi i (n x + m y) / (N 3^p)}]
                        (pixel (y, x); Gaussians from Philox tag 6, subsequence mode j, counter
                        4 (p - 1) + k for directions 2k, 2k + 1 of (n, m) = (-1,-1), (0,-1), (1,-1),
-                       (-1,0), (1,0), (-1,1), (0,1), (1,1)).  Not with DFP2S_FACTOR_FULL
-                       (DFP2S_EUNSUPPORTED). */
+                       (-1,0), (1,0), (-1,1), (0,1), (1,1)).  Only with DFP2S_FACTOR_FACTORED
+                       (else DFP2S_EUNSUPPORTED). */
 } dfp2s_factor_params;
 
 /* Builds the factor (allocates device memory, synchronises `stream` before
@@ -137,6 +140,19 @@ int dfp2s_factor_info(const dfp2s_factor* f, int* J, int* N, size_t* scratch_byt
  * and uses the factor's scratch.  Errors: EINVAL, ECUDA. */
 int dfp2s_sample_zernike_fields(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
                                 int H, int W, float* fields_dev, void* stream);
+
+/* The dense-root form of the sampler (Sec. III-A per frequency, Eq. A tilde):
+ * E(f) = F(f) xi(f), F the symmetric root of L diag(lambda(f)) L^T, xi the
+ * Fourier-domain noise of dfp2s_sample_zernike_fields (the same Philox
+ * streams), then the inverse FFT per mode, times (D/r0)^{5/6}.  Same
+ * covariance as the factored form, other samples; the fields come out mixed.
+ * Needs a DFP2S_FACTOR_DENSE factor (else EINVAL); uses its scratch and the
+ * J^2 (N/2+1) N floats of F (read once per frame).  Errors: EINVAL, ECUDA. */
+int dfp2s_sample_zernike_fields_dense(const dfp2s_factor* f, double D_over_r0, uint64_t seed, uint32_t frame,
+                                      int H, int W, float* fields_dev, void* stream);
+/* Copies F (float32, [j * J + i][kx * N + ky], kx = 0..N/2, D/r0 = 1) of a
+ * DFP2S_FACTOR_DENSE factor to dst_dev.  Errors: EINVAL, ECUDA. */
+int dfp2s_factor_copy_dense_root(const dfp2s_factor* f, float* dst_dev, void* stream);
 
 /* The exact sampler (Sec. III-B): fields whose every auto- and cross-covariance
  * at every displacement is the full homogeneous tensor A (the slices A_{i,j}(s)

@@ -59,6 +59,8 @@ SIGNATURES = {
     "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_ar1": (_i, [_vp, _d, _u64, _u32, _d, _i, _i, _vp, _vp, _vp]),
     "dfp2s_sample_zernike_fields_full": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_sample_zernike_fields_dense": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_factor_copy_dense_root": (_i, [_vp, _vp, _vp]),
     "dfp2s_aperture_statistics": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
     "dfp2s_tilt_statistics": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_noalloc": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
@@ -223,6 +225,24 @@ def sample_zernike_fields_full(factor: SpectralFactor, D_over_r0: float, seed: i
         out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
     _check(load().dfp2s_sample_zernike_fields_full(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
                                                    _stream(stream)))
+    return out
+
+
+def sample_zernike_fields_dense(factor: SpectralFactor, D_over_r0: float, seed: int, frame: int, H: int, W: int,
+                                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Fields from the per-frequency symmetric root of L diag(lambda) L^T; the factor needs kind=FACTOR_DENSE."""
+    if out is None:
+        out = torch.empty(factor.J, H, W, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_sample_zernike_fields_dense(factor.handle, D_over_r0, seed, frame, H, W, _ptr(out),
+                                                    _stream(stream)))
+    return out
+
+
+def dense_root(factor: SpectralFactor, stream=None) -> torch.Tensor:
+    """F of a FACTOR_DENSE factor: (J, J, N/2+1, N) float32, [j, i, kx, ky], D/r0 = 1."""
+    J, N = factor.J, factor.N
+    out = torch.empty(J, J, N // 2 + 1, N, dtype=torch.float32, device="cuda")
+    _check(load().dfp2s_factor_copy_dense_root(factor.handle, _ptr(out), _stream(stream)))
     return out
 
 

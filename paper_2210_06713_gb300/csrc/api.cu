@@ -131,6 +131,8 @@ static void factor_free(dfp2s_factor* f) {
   cudaFree(f->d.eta);
   cudaFree(f->d.sh_amp);
   cudaFree(f->d.sh_coef);
+  cudaFree(f->d.dense);
+  cudaFree(f->d.espec);
   delete f;
 }
 
@@ -142,10 +144,11 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
   CHECK_ARG(p->pix_per_D > 0 && p->pix_per_D <= 64, "pix_per_D out of range");
   CHECK_ARG(p->kind == DFP2S_FACTOR_FACTORED || p->kind == DFP2S_FACTOR_DENSE || p->kind == DFP2S_FACTOR_FULL,
             "unknown factor kind");
-  if (p->kind == DFP2S_FACTOR_DENSE) return dfp2s_fail(DFP2S_EUNSUPPORTED, "dense factor not built in this version");
+  if (p->kind == DFP2S_FACTOR_DENSE && p->J > 48)
+    return dfp2s_fail(DFP2S_EUNSUPPORTED, "the dense root is built for J <= 48 (J = %d)", p->J);
   CHECK_ARG(p->subharmonic_levels >= 0 && p->subharmonic_levels <= 12, "subharmonic levels %d out of [0, 12]",
             p->subharmonic_levels);
-  if (p->kind == DFP2S_FACTOR_FULL && p->subharmonic_levels > 0)
+  if (p->kind != DFP2S_FACTOR_FACTORED && p->subharmonic_levels > 0)
     return dfp2s_fail(DFP2S_EUNSUPPORTED, "subharmonics are built for the factored sampler only");
   dfp2s_factor* f = new dfp2s_factor();
   memset(&f->d, 0, sizeof(f->d));
@@ -164,6 +167,13 @@ extern "C" int dfp2s_build_spectral_factor(const dfp2s_factor_params* p, dfp2s_f
       (e = dfp2s_device_malloc((void**)&f->d.scratch, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
     factor_free(f);
     return dfp2s_fail_cuda(e, "factor allocation");
+  }
+  if (p->kind == DFP2S_FACTOR_DENSE) {
+    if ((e = dfp2s_device_malloc((void**)&f->d.dense, (size_t)p->J * p->J * half * sizeof(float))) != cudaSuccess ||
+        (e = dfp2s_device_malloc((void**)&f->d.espec, (size_t)p->J * half * sizeof(float2))) != cudaSuccess) {
+      factor_free(f);
+      return dfp2s_fail_cuda(e, "dense-root table allocation");
+    }
   }
   if (p->subharmonic_levels > 0) {
     const size_t n = (size_t)p->J * p->subharmonic_levels * 8;
@@ -241,6 +251,25 @@ extern "C" int dfp2s_sample_zernike_fields_full(const dfp2s_factor* f, double D_
   CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
   const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
   CHECK_LAUNCH(dfp2s_launch_sample_fields_full(&f->d, H, W, seed, frame, scale, fields, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_sample_zernike_fields_dense(const dfp2s_factor* f, double D_over_r0, uint64_t seed,
+                                                 uint32_t frame, int H, int W, float* fields, void* stream) {
+  CHECK_ARG(f && fields, "null argument");
+  CHECK_ARG(f->kind == DFP2S_FACTOR_DENSE, "the factor was not built with DFP2S_FACTOR_DENSE");
+  CHECK_ARG(H >= 1 && W >= 1 && H <= f->d.N && W <= f->d.N, "frame %dx%d does not fit the %d grid", H, W, f->d.N);
+  CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
+  const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+  CHECK_LAUNCH(dfp2s_launch_sample_fields_dense(&f->d, H, W, seed, frame, scale, fields, as_stream(stream)));
+  return DFP2S_OK;
+}
+
+extern "C" int dfp2s_factor_copy_dense_root(const dfp2s_factor* f, float* dst_dev, void* stream) {
+  CHECK_ARG(f && dst_dev, "null argument");
+  CHECK_ARG(f->kind == DFP2S_FACTOR_DENSE, "the factor was not built with DFP2S_FACTOR_DENSE");
+  const size_t n = (size_t)f->d.J * f->d.J * (f->d.N / 2 + 1) * f->d.N;
+  DFP2S_CUDA_TRY(cudaMemcpyAsync(dst_dev, f->d.dense, n * sizeof(float), cudaMemcpyDeviceToDevice, as_stream(stream)));
   return DFP2S_OK;
 }
 

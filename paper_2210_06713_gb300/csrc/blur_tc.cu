@@ -146,41 +146,70 @@ __global__ void k_pad_shifted(const float* __restrict__ img, int C, int H, int W
 
 // The same planes for the tilt-warped image, without the FP32 warped image: the
 // value at padded (r, x) of shift sh is the warped pixel (clamp(r - 16),
-// clamp(x + sh - 16)) (tilt_sample, as in the warp kernel).  A thread covers
-// columns 8u .. 8u + 7 of padded row r: per channel it warps the 15 clamped
-// columns 8u - 16 .. 8u - 2 and writes one 16-byte run per shift.
-__global__ void __launch_bounds__(128, 6)
+// clamp(x + sh - 16)) (tilt_sample, as in the warp kernel).  One CTA per padded
+// row and channel: the row's warped samples at clamped columns i - 16,
+// i < Wq + 7, go to shared memory once (as bfloat16 bits; eight samples per
+// thread at a time, their tilt loads and then their gathers all in flight),
+// then each thread takes sixteen consecutive samples with two 16-byte loads and
+// writes the eight shifted 16-byte runs of its eight columns (funnel shifts for
+// the odd shifts; consecutive threads, consecutive runs of each shift plane).
+__global__ void __launch_bounds__(128)
     k_warp_pad_shifted(const float* __restrict__ img, int C, int H, int W, const float* __restrict__ a2,
                        const float* __restrict__ a3, int Wq, float centre, __nv_bfloat16* __restrict__ P, int mixed,
                        float m00, float m10, float m11) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
-  if (8 * u >= Wq) return;
+  extern __shared__ __align__(16) unsigned short wrow[];  // Wq + 8 entries
+  const int r = blockIdx.x, c = blockIdx.y;
   const int R = H + 32;
   const int yp = min(max(r - 16, 0), H - 1);
   const size_t plane = (size_t)R * Wq;
   const float* t2 = a2 + (size_t)yp * W;
   const float* t3 = a3 + (size_t)yp * W;
-  for (int c = 0; c < C; ++c) {
-    const float* I = img + (size_t)c * H * W;
-    uint32_t h[15];  // bf16 bits of the 15 warped samples
+  const float* I = img + (size_t)c * H * W;
+  const int n = Wq + 7;
+  if (threadIdx.x == 0) wrow[n] = 0;
+  for (int base = 0; base < n; base += 8 * blockDim.x) {
+    float s2[8], s3[8];
 #pragma unroll
-    for (int i = 0; i < 15; ++i) {
-      const int x = min(max(8 * u - 16 + i, 0), W - 1);
-      float s2 = __ldg(t2 + x), s3 = __ldg(t3 + x);
-      if (mixed) {  // the tilt rows of a = scale L u, in the mixing kernel's operation order
-        s3 = fmaf(m11, s3, fmaf(m10, s2, 0.f));
-        s2 = fmaf(m00, s2, 0.f);
-      }
-      const float v = tilt_sample(I, H, W, x, yp, s2, s3);
-      h[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - centre));
+    for (int k = 0; k < 8; ++k) {
+      const int i = base + k * blockDim.x + threadIdx.x;
+      const int x = min(max(i - 16, 0), W - 1);
+      s2[k] = i < n ? __ldg(t2 + x) : 0.f;
+      s3[k] = i < n ? __ldg(t3 + x) : 0.f;
     }
-    __nv_bfloat16* dst = P + ((size_t)c * NSHIFT) * plane + (size_t)r * Wq + 8 * u;
 #pragma unroll
-    for (int sh = 0; sh < NSHIFT; ++sh)
-      *reinterpret_cast<uint4*>(dst + sh * plane) =
-          make_uint4(h[sh] | (h[sh + 1] << 16), h[sh + 2] | (h[sh + 3] << 16), h[sh + 4] | (h[sh + 5] << 16),
-                     h[sh + 6] | (h[sh + 7] << 16));
+    for (int k = 0; k < 8; ++k) {
+      const int i = base + k * blockDim.x + threadIdx.x;
+      if (i < n) {
+        const int x = min(max(i - 16, 0), W - 1);
+        float u2 = s2[k], u3 = s3[k];
+        if (mixed) {  // the tilt rows of a = scale L u, in the mixing kernel's operation order
+          u3 = fmaf(m11, u3, fmaf(m10, u2, 0.f));
+          u2 = fmaf(m00, u2, 0.f);
+        }
+        const float v = tilt_sample(I, H, W, x, yp, u2, u3);
+        wrow[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - centre));
+      }
+    }
+  }
+  __syncthreads();
+  const int runs = Wq / 8;
+  __nv_bfloat16* dst = P + ((size_t)c * NSHIFT) * plane + (size_t)r * Wq;
+  const uint4* w4 = reinterpret_cast<const uint4*>(wrow);
+  for (int u = threadIdx.x; u < runs; u += blockDim.x) {
+    const uint4 lo = w4[u], hi = w4[u + 1];  // samples 8u .. 8u + 15 (the last run reads up to Wq + 7)
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int sh = 0; sh < NSHIFT; ++sh) {
+      const int m = sh >> 1;
+      uint4 v;
+      if (sh & 1) {
+        v = make_uint4(__funnelshift_r(w[m], w[m + 1], 16), __funnelshift_r(w[m + 1], w[m + 2], 16),
+                       __funnelshift_r(w[m + 2], w[m + 3], 16), __funnelshift_r(w[m + 3], w[m + 4], 16));
+      } else {
+        v = make_uint4(w[m], w[m + 1], w[m + 2], w[m + 3]);
+      }
+      *reinterpret_cast<uint4*>(dst + sh * plane + 8 * u) = v;
+    }
   }
 }
 
@@ -657,9 +686,8 @@ int dfp2s_launch_blur_tc_prepare_warp(dfp2s_p2s_dev* p, const float* img, int C,
   const int rc = blur_tc_scratch(p, C, H, W, st);
   if (rc != DFP2S_OK) return rc;
   const int Wq = (W + TM - 1) / TM * TM + 64;
-  k_warp_pad_shifted<<<dim3((Wq / 8 + 127) / 128, H + 32), 128, 0, st>>>(img, C, H, W, a2, a3, Wq, 0.5f, p->pad,
-                                                                          m != nullptr, m ? m[0] : 1.f, m ? m[1] : 0.f,
-                                                                          m ? m[2] : 1.f);
+  k_warp_pad_shifted<<<dim3(H + 32, C), 128, (size_t)(Wq + 8) * sizeof(unsigned short), st>>>(
+      img, C, H, W, a2, a3, Wq, 0.5f, p->pad, m != nullptr, m ? m[0] : 1.f, m ? m[1] : 0.f, m ? m[2] : 1.f);
   p->prep_C = C;
   p->prep_H = H;
   p->prep_W = W;

@@ -304,6 +304,111 @@ __global__ void k_full_modes(const ModeInfo* __restrict__ modes, int J, const do
   out[j] = o;
 }
 
+// ---- the dense per-frequency root (Sec. III-A's eigen-root form applied per frequency; reading R6)
+// For half-plane bin k: S(k) = L diag(lambda(k)) L^T (J x J, FP64, D/r0 = 1), its eigendecomposition by cyclic
+// Jacobi rotations, and the symmetric root F = U diag(sqrt(max(ev, 0))) U^T, stored in FP32 as F[j * J + i][bin]
+// (bins contiguous).  One warp per matrix: the J/2 disjoint pairs of a round-robin round rotate at once (rows,
+// then columns and the eigenvector columns), sweeps until the off-diagonal mass is below 1e-30 of the diagonal's
+// (at most kDenseSweeps); the matrix lives in shared memory, J padded to an even JP with a zero row and column.
+constexpr int kDenseSweeps = 16;
+constexpr int kDenseWarps = 4;  // matrices per CTA
+
+DFP2S_DEV int dense_pair_member(int t, int r, int JP) { return t == 0 ? 0 : ((t - 1 + r) % (JP - 1)) + 1; }
+
+__global__ void __launch_bounds__(32 * kDenseWarps) k_dense_root(const ModeInfo* __restrict__ modes, int J, int JP,
+                                                              int N, const double* __restrict__ G, int noct,
+                                                              const double* __restrict__ sums,
+                                                              const double* __restrict__ L64, float* __restrict__ F,
+                                                              long long nbins) {
+  extern __shared__ double dsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int JJ = JP * JP;
+  double* A = dsm + (size_t)warp * (2 * JJ + 2 * JP);
+  double* V = A + JJ;
+  double* lam = V + JJ;  // JP
+  double* cs = lam + JP;  // JP: (c, s) per pair
+  for (long long bin = (long long)blockIdx.x * kDenseWarps + warp; bin < nbins;
+       bin += (long long)gridDim.x * kDenseWarps) {
+    const int kx = (int)(bin / N), ky = (int)(bin - (long long)kx * N);
+    for (int j = lane; j < JP; j += 32)
+      lam[j] = j < J ? (double)N * N * mode_power(modes[j], kx, ky, N, G, noct) / sums[j] : 0.0;
+    __syncwarp();
+    for (int e = lane; e < JJ; e += 32) {
+      const int a = e / JP, b = e - a * JP;
+      double v = 0.0;
+      if (a < J && b < J) {
+        const int kmax = a < b ? a : b;
+        for (int k = 0; k <= kmax; ++k) v = fma(L64[a * J + k] * lam[k], L64[b * J + k], v);
+      }
+      A[e] = v;
+      V[e] = a == b ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < kDenseSweeps; ++sweep) {
+      double off = 0.0, dia = 0.0;
+      for (int e = lane; e < JJ; e += 32) {
+        const int a = e / JP, b = e - a * JP;
+        if (a == b) dia += A[e] * A[e];
+        else off += A[e] * A[e];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        dia += __shfl_xor_sync(0xffffffffu, dia, o);
+      }
+      if (!(off > 1e-30 * dia)) break;  // warp-uniform (reduced values)
+      for (int r = 0; r < JP - 1; ++r) {
+        for (int q2 = lane; q2 < JP / 2; q2 += 32) {
+          const int p = dense_pair_member(q2, r, JP), q = dense_pair_member(JP - 1 - q2, r, JP);
+          const double apq = A[p * JP + q];
+          double c = 1.0, sn = 0.0;
+          if (apq != 0.0) {
+            const double tau = (A[q * JP + q] - A[p * JP + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+          cs[2 * q2] = c;
+          cs[2 * q2 + 1] = sn;
+        }
+        __syncwarp();
+        for (int e = lane; e < (JP / 2) * JP; e += 32) {  // rows p, q of A
+          const int q2 = e / JP, k = e - q2 * JP;
+          const int p = dense_pair_member(q2, r, JP), q = dense_pair_member(JP - 1 - q2, r, JP);
+          const double c = cs[2 * q2], sn = cs[2 * q2 + 1];
+          const double x = A[p * JP + k], y = A[q * JP + k];
+          A[p * JP + k] = c * x - sn * y;
+          A[q * JP + k] = sn * x + c * y;
+        }
+        __syncwarp();
+        for (int e = lane; e < (JP / 2) * JP; e += 32) {  // columns p, q of A and of V
+          const int q2 = e / JP, k = e - q2 * JP;
+          const int p = dense_pair_member(q2, r, JP), q = dense_pair_member(JP - 1 - q2, r, JP);
+          const double c = cs[2 * q2], sn = cs[2 * q2 + 1];
+          const double x = A[k * JP + p], y = A[k * JP + q];
+          A[k * JP + p] = c * x - sn * y;
+          A[k * JP + q] = sn * x + c * y;
+          const double u = V[k * JP + p], w = V[k * JP + q];
+          V[k * JP + p] = c * u - sn * w;
+          V[k * JP + q] = sn * u + c * w;
+        }
+        __syncwarp();
+      }
+    }
+    for (int j = lane; j < JP; j += 32) {
+      const double ev = A[j * JP + j];
+      lam[j] = ev > 0.0 ? sqrt(ev) : 0.0;  // rounding of a near-singular matrix: negative eigenvalues clamp to 0
+    }
+    __syncwarp();
+    for (int e = lane; e < J * J; e += 32) {
+      const int a = e / J, b = e - a * J;
+      double v = 0.0;
+      for (int k = 0; k < JP; ++k) v = fma(V[a * JP + k] * lam[k], V[b * JP + k], v);
+      F[(size_t)e * nbins + bin] = (float)v;
+    }
+    __syncwarp();  // the buffers are rewritten by the warp's next matrix
+  }
+}
+
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
@@ -490,6 +595,20 @@ int dfp2s_factor_build_device(dfp2s_factor_dev* f, cudaStream_t st) {
   }
   k_lambda_write<<<blocks, 256, 0, st>>>(dmodes.p, J, N, G.p, noct, sums.p, f->mult);
   DFP2S_CUDA_TRY(cudaGetLastError());
+  if (f->dense) {
+    const int JP = (J + 1) / 2 * 2;
+    const size_t smem = (size_t)kDenseWarps * (2 * JP * JP + 2 * JP) * sizeof(double);
+    DFP2S_CUDA_TRY(cudaFuncSetAttribute(k_dense_root, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long nbins = (long long)(N / 2 + 1) * N;
+    const long long want = (nbins + kDenseWarps - 1) / kDenseWarps;
+    const int grid = (int)(want < 8LL * sms ? want : 8LL * sms);
+    k_dense_root<<<grid, 32 * kDenseWarps, smem, st>>>(dmodes.p, J, JP, N, G.p, noct, sums.p, f->L64, f->dense,
+                                                      nbins);
+    DFP2S_CUDA_TRY(cudaGetLastError());
+  }
   DevBuf<double> gtab2, Gp;
   DevBuf<int> dpa, dpb;
   if (f->fchol) {

@@ -298,7 +298,7 @@ __global__ void k_sh_coeffs(const float* __restrict__ amp, int J, int levels, ui
 // Re(C_0) + Re(C_1 u) + Re(C_{-1} conj u) = A + B u.x + D u.y per mode and level.  One CTA per row.
 __global__ void __launch_bounds__(256) k_sh_add(float* __restrict__ fields, int J, int H, int W, int N, int levels,
                                              const float2* __restrict__ coef) {
-  extern __shared__ float shc[];  // [j][p][3]: A, B, D
+  extern __shared__ float4 shc[];  // [j][p]: A, B, D, 0
   const int y = blockIdx.x;
   const size_t plane = (size_t)H * W;
   for (int e = threadIdx.x; e < J * levels; e += blockDim.x) {
@@ -313,9 +313,8 @@ __global__ void __launch_bounds__(256) k_sh_add(float* __restrict__ fields, int 
     const float c0x = c[1].x * vm.x - c[1].y * vm.y + c[6].x * vp.x - c[6].y * vp.y;
     const float2 c1 = make_float2(c[2].x * vm.x - c[2].y * vm.y + c[4].x + c[7].x * vp.x - c[7].y * vp.y,
                                   c[2].x * vm.y + c[2].y * vm.x + c[4].y + c[7].x * vp.y + c[7].y * vp.x);
-    shc[3 * e] = c0x;
-    shc[3 * e + 1] = c1.x + cm1.x;  // B: Re(C_1 u) + Re(C_-1 conj u) = (C1.x + Cm1.x) u.x + (Cm1.y - C1.y) u.y
-    shc[3 * e + 2] = cm1.y - c1.y;  // D
+    // Re(C_1 u) + Re(C_-1 conj u) = (C1.x + Cm1.x) u.x + (Cm1.y - C1.y) u.y
+    shc[e] = make_float4(c0x, c1.x + cm1.x, cm1.y - c1.y, 0.f);
   }
   __syncthreads();
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
@@ -324,16 +323,25 @@ __global__ void __launch_bounds__(256) k_sh_add(float* __restrict__ fields, int 
     for (int p = 0; p < 12; ++p)
       if (p < levels) sincospif(2.f * (float)x / ((float)N * dfp2s_pow3f(p + 1)), &u[p].y, &u[p].x);
     float* f = fields + (size_t)y * W + x;
-    for (int j = 0; j < J; ++j) {
-      float add = 0.f;
+    for (int j0 = 0; j0 < J; j0 += 4) {  // four modes at a time: their loads in flight together
+      float v[4];
 #pragma unroll
-      for (int p = 0; p < 12; ++p) {
-        if (p < levels) {
-          const float* t = shc + 3 * (j * levels + p);
-          add += t[0] + t[1] * u[p].x + t[2] * u[p].y;
+      for (int k = 0; k < 4; ++k) v[k] = j0 + k < J ? f[(size_t)(j0 + k) * plane] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float add = 0.f;
+#pragma unroll
+        for (int p = 0; p < 12; ++p) {
+          if (p < levels && j0 + k < J) {
+            const float4 t = shc[(j0 + k) * levels + p];
+            add += t.x + t.y * u[p].x + t.z * u[p].y;
+          }
         }
+        v[k] += add;
       }
-      f[(size_t)j * plane] += add;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (j0 + k < J) f[(size_t)(j0 + k) * plane] = v[k];
     }
   }
 }
@@ -402,7 +410,7 @@ int dfp2s_launch_sample_fields(float2* S, const float* mult, const float2* tw, i
   if (sh && sh->sh_levels > 0) {
     const int L = sh->sh_levels;
     k_sh_coeffs<<<(J * L * 4 + 255) / 256, 256, 0, st>>>(sh->sh_amp, J, L, seed, frame, sh->sh_coef);
-    k_sh_add<<<H, 256, (size_t)J * L * 3 * sizeof(float), st>>>(fields, J, H, W, N, L, sh->sh_coef);
+    k_sh_add<<<H, 256, (size_t)J * L * sizeof(float4), st>>>(fields, J, H, W, N, L, sh->sh_coef);
   }
   if (!mix) return dfp2s_launch_status();
   if (prev) launch_mix_any<true>(fields, L, scale * sqrtf(1.f - alpha * alpha), J, npix, prev, alpha, st);

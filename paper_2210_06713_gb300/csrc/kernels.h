@@ -38,6 +38,9 @@ struct dfp2s_factor_dev {
                                   // [a(a+1)/2 + b][o(o+1)/2 + r]
   struct dfp2s_full_mode* fmode;  // J mode constants
   float2* eta;                    // R x (N/2+1) x N order fields, then R x (N + N/2 + 1) for the Nyquist lines
+  // the dense per-frequency root (factor kind DFP2S_FACTOR_DENSE; null otherwise)
+  float* dense;                   // F[j * J + i][bin], bin = kx * N + ky over the half plane, FP32
+  float2* espec;                  // J x (N/2+1) x N: this frame's E = F xi (per-frame scratch)
   // subharmonic levels of the factored sampler (0: none)
   int sh_levels;
   float* sh_amp;                  // J x levels x 8: s_{j,p,d}, normalised with lambda to unit variance
@@ -49,6 +52,9 @@ struct dfp2s_full_mode {
   int o, m, odd, pad;
   float pre_re, pre_im, kappa0, pad2;
 };
+// fields_dense.cu -- the dense-root sampler's per-frame passes (needs a factor built with DFP2S_FACTOR_DENSE)
+int dfp2s_launch_sample_fields_dense(const dfp2s_factor_dev* f, int H, int W, uint64_t seed, uint32_t frame,
+                                     float scale, float* fields, cudaStream_t st);
 // Number of distinct radial orders among Noll modes 2..J+1.
 int dfp2s_radial_order_count(int J);
 // fields_full.cu -- the full sampler's per-frame passes (needs a factor built with the full tables)
