@@ -441,6 +441,16 @@ int dfp2s_aperture_statistics(const float* fields_dev, int J, int H, int W, int 
  * 0 <= max_lag < min(H, W), max_lag <= 1024.  Errors: EINVAL, ENOMEM, ECUDA. */
 int dfp2s_tilt_statistics(const float* fields_dev, int H, int W, int max_lag, double* out_dev, void* stream);
 
+/* Which field sampler a context's frames use: the factored form of Sec. III-C
+ * (the default), the dense per-frequency root (needs a DFP2S_FACTOR_DENSE
+ * factor) or the full cross-spectral density without the approximation
+ * (needs DFP2S_FACTOR_FULL).  The last two give mixed fields: exact frames
+ * skip the mixing pass, learned frames feed the network's own first layer
+ * W1 diag(in_scale) and warp by the fields' tilt rows.  Errors: EINVAL. */
+#define DFP2S_FIELDS_FACTORED 0
+#define DFP2S_FIELDS_DENSE 1
+#define DFP2S_FIELDS_FULL 2
+
 /* ---------------------------------------------------------------- frames
  * A context binds a factor and a P2S handle and owns the per-frame scratch
  * (fields, warped image, weights) for frames up to max_C x max_H x max_W. */
@@ -448,6 +458,7 @@ typedef struct dfp2s_ctx dfp2s_ctx;
 int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int max_C, int max_H, int max_W,
                      dfp2s_ctx** out);
 int dfp2s_ctx_destroy(dfp2s_ctx* c);
+int dfp2s_ctx_set_field_sampler(dfp2s_ctx* c, int sampler);
 
 /* Fig. dfp2s: one frame.  fields (Sec. III-C) -> tilt warp -> P2S weights
  * (FP32) -> blur (p2s_mode EXACT: FP32 CUDA-core blur; LEARNED: the network's

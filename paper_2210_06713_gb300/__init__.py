@@ -21,6 +21,7 @@ OK = 0
 W_F32, W_BF16 = 0, 1
 P2S_EXACT, P2S_LEARNED, P2S_LEARNED_FP32 = 0, 1, 2
 FACTOR_FACTORED, FACTOR_DENSE, FACTOR_FULL = 0, 1, 2
+FIELDS_FACTORED, FIELDS_DENSE, FIELDS_FULL = 0, 1, 2
 KS = 33
 MAX_J = 64
 MAX_K = 128
@@ -59,6 +60,7 @@ SIGNATURES = {
     "dfp2s_sample_zernike_fields": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_sample_zernike_fields_ar1": (_i, [_vp, _d, _u64, _u32, _d, _i, _i, _vp, _vp, _vp]),
     "dfp2s_sample_zernike_fields_full": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
+    "dfp2s_ctx_set_field_sampler": (_i, [_vp, _i]),
     "dfp2s_sample_zernike_fields_dense": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_factor_copy_dense_root": (_i, [_vp, _vp, _vp]),
     "dfp2s_aperture_statistics": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
@@ -498,6 +500,10 @@ class Simulator:
         _check(load().dfp2s_simulate_frame(self._h, _ptr(img), C, H, W, D_over_r0, seed, frame, mode, _ptr(out),
                                            _stream(stream)))
         return out
+
+    def set_field_sampler(self, sampler: int) -> None:
+        """FIELDS_FACTORED (default), FIELDS_DENSE (a FACTOR_DENSE factor) or FIELDS_FULL (a FACTOR_FULL factor)."""
+        _check(load().dfp2s_ctx_set_field_sampler(self._h, sampler))
 
     def buffers(self, J: int, C: int, H: int, W: int, K: int, w_dtype=torch.float32):
         f, wp, w = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()

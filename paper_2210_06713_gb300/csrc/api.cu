@@ -683,7 +683,27 @@ struct dfp2s_ctx {
   int nev;
   unsigned long long frames;
   int field_variant;  // column-pass kernel of the field sampler (-1: the default)
+  int field_sampler;  // DFP2S_FIELDS_FACTORED, _DENSE or _FULL
 };
+
+extern "C" int dfp2s_ctx_set_field_sampler(dfp2s_ctx* c, int sampler) {
+  CHECK_ARG(c, "null context");
+  CHECK_ARG(sampler == DFP2S_FIELDS_FACTORED || sampler == DFP2S_FIELDS_DENSE || sampler == DFP2S_FIELDS_FULL,
+            "unknown field sampler %d", sampler);
+  CHECK_ARG(sampler != DFP2S_FIELDS_DENSE || c->f->kind == DFP2S_FACTOR_DENSE,
+            "the dense sampler needs a DFP2S_FACTOR_DENSE factor");
+  CHECK_ARG(sampler != DFP2S_FIELDS_FULL || c->f->kind == DFP2S_FACTOR_FULL,
+            "the full sampler needs a DFP2S_FACTOR_FULL factor");
+  c->field_sampler = sampler;
+  return DFP2S_OK;
+}
+
+// The mixed fields a (J x H x W) of a frame by the dense or the full sampler (no mixing pass follows).
+static int ctx_mixed_fields(dfp2s_ctx* c, int H, int W, uint64_t seed, uint32_t frame, float scale, cudaStream_t st) {
+  if (c->field_sampler == DFP2S_FIELDS_DENSE)
+    return dfp2s_launch_sample_fields_dense(&c->f->d, H, W, seed, frame, scale, c->fields, st);
+  return dfp2s_launch_sample_fields_full(&c->f->d, H, W, seed, frame, scale, c->fields, st);
+}
 
 int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant) {
   if (!c || variant < -1 || variant > 1) return dfp2s_fail(DFP2S_EINVAL, "bad field-sampler variant %d", variant);
@@ -721,6 +741,7 @@ extern "C" int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int m
   c->nev = 0;
   c->frames = 0;
   c->field_variant = -1;
+  c->field_sampler = DFP2S_FIELDS_FACTORED;
   const size_t npix = (size_t)maxH * maxW;
   const int J = f->d.J;
   float lt[4] = {1.f, 0.f, 0.f, 1.f};
@@ -826,6 +847,25 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
     CHECK_ARG(H <= c->f->d.N && W <= c->f->d.N && D_over_r0 >= 0 && D_over_r0 <= 1e4, "bad frame arguments");
     cudaStream_t st = as_stream(stream);
     const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
+    if (c->field_sampler != DFP2S_FIELDS_FACTORED) {
+      // the dense and the full samplers give the mixed fields a: the warp reads their tilt rows as they are and the
+      // network takes its own first layer W1 diag(in_scale)
+      CHECK_LAUNCH(ctx_mixed_fields(c, H, W, seed, frame, scale, st));
+      mark(1);
+      rc = dfp2s_launch_blur_tc_prepare_warp(const_cast<dfp2s_p2s_dev*>(pd), img, C, H, W, c->fields,
+                                             c->fields + npix, st, nullptr);
+      if (rc == DFP2S_ENOMEM) return dfp2s_fail(rc, "blur scratch allocation");
+      if (rc == DFP2S_EUNSUPPORTED) return dfp2s_fail(rc, "tensor-core blur supports K <= 128");
+      if (rc != DFP2S_OK) return dfp2s_fail_cuda(dfp2s_launch_error(), "warp + tensor-core blur preparation");
+      mark(2);
+      CHECK_LAUNCH(dfp2s_launch_mlp_tc(pd, c->fields, H * W, c->w, DFP2S_W_F32, st));
+      mark(3);
+      rc = dfp2s_basis_blur_tc_run(c->p, C, H, W, c->w, DFP2S_W_F32, out, stream);
+      if (rc) return rc;
+      mark(4);
+      if (ev) ++c->frames;
+      return DFP2S_OK;
+    }
     CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
                                             seed, frame, c->f->d.L32, scale, c->fields, st, nullptr, 0.f, false,
                                             c->field_variant, &c->f->d));
@@ -847,9 +887,14 @@ extern "C" int dfp2s_simulate_frame(dfp2s_ctx* c, const float* img, int C, int H
   } else {
     CHECK_ARG(D_over_r0 >= 0 && D_over_r0 <= 1e4, "D/r0 = %g out of range", D_over_r0);
     const float scale = (float)pow(D_over_r0, 5.0 / 6.0);
-    CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H, W,
-                                            seed, frame, c->f->d.L32, scale, c->fields, as_stream(stream), nullptr,
-                                            0.f, true, c->field_variant, &c->f->d));
+    if (c->field_sampler != DFP2S_FIELDS_FACTORED) {
+      CHECK_ARG(H <= c->f->d.N && W <= c->f->d.N, "frame does not fit the %d grid", c->f->d.N);
+      CHECK_LAUNCH(ctx_mixed_fields(c, H, W, seed, frame, scale, as_stream(stream)));
+    } else {
+      CHECK_LAUNCH(dfp2s_launch_sample_fields(c->f->d.scratch, c->f->d.mult, c->f->d.tw, c->f->d.N, c->f->d.J, H,
+                                              W, seed, frame, c->f->d.L32, scale, c->fields, as_stream(stream),
+                                              nullptr, 0.f, true, c->field_variant, &c->f->d));
+    }
     mark(1);
     rc = dfp2s_tilt_warp(img, C, H, W, c->fields, c->fields + npix, c->warped, stream);
     if (rc) return rc;

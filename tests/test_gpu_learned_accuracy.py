@@ -48,6 +48,20 @@ def test_learned_frame_within_tolerance_of_exact_frame(trained, d):
     assert max(errs) <= TOL, errs
 
 
+@pytest.mark.parametrize("d", [1.0, 2.0, 4.0])
+def test_learned_frame_within_tolerance_with_the_full_sampler(trained, d):
+    # frames whose fields come from the full cross-spectral density (no approximation): the same network and
+    # tolerance (the per-pixel vectors keep Noll's covariance)
+    lib, P, _, img, _ = trained
+    C, H, W = img.shape
+    sim = lib.Simulator(lib.SpectralFactor(36, lib.grid_size(H, W, 8.0), 8.0, kind=lib.FACTOR_FULL), P, C, H, W)
+    sim.set_field_sampler(lib.FIELDS_FULL)
+    ex = sim.simulate_frame(img, d, 77, 0, lib.P2S_EXACT).double()
+    le = sim.simulate_frame(img, d, 77, 0, lib.P2S_LEARNED).double()
+    P.check()
+    assert float((le - ex).norm() / ex.norm()) <= TOL
+
+
 def test_learned_and_exact_weights_keep_unit_flux(trained):
     # both P2S forms return weights whose PSF keeps unit sum: s^T w = 1, s_k = sum_u phi_k(u) (reading R28)
     lib, P, sim, img, basis = trained
