@@ -250,6 +250,38 @@ def large_frame(d, S, device, stream, flush):
     return res
 
 
+def full_sampler_frames(d, S, device, stream, flush):
+    """512 x 512 x 3 learned frames whose fields come from the full cross-spectral density (no approximation):
+    frames/s with the stage events (L2 flushed between frames) and rel-L2 against the exact frame at D/r0 = 4."""
+    import torch
+    H, W, C = S["H"], S["W"], S["C"]
+    sim = d.Simulator(d.SpectralFactor(J, S["N"], PIX_PER_D, kind=d.FACTOR_FULL), S["P"], C, H, W)
+    sim.set_field_sampler(d.FIELDS_FULL)
+    out = torch.empty(C, H, W, device=device)
+    for i in range(3):
+        sim.simulate_frame(S["img"], 2.0, 600, i, d.P2S_LEARNED, out=out, stream=stream)
+    torch.cuda.synchronize()
+    nt = 10
+    sim.stage_timing(nt)
+    for i in range(nt):
+        flush.zero_()
+        sim.simulate_frame(S["img"], S["dlist"][i % len(S["dlist"])], 600, 3 + i, d.P2S_LEARNED, out=out,
+                           stream=stream)
+    st = sim.stage_times(nt).astype(np.float64)
+    sim.stage_timing(0)
+    ms = float(st.sum(axis=1).mean())
+    ex = sim.simulate_frame(S["img"], 4.0, 77, 0, d.P2S_EXACT).double()
+    le = sim.simulate_frame(S["img"], 4.0, 77, 0, d.P2S_LEARNED).double()
+    S["P"].check()
+    res = {"workload": "512x512x3, J=36, N=1024, K=100, fields of the full cross-spectral density",
+           "frames_per_s": 1e3 / ms, "ms_per_frame": ms,
+           "stage_ms": dict(zip(["fields", "warp", "p2s", "blur"], st.mean(axis=0).tolist())),
+           "rel_l2_learned_vs_exact_dr4": float((le - ex).norm() / ex.norm())}
+    del sim
+    torch.cuda.empty_cache()
+    return res
+
+
 def full_sampler_timing(d, device, stream, flush, peak_gbs):
     """The exact sampler of the full cross-spectral density (no approximation) against the factored sampler with
     its mixing pass, J = 36, at the 512 x 512 frame's grid (N = 1024) and at 3840 x 2160 (N = 4096): ms per
@@ -582,6 +614,11 @@ def run_ours(args, rank, world, device):
                                                                                   peaks["hbm_gbs"])
         except RuntimeError as exc:
             line["workloads"]["full_cross_spectrum_fields"] = {"unavailable": str(exc).splitlines()[0][:160]}
+    if args.workload == "512" and args.mode == "learned" and not args.no_full_sampler:
+        try:
+            line["workloads"]["full_cross_spectrum_frames"] = full_sampler_frames(d, S, device, stream, flush)
+        except RuntimeError as exc:
+            line["workloads"]["full_cross_spectrum_frames"] = {"unavailable": str(exc).splitlines()[0][:160]}
     if args.workload == "512" and args.mode == "learned" and not args.no_batched:
         line.setdefault("workloads", {})
         try:
