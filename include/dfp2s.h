@@ -459,6 +459,12 @@ int dfp2s_ctx_create(const dfp2s_factor* f, const dfp2s_p2s* p, int max_C, int m
                      dfp2s_ctx** out);
 int dfp2s_ctx_destroy(dfp2s_ctx* c);
 int dfp2s_ctx_set_field_sampler(dfp2s_ctx* c, int sampler);
+/* The factored sampler's column-pass kernel for this context's frames (the
+ * batch engine's autotuner sets it per shape class): 0 one FFT group per
+ * column at the compiler's register budget, 1 three CTAs per SM (at most 80
+ * registers; N <= 2048), -1 the default (1 at N = 1024, else 0).  Same fields
+ * bit for bit.  Errors: EINVAL. */
+int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant);
 
 /* Fig. dfp2s: one frame.  fields (Sec. III-C) -> tilt warp -> P2S weights
  * (FP32) -> blur (p2s_mode EXACT: FP32 CUDA-core blur; LEARNED: the network's

@@ -61,6 +61,7 @@ SIGNATURES = {
     "dfp2s_sample_zernike_fields_ar1": (_i, [_vp, _d, _u64, _u32, _d, _i, _i, _vp, _vp, _vp]),
     "dfp2s_sample_zernike_fields_full": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_ctx_set_field_sampler": (_i, [_vp, _i]),
+    "dfp2s_ctx_set_field_variant": (_i, [_vp, _i]),
     "dfp2s_sample_zernike_fields_dense": (_i, [_vp, _d, _u64, _u32, _i, _i, _vp, _vp]),
     "dfp2s_factor_copy_dense_root": (_i, [_vp, _vp, _vp]),
     "dfp2s_aperture_statistics": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
@@ -500,6 +501,10 @@ class Simulator:
         _check(load().dfp2s_simulate_frame(self._h, _ptr(img), C, H, W, D_over_r0, seed, frame, mode, _ptr(out),
                                            _stream(stream)))
         return out
+
+    def set_field_variant(self, variant: int) -> None:
+        """The factored sampler's column-pass kernel: 0, 1, or -1 for the default (same fields)."""
+        _check(load().dfp2s_ctx_set_field_variant(self._h, variant))
 
     def set_field_sampler(self, sampler: int) -> None:
         """FIELDS_FACTORED (default), FIELDS_DENSE (a FACTOR_DENSE factor) or FIELDS_FULL (a FACTOR_FULL factor)."""

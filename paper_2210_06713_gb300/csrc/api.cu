@@ -705,7 +705,7 @@ static int ctx_mixed_fields(dfp2s_ctx* c, int H, int W, uint64_t seed, uint32_t 
   return dfp2s_launch_sample_fields_full(&c->f->d, H, W, seed, frame, scale, c->fields, st);
 }
 
-int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant) {
+extern "C" int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant) {
   if (!c || variant < -1 || variant > 1) return dfp2s_fail(DFP2S_EINVAL, "bad field-sampler variant %d", variant);
   c->field_variant = variant;
   return DFP2S_OK;

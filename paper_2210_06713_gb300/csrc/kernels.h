@@ -161,6 +161,4 @@ int dfp2s_launch_blur_tc(dfp2s_p2s_dev* p, const float* img, int C, int H, int W
 int dfp2s_launch_blur(const dfp2s_p2s_dev* p, const float* img, int C, int H, int W, const void* w, int w_dtype,
                       float* out, cudaStream_t st);
 
-// api.cu -- frame contexts (the opaque handle of include/dfp2s.h): the column-pass variant of the field sampler
-// its frames use (see dfp2s_launch_sample_fields; -1 = the default)
-int dfp2s_ctx_set_field_variant(dfp2s_ctx* c, int variant);
+// api.cu -- frame contexts: dfp2s_ctx_set_field_variant is declared in include/dfp2s.h
