@@ -94,12 +94,38 @@ DFP2S_DEV float tanh_approx(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-DFP2S_DEV float gelu2x(float z) {
+// Per activation: s = min(z^2, Z2MAX), q = (c2 s + c1) s + c0 (the fit's coefficients times ln2 / 2), and
+// 2 GELU(z) = z tanh(z q) + z; two activations at a time with the two-lane FP32 instructions (fma/mul .rn.f32x2,
+// each lane rounded as the scalar instruction is), so the multiplies and the polynomial issue once per pair.
+DFP2S_DEV uint64_t pack2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+DFP2S_DEV float2 unpack2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+DFP2S_DEV uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DFP2S_DEV uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+DFP2S_DEV float2 gelu2x_pair(float za, float zb) {
   constexpr float h = DFP2S_GELU_TANH_SCALE;
   constexpr float c0 = DFP2S_GELU_C0 * h, c1 = DFP2S_GELU_C1 * h, c2 = DFP2S_GELU_C2 * h;
-  const float s = fminf(z * z, DFP2S_GELU_Z2MAX);
-  const float q = fmaf(fmaf(c2, s, c1), s, c0);
-  return fmaf(z, tanh_approx(z * q), z);
+  const uint64_t z = pack2(za, zb);
+  const float2 zz = unpack2(mul2(z, z));
+  const uint64_t sv = pack2(fminf(zz.x, DFP2S_GELU_Z2MAX), fminf(zz.y, DFP2S_GELU_Z2MAX));
+  const uint64_t q = fma2(fma2(pack2(c2, c2), sv, pack2(c1, c1)), sv, pack2(c0, c0));
+  const float2 a = unpack2(mul2(z, q));
+  return unpack2(fma2(z, pack2(tanh_approx(a.x), tanh_approx(a.y)), z));
 }
 
 // byte offset of element (row, k) in a K-major no-swizzle tile with `kgroups` 8-element K groups per row group
@@ -186,7 +212,8 @@ DFP2S_DEV void epilogue_gelu(Smem& s, uint32_t R, int warp, int lane, bool skip)
       uint32_t packed[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu2x(cur[2 * e]), gelu2x(cur[2 * e + 1]));
+        const float2 g = gelu2x_pair(cur[2 * e], cur[2 * e + 1]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(g.x, g.y);
         packed[e] = *reinterpret_cast<uint32_t*>(&h2);
       }
       umma::tmem_st8(base + 64 * c, packed);
@@ -441,21 +468,28 @@ __global__ void __launch_bounds__(THREADS, 1)
       // the unit-flux weights w + (1 - s^T w) s / (s^T s) into FP32 rows of stride KS in the staging area
       const int ngrp = NP3 / 16;
       float o[2][16];
-      float mp = 0.f;
+      uint64_t mp2 = 0;  // two lanes of the flux partial sum (even and odd columns)
 #pragma unroll
       for (int iq = 0; iq < 2; ++iq) {
         const int q = sl + 4 * iq;
         if (q < ngrp) {
           umma::tmem_ld16(P + lane_base + q * 16, o[iq]);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < 16; i += 2) {  // pairs of columns: two-lane FP32 FMAs, 8-byte broadcast loads
             const int k = q * 16 + i;
-            o[iq][i] = fmaf(o[iq][i], s.s3[k], s.c3[k]);
-            mp = fmaf(o[iq][i], s.fs[k], mp);
+            const float2 sc = *reinterpret_cast<const float2*>(&s.s3[k]);
+            const float2 cc = *reinterpret_cast<const float2*>(&s.c3[k]);
+            const float2 fc = *reinterpret_cast<const float2*>(&s.fs[k]);
+            const uint64_t y = fma2(pack2(o[iq][i], o[iq][i + 1]), pack2(sc.x, sc.y), pack2(cc.x, cc.y));
+            mp2 = fma2(y, pack2(fc.x, fc.y), mp2);
+            const float2 yy = unpack2(y);
+            o[iq][i] = yy.x;
+            o[iq][i + 1] = yy.y;
           }
         }
       }
-      s.mpart[sl][p] = mp;
+      const float2 mpp = unpack2(mp2);
+      s.mpart[sl][p] = mpp.x + mpp.y;
       umma::fence_before_sync();
       bar_quarter(q4);
       const float cfl = 1.f - ((s.mpart[0][p] + s.mpart[1][p]) + (s.mpart[2][p] + s.mpart[3][p]));
@@ -467,12 +501,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int i4 = 0; i4 < 4; ++i4) {
             const int k = q * 16 + 4 * i4;
             if (k < K) {
-              float4 v;
-              v.x = fmaf(cfl, s.fg[k + 0], o[iq][4 * i4 + 0]);
-              v.y = fmaf(cfl, s.fg[k + 1], o[iq][4 * i4 + 1]);
-              v.z = fmaf(cfl, s.fg[k + 2], o[iq][4 * i4 + 2]);
-              v.w = fmaf(cfl, s.fg[k + 3], o[iq][4 * i4 + 3]);
-              *reinterpret_cast<float4*>(stage + p * KS + k) = v;
+              const float4 g = *reinterpret_cast<const float4*>(&s.fg[k]);
+              const uint64_t c2 = pack2(cfl, cfl);
+              const float2 a = unpack2(fma2(c2, pack2(g.x, g.y), pack2(o[iq][4 * i4 + 0], o[iq][4 * i4 + 1])));
+              const float2 b = unpack2(fma2(c2, pack2(g.z, g.w), pack2(o[iq][4 * i4 + 2], o[iq][4 * i4 + 3])));
+              *reinterpret_cast<float4*>(stage + p * KS + k) = make_float4(a.x, a.y, b.x, b.y);
             }
           }
         }
