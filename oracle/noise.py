@@ -19,7 +19,9 @@ R8  word w -> u = (2 (w >> 9) + 1) 2^-24, an odd multiple of 2^-24 in (0, 1)
     [sqrt(1/2), sqrt(2)), atanh series to s^11); cos/sin of 2 pi u as a
     quadrant taken exactly from the integer (w >> 9) plus Taylor series of
     sin and cos of (pi/2) r on r in [-1/2, 1/2].  Every step is one IEEE FP32
-    operation (no fused multiply-add) in a fixed order.
+    operation in a fixed order, and the steps of the form x y + z (the Horner
+    steps of the three polynomials, the atanh series' s^3 p + 2s, and the two
+    e ln2 terms) are fused multiply-adds, x y + z with one rounding (fma_f32).
 R27 The field sampler takes its white noise in the Fourier domain.  For real
     e ~ N(0, I) on the N x N torus, E = FFT2(e) is Hermitian (E(-k) = conj E(k))
     with independent components: Re and Im of each conjugate pair N(0, N^2 / 2),
@@ -90,6 +92,29 @@ def philox_words(seed: int, sub: int, q: np.ndarray):
 
 # --------------------------------------------------------------- FP32 math
 F = np.float32
+
+
+def fma_f32(a, b, c) -> np.ndarray:
+    """x y + z rounded once to FP32 (round to nearest, ties to even), for normal FP32 inputs.
+
+    The product of two FP32 values is exact in FP64 (48 significant bits).  The FP64 sum is rounded to odd
+    (TwoSum gives its exact error; an inexact sum with an even last bit moves one FP64 ulp towards the exact
+    value), and a round-to-odd result with 53 >= 24 + 2 bits rounds to FP32 exactly as the exact sum would
+    (Boldo and Melquiond, "Emulation of FMA and correctly rounded sums: proved algorithms using rounding to
+    odd", IEEE Trans. Computers 57(4), 2008).
+    """
+    a = np.asarray(a, dtype=np.float32).astype(np.float64)
+    b = np.asarray(b, dtype=np.float32).astype(np.float64)
+    c = np.asarray(c, dtype=np.float32).astype(np.float64)
+    p = a * b
+    s = p + c
+    bp = s - p
+    err = (p - (s - bp)) + (c - bp)
+    odd = (s.view(np.uint64) & np.uint64(1)) != 0
+    fix = (err != 0) & ~odd
+    s = np.where(fix, np.nextafter(s, np.where(err > 0, np.inf, -np.inf)), s)
+    return s.astype(np.float32)
+
 _SQRT2 = F(math.sqrt(2.0))
 # ln 2 split: a 12-significant-bit head (so e * head is exact) and the FP32 rest
 _LN2_HI = F(math.ldexp(math.floor(math.ldexp(math.log(2.0), 12)), -12))
@@ -124,16 +149,11 @@ def log_f32(u: np.ndarray) -> np.ndarray:
     s2 = s * s
     p = _LOG_C[0]
     for c in _LOG_C[1:]:
-        p = p * s2
-        p = p + c
-    t = s * s2
-    t = t * p
-    logm = (s + s) + t
+        p = fma_f32(p, s2, c)
+    logm = fma_f32(s * s2, p, s + s)
     ef = e.astype(np.float32)
-    lo = ef * _LN2_LO
-    lo = lo + logm
-    hi = ef * _LN2_HI
-    return (hi + lo).astype(np.float32)
+    lo = fma_f32(ef, _LN2_LO, logm)
+    return fma_f32(ef, _LN2_HI, lo)  # e * head is exact (12-bit head, |e| <= 149)
 
 
 def sincos_2pi_f32(k: np.ndarray):
@@ -150,15 +170,12 @@ def sincos_2pi_f32(k: np.ndarray):
     r2 = r * r
     sp = _SIN_C[0]
     for c in _SIN_C[1:]:
-        sp = sp * r2
-        sp = sp + c
+        sp = fma_f32(sp, r2, c)
     s = r * sp
     cp = _COS_C[0]
     for c in _COS_C[1:]:
-        cp = cp * r2
-        cp = cp + c
-    c = cp * r2
-    c = c + F(1.0)
+        cp = fma_f32(cp, r2, c)
+    c = fma_f32(cp, r2, F(1.0))
     qm = q & 3
     cosv = np.select([qm == 0, qm == 1, qm == 2], [c, -s, -c], s).astype(np.float32)
     sinv = np.select([qm == 0, qm == 1, qm == 2], [s, c, -s], -c).astype(np.float32)

@@ -95,3 +95,52 @@ def test_streams_are_distinct():
     e = noise.gaussian_block(0, noise.TAG_BASIS, 0, 0, 8, 8)
     for x in (b, c, d, e):
         assert not np.array_equal(a, x)
+
+def _round_to_f32(x):
+    """Exact rational x rounded to the nearest FP32 (ties to even), for |x| in the normal range or 0."""
+    from fractions import Fraction
+    if x == 0:
+        return 0.0
+    sign = -1 if x < 0 else 1
+    x = abs(x)
+    e = x.numerator.bit_length() - x.denominator.bit_length()
+    while Fraction(2) ** e > x:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= x:
+        e += 1
+    scaled = x / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    q = scaled.numerator // scaled.denominator
+    rem = scaled - q
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    return sign * float(Fraction(q) * Fraction(2) ** (e - 23))
+
+
+def test_fma_f32_is_correctly_rounded():
+    # against exact rational arithmetic: random triples over many exponents, near-cancellations and exact ties
+    from fractions import Fraction
+    rng = np.random.default_rng(0)
+    n = 3000
+    a = (rng.standard_normal(n) * 2.0 ** rng.integers(-20, 20, n)).astype(np.float32)
+    b = (rng.standard_normal(n) * 2.0 ** rng.integers(-20, 20, n)).astype(np.float32)
+    c = (rng.standard_normal(n) * 2.0 ** rng.integers(-40, 40, n)).astype(np.float32)
+    c[: n // 4] = (-(a[: n // 4].astype(np.float64) * b[: n // 4]) * (1 + 1e-6)).astype(np.float32)  # cancellation
+    # ties: a*b exact with 48 bits, c chosen so that the sum lies halfway between two FP32 values
+    t = n // 4
+    a[t:2 * t] = np.float32(1.0) + np.float32(2.0 ** -23) * rng.integers(1, 2 ** 10, t).astype(np.float32)
+    b[t:2 * t] = np.float32(1.0) + np.float32(2.0 ** -23) * rng.integers(1, 2 ** 10, t).astype(np.float32)
+    c[t:2 * t] = np.float32(2.0 ** -24) * rng.choice([1.0, -1.0, 3.0], t).astype(np.float32)
+    # exact ties: (1 + 2^-12)^2 = 1 + 2^-11 + 2^-24 lies halfway between two FP32 values (ulp 2^-23 at 1)
+    x = np.float32(1 + 2.0 ** -12)
+    a[:4], b[:4] = x, x
+    c[:4] = np.array([0.0, 2.0 ** -40, -2.0 ** -40, 2.0 ** -23], dtype=np.float32)
+    got = noise.fma_f32(a, b, c).astype(np.float64)
+    assert got[0] == 1 + 2.0 ** -11                  # the tie goes to the even neighbour
+    assert got[1] == 1 + 2.0 ** -11 + 2.0 ** -23     # just above the tie: up
+    assert got[2] == 1 + 2.0 ** -11                  # just below: down
+    for i in range(n):
+        want = _round_to_f32(Fraction(float(a[i])) * Fraction(float(b[i])) + Fraction(float(c[i])))
+        assert got[i] == want, (i, a[i], b[i], c[i], got[i], want)
+    # and it is not the two-rounding sum
+    two = ((a * b).astype(np.float32) + c).astype(np.float64)
+    assert np.any(two != got)
