@@ -48,6 +48,8 @@ DFP2S_DEV float dfp2s_small_int_to_float(int v) { return __fsub_rn(__int_as_floa
 // ln(u) for a positive normal FP32 u: u = 2^e m with m in [sqrt(1/2), sqrt(2)),
 // ln m = 2 atanh(s) = 2s + s^3 (2/3 + s^2 (2/5 + s^2 (2/7 + s^2 (2/9 + s^2 2/11)))),
 // s = (m-1)/(m+1); e ln 2 with ln 2 split into a 12-bit head and an FP32 tail.
+// The x y + z steps are fused multiply-adds (one rounding each), the rest one
+// IEEE operation each, in this order: the oracle reproduces every bit.
 DFP2S_DEV float dfp2s_log(float u) {
   const uint32_t bits = __float_as_uint(u);
   int e = (int)(bits >> 23) - 127;
@@ -58,19 +60,15 @@ DFP2S_DEV float dfp2s_log(float u) {
   }
   const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
   const float s2 = __fmul_rn(s, s);
-  float p = 0x1.745d18p-3f;                         // 2/11
-  p = __fadd_rn(__fmul_rn(p, s2), 0x1.c71c72p-3f);  // 2/9
-  p = __fadd_rn(__fmul_rn(p, s2), 0x1.24924ap-2f);  // 2/7
-  p = __fadd_rn(__fmul_rn(p, s2), 0x1.99999ap-2f);  // 2/5
-  p = __fadd_rn(__fmul_rn(p, s2), 0x1.555556p-1f);  // 2/3
-  float t = __fmul_rn(s, s2);
-  t = __fmul_rn(t, p);
-  const float logm = __fadd_rn(__fadd_rn(s, s), t);
-  const float ef = dfp2s_small_int_to_float(e);  // |e| <= 149
-  float lo = __fmul_rn(ef, 0x1.0bfbe8p-15f);  // ln2 - head
-  lo = __fadd_rn(lo, logm);
-  const float hi = __fmul_rn(ef, 0x1.62ep-1f);  // head of ln 2 (12 significant bits)
-  return __fadd_rn(hi, lo);
+  float p = 0x1.745d18p-3f;                // 2/11
+  p = __fmaf_rn(p, s2, 0x1.c71c72p-3f);  // 2/9
+  p = __fmaf_rn(p, s2, 0x1.24924ap-2f);  // 2/7
+  p = __fmaf_rn(p, s2, 0x1.99999ap-2f);  // 2/5
+  p = __fmaf_rn(p, s2, 0x1.555556p-1f);  // 2/3
+  const float logm = __fmaf_rn(__fmul_rn(s, s2), p, __fadd_rn(s, s));
+  const float ef = dfp2s_small_int_to_float(e);        // |e| <= 149
+  const float lo = __fmaf_rn(ef, 0x1.0bfbe8p-15f, logm);  // ln2 - head
+  return __fmaf_rn(ef, 0x1.62ep-1f, lo);                 // head of ln 2 (12 significant bits: e * head exact)
 }
 
 // cos and sin of 2 pi u, u = (2k+1) 2^-24.  Quarter turns v = 4u = (2k+1) 2^-22;
@@ -84,17 +82,17 @@ DFP2S_DEV void dfp2s_sincos_2pi(uint32_t k, float* cs, float* sn) {
   const float r = __fmul_rn(dfp2s_small_int_to_float(rnum), 0x1.0p-22f);  // |rnum| <= 2^21
   const float r2 = __fmul_rn(r, r);
   float sp = 0x1.507834p-13f;
-  sp = __fadd_rn(__fmul_rn(sp, r2), -0x1.32d2ccp-8f);
-  sp = __fadd_rn(__fmul_rn(sp, r2), 0x1.466bc6p-4f);
-  sp = __fadd_rn(__fmul_rn(sp, r2), -0x1.4abbcep-1f);
-  sp = __fadd_rn(__fmul_rn(sp, r2), 0x1.921fb6p+0f);
+  sp = __fmaf_rn(sp, r2, -0x1.32d2ccp-8f);
+  sp = __fmaf_rn(sp, r2, 0x1.466bc6p-4f);
+  sp = __fmaf_rn(sp, r2, -0x1.4abbcep-1f);
+  sp = __fmaf_rn(sp, r2, 0x1.921fb6p+0f);
   const float s = __fmul_rn(r, sp);
   float cp = -0x1.a6d1f2p-16f;
-  cp = __fadd_rn(__fmul_rn(cp, r2), 0x1.e1f506p-11f);
-  cp = __fadd_rn(__fmul_rn(cp, r2), -0x1.55d3c8p-6f);
-  cp = __fadd_rn(__fmul_rn(cp, r2), 0x1.03c1fp-2f);
-  cp = __fadd_rn(__fmul_rn(cp, r2), -0x1.3bd3ccp+0f);
-  const float c = __fadd_rn(__fmul_rn(cp, r2), 1.0f);
+  cp = __fmaf_rn(cp, r2, 0x1.e1f506p-11f);
+  cp = __fmaf_rn(cp, r2, -0x1.55d3c8p-6f);
+  cp = __fmaf_rn(cp, r2, 0x1.03c1fp-2f);
+  cp = __fmaf_rn(cp, r2, -0x1.3bd3ccp+0f);
+  const float c = __fmaf_rn(cp, r2, 1.0f);
   switch ((int)(q & 3)) {
     case 0: *cs = c; *sn = s; break;
     case 1: *cs = -s; *sn = c; break;
@@ -115,12 +113,133 @@ DFP2S_DEV float2 dfp2s_box_muller(uint32_t wa, uint32_t wb) {
   return make_float2(__fmul_rn(r, c), __fmul_rn(r, s));
 }
 
-// Four Gaussians for positions 4q..4q+3 of one (seed, sub) stream.
+// ---- the two Box-Muller transforms of a Philox block in lockstep on the two-lane FP32 instructions
+// (add/sub/mul/fma .rn.f32x2 round each lane as the scalar __fadd_rn / __fsub_rn / __fmul_rn / __fmaf_rn do, so
+// every Gaussian is the same bits as dfp2s_box_muller's; the divisions, square roots, bit manipulations and
+// quadrant selections stay per lane).  Every multiply feeds a multiply, a fused multiply-add, a square root or
+// a result, never an add: the assembler fuses a two-lane multiply followed by a two-lane add into one fused
+// operation, which the unfused steps would not survive.
+DFP2S_DEV uint64_t dfp2s_pk(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+DFP2S_DEV float2 dfp2s_upk(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+DFP2S_DEV uint64_t dfp2s_add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DFP2S_DEV uint64_t dfp2s_sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DFP2S_DEV uint64_t dfp2s_mul2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DFP2S_DEV uint64_t dfp2s_fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+DFP2S_DEV uint64_t dfp2s_splat(float a) { return dfp2s_pk(a, a); }
+
+// dfp2s_log of two values (the same operations in the same order, lane by lane)
+DFP2S_DEV uint64_t dfp2s_log2x(float u0, float u1) {
+  float mv[2];
+  int ev[2];
+  const float uu[2] = {u0, u1};
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const uint32_t bits = __float_as_uint(uu[l]);
+    int e = (int)(bits >> 23) - 127;
+    float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+    if (m > 0x1.6a09e6p+0f) {
+      m = __fmul_rn(m, 0.5f);  // exact: a fused m 0.5 - 1 below gives the same bits
+      e += 1;
+    }
+    mv[l] = m;
+    ev[l] = e;
+  }
+  const uint64_t m2 = dfp2s_pk(mv[0], mv[1]);
+  const float2 num = dfp2s_upk(dfp2s_sub2(m2, dfp2s_splat(1.0f)));
+  const float2 den = dfp2s_upk(dfp2s_add2(m2, dfp2s_splat(1.0f)));
+  const uint64_t s = dfp2s_pk(__fdiv_rn(num.x, den.x), __fdiv_rn(num.y, den.y));
+  const uint64_t s2 = dfp2s_mul2(s, s);
+  uint64_t p = dfp2s_splat(0x1.745d18p-3f);
+  p = dfp2s_fma2(p, s2, dfp2s_splat(0x1.c71c72p-3f));
+  p = dfp2s_fma2(p, s2, dfp2s_splat(0x1.24924ap-2f));
+  p = dfp2s_fma2(p, s2, dfp2s_splat(0x1.99999ap-2f));
+  p = dfp2s_fma2(p, s2, dfp2s_splat(0x1.555556p-1f));
+  const uint64_t logm = dfp2s_fma2(dfp2s_mul2(s, s2), p, dfp2s_add2(s, s));
+  const uint64_t ef = dfp2s_pk(dfp2s_small_int_to_float(ev[0]), dfp2s_small_int_to_float(ev[1]));
+  const uint64_t lo = dfp2s_fma2(ef, dfp2s_splat(0x1.0bfbe8p-15f), logm);
+  return dfp2s_fma2(ef, dfp2s_splat(0x1.62ep-1f), lo);
+}
+
+// dfp2s_sincos_2pi of two arguments, lane by lane
+DFP2S_DEV void dfp2s_sincos_2pi_2x(uint32_t k0, uint32_t k1, float2* cs, float2* sn) {
+  const uint32_t kk[2] = {k0, k1};
+  float rv[2];
+  int32_t qv[2];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const int32_t num = 2 * (int32_t)kk[l] + 1;
+    const int32_t q = (num + (1 << 21)) >> 22;
+    rv[l] = dfp2s_small_int_to_float(num - (q << 22));
+    qv[l] = q;
+  }
+  const uint64_t r = dfp2s_mul2(dfp2s_pk(rv[0], rv[1]), dfp2s_splat(0x1.0p-22f));
+  const uint64_t r2 = dfp2s_mul2(r, r);
+  uint64_t sp = dfp2s_splat(0x1.507834p-13f);
+  sp = dfp2s_fma2(sp, r2, dfp2s_splat(-0x1.32d2ccp-8f));
+  sp = dfp2s_fma2(sp, r2, dfp2s_splat(0x1.466bc6p-4f));
+  sp = dfp2s_fma2(sp, r2, dfp2s_splat(-0x1.4abbcep-1f));
+  sp = dfp2s_fma2(sp, r2, dfp2s_splat(0x1.921fb6p+0f));
+  const float2 s = dfp2s_upk(dfp2s_mul2(r, sp));
+  uint64_t cp = dfp2s_splat(-0x1.a6d1f2p-16f);
+  cp = dfp2s_fma2(cp, r2, dfp2s_splat(0x1.e1f506p-11f));
+  cp = dfp2s_fma2(cp, r2, dfp2s_splat(-0x1.55d3c8p-6f));
+  cp = dfp2s_fma2(cp, r2, dfp2s_splat(0x1.03c1fp-2f));
+  cp = dfp2s_fma2(cp, r2, dfp2s_splat(-0x1.3bd3ccp+0f));
+  const float2 c = dfp2s_upk(dfp2s_fma2(cp, r2, dfp2s_splat(1.0f)));
+  const float sv[2] = {s.x, s.y}, cvv[2] = {c.x, c.y};
+  float oc[2], os[2];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    switch ((int)(qv[l] & 3)) {
+      case 0: oc[l] = cvv[l]; os[l] = sv[l]; break;
+      case 1: oc[l] = -sv[l]; os[l] = cvv[l]; break;
+      case 2: oc[l] = -cvv[l]; os[l] = -sv[l]; break;
+      default: oc[l] = sv[l]; os[l] = -cvv[l]; break;
+    }
+  }
+  *cs = make_float2(oc[0], oc[1]);
+  *sn = make_float2(os[0], os[1]);
+}
+
+// Four Gaussians for positions 4q..4q+3 of one (seed, sub) stream: dfp2s_box_muller(w.x, w.y) and
+// dfp2s_box_muller(w.z, w.w), evaluated together.
 DFP2S_DEV float4 dfp2s_gauss4(uint64_t seed, uint64_t sub, uint64_t q) {
   const uint4 w = philox_at(seed, sub, q);
-  const float2 a = dfp2s_box_muller(w.x, w.y);
-  const float2 b = dfp2s_box_muller(w.z, w.w);
-  return make_float4(a.x, a.y, b.x, b.y);
+  const uint32_t ka = w.x >> 9, kb = w.z >> 9;
+  const uint64_t ua = dfp2s_sub2(dfp2s_pk(__uint_as_float(0x3F800000u | ka), __uint_as_float(0x3F800000u | kb)),
+                                 dfp2s_splat(0x1.fffffep-1f));
+  const float2 uv = dfp2s_upk(ua);
+  const float2 t = dfp2s_upk(dfp2s_mul2(dfp2s_log2x(uv.x, uv.y), dfp2s_splat(-2.0f)));
+  const uint64_t r = dfp2s_pk(__fsqrt_rn(t.x), __fsqrt_rn(t.y));
+  float2 c, s;
+  dfp2s_sincos_2pi_2x(w.y >> 9, w.w >> 9, &c, &s);
+  const float2 zc = dfp2s_upk(dfp2s_mul2(r, dfp2s_pk(c.x, c.y)));
+  const float2 zs = dfp2s_upk(dfp2s_mul2(r, dfp2s_pk(s.x, s.y)));
+  return make_float4(zc.x, zs.x, zc.y, zs.y);
 }
 
 DFP2S_DEV uint64_t dfp2s_subsequence(uint32_t tag, uint32_t frame, uint32_t mode) {
