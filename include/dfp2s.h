@@ -196,7 +196,7 @@ int dfp2s_sample_zernike_fields_ar1(const dfp2s_factor* f, double D_over_r0, uin
  * every GPU that loads the library, held until the process exits.  The paper
  * has no counterpart; this is a deployment variant of the same computation.
  *   - Requires J (N/2+1) N * 8 <= DFP2S_NOALLOC_SCRATCH_BYTES (e.g. N = 512
- *     with J <= 45, N = 256 with J <= 64); larger factors get DFP2S_EINVAL.
+ *     with J <= 47, N = 256 with J <= 64); larger factors get DFP2S_EINVAL.
  *   - The factor must live on the current device (DFP2S_EINVAL otherwise).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress with that device current); make that first call
