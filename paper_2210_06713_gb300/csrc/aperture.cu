@@ -262,67 +262,127 @@ __global__ void __launch_bounds__(256) k_aperture_otf(const double* __restrict__
   }
 }
 
-// ---- tilt correlation and DTV: per (direction, lag) CTA row, grid-stride over the pixel pairs, eight sums
-constexpr int TB = 16;  // CTAs per lag
+// ---- tilt correlation and DTV.  The frame is cut into tiles of TILT_R rows x TILT_C columns; a CTA walks its
+// tiles, and on each its eight warps take the (direction, lag) items in turn.  Lane l holds the tile's pixels p in
+// columns x0 + l + 32 i of both tilt fields in registers, as two-lane FP32 values (Noll 2, Noll 3), for all its
+// items; per item it loads only the partners p + d and forms the eight sums on two-lane FP32 instructions (at most
+// TILT_R x TILT_C / 32 = 32 pairs per lane).  No load sits behind a branch: a tile inside the item's window takes
+// an unguarded path, an edge tile clamps the addresses of the pairs outside the window and adds zeros for them, so
+// that a lane's 64 partner loads are in flight together.  The warp folds its lanes by recursive halving (each step exchanges
+// half of the values still held), and the item's eight sums go into the CTA's FP64 accumulators in shared memory
+// (an item belongs to one warp: no atomics).  Partner rows are shared by many lags and stay in L1.  When the frame
+// has fewer tiles than four per SM the items are also split over `ig` CTA groups (item = g + ig * local index).
+// k_tilt_sum adds the CTAs' FP64 sums in a fixed order and divides by the pair count.
+constexpr int TILT_R = 8, TILT_C = 128, TILT_THREADS = 256;
 
-__global__ void __launch_bounds__(256) k_tilt_partial(const float* __restrict__ a, int H, int W, int max_lag,
-                                                   double* __restrict__ part) {
-  const int row = blockIdx.y;  // dir * (max_lag + 1) + d
-  const int dir = row / (max_lag + 1), d = row - dir * (max_lag + 1);
-  const int h = dir == 0 ? H : H - d, w = dir == 0 ? W - d : W;
-  const long long n = (long long)h * w;
+__global__ void __launch_bounds__(TILT_THREADS) k_tilt_partial(const float* __restrict__ a, int H, int W,
+                                                               int max_lag, int ntx, int ntiles, int ig,
+                                                               double* __restrict__ part) {
+  constexpr int CI = TILT_C / 32;
+  extern __shared__ double sacc[];  // [local item][8]
+  const int items = 2 * (max_lag + 1);
+  const int g = blockIdx.y;
+  const int nloc = (items - g + ig - 1) / ig;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < nloc * 8; i += TILT_THREADS) sacc[i] = 0.0;
+  __syncthreads();
   const size_t plane = (size_t)H * W;
-  const size_t off = dir == 0 ? (size_t)d : (size_t)d * W;
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  double dacc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int cnt = 0;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(p / w), x = (int)(p - (long long)y * w);
-    const size_t o = (size_t)y * W + x;
-    const float ux = a[o], vx = a[o + off], uy = a[plane + o], vy = a[plane + o + off];
-    const float dx = ux - vx, dy = uy - vy;
-    acc[0] = fmaf(ux, vx, acc[0]);
-    acc[1] = fmaf(uy, vy, acc[1]);
-    acc[2] = fmaf(dx, dx, acc[2]);
-    acc[3] = fmaf(dy, dy, acc[3]);
-    acc[4] = fmaf(ux, ux, acc[4]);
-    acc[5] = fmaf(vx, vx, acc[5]);
-    acc[6] = fmaf(uy, uy, acc[6]);
-    acc[7] = fmaf(vy, vy, acc[7]);
-    if (++cnt == 64) {  // FP32 over at most 64 pairs, then FP64
+  const uint64_t zero = dfp2s_pk(0.f, 0.f);
+  const int kk = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);  // the sum lane kk ends with
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    const int y0 = ty * TILT_R, x0 = tx * TILT_C;
+    uint64_t u[TILT_R][CI];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        dacc[k] += acc[k];
-        acc[k] = 0.f;
+    for (int r = 0; r < TILT_R; ++r)
+#pragma unroll
+      for (int i = 0; i < CI; ++i) {
+        const int y = y0 + r, x = x0 + lane + 32 * i;
+        const bool in = y < H && x < W;
+        const size_t o = in ? (size_t)y * W + x : 0;
+        const uint64_t v = dfp2s_pk(__ldg(a + o), __ldg(a + plane + o));
+        u[r][i] = in ? v : zero;
       }
-      cnt = 0;
+    for (int li = warp; li < nloc; li += TILT_THREADS / 32) {
+      const int item = g + ig * li;
+      const int dir = item > max_lag ? 1 : 0, d = item - dir * (max_lag + 1);
+      const int xe = min(x0 + TILT_C, dir ? W : W - d);  // pairs need x + d < W (dir 0) ...
+      const int ye = min(y0 + TILT_R, dir ? H - d : H);  // ... or y + d < H (dir 1)
+      const size_t off = dir ? (size_t)d * W : (size_t)d;
+      // (a2 a2', a3 a3'), (da2^2, da3^2), (a2^2, a3^2), (a2'^2, a3'^2)
+      uint64_t suv = zero, sdd = zero, suu = zero, svv = zero;
+      const int xl = x0 + lane;
+      if (y0 + TILT_R <= ye && x0 + TILT_C <= xe) {  // every pair of the tile: no guards, all loads in flight
+#pragma unroll
+        for (int r = 0; r < TILT_R; ++r)
+#pragma unroll
+          for (int i = 0; i < CI; ++i) {
+            const size_t o = (size_t)(y0 + r) * W + xl + 32 * i + off;
+            const uint64_t v = dfp2s_pk(__ldg(a + o), __ldg(a + plane + o));
+            const uint64_t dd = dfp2s_sub2(u[r][i], v);
+            suv = dfp2s_fma2(u[r][i], v, suv);
+            sdd = dfp2s_fma2(dd, dd, sdd);
+            suu = dfp2s_fma2(u[r][i], u[r][i], suu);
+            svv = dfp2s_fma2(v, v, svv);
+          }
+      } else {  // the window's edge: pairs outside it load element 0 and add zeros
+#pragma unroll
+        for (int r = 0; r < TILT_R; ++r)
+#pragma unroll
+          for (int i = 0; i < CI; ++i) {
+            const bool in = y0 + r < ye && xl + 32 * i < xe;
+            const size_t o = in ? (size_t)(y0 + r) * W + xl + 32 * i + off : 0;
+            uint64_t v = dfp2s_pk(__ldg(a + o), __ldg(a + plane + o));
+            v = in ? v : zero;
+            const uint64_t uv = in ? u[r][i] : zero;
+            const uint64_t dd = dfp2s_sub2(uv, v);
+            suv = dfp2s_fma2(uv, v, suv);
+            sdd = dfp2s_fma2(dd, dd, sdd);
+            suu = dfp2s_fma2(uv, uv, suu);
+            svv = dfp2s_fma2(v, v, svv);
+          }
+      }
+      const float2 p0 = dfp2s_upk(suv), p1 = dfp2s_upk(sdd), p2 = dfp2s_upk(suu), p3 = dfp2s_upk(svv);
+      const float s[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p3.x, p2.y, p3.y};
+      float t4[4], t2[2];
+      const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        t4[k] = (h4 ? s[k + 4] : s[k]) + __shfl_xor_sync(0xffffffffu, h4 ? s[k] : s[k + 4], 16);
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        t2[k] = (h3 ? t4[k + 2] : t4[k]) + __shfl_xor_sync(0xffffffffu, h3 ? t4[k] : t4[k + 2], 8);
+      float t = (h2 ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? t2[0] : t2[1], 4);
+      t += __shfl_xor_sync(0xffffffffu, t, 2);
+      t += __shfl_xor_sync(0xffffffffu, t, 1);
+      if ((lane & 3) == 0) sacc[li * 8 + kk] += (double)t;
     }
   }
-  __shared__ double red[8][8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    double v = dacc[k] + acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
-  }
   __syncthreads();
-  if (threadIdx.x < 8) {
-    double v = 0.0;
-    for (int wi = 0; wi < 8; ++wi) v += red[wi][threadIdx.x];
-    part[((size_t)row * TB + blockIdx.x) * 8 + threadIdx.x] = v;
+  for (int i = threadIdx.x; i < nloc * 8; i += TILT_THREADS) {
+    const int li = i >> 3, k = i & 7;
+    part[((size_t)(g + ig * li) * 8 + k) * gridDim.x + blockIdx.x] = sacc[i];
   }
 }
 
-__global__ void k_tilt_sum(const double* __restrict__ part, int H, int W, int max_lag, double* __restrict__ out) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int rows = 2 * (max_lag + 1);
-  if (e >= rows * 8) return;
-  const int row = e / 8, k = e - row * 8;
-  const int dir = row / (max_lag + 1), d = row - dir * (max_lag + 1);
-  const double n = dir == 0 ? (double)H * (W - d) : (double)(H - d) * W;
+// one CTA per (item, sum): the nb CTA sums of that item in FP64, divided by the item's pair count
+__global__ void __launch_bounds__(256) k_tilt_sum(const double* __restrict__ part, int nb, int H, int W,
+                                                  int max_lag, double* __restrict__ out) {
+  __shared__ double red[8];
+  const int e = blockIdx.x;
+  const int item = e >> 3;
+  const int dir = item > max_lag ? 1 : 0, d = item - dir * (max_lag + 1);
   double acc = 0.0;
-  for (int b = 0; b < TB; ++b) acc += part[((size_t)row * TB + b) * 8 + k];
-  out[e] = acc / n;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(size_t)e * nb + b];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const double n = dir == 0 ? (double)H * (W - d) : (double)(H - d) * W;
+    out[e] = t / n;
+  }
 }
 
 }  // namespace
@@ -363,12 +423,28 @@ int dfp2s_launch_aperture_statistics(const float* fields, int J, int H, int W, i
 }
 
 int dfp2s_launch_tilt_statistics(const float* fields, int H, int W, int max_lag, double* out, cudaStream_t st) {
-  const int rows = 2 * (max_lag + 1);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = 2 * (max_lag + 1);
+  const int ntx = (W + TILT_C - 1) / TILT_C, nty = (H + TILT_R - 1) / TILT_R;
+  const int ntiles = ntx * nty;
+  // CTAs resident per SM (the kernel is register-limited; the shared accumulators grow with the lags)
+  const size_t smem1 = (size_t)items * 8 * sizeof(double);  // one group: at most 2050 x 64 B (max_lag <= 1024)
+  if (smem1 > 48 * 1024) cudaFuncSetAttribute(k_tilt_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  int resident = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_tilt_partial, TILT_THREADS, smem1);
+  if (resident < 1) resident = 1;
+  // fewer tiles than resident CTAs: split the items over CTA groups as well
+  int ig = ntiles >= resident * sms ? 1 : (resident * sms + ntiles - 1) / ntiles;
+  if (ig > items) ig = items;
+  const size_t smem = (size_t)((items + ig - 1) / ig) * 8 * sizeof(double);
+  const int nb = ntiles < sms * resident ? ntiles : sms * resident;
   double* part = nullptr;
-  if (dfp2s_device_malloc_async((void**)&part, (size_t)rows * TB * 8 * sizeof(double), st) != cudaSuccess)
+  if (dfp2s_device_malloc_async((void**)&part, (size_t)items * 8 * nb * sizeof(double), st) != cudaSuccess)
     return DFP2S_ENOMEM;
-  k_tilt_partial<<<dim3(TB, rows), 256, 0, st>>>(fields, H, W, max_lag, part);
-  k_tilt_sum<<<(rows * 8 + 255) / 256, 256, 0, st>>>(part, H, W, max_lag, out);
+  k_tilt_partial<<<dim3(nb, ig), TILT_THREADS, smem, st>>>(fields, H, W, max_lag, ntx, ntiles, ig, part);
+  k_tilt_sum<<<items * 8, 256, 0, st>>>(part, nb, H, W, max_lag, out);
   const bool ok = dfp2s_launch_status() == DFP2S_OK;
   cudaFreeAsync(part, st);
   return ok ? DFP2S_OK : DFP2S_ECUDA;
