@@ -8,10 +8,10 @@
 // the 33 x 33 window at rows and columns 16..48).  One CTA (256 threads) per SM walks the realisations:
 //   phi = sum_j a_j Z_j on the window (FP32, the Zernike table evaluated in FP64 at the call), the plane
 //   c0 + c1 x + c2 y of least squares over the aperture (X^T X is diagonal on the symmetric aperture: three block
-//   sums), the squared phase differences of every aperture pair at x and y offsets 1..32 (shared-memory atomics,
-//   folded per realisation into FP64 sums), and two 64 x 64 FFTs at once (64 thread pairs per grid, the register
-//   FFT of the field sampler): P e^{-j phi} and P e^{-j (phi - plane)}.  |X|^2 accumulates in FP64 in shared
-//   memory, each grid point owned by one thread.  The OTF is the normalised inverse transform of the mean PSF (the
+//   sums), the squared phase differences of every aperture pair at x and y offsets 1..32 (a warp per offset and
+//   direction, a lane per window line; folded per realisation into FP64 sums), and two 64 x 64 FFTs at once (64 thread pairs per grid, the register
+//   FFT of the field sampler): P e^{-j phi} and P e^{-j (phi - plane)}.  |X|^2 of each grid point is owned by one
+//   thread: summed in FP32 registers over 16 realisations, then into FP64 sums in shared memory.  The OTF is the normalised inverse transform of the mean PSF (the
 //   mean autocorrelation, by linearity), taken by a finishing kernel in FP64 after a fixed-order sum over CTAs.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -32,23 +32,26 @@ constexpr int THREADS = 256;
 constexpr int US = GN + 1;        // padded row stride of the pupil grids (complex)
 constexpr int GBUF = fftr::Plan<GN>::BUF;  // 66 entries per FFT group
 constexpr int NPART = 2 * SFL + 2 * GN * GN;  // per-CTA partial sums
+constexpr int QS = (WQ + THREADS - 1) / THREADS;  // window samples per thread
+constexpr int PSF_FOLD = 16;  // realisations summed in FP32 before a fold into the FP64 PSF sums
 
-// Z_j on the window for j = Noll 2..J+1 ([j][q], q = row * 33 + column, zero outside the aperture), the window
-// coordinates, and the 64 twiddles exp(-2 pi i m / 64).
+// Z_j on the window for j = Noll 2..J+1 ([j][q], q = row * 33 + column, zero outside the aperture) and the 64
+// twiddles exp(-2 pi i m / 64).
 __global__ void k_aperture_tables(int J, float* __restrict__ Z, float2* __restrict__ tw) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < GN) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // one table entry (mode j, sample q) per thread
+  if (e < GN) {
     double s, c;
-    sincospi(-2.0 * q / GN, &s, &c);
-    tw[q] = make_float2((float)c, (float)s);
+    sincospi(-2.0 * e / GN, &s, &c);
+    tw[e] = make_float2((float)c, (float)s);
   }
-  if (q >= WQ) return;
+  if (e >= J * WQ) return;
+  const int j = e / WQ, q = e - j * WQ;
   const int i = q / WS, l = q - i * WS;
   const int iy = i - 16, ix = l - 16;
   const double x = ix / 16.0, y = iy / 16.0;
   const bool inside = ix * ix + iy * iy <= 256;
   const double rho = sqrt(x * x + y * y), th = atan2(y, x);
-  for (int j = 0; j < J; ++j) Z[(size_t)j * WQ + q] = inside ? (float)dfp2s_zernike(j + 2, rho, th) : 0.f;
+  Z[e] = inside ? (float)dfp2s_zernike(j + 2, rho, th) : 0.f;
 }
 
 struct ApSmem {
@@ -83,24 +86,74 @@ __global__ void __launch_bounds__(THREADS, 1) k_aperture_partial(const float* __
         sxx += (ix / 16.0) * (ix / 16.0);
       }
   const float inv_na = (float)(1.0 / na), inv_sxx = (float)(1.0 / sxx);
+  // |X|^2 of this thread's 32 grid points (column (tid >> 1) & 63, rows (tid & 1) + 2 m of set tid >> 7: the same
+  // points in every realisation), summed in FP32 over PSF_FOLD realisations, then added to the FP64 sums
+  constexpr int PV = fftr::Plan<GN>::V;
+  float pacc[PV];
+#pragma unroll
+  for (int m = 0; m < PV; ++m) pacc[m] = 0.f;
+  int nacc = 0;
+  const int pset = (tid >> 1) >> 6, pcol = (tid >> 1) & 63, prow = tid & 1;
+  auto fold = [&]() {
+#pragma unroll
+    for (int m = 0; m < PV; ++m) {
+      s.psf[pset][(prow + 2 * m) * GN + pcol] += (double)pacc[m];
+      pacc[m] = 0.f;
+    }
+    nacc = 0;
+  };
+  // the Zernike vector of a realisation is loaded one realisation ahead
+  auto coeff = [&](long long r) {
+    const int ry = (int)(r / nx), rx = (int)(r - (long long)ry * nx);
+    return __ldg(fields + (size_t)tid * plane + (size_t)(ry * step) * W + (size_t)(rx * step));
+  };
+  float anext = tid < J && blockIdx.x < nreal ? coeff(blockIdx.x) : 0.f;
   __syncthreads();
   for (long long r = blockIdx.x; r < nreal; r += gridDim.x) {
-    const int ry = (int)(r / nx), rx = (int)(r - (long long)ry * nx);
-    const size_t pix = (size_t)(ry * step) * W + (size_t)(rx * step);
-    if (tid < J) s.a[tid] = fields[(size_t)tid * plane + pix];
+    if (tid < J) s.a[tid] = anext;
+    if (tid < J && r + gridDim.x < nreal) anext = coeff(r + gridDim.x);
     __syncthreads();
-    // ---- phase on the window and the plane-fit sums
+    // ---- phase on the window and the plane-fit sums.  Thread t owns samples q = t + 256 k (k < QS); the J loop
+    // runs six modes at a time so that 6 QS table loads are in flight together (the table does not fit beside the
+    // shared arrays and is read from L2); each sample's FMA chain still runs over j in order.
+    float v[QS];
+#pragma unroll
+    for (int k = 0; k < QS; ++k) v[k] = 0.f;
+    int qc[QS];
+#pragma unroll
+    for (int k = 0; k < QS; ++k) qc[k] = min(tid + THREADS * k, WQ - 1);  // clamped: the tail's loads stay in bounds
+    int j = 0;
+    for (; j + 6 <= J; j += 6) {
+      float z[6][QS];
+#pragma unroll
+      for (int u = 0; u < 6; ++u)
+#pragma unroll
+        for (int k = 0; k < QS; ++k) z[u][k] = __ldg(Z + (size_t)(j + u) * WQ + qc[k]);
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const float aj = s.a[j + u];
+#pragma unroll
+        for (int k = 0; k < QS; ++k) v[k] = fmaf(aj, z[u][k], v[k]);
+      }
+    }
+    for (; j < J; ++j) {
+      const float aj = s.a[j];
+#pragma unroll
+      for (int k = 0; k < QS; ++k) v[k] = fmaf(aj, __ldg(Z + (size_t)j * WQ + qc[k]), v[k]);
+    }
     float p0 = 0.f, p1 = 0.f, p2 = 0.f;
-    for (int q = tid; q < WQ; q += THREADS) {
-      float v = 0.f;
-      for (int j = 0; j < J; ++j) v = fmaf(s.a[j], __ldg(Z + (size_t)j * WQ + q), v);
-      const int i = q / WS, l = q - i * WS;
-      const bool inside = (i - 16) * (i - 16) + (l - 16) * (l - 16) <= 256;
-      v = inside ? v : 0.f;
-      s.phi[0][q] = v;
-      p0 += v;
-      p1 = fmaf(v, (l - 16) * 0.0625f, p1);
-      p2 = fmaf(v, (i - 16) * 0.0625f, p2);
+#pragma unroll
+    for (int k = 0; k < QS; ++k) {
+      const int q = tid + THREADS * k;
+      if (q < WQ) {
+        const int i = q / WS, l = q - i * WS;
+        const bool inside = (i - 16) * (i - 16) + (l - 16) * (l - 16) <= 256;
+        const float vq = inside ? v[k] : 0.f;
+        s.phi[0][q] = vq;
+        p0 += vq;
+        p1 = fmaf(vq, (l - 16) * 0.0625f, p1);
+        p2 = fmaf(vq, (i - 16) * 0.0625f, p2);
+      }
     }
     for (int off = 16; off > 0; off >>= 1) {
       p0 += __shfl_xor_sync(0xffffffffu, p0, off);
@@ -127,21 +180,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_aperture_partial(const float* __
       const bool inside = (i - 16) * (i - 16) + (l - 16) * (l - 16) <= 256;
       s.phi[1][q] = inside ? s.phi[0][q] - (c0 + c1 * ((l - 16) * 0.0625f) + c2 * ((i - 16) * 0.0625f)) : 0.f;
     }
-    // ---- structure function: task (direction, offset d, window line) sums the pairs along the line
-    for (int task = tid; task < 2 * (SFL - 1) * WS; task += THREADS) {
-      const int dir = task / ((SFL - 1) * WS);
-      const int rem = task - dir * (SFL - 1) * WS;
-      const int d = 1 + rem / WS, line = rem - (d - 1) * WS;
-      float acc = 0.f;
-      for (int u = 0; u + d < WS; ++u) {
-        const int ia = dir == 0 ? line : u, la = dir == 0 ? u : line;
-        const int ib = dir == 0 ? line : u + d, lb = dir == 0 ? u + d : line;
-        const bool in = (ia - 16) * (ia - 16) + (la - 16) * (la - 16) <= 256 &&
-                        (ib - 16) * (ib - 16) + (lb - 16) * (lb - 16) <= 256;
-        const float df = s.phi[0][ia * WS + la] - s.phi[0][ib * WS + lb];
-        acc = in ? fmaf(df, df, acc) : acc;
+    // ---- structure function: warp w takes the (direction, offset d) pairs w, w + 8, ...; lane = window line
+    // (line 32 holds one aperture sample, no pairs), its pairs inside the aperture summed in FP32, the lanes folded
+    // and the sum written by lane 0 (one writer per entry).  The loop runs over the whole line in every lane, so that
+    // the lanes' shared-memory reads fall in distinct banks, and masks the pairs outside the aperture.
+    {
+      const int t = lane - 16;
+      int h = (int)sqrtf((float)(256 - t * t));  // samples 16 - h .. 16 + h of the line are inside
+      while (h * h > 256 - t * t) --h;
+      while ((h + 1) * (h + 1) <= 256 - t * t) ++h;
+      for (int pr = warp; pr < 2 * (SFL - 1); pr += THREADS / 32) {
+        const int dir = pr / (SFL - 1), d = 1 + pr - dir * (SFL - 1);
+        const int ea = dir == 0 ? lane * WS : lane, st = dir == 0 ? 1 : WS;  // sample u of the line at ea + u st
+        float acc = 0.f;
+#pragma unroll 4
+        for (int u = 0; u + d < WS; ++u) {
+          const float df = s.phi[0][ea + u * st] - s.phi[0][ea + (u + d) * st];
+          acc = (u >= 16 - h && u + d <= 16 + h) ? fmaf(df, df, acc) : acc;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s.sf[dir * SFL + d] = acc;
       }
-      atomicAdd(&s.sf[dir * SFL + d], acc);
     }
     __syncthreads();  // phi[1] and the sums complete
     if (tid < 2 * SFL) {
@@ -191,11 +250,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_aperture_partial(const float* __
 #pragma unroll
       for (int m = 0; m < fftr::Plan<GN>::V; ++m) {
         const float2 x = v[fftr::OutIndex<GN>::reg(m)];
-        s.psf[set][(t + 2 * m) * GN + col] += (double)x.x * x.x + (double)x.y * x.y;
+        pacc[m] = fmaf(x.x, x.x, fmaf(x.y, x.y, pacc[m]));
       }
+      if (++nacc == PSF_FOLD) fold();
     }
     __syncthreads();  // the grids and buffers are rewritten by the next realisation
   }
+  if (nacc > 0) fold();
+  __syncthreads();  // every thread's last fold before the sums are written out
   double* out = part + (size_t)blockIdx.x * NPART;
   if (tid < 2 * SFL) out[tid] = sf_acc;
   for (int e = tid; e < 2 * GN * GN; e += THREADS) out[2 * SFL + e] = (&s.psf[0][0])[e];
@@ -224,42 +286,41 @@ __global__ void k_aperture_sum(const double* __restrict__ part, int nb, long lon
   }
 }
 
-// OTF of grid `set`: H(nu) = Re sum_k psf(k) e^{+2 pi i k.nu / 64} / sum_k psf(k), separable, FP64; one CTA.
-constexpr size_t kOtfSmem = (size_t)GN * GN * sizeof(double2) + 2 * GN * sizeof(double);
+// OTF of grid `set` (Eqs. H_LE, H_SE): H(nu) = Re sum_k psf(k) e^{+2 pi i k.nu / 64} / sum_k psf(k), separable,
+// FP64.  k_otf_rows: CTA (ky, set), thread nu_x: T1[set][ky][nu_x] = sum_kx psf(ky, kx) e^{+2 pi i kx nu_x / 64};
+// k_otf_cols: CTA (nu_y, set), thread nu_x: the transform of T1 over ky, divided by the PSF sum (T1 at nu_x = 0
+// summed over ky).  128 CTAs each: the 2 x 2 x 64^3 FP64 multiply-adds spread over the SMs.
+__global__ void __launch_bounds__(GN) k_otf_rows(const double* __restrict__ sums, double2* __restrict__ T1) {
+  __shared__ double cs[GN], sn[GN], row[GN];
+  const int ky = blockIdx.x, set = blockIdx.y, vx = threadIdx.x;
+  sincospi(2.0 * vx / GN, &sn[vx], &cs[vx]);
+  row[vx] = sums[((size_t)set * GN + ky) * GN + vx];
+  __syncthreads();
+  double re = 0.0, im = 0.0;
+  for (int kx = 0; kx < GN; ++kx) {
+    const double v = row[kx];
+    const int m = (kx * vx) & (GN - 1);
+    re = fma(v, cs[m], re);
+    im = fma(v, sn[m], im);
+  }
+  T1[((size_t)set * GN + ky) * GN + vx] = make_double2(re, im);
+}
 
-__global__ void __launch_bounds__(256) k_aperture_otf(const double* __restrict__ sums, double* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char otf_raw[];
-  double2* T1 = reinterpret_cast<double2*>(otf_raw);  // [ky][nu_x]
-  double* cs = reinterpret_cast<double*>(otf_raw + (size_t)GN * GN * sizeof(double2));
-  double* sn = cs + GN;
-  const int set = blockIdx.x;
-  const double* p = sums + (size_t)set * GN * GN;
-  for (int m = threadIdx.x; m < GN; m += blockDim.x) sincospi(2.0 * m / GN, &sn[m], &cs[m]);
+__global__ void __launch_bounds__(GN) k_otf_cols(const double2* __restrict__ T1, double* __restrict__ out) {
+  __shared__ double cs[GN], sn[GN];
+  const int vy = blockIdx.x, set = blockIdx.y, vx = threadIdx.x;
+  sincospi(2.0 * vx / GN, &sn[vx], &cs[vx]);
   __syncthreads();
-  for (int e = threadIdx.x; e < GN * GN; e += blockDim.x) {
-    const int ky = e / GN, vx = e - ky * GN;
-    double re = 0.0, im = 0.0;
-    for (int kx = 0; kx < GN; ++kx) {
-      const double v = p[ky * GN + kx];
-      const int m = (kx * vx) & (GN - 1);
-      re = fma(v, cs[m], re);
-      im = fma(v, sn[m], im);
-    }
-    T1[e] = make_double2(re, im);
-  }
-  __syncthreads();
+  const double2* t1 = T1 + (size_t)set * GN * GN;
   double total = 0.0;
-  for (int ky = 0; ky < GN; ++ky) total += T1[ky * GN].x;  // nu = 0: the sum of the PSF
-  for (int e = threadIdx.x; e < GN * GN; e += blockDim.x) {
-    const int vy = e / GN, vx = e - vy * GN;
-    double re = 0.0;
-    for (int ky = 0; ky < GN; ++ky) {
-      const double2 t = T1[ky * GN + vx];
-      const int m = (ky * vy) & (GN - 1);
-      re += t.x * cs[m] - t.y * sn[m];
-    }
-    out[(size_t)set * GN * GN + e] = re / total;
+  for (int ky = 0; ky < GN; ++ky) total += t1[ky * GN].x;  // nu = 0: the sum of the PSF
+  double re = 0.0;
+  for (int ky = 0; ky < GN; ++ky) {
+    const double2 t = t1[ky * GN + vx];
+    const int m = (ky * vy) & (GN - 1);
+    re += t.x * cs[m] - t.y * sn[m];
   }
+  out[((size_t)set * GN + vy) * GN + vx] = re / total;
 }
 
 // ---- tilt correlation and DTV.  The frame is cut into tiles of TILT_R rows x TILT_C columns; a CTA walks its
@@ -397,26 +458,29 @@ int dfp2s_launch_aperture_statistics(const float* fields, int J, int H, int W, i
   float* Z = nullptr;
   float2* tw = nullptr;
   double *part = nullptr, *sums = nullptr;
+  double2* T1 = nullptr;
   auto release = [&]() {
     if (Z) cudaFreeAsync(Z, st);
     if (tw) cudaFreeAsync(tw, st);
     if (part) cudaFreeAsync(part, st);
     if (sums) cudaFreeAsync(sums, st);
+    if (T1) cudaFreeAsync(T1, st);
   };
   if (dfp2s_device_malloc_async((void**)&Z, (size_t)J * WQ * sizeof(float), st) != cudaSuccess ||
       dfp2s_device_malloc_async((void**)&tw, GN * sizeof(float2), st) != cudaSuccess ||
       dfp2s_device_malloc_async((void**)&part, (size_t)nb * NPART * sizeof(double), st) != cudaSuccess ||
-      dfp2s_device_malloc_async((void**)&sums, (size_t)2 * GN * GN * sizeof(double), st) != cudaSuccess) {
+      dfp2s_device_malloc_async((void**)&sums, (size_t)2 * GN * GN * sizeof(double), st) != cudaSuccess ||
+      dfp2s_device_malloc_async((void**)&T1, (size_t)2 * GN * GN * sizeof(double2), st) != cudaSuccess) {
     release();
     return DFP2S_ENOMEM;
   }
   const size_t smem = sizeof(ApSmem);
   cudaFuncSetAttribute(k_aperture_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_aperture_tables<<<(WQ + 255) / 256, 256, 0, st>>>(J, Z, tw);
+  k_aperture_tables<<<(J * WQ + 255) / 256, 256, 0, st>>>(J, Z, tw);
   k_aperture_partial<<<nb, THREADS, smem, st>>>(fields, J, H, W, step, nx, nreal, Z, tw, part);
   k_aperture_sum<<<(NPART + 255) / 256, 256, 0, st>>>(part, nb, nreal, sums, out);
-  cudaFuncSetAttribute(k_aperture_otf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOtfSmem);
-  k_aperture_otf<<<2, 256, kOtfSmem, st>>>(sums, out + 2 * SFL);
+  k_otf_rows<<<dim3(GN, 2), GN, 0, st>>>(sums, T1);
+  k_otf_cols<<<dim3(GN, 2), GN, 0, st>>>(T1, out + 2 * SFL);
   const bool ok = dfp2s_launch_status() == DFP2S_OK;
   release();
   return ok ? DFP2S_OK : DFP2S_ECUDA;
