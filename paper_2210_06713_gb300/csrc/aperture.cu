@@ -9,10 +9,11 @@
 //   phi = sum_j a_j Z_j on the window (FP32, the Zernike table evaluated in FP64 at the call), the plane
 //   c0 + c1 x + c2 y of least squares over the aperture (X^T X is diagonal on the symmetric aperture: three block
 //   sums), the squared phase differences of every aperture pair at x and y offsets 1..32 (a warp per offset and
-//   direction, a lane per window line; folded per realisation into FP64 sums), and two 64 x 64 FFTs at once (64 thread pairs per grid, the register
-//   FFT of the field sampler): P e^{-j phi} and P e^{-j (phi - plane)}.  |X|^2 of each grid point is owned by one
-//   thread: summed in FP32 registers over 16 realisations, then into FP64 sums in shared memory.  The OTF is the normalised inverse transform of the mean PSF (the
-//   mean autocorrelation, by linearity), taken by a finishing kernel in FP64 after a fixed-order sum over CTAs.
+//   direction, a lane per window line; folded per realisation into FP64 sums), and two 64 x 64 FFTs at once (64
+//   thread pairs per grid, the register FFT of the field sampler): P e^{-j phi} and P e^{-j (phi - plane)}.
+//   |X|^2 of each grid point is owned by one thread: summed in FP32 registers over 16 realisations, then into FP64
+//   sums in shared memory.  The OTF is the normalised inverse transform of the mean PSF (the mean
+//   autocorrelation, by linearity), taken in FP64 by two separable passes after a fixed-order sum over CTAs.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -329,11 +330,11 @@ __global__ void __launch_bounds__(GN) k_otf_cols(const double2* __restrict__ T1,
 // items; per item it loads only the partners p + d and forms the eight sums on two-lane FP32 instructions (at most
 // TILT_R x TILT_C / 32 = 32 pairs per lane).  No load sits behind a branch: a tile inside the item's window takes
 // an unguarded path, an edge tile clamps the addresses of the pairs outside the window and adds zeros for them, so
-// that a lane's 64 partner loads are in flight together.  The warp folds its lanes by recursive halving (each step exchanges
-// half of the values still held), and the item's eight sums go into the CTA's FP64 accumulators in shared memory
-// (an item belongs to one warp: no atomics).  Partner rows are shared by many lags and stay in L1.  When the frame
-// has fewer tiles than four per SM the items are also split over `ig` CTA groups (item = g + ig * local index).
-// k_tilt_sum adds the CTAs' FP64 sums in a fixed order and divides by the pair count.
+// that a lane's 64 partner loads are in flight together.  The warp folds its lanes by recursive halving (each step
+// exchanges half of the values still held), and the item's eight sums go into the CTA's FP64 accumulators in
+// shared memory (an item belongs to one warp: no atomics).  Partner rows are shared by many lags and stay in L1.
+// When the frame has fewer tiles than resident CTAs the items are also split over `ig` CTA groups (item = g + ig *
+// local index).  k_tilt_sum adds the CTAs' FP64 sums in a fixed order and divides by the pair count.
 constexpr int TILT_R = 8, TILT_C = 128, TILT_THREADS = 256;
 
 __global__ void __launch_bounds__(TILT_THREADS) k_tilt_partial(const float* __restrict__ a, int H, int W,
