@@ -4,13 +4,18 @@
 //
 //   C_l[i][j] = (1 / n_l) sum over pixels x with x + d_l in the frame of a_i(x) a_j(x + d_l)
 //
-// One block row per lag: each block takes runs of 32 valid pixels (a grid-stride
-// walk over them), stages a(x) and a(x + d) for the run in shared memory, and
-// each thread accumulates a 4 x 4 register tile of (i, j) pairs (i = ti + 16 m,
-// j = tj + 16 n for thread (ti, tj) of a 16 x 16 arrangement): products and the
-// run's sum in FP32, the runs in FP32 with Kahan compensation (FP64 arithmetic
-// is a small fraction of the FP32 rate on this part).  A second kernel sums the
-// blocks' partials in FP64 in a fixed order.
+// Per lag a J x J x n_l contraction.  A CTA takes runs of RUN valid pixels (a
+// grid-stride walk over them) and stages a(x) and a(x + d) for the run in shared
+// memory ([pixel][field], the fields padded to NBI x TB with zeros); the next
+// run's values are loaded into registers meanwhile.  The J x J pairs are cut
+// into TB x TB register tiles, one per thread of a group of NBI^2 threads
+// (NBI = ceil(J / TB)); the CTA holds floor(256 / NBI^2) groups, and group g
+// sums pixels g, g + ng, ... of each run: per pixel 2 TB / 2 eight-byte shared
+// loads and TB^2 FMAs.  The sums of FOLD_RUNS runs (plain FP32) enter FP32
+// accumulators with Kahan compensation (FP64 arithmetic is a small fraction of
+// the FP32 rate on this part); at the end the groups' sums are added in FP64 in
+// group order in shared memory, and a second kernel sums the CTAs' partials in
+// FP64 in a fixed order.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -18,15 +23,25 @@
 
 namespace {
 
-constexpr int RUN = 32;
+constexpr int RUN = 64;
 constexpr int THREADS = 256;
-constexpr int T4 = DFP2S_MAX_J / 16;  // register tile side (4)
+constexpr int TB = 6;                                 // register tile side
+constexpr int NBI_MAX = (DFP2S_MAX_J + TB - 1) / TB;  // 11
+constexpr int JPAD = NBI_MAX * TB;                    // 66 fields per staged pixel (even: 8-byte loads)
+constexpr int SPLIT = THREADS / RUN;                  // staging: field groups of a pixel
+constexpr int NJ = (DFP2S_MAX_J + SPLIT - 1) / SPLIT; // fields per staging thread
+constexpr int FOLD_RUNS = 4;                          // runs summed in plain FP32 before a compensated fold
+
+struct CovSmem {
+  float xs[RUN][JPAD], ys[RUN][JPAD];
+  double red[DFP2S_MAX_J * DFP2S_MAX_J];
+};
 
 __global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restrict__ a, int J, int H, int W,
                                                          const int2* __restrict__ lags, int nb,
                                                          double* __restrict__ part) {
-  // [pixel][field], rows padded to an odd stride: the staging writes walk the pixels, the sums walk the fields
-  __shared__ float xs[RUN][DFP2S_MAX_J + 1], ys[RUN][DFP2S_MAX_J + 1];
+  extern __shared__ __align__(16) unsigned char cov_raw[];
+  CovSmem& s = *reinterpret_cast<CovSmem*>(cov_raw);
   const int l = blockIdx.y;
   const int2 d = lags[l];  // (dy, dx)
   const int y0 = max(0, -d.x), y1 = min(H, H - d.x), x0 = max(0, -d.y), x1 = min(W, W - d.y);
@@ -35,77 +50,109 @@ __global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restr
   const long long runs = (n + RUN - 1) / RUN;
   const size_t plane = (size_t)H * W;
   const int npairs = J * J;
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
-  float acc[T4][T4], cmp[T4][T4];  // compensated sums over the runs
+  const int nbi = (J + TB - 1) / TB, G = nbi * nbi, ng = THREADS / G;
+  const int grp = threadIdx.x / G, w = threadIdx.x - grp * G;
+  const bool active = grp < ng;
+  const int i0 = (w / nbi) * TB, j0 = (w - (w / nbi) * nbi) * TB;
+  for (int e = threadIdx.x; e < RUN * JPAD; e += THREADS) {  // the padding fields stay zero
+    (&s.xs[0][0])[e] = 0.f;
+    (&s.ys[0][0])[e] = 0.f;
+  }
+  for (int e = threadIdx.x; e < npairs; e += THREADS) s.red[e] = 0.0;
+  float acc[TB][TB], cmp[TB][TB];  // compensated sums over the runs
 #pragma unroll
-  for (int m = 0; m < T4; ++m)
+  for (int m = 0; m < TB; ++m)
 #pragma unroll
-    for (int k = 0; k < T4; ++k) acc[m][k] = cmp[m][k] = 0.f;
-  // staging role of this thread: pixel q of a run for fields jg, jg + 8, ... (up to 8 of them); the next run's
-  // values are loaded into registers while the current one is summed
-  const int q = threadIdx.x & (RUN - 1), jg = threadIdx.x / RUN;
-  constexpr int NJ = DFP2S_MAX_J / (THREADS / RUN);
+    for (int k = 0; k < TB; ++k) acc[m][k] = cmp[m][k] = 0.f;
+  // staging role: pixel q of a run for fields jg, jg + SPLIT, ...
+  const int q = threadIdx.x % RUN, jg = threadIdx.x / RUN;
   float nx_[NJ], ny_[NJ];
   auto load_run = [&](long long r) {
     const long long p = r * RUN + q;
     const bool in = r < runs && p < n;
     const int pi = in ? (int)p : 0;  // n < 2^31
     const int yy = pi / nx, xx = pi - yy * nx;
-    const size_t o1 = (size_t)(y0 + yy) * W + (x0 + xx);
-    const size_t o2 = (size_t)(y0 + yy + d.x) * W + (x0 + xx + d.y);
+    const float* p1 = a + jg * plane + (size_t)(y0 + yy) * W + (x0 + xx);
+    const float* p2 = a + jg * plane + (size_t)(y0 + yy + d.x) * W + (x0 + xx + d.y);
 #pragma unroll
     for (int e = 0; e < NJ; ++e) {
-      const int j = jg + e * (THREADS / RUN);
-      nx_[e] = (in && j < J) ? a[j * plane + o1] : 0.f;
-      ny_[e] = (in && j < J) ? a[j * plane + o2] : 0.f;
+      const bool ld = in && jg + e * SPLIT < J;
+      nx_[e] = ld ? __ldg(p1) : 0.f;
+      ny_[e] = ld ? __ldg(p2) : 0.f;
+      p1 += SPLIT * plane;
+      p2 += SPLIT * plane;
     }
   };
-  load_run(blockIdx.x);
-  for (long long r = blockIdx.x; r < runs; r += nb) {
-    __syncthreads();  // the previous run's reads are done
+  float sm[TB][TB];  // the group's plain FP32 sums since the last fold
 #pragma unroll
-    for (int e = 0; e < NJ; ++e) {
-      xs[q][jg + e * (THREADS / RUN)] = nx_[e];
-      ys[q][jg + e * (THREADS / RUN)] = ny_[e];
-    }
-    __syncthreads();
-    load_run(r + nb);
-    float sm[T4][T4];
+  for (int m = 0; m < TB; ++m)
 #pragma unroll
-    for (int m = 0; m < T4; ++m)
+    for (int k = 0; k < TB; ++k) sm[m][k] = 0.f;
+  auto fold = [&]() {
 #pragma unroll
-      for (int k = 0; k < T4; ++k) sm[m][k] = 0.f;
-    const int nm = (J - ti + 15) / 16, nk = (J - tj + 15) / 16;  // tile rows / columns inside J
-#pragma unroll 4
-    for (int qq = 0; qq < RUN; ++qq) {
-      float xv[T4], yv[T4];
+    for (int m = 0; m < TB; ++m)
 #pragma unroll
-      for (int m = 0; m < T4; ++m) xv[m] = m < nm ? xs[qq][ti + 16 * m] : 0.f;
-#pragma unroll
-      for (int k = 0; k < T4; ++k) yv[k] = k < nk ? ys[qq][tj + 16 * k] : 0.f;
-#pragma unroll
-      for (int m = 0; m < T4; ++m)
-#pragma unroll
-        for (int k = 0; k < T4; ++k) sm[m][k] = fmaf(xv[m], yv[k], sm[m][k]);
-    }
-#pragma unroll
-    for (int m = 0; m < T4; ++m)
-#pragma unroll
-      for (int k = 0; k < T4; ++k) {
+      for (int k = 0; k < TB; ++k) {
         const float y = __fsub_rn(sm[m][k], cmp[m][k]);
         const float t = __fadd_rn(acc[m][k], y);
         cmp[m][k] = __fsub_rn(__fsub_rn(t, acc[m][k]), y);
         acc[m][k] = t;
+        sm[m][k] = 0.f;
       }
-  }
+  };
+  int since = 0;
+  load_run(blockIdx.x);
+  for (long long r = blockIdx.x; r < runs; r += nb) {
+    __syncthreads();  // the previous run's reads are done (and, the first time, the zero fill)
 #pragma unroll
-  for (int m = 0; m < T4; ++m)
-#pragma unroll
-    for (int k = 0; k < T4; ++k) {
-      const int i = ti + 16 * m, j = tj + 16 * k;
-      if (i < J && j < J)
-        part[((size_t)l * nb + blockIdx.x) * npairs + i * J + j] = (double)acc[m][k] - (double)cmp[m][k];
+    for (int e = 0; e < NJ; ++e) {
+      const int j = jg + e * SPLIT;
+      if (j < J) {
+        s.xs[q][j] = nx_[e];
+        s.ys[q][j] = ny_[e];
+      }
     }
+    __syncthreads();
+    load_run(r + nb);
+    if (active) {
+      for (int qq = grp; qq < RUN; qq += ng) {
+        float xv[TB], yv[TB];
+#pragma unroll
+        for (int m = 0; m < TB; m += 2) {
+          const float2 x2 = *reinterpret_cast<const float2*>(&s.xs[qq][i0 + m]);
+          const float2 y2 = *reinterpret_cast<const float2*>(&s.ys[qq][j0 + m]);
+          xv[m] = x2.x;
+          xv[m + 1] = x2.y;
+          yv[m] = y2.x;
+          yv[m + 1] = y2.y;
+        }
+#pragma unroll
+        for (int m = 0; m < TB; ++m)
+#pragma unroll
+          for (int k = 0; k < TB; ++k) sm[m][k] = fmaf(xv[m], yv[k], sm[m][k]);
+      }
+      if (++since == FOLD_RUNS) {
+        fold();
+        since = 0;
+      }
+    }
+  }
+  if (active) fold();
+  // the groups' sums in FP64, in group order
+  for (int g = 0; g < ng; ++g) {
+    __syncthreads();
+    if (grp == g) {
+#pragma unroll
+      for (int m = 0; m < TB; ++m)
+#pragma unroll
+        for (int k = 0; k < TB; ++k) {
+          const int i = i0 + m, j = j0 + k;
+          if (i < J && j < J) s.red[i * J + j] += (double)acc[m][k] - (double)cmp[m][k];
+        }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < npairs; e += THREADS) part[((size_t)l * nb + blockIdx.x) * npairs + e] = s.red[e];
 }
 
 __global__ void k_cov_reduce(const double* __restrict__ part, int nb, int npairs, const int2* __restrict__ lags,
@@ -129,7 +176,7 @@ int dfp2s_launch_field_covariance(const float* a, int J, int H, int W, const int
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long npix = (long long)H * W;
   const long long runs = (npix + RUN - 1) / RUN;
-  const int nb = (int)(runs < 2LL * sms ? runs : 2LL * sms);
+  const int nb = (int)(runs < sms ? runs : sms);  // one CTA per SM and lag
   const int npairs = J * J;
   int2* dl = nullptr;
   double* part = nullptr;
@@ -144,7 +191,8 @@ int dfp2s_launch_field_covariance(const float* a, int J, int H, int W, const int
     cudaFreeAsync(part, st);
     return DFP2S_ECUDA;
   }
-  k_cov_partial<<<dim3(nb, n_lags), THREADS, 0, st>>>(a, J, H, W, dl, nb, part);
+  cudaFuncSetAttribute(k_cov_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CovSmem));
+  k_cov_partial<<<dim3(nb, n_lags), THREADS, sizeof(CovSmem), st>>>(a, J, H, W, dl, nb, part);
   k_cov_reduce<<<dim3((npairs + 255) / 256, n_lags), 256, 0, st>>>(part, nb, npairs, dl, H, W, out);
   const bool ok = dfp2s_launch_status() == DFP2S_OK;
   cudaFreeAsync(dl, st);

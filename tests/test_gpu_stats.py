@@ -16,10 +16,15 @@ def lib():
     return d
 
 
-def test_covariance_matches_oracle(lib):
-    J, H, W = 36, 50, 37
+@pytest.mark.parametrize("J,H,W", [
+    (36, 50, 37),
+    (3, 300, 211),   # one register tile per pixel group, 28 groups per CTA; many runs per CTA
+    (15, 130, 97),   # tiles cut by J
+    (64, 40, 33),    # the largest J: 121 threads per group, two groups
+])
+def test_covariance_matches_oracle(lib, J, H, W):
     a = synthetic.random_fields(J, H, W, scale=0.7, seed=4)
-    lags = [(0, 0), (1, 0), (0, 1), (-3, 2), (7, -5), (49, 36)]
+    lags = [(0, 0), (1, 0), (0, 1), (-3, 2), (7, -5), (H - 1, W - 1)]
     g = lib.field_covariance(torch.as_tensor(a, dtype=torch.float32, device="cuda"), lags).cpu().numpy()
     o = stats.field_covariance(a.astype(np.float32), lags)
     assert np.linalg.norm(g - o) / np.linalg.norm(o) < 1e-6
