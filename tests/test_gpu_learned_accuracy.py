@@ -62,6 +62,21 @@ def test_learned_frame_within_tolerance_with_the_full_sampler(trained, d):
     assert float((le - ex).norm() / ex.norm()) <= TOL
 
 
+@pytest.mark.parametrize("d", [1.0, 4.0])
+def test_bf16_blur_share_of_the_frame_error(trained, d):
+    # the tensor-core blur's own share of the learned frame's error: the exact weights through the BF16-operand
+    # blur against the FP32 blur of the exact frame, on the benchmark's image and SVD basis at full size.  Its part
+    # of the 2e-3 frame tolerance: about 5.4e-4 at every D/r0 (image and basis rounded to bfloat16, FP32 sums)
+    lib, P, sim, img, _ = trained
+    C, H, W = img.shape
+    f = lib.sample_zernike_fields(sim.factor, d, 13, 0, H, W)
+    w = lib.p2s_weights(P, lib.P2S_EXACT, f)
+    ref = lib.basis_blur(P, img, w).double()
+    tc = lib.basis_blur_tc(P, img, w).double()
+    P.check()
+    assert float((tc - ref).norm() / ref.norm()) <= 8e-4
+
+
 def test_learned_and_exact_weights_keep_unit_flux(trained):
     # both P2S forms return weights whose PSF keeps unit sum: s^T w = 1, s_k = sum_u phi_k(u) (reading R28)
     lib, P, sim, img, basis = trained
