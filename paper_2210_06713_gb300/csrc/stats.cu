@@ -13,9 +13,9 @@
 // sums pixels g, g + ng, ... of each run: per pixel 2 TB / 2 eight-byte shared
 // loads and TB^2 FMAs.  The sums of FOLD_RUNS runs (plain FP32) enter FP32
 // accumulators with Kahan compensation (FP64 arithmetic is a small fraction of
-// the FP32 rate on this part); at the end the groups' sums are added in FP64 in
-// group order in shared memory, and a second kernel sums the CTAs' partials in
-// FP64 in a fixed order.
+// the FP32 rate on this part); at the end the groups' sums are added in group
+// order in shared memory (compensated FP32), and a second kernel sums the CTAs'
+// partials in FP64 in a fixed order.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -34,7 +34,7 @@ constexpr int FOLD_RUNS = 4;                          // runs summed in plain FP
 
 struct CovSmem {
   float xs[RUN][JPAD], ys[RUN][JPAD];
-  double red[DFP2S_MAX_J * DFP2S_MAX_J];
+  float red_s[DFP2S_MAX_J * DFP2S_MAX_J], red_c[DFP2S_MAX_J * DFP2S_MAX_J];  // the groups' sum, compensation
 };
 
 __global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restrict__ a, int J, int H, int W,
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restr
     (&s.xs[0][0])[e] = 0.f;
     (&s.ys[0][0])[e] = 0.f;
   }
-  for (int e = threadIdx.x; e < npairs; e += THREADS) s.red[e] = 0.0;
+  for (int e = threadIdx.x; e < npairs; e += THREADS) s.red_s[e] = s.red_c[e] = 0.f;
   float acc[TB][TB], cmp[TB][TB];  // compensated sums over the runs
 #pragma unroll
   for (int m = 0; m < TB; ++m)
@@ -138,7 +138,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restr
     }
   }
   if (active) fold();
-  // the groups' sums in FP64, in group order
+  // the groups' compensated sums, in group order, by compensated FP32 additions in shared memory (FP64 once per
+  // pair at the end: FP64 arithmetic runs at a small fraction of the FP32 rate here)
+  auto kahan = [](float& sum, float& c, float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(sum, y);
+    c = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+  };
   for (int g = 0; g < ng; ++g) {
     __syncthreads();
     if (grp == g) {
@@ -147,12 +154,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_cov_partial(const float* __restr
 #pragma unroll
         for (int k = 0; k < TB; ++k) {
           const int i = i0 + m, j = j0 + k;
-          if (i < J && j < J) s.red[i * J + j] += (double)acc[m][k] - (double)cmp[m][k];
+          if (i < J && j < J) {
+            kahan(s.red_s[i * J + j], s.red_c[i * J + j], acc[m][k]);
+            kahan(s.red_s[i * J + j], s.red_c[i * J + j], -cmp[m][k]);
+          }
         }
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < npairs; e += THREADS) part[((size_t)l * nb + blockIdx.x) * npairs + e] = s.red[e];
+  for (int e = threadIdx.x; e < npairs; e += THREADS)
+    part[((size_t)l * nb + blockIdx.x) * npairs + e] = (double)s.red_s[e] - (double)s.red_c[e];
 }
 
 __global__ void k_cov_reduce(const double* __restrict__ part, int nb, int npairs, const int2* __restrict__ lags,
