@@ -222,15 +222,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_aperture_partial(const float* __
       s.U[set][(W0 + i) * US + k] = u;
     }
     __syncthreads();
-    // ---- row transforms (rows 16..48 of each grid; every pair runs the transform, the others on zeros)
+    // ---- row transforms of the 2 x 33 filled rows (rows 16..48 of each grid): thread pair g < 66 takes row
+    // g % 33 of grid g / 33; the FFT synchronises whole warps, so the five warps holding those pairs run it (pairs
+    // 66..79 on zeros) and the other three skip it
     {
-      const int g = tid >> 1, t = tid & 1, set = g >> 6, rr = g & 63;
-      const bool live = rr < WS;
-      float2* row = s.U[set] + (W0 + (live ? rr : 0)) * US;
+      const int g = tid >> 1, t = tid & 1;
+      const bool live = g < 2 * WS;
+      const int set = live ? g / WS : 0, rr = live ? g - set * WS : 0;
+      float2* row = s.U[set] + (W0 + rr) * US;
       float2 v[fftr::Plan<GN>::V];
+      if (warp < (4 * WS + 31) / 32) {
 #pragma unroll
-      for (int m = 0; m < fftr::Plan<GN>::V; ++m) v[m] = live ? row[t + 2 * m] : make_float2(0.f, 0.f);
-      fftr::fft<GN, false>(v, s.gbuf[g], t, tw);
+        for (int m = 0; m < fftr::Plan<GN>::V; ++m) v[m] = live ? row[t + 2 * m] : make_float2(0.f, 0.f);
+        fftr::fft<GN, false>(v, s.gbuf[g], t, tw);
+      }
       __syncthreads();  // every row read before any is written
       if (live) {
 #pragma unroll
